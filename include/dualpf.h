@@ -1,0 +1,166 @@
+/*
+ * dualpf.h -- C ABI of the GB300 dual-resolution phase-field library.
+ *
+ * One time step of the coupled Cahn-Hilliard / Navier-Stokes / Oldroyd-B
+ * problem of arXiv 2111.04577 (Section 2, Eqs. NS1-NS16 with the
+ * log-conformation of Eqs. NS17-NS24), discretised as in Section 3:
+ * phase field phi on a mesh twice as fine as the flow mesh (Section 3.1,
+ * Fig. 1), Dong's split Cahn-Hilliard scheme (Section 3.2.1, Eqs. NS25-NS34),
+ * the constant-coefficient Navier-Stokes split (Section 3.2.2, Eqs.
+ * NS35-NS39) and the RK2-TVD log-conformation update (Section 3.2.3,
+ * Eqs. NS40-NS46), coupled by the transfers of Eqs. dual1-dual3.
+ *
+ * Conventions shared by every entry point
+ *  - Return value: 0 on success, a negative PF_ERR_* code otherwise; the
+ *    message of the last failure is returned by pf_last_error().
+ *  - Streams: all device work is enqueued on the cudaStream_t given to
+ *    pf_init_grid (NULL = legacy default stream).  pf_get_fields and
+ *    pf_diagnostics synchronise that stream before returning.
+ *  - Ownership: the library allocates and owns every field buffer of a
+ *    context; callers own the src/dst buffers they pass in.  Nothing is
+ *    retained after a call returns.
+ *  - Layout: every field is a dense array, x fastest, then y, then z
+ *    (C order [z][y][x]).  Coarse mesh nx x ny x nz cells of side dx
+ *    (ny = 1: two-dimensional x-z problem), periodic in x and y, walls at
+ *    z = 0 and z = lz.  u and v live on the x- and y-faces (nz*ny*nx values,
+ *    u[k][j][i] on the face x = i*dx), w on the z-faces including both walls
+ *    ((nz+1)*ny*nx values, w = 0 on the walls), p at centres.  The phase
+ *    field lives on the fine mesh of r*nx x ry*ny x r*nz cells (r = 2 for
+ *    dual resolution, 1 for single resolution; ry = r in 3D, 1 in 2D);
+ *    coarse cell i holds fine cells r*i .. r*i+r-1.  Tensor fields (THETA,
+ *    TAU, TAU_OLD) are component-major: 3 components (xx, xz, zz) in 2D,
+ *    6 (xx, yy, zz, xy, xz, yz) in 3D, each a coarse centre array.
+ *  - Element type: a context computes and stores in double (PF_FP64) or in
+ *    float with FP64 kept in the named places (PF_MIXED).  pf_set_fields and
+ *    pf_get_fields move elements of the context's storage type: double for
+ *    PF_FP64, float for PF_MIXED (see pf_field_info).
+ */
+#ifndef DUALPF_H
+#define DUALPF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  PF_OK = 0,
+  PF_ERR_ARG = -1,          /* invalid argument or call order                 */
+  PF_ERR_DISCRIMINANT = -2, /* S below the bound of Eq. NS30                  */
+  PF_ERR_UNSUPPORTED = -3,  /* D_w != 0, Giesekus alpha != 0, size not 2^a3^b5^c7^d */
+  PF_ERR_NONFINITE = -4,    /* the FP64 phi-mass check saw NaN/Inf            */
+  PF_ERR_TIMEOUT = -5,      /* a bounded device-side wait expired             */
+  PF_ERR_CUDA = -6,         /* a CUDA runtime call failed                     */
+  PF_ERR_NOMEM = -7         /* device allocation failed                       */
+};
+
+enum { PF_FP64 = 0, PF_MIXED = 1 };
+
+/* Field identifiers for pf_set_fields / pf_get_fields. */
+enum {
+  PF_PHI = 0,      /* fine, phi^n                                   */
+  PF_PHI_OLD = 1,  /* fine, phi^{n-1}                               */
+  PF_U = 2, PF_U_OLD = 3,
+  PF_V = 4, PF_V_OLD = 5,
+  PF_W = 6, PF_W_OLD = 7,
+  PF_P = 8, PF_P_OLD = 9,
+  PF_THETA = 10,   /* log-conformation Theta^n (Eq. NS20)           */
+  PF_TAU = 11,     /* weighted polymer stress tau^n = (1+phi)/2 tau_p (Eq. NS12) */
+  PF_TAU_OLD = 12,
+  PF_G = 13,       /* fine chemical potential G^n (Eq. NS5), read-only */
+  PF_NFIELDS = 14
+};
+
+/* Step flags for pf_step_ex. */
+enum {
+  PF_STEP_CH_ONLY = 1,  /* advance phi only (velocity held fixed); for tests */
+  PF_STEP_NO_GRAPH = 2  /* launch kernels directly instead of replaying the CUDA graph */
+};
+
+typedef struct pf_ctx pf_ctx;
+
+/* Grid of Section 3.1 (Fig. 1).  nx, ny, nz: COARSE cells, each of the form
+ * 2^a 3^b 5^c 7^d, nz >= 2; cells must be cubes (lx/nx = ly/ny = lz/nz;
+ * ly is ignored when ny = 1).  dual = 1: phi on the 2x finer mesh, 0: phi on
+ * the coarse mesh (single resolution). */
+typedef struct {
+  int nx, ny, nz;
+  double lx, ly, lz;
+  int precision; /* PF_FP64 | PF_MIXED */
+  int dual;
+} pf_grid_desc;
+
+/* Physical parameters (Section 2.1; the droplet phase phi = +1 is fluid 1).
+ * mu1, mu2: total viscosities; the droplet is viscoelastic when wi > 0 and
+ * beta < 1, with solvent mu_s1 = beta mu1 and polymer mu_p1 = (1-beta) mu1
+ * (Eq. NS12, second approach).  mobility: M of Eq. NS1.  sigma, eta: Eq. NS7.
+ * theta_*_deg: equilibrium angles of Eq. NS16 at z = 0 and z = lz, measured
+ * through phase 1.  dw: must be 0 (static contact angle).  alpha_giesekus:
+ * must be 0 (Oldroyd-B).  S = 0 selects the smallest S of Eq. NS30; nu_m = 0
+ * selects nu_m = max(mu_s)/(2 min(rho)) (text after Eq. NS39).  uw_*: x
+ * velocity of the walls.  g*: body acceleration (f_ext = rho g). */
+typedef struct {
+  double rho1, rho2, mu1, mu2;
+  double sigma, eta, mobility;
+  double theta_bot_deg, theta_top_deg, dw;
+  double wi, beta, alpha_giesekus;
+  double dt, S, nu_m;
+  double uw_bot, uw_top, gx, gy, gz;
+} pf_params;
+
+/* Create a context for grid *g and allocate all fields on the current CUDA
+ * device (all zero).  stream: a cudaStream_t or NULL.  On success *out owns
+ * the context; release it with pf_destroy.  Errors: PF_ERR_ARG (bad sizes,
+ * non-cubic cells), PF_ERR_UNSUPPORTED (a size with a prime factor > 7),
+ * PF_ERR_NOMEM, PF_ERR_CUDA. */
+int pf_init_grid(pf_ctx** out, const pf_grid_desc* g, void* stream);
+
+/* Set the physical parameters and derive the scheme's constants:
+ * lambda (Eq. NS7), S (Eq. NS30), alpha (Eq. NS29), c = alpha + S/eta^2,
+ * rho0 and nu_m (text after Eq. NS39).  May be called again between steps.
+ * Errors: PF_ERR_ARG (non-positive rho, sigma, eta, mobility, dt, or an
+ * angle outside [0, 180]), PF_ERR_DISCRIMINANT (S below Eq. NS30),
+ * PF_ERR_UNSUPPORTED (dw != 0 or alpha_giesekus != 0). */
+int pf_set_params(pf_ctx* ctx, const pf_params* prm);
+
+/* Number of elements and element size (bytes) of a field. */
+int pf_field_info(const pf_ctx* ctx, int field_id, size_t* count, size_t* elem_bytes);
+
+/* Copy one field into the context from host (src_on_device = 0) or device
+ * memory.  bytes must equal count*elem_bytes of pf_field_info.  Setting
+ * PF_PHI also sets PF_PHI_OLD to the same values, and likewise U/V/W/P/TAU set
+ * their *_OLD twin (the start-up reading phi^{-1} = phi^0; set the _OLD field
+ * afterwards to resume from a full BDF2 state).  Errors: PF_ERR_ARG. */
+int pf_set_fields(pf_ctx* ctx, int field_id, const void* src, size_t bytes, int src_on_device);
+
+/* Advance nsteps time steps (Section 3.2 order: CH, restriction, NS,
+ * polymer), replaying a captured CUDA graph per step.  Every 50 steps and
+ * at the end, the FP64 phi-mass is checked; NaN/Inf -> PF_ERR_NONFINITE.
+ * Asynchronous otherwise. */
+int pf_step(pf_ctx* ctx, int nsteps);
+int pf_step_ex(pf_ctx* ctx, int nsteps, int flags);
+
+/* Copy one field out (synchronises the stream).  bytes as for pf_set_fields. */
+int pf_get_fields(pf_ctx* ctx, int field_id, void* dst, size_t bytes, int dst_on_device);
+
+/* FP64 global reductions of phi^n (synchronises the stream):
+ * out[0] mass = sum(phi) h^d;
+ * out[1] free energy lambda sum(|grad phi|^2/2 + (phi^2-1)^2/(4 eta^2)) h^d
+ *        + sum_walls f_w(phi_w) h^(d-1)  (Eqs. NS5-NS7, NS16);
+ * out[2] wetted length (2D) / area (3D) sum_bottom (1+phi_w)/2 h^(d-1);
+ * out[3..5] centroid of (1+phi)/2 in x, y, z.
+ * phi_w = 1.5 phi_0 - 0.5 phi_1 is the wall value of the contact-angle law. */
+int pf_diagnostics(pf_ctx* ctx, double out[6]);
+
+/* Message of the last failed call on ctx (or of the last failed
+ * pf_init_grid when ctx is NULL).  Valid until the next call. */
+const char* pf_last_error(const pf_ctx* ctx);
+
+/* Free all device memory and graphs of ctx.  ctx may be NULL. */
+void pf_destroy(pf_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DUALPF_H */

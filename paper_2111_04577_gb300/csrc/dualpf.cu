@@ -1,0 +1,694 @@
+// Step orchestrator and C ABI of the dual-resolution phase-field library.
+//
+// A context owns every field of the coupled problem on one GPU, the spectral
+// work arrays of the fine Cahn-Hilliard solves and of the coarse
+// Navier-Stokes solves, the FFT twiddles and eigenvalues, and one CUDA graph
+// per (phase parity, flow parity, flags) that replays a whole time step in the
+// order of Section 3.2: CH on the fine mesh (Eqs. dual1, NS25-NS34), the
+// chemical potential and restriction (Eqs. NS5, dual2, dual3), the NS
+// projection step (Eqs. NS35-NS39) and the polymer (Eqs. NS40-NS46).  Time
+// levels rotate by pointer parity, never by copies.
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/dualpf.h"
+#include "ch.cuh"
+#include "ns.cuh"
+#include "polymer.cuh"
+#include "reduce.cuh"
+#include "spectral.cuh"
+
+namespace pf {
+
+struct ApiError : std::runtime_error {
+  int code;
+  ApiError(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+static bool smooth(int n) {
+  if (n < 1) return false;
+  for (int p : {2, 3, 5, 7})
+    while (n % p == 0) n /= p;
+  return n == 1;
+}
+
+static FftPlan make_plan(int n) {
+  FftPlan pl{};
+  pl.n = n;
+  int m = n;
+  std::vector<int> r;
+  while (m % 4 == 0) { r.push_back(4); m /= 4; }
+  while (m % 2 == 0) { r.push_back(2); m /= 2; }
+  for (int p : {3, 5, 7})
+    while (m % p == 0) { r.push_back(p); m /= p; }
+  if (m != 1 || r.size() > 24) throw ApiError(PF_ERR_UNSUPPORTED, "FFT length " + std::to_string(n) + " is not 2^a 3^b 5^c 7^d");
+  pl.ns = (int)r.size();
+  for (size_t i = 0; i < r.size(); ++i) pl.radix[i] = r[i];
+  return pl;
+}
+
+// ---------------------------------------------------------------------------
+// device memory registry
+// ---------------------------------------------------------------------------
+struct Arena {
+  std::vector<void*> ptrs;
+  size_t total = 0;
+  template <class X>
+  X* get(size_t count) {
+    if (count == 0) count = 1;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(X));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw ApiError(PF_ERR_NOMEM, "cudaMalloc of " + std::to_string(count * sizeof(X)) + " bytes failed");
+    }
+    PF_CUDA_TRY(cudaMemset(p, 0, count * sizeof(X)));
+    ptrs.push_back(p);
+    total += count * sizeof(X);
+    return static_cast<X*>(p);
+  }
+  ~Arena() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+};
+
+// producers / consumers for the x transforms of plain arrays
+template <class T>
+struct ArrPro {
+  const T* a;
+  int n;
+  __device__ __forceinline__ T operator()(int line, int x) const { return a[(size_t)line * n + x]; }
+};
+template <class T>
+struct ArrEpi {
+  T* a;
+  int n;
+  __device__ __forceinline__ void operator()(int line, int x, T v) const { a[(size_t)line * n + x] = v; }
+};
+
+struct ImplBase {
+  virtual ~ImplBase() {}
+  virtual void set_params(const pf_params& prm) = 0;
+  virtual void field_info(int f, size_t* count, size_t* eb) const = 0;
+  virtual void set_field(int f, const void* src, size_t bytes, int on_dev) = 0;
+  virtual void get_field(int f, void* dst, size_t bytes, int on_dev) = 0;
+  virtual void step(int nsteps, int flags) = 0;
+  virtual void diagnostics(double out[6]) = 0;
+};
+
+static Phys derive(const pf_params& q, const pf_grid_desc& g) {
+  (void)g;
+  if (!(q.rho1 > 0 && q.rho2 > 0 && q.sigma > 0 && q.eta > 0 && q.mobility > 0 && q.dt > 0 && q.mu1 >= 0 &&
+        q.mu2 >= 0))
+    throw ApiError(PF_ERR_ARG, "rho1, rho2, sigma, eta, mobility, dt must be > 0 and mu1, mu2 >= 0");
+  if (q.theta_bot_deg < 0 || q.theta_bot_deg > 180 || q.theta_top_deg < 0 || q.theta_top_deg > 180)
+    throw ApiError(PF_ERR_ARG, "contact angles must lie in [0, 180] degrees");
+  if (q.dw != 0.0) throw ApiError(PF_ERR_UNSUPPORTED, "dynamic contact angle D_w != 0 is not supported");
+  if (q.alpha_giesekus != 0.0) throw ApiError(PF_ERR_UNSUPPORTED, "Giesekus alpha != 0 is not supported");
+  Phys p{};
+  p.dt = q.dt;
+  p.gamma0 = 1.5;
+  p.eta = q.eta;
+  p.lam = 3.0 * q.sigma * q.eta / (2.0 * std::sqrt(2.0));            // Eq. NS7
+  p.mob = q.mobility;
+  p.Ml = p.mob * p.lam;
+  const double smin = q.eta * q.eta * std::sqrt(4.0 * p.gamma0 / (p.Ml * q.dt));  // Eq. NS30
+  const double S = q.S > 0 ? q.S : smin;
+  if (S < smin * (1.0 - 1e-12)) throw ApiError(PF_ERR_DISCRIMINANT, "S is below the bound of Eq. NS30");
+  double disc = 1.0 - 4.0 * p.gamma0 * std::pow(q.eta, 4) / (p.Ml * q.dt * S * S);
+  if (disc < 0) disc = 0;
+  p.S = S;
+  p.alpha = -S / (2.0 * q.eta * q.eta) * (1.0 + std::sqrt(disc));     // Eq. NS29
+  p.c = p.alpha + S / (q.eta * q.eta);
+  p.cos_bot = std::cos(q.theta_bot_deg * M_PI / 180.0);
+  p.cos_top = std::cos(q.theta_top_deg * M_PI / 180.0);
+  p.visco = (q.wi > 0 && q.beta < 1.0) ? 1 : 0;
+  const double beta = p.visco ? q.beta : 1.0;
+  p.rho1 = q.rho1;
+  p.rho2 = q.rho2;
+  p.rho0 = std::min(q.rho1, q.rho2);
+  p.mu_s1 = beta * q.mu1;
+  p.mu_p1 = (1.0 - beta) * q.mu1;
+  p.mu_s2 = q.mu2;
+  p.lam_h = q.wi;
+  p.nu_m = q.nu_m > 0 ? q.nu_m : 0.5 * std::max(p.mu_s1, p.mu_s2) / p.rho0;
+  if (!(p.nu_m > 0)) throw ApiError(PF_ERR_ARG, "nu_m must be > 0 (give a viscosity)");
+  p.uw_bot = q.uw_bot;
+  p.uw_top = q.uw_top;
+  p.gx = q.gx;
+  p.gy = q.gy;
+  p.gz = q.gz;
+  return p;
+}
+
+template <class T, class TC>
+struct Impl : ImplBase {
+  pf_grid_desc g;
+  Dims d{};
+  Phys p{};
+  double sigma = 1.0;
+  bool have_params = false;
+  cudaStream_t st;
+  Arena ar;
+  int ncomp;
+  // fields
+  T *phi[2], *u[2], *v[2], *w[2], *pr[2];
+  T *theta[6], *theta1[6], *tau[2][6];
+  T *mu, *G;
+  double* gwall;
+  Restricted<T> rs{};
+  T *ru, *rv, *rw, *wt, *pp, *dv;
+  cpx<T> *spF, *spU, *spV, *spW, *spP;
+  int pF, pC;
+  FftPlan plFx, plFy, plCx, plCy;
+  cpx<T> *twFx, *twFy, *twCx, *twCy;
+  double *eFx, *eFy, *eCx, *eCy;
+  double* zwork;
+  double* partial;
+  int nred_blocks = 0;
+  int pc = 0, fc = 0;  // parities: phi^n = phi[pc]; u^n = u[fc], ...
+  std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;
+  long long steps_done = 0;
+
+  Impl(const pf_grid_desc& gd, cudaStream_t s) : g(gd), st(s) {
+    d.nx = g.nx;
+    d.ny = g.ny;
+    d.nz = g.nz;
+    d.dim = g.ny == 1 ? 2 : 3;
+    d.r = g.dual ? 2 : 1;
+    d.ry = d.dim == 3 ? d.r : 1;
+    d.fnx = d.r * g.nx;
+    d.fny = d.ry * g.ny;
+    d.fnz = d.r * g.nz;
+    d.dx = g.lx / g.nx;
+    d.h = d.dx / d.r;
+    ncomp = d.dim == 2 ? 3 : 6;
+    const size_t nf = (size_t)d.fnx * d.fny * d.fnz;
+    const size_t nc = (size_t)d.nx * d.ny * d.nz;
+    const size_t ncw = (size_t)d.nx * d.ny * (d.nz + 1);
+    for (int q = 0; q < 2; ++q) {
+      phi[q] = ar.get<T>(nf);
+      u[q] = ar.get<T>(nc);
+      v[q] = d.dim == 3 ? ar.get<T>(nc) : ar.get<T>(1);
+      w[q] = ar.get<T>(ncw);
+      pr[q] = ar.get<T>(nc);
+      for (int c = 0; c < 6; ++c) tau[q][c] = c < ncomp ? ar.get<T>(nc) : nullptr;
+    }
+    for (int c = 0; c < 6; ++c) {
+      theta[c] = c < ncomp ? ar.get<T>(nc) : nullptr;
+      theta1[c] = c < ncomp ? ar.get<T>(nc) : nullptr;
+    }
+    mu = ar.get<T>(nf);
+    G = ar.get<T>(nf);
+    gwall = ar.get<double>(2 * (size_t)d.fnx * d.fny);
+    rs.phic = ar.get<T>(nc);
+    rs.Gc = ar.get<T>(nc);
+    rs.phifx = ar.get<T>(nc);
+    rs.Gfx = ar.get<T>(nc);
+    rs.phify = d.dim == 3 ? ar.get<T>(nc) : rs.phifx;
+    rs.Gfy = d.dim == 3 ? ar.get<T>(nc) : rs.Gfx;
+    rs.phifz = ar.get<T>(ncw);
+    rs.Gfz = ar.get<T>(ncw);
+    rs.phiexz = ar.get<T>(ncw);
+    rs.phiexy = d.dim == 3 ? ar.get<T>(nc) : rs.phic;
+    rs.phieyz = d.dim == 3 ? ar.get<T>(ncw) : rs.phifz;
+    ru = ar.get<T>(nc);
+    rv = ar.get<T>(nc);
+    rw = ar.get<T>(nc);
+    wt = ar.get<T>(nc);
+    pp = ar.get<T>(nc);
+    dv = ar.get<T>(nc);
+    pF = ((d.fnx / 2 + 1) + 1) & ~1;
+    pC = ((d.nx / 2 + 1) + 1) & ~1;
+    spF = ar.get<cpx<T>>((size_t)pF * d.fny * d.fnz);
+    spU = ar.get<cpx<T>>((size_t)pC * d.ny * d.nz);
+    spV = d.dim == 3 ? ar.get<cpx<T>>((size_t)pC * d.ny * d.nz) : spU;
+    spW = ar.get<cpx<T>>((size_t)pC * d.ny * d.nz);
+    spP = ar.get<cpx<T>>((size_t)pC * d.ny * d.nz);
+    plFx = make_plan(d.fnx);
+    plCx = make_plan(d.nx);
+    plFy = make_plan(d.fny);
+    plCy = make_plan(d.ny);
+    twFx = twiddles(d.fnx);
+    twFy = twiddles(d.fny);
+    twCx = twiddles(d.nx);
+    twCy = twiddles(d.ny);
+    eFx = eigs(d.fnx, d.h, d.fnx / 2 + 1);
+    eFy = d.dim == 3 ? eigs(d.fny, d.h, d.fny) : eigs(1, d.h, 1);
+    eCx = eigs(d.nx, d.dx, d.nx / 2 + 1);
+    eCy = d.dim == 3 ? eigs(d.ny, d.dx, d.ny) : eigs(1, d.dx, 1);
+    zwork = ar.get<double>(4 * (size_t)(d.nz + 2));
+    nred_blocks = 2 * 152;
+    partial = ar.get<double>((size_t)nred_blocks * RED_N);
+    set_smem_limits();
+  }
+
+  ~Impl() override {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+  }
+
+  cpx<T>* twiddles(int n) {
+    std::vector<cpx<T>> h(n);
+    for (int m = 0; m < n; ++m) {
+      const double a = 2.0 * M_PI * (double)m / (double)n;
+      h[m] = mk<T>((T)std::cos(a), (T)-std::sin(a));
+    }
+    cpx<T>* dptr = ar.get<cpx<T>>(n);
+    PF_CUDA_TRY(cudaMemcpy(dptr, h.data(), n * sizeof(cpx<T>), cudaMemcpyHostToDevice));
+    return dptr;
+  }
+  double* eigs(int n, double hh, int count) {
+    std::vector<double> h(count);
+    for (int k = 0; k < count; ++k) {
+      const double s = std::sin(M_PI * (double)k / (double)n);
+      h[k] = -4.0 / (hh * hh) * s * s;
+    }
+    double* dptr = ar.get<double>(count);
+    PF_CUDA_TRY(cudaMemcpy(dptr, h.data(), count * sizeof(double), cudaMemcpyHostToDevice));
+    return dptr;
+  }
+
+  static constexpr int kMaxSmem = 200 * 1024;
+  void set_smem_limits() {
+    PF_CUDA_TRY(cudaFuncSetAttribute(k_fft_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PF_CUDA_TRY(cudaFuncSetAttribute(k_zsolve<T, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PF_CUDA_TRY(cudaFuncSetAttribute(k_rfft_x<T, ChRhs<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PF_CUDA_TRY(cudaFuncSetAttribute(k_rfft_x<T, ArrPro<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PF_CUDA_TRY(cudaFuncSetAttribute(k_irfft_x<T, ChFinish<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PF_CUDA_TRY(cudaFuncSetAttribute(k_irfft_x<T, ArrEpi<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+  }
+
+  // ------------------------------------------------------------------ launches
+  static int blocks_for(size_t n, int bs = 256) {
+    size_t b = (n + bs - 1) / bs;
+    const size_t cap = 152 * 16;
+    return (int)(b < cap ? (b == 0 ? 1 : b) : cap);
+  }
+  template <class Pro>
+  void rfft_x(Pro pro, cpx<T>* out, int n, int nlines, int pitch, const FftPlan& pl, const cpx<T>* tw) {
+    const int npair = std::max(1, 1024 / n);
+    const int pairs = (nlines + 1) / 2;
+    const int grid = (pairs + npair - 1) / npair;
+    const size_t sm = 2 * (size_t)npair * n * sizeof(cpx<T>);
+    k_rfft_x<T, Pro><<<grid, 256, sm, st>>>(pro, out, n, nlines, pitch, pl, tw, npair);
+  }
+  template <class Epi>
+  void irfft_x(const cpx<T>* in, Epi epi, int n, int nlines, int pitch, const FftPlan& pl, const cpx<T>* tw, T scale) {
+    const int npair = std::max(1, 1024 / n);
+    const int pairs = (nlines + 1) / 2;
+    const int grid = (pairs + npair - 1) / npair;
+    const size_t sm = 2 * (size_t)npair * n * sizeof(cpx<T>);
+    k_irfft_x<T, Epi><<<grid, 256, sm, st>>>(in, epi, n, nlines, pitch, pl, tw, npair, scale);
+  }
+  void fft_y(cpx<T>* data, int ny, int pitch, int ncol, int levels, const FftPlan& pl, const cpx<T>* tw, int sign) {
+    const int tx = sizeof(T) == 4 ? 8 : 4;
+    dim3 grid((ncol + tx - 1) / tx, levels);
+    const size_t sm = 2 * (size_t)ny * tx * sizeof(cpx<T>);
+    k_fft_y<T><<<grid, 256, sm, st>>>(data, ny, pitch, ncol, pl, tw, sign, tx);
+  }
+  void zsolve(cpx<T>* data, int rows, int ny, int pitch, int ncol, const double* ex, const double* ey, int bc,
+              double h2, double s1, double s2, bool two, double scale, bool poisson) {
+    ZSolve zs{};
+    zs.rows = rows;
+    zs.ny = ny;
+    zs.pitch = pitch;
+    zs.ncol = ncol;
+    zs.bc = bc;
+    zs.two = two ? 1 : 0;
+    zs.same = (!two || std::fabs(s1 - s2) <= 1e-14 * std::fabs(s1)) ? 1 : 0;
+    zs.skip_zero = poisson ? 1 : 0;
+    zs.h2 = h2;
+    zs.shift1 = s1;
+    zs.shift2 = s2;
+    zs.scale = scale;
+    const int tx = 16;
+    const size_t sm = (size_t)rows * tx * sizeof(TC) * (zs.same ? 3 : 4);
+    dim3 grid((ncol + tx - 1) / tx, ny);
+    k_zsolve<T, TC><<<grid, 2 * tx, sm, st>>>(data, ex, ey, zs, tx);
+    if (poisson) k_zero_mode<T><<<1, 32, 0, st>>>(data, rows, ny, pitch, h2, scale, zwork);
+  }
+
+  // one transform solve on the coarse mesh: rhs (real, lines of nx) -> out
+  void coarse_solve(const T* rhs, T* out, cpx<T>* sp, int rows, int bc, double shift, bool poisson) {
+    const int nlines = d.ny * rows;
+    rfft_x(ArrPro<T>{rhs, d.nx}, sp, d.nx, nlines, pC, plCx, twCx);
+    if (d.dim == 3) fft_y(sp, d.ny, pC, d.nx / 2 + 1, rows, plCy, twCy, -1);
+    zsolve(sp, rows, d.ny, pC, d.nx / 2 + 1, eCx, eCy, bc, d.dx * d.dx, shift, shift, false,
+           1.0 / ((double)d.nx * d.ny), poisson);
+    if (d.dim == 3) fft_y(sp, d.ny, pC, d.nx / 2 + 1, rows, plCy, twCy, +1);
+    irfft_x(sp, ArrEpi<T>{out, d.nx}, d.nx, nlines, pC, plCx, twCx, (T)1);
+  }
+
+  void launch_step(int flags) {
+    const int po = pc ^ 1, fo = fc ^ 1;
+    const int nb = 256;
+    const size_t nf = (size_t)d.fnx * d.fny * d.fnz;
+    // ---- Cahn-Hilliard on the fine mesh ----
+    FineView<T> fv{phi[pc], phi[po]};
+    k_ch_mu<T><<<blocks_for(nf), nb, 0, st>>>(fv, mu, gwall, d, p);
+    ChRhs<T> rhs;
+    rhs.f = fv;
+    rhs.mu = mu;
+    rhs.vel = CoarseVel<T>{u[fc], u[fo], v[fc], v[fo], w[fc], w[fo]};
+    rhs.d = d;
+    rhs.inv_mldt = (T)(1.0 / (p.Ml * p.dt));
+    rhs.inv_ml = (T)(1.0 / p.Ml);
+    rhs.ih = (T)(1.0 / d.h);
+    rhs.ih2 = (T)(1.0 / (d.h * d.h));
+    const int nlf = d.fny * d.fnz;
+    rfft_x(rhs, spF, d.fnx, nlf, pF, plFx, twFx);
+    if (d.dim == 3) fft_y(spF, d.fny, pF, d.fnx / 2 + 1, d.fnz, plFy, twFy, -1);
+    zsolve(spF, d.fnz, d.fny, pF, d.fnx / 2 + 1, eFx, eFy, Z_NEUMANN, d.h * d.h, p.c, -p.alpha, true,
+           1.0 / ((double)d.fnx * d.fny), false);
+    if (d.dim == 3) fft_y(spF, d.fny, pF, d.fnx / 2 + 1, d.fnz, plFy, twFy, +1);
+    irfft_x(spF, ChFinish<T>{phi[pc], phi[po], d.fnx}, d.fnx, nlf, pF, plFx, twFx, (T)1);
+    k_ch_G<T><<<blocks_for(nf), nb, 0, st>>>(phi[po], gwall, G, d, p);
+    if (flags & PF_STEP_CH_ONLY) return;
+    // ---- restriction to the coarse mesh ----
+    const size_t ncw = (size_t)d.nx * d.ny * (d.nz + 1);
+    const size_t nc = (size_t)d.nx * d.ny * d.nz;
+    k_restrict<T><<<blocks_for(ncw), nb, 0, st>>>(phi[po], G, rs, d);
+    // ---- Navier-Stokes ----
+    NsAcc<T> A;
+    A.a.un = u[fc];
+    A.a.uo = u[fo];
+    A.a.vn = v[fc];
+    A.a.vo = v[fo];
+    A.a.wn = w[fc];
+    A.a.wo = w[fo];
+    A.a.pn = pr[fc];
+    A.a.po = pr[fo];
+    for (int c = 0; c < 6; ++c) {
+      A.a.tn[c] = tau[fc][c];
+      A.a.to[c] = tau[fo][c];
+    }
+    A.a.rs = rs;
+    A.d = d;
+    A.p = p;
+    k_ns_rhs<T><<<blocks_for(nc), nb, 0, st>>>(A, ru, rv, rw, p.visco);
+    const double kk = p.gamma0 / (p.dt * p.nu_m);
+    // u~, v~ land in the n-1 buffers (free once the right sides exist)
+    coarse_solve(ru, u[fo], spU, d.nz, Z_DIRICH, kk, false);
+    if (d.dim == 3) coarse_solve(rv, v[fo], spV, d.nz, Z_DIRICH, kk, false);
+    coarse_solve(rw, wt, spW, d.nz - 1, Z_FACES, kk, false);
+    k_div<T><<<blocks_for(nc), nb, 0, st>>>(u[fo], v[fo], wt, dv, d, (T)(p.gamma0 * p.rho0 / p.dt));
+    coarse_solve(dv, pp, spP, d.nz, Z_NEUMANN, 0.0, true);
+    k_correct<T><<<blocks_for(ncw), nb, 0, st>>>(u[fo], v[fo], wt, w[fo], pp, pr[fc], pr[fo], d,
+                                                  (T)(p.dt / (p.gamma0 * p.rho0)));
+    // ---- polymer ----
+    if (p.visco) {
+      PolyIn<T> P{};
+      P.u = u[fo];
+      P.v = v[fo];
+      P.w = w[fo];
+      P.phic = rs.phic;
+      for (int c = 0; c < ncomp; ++c) {
+        P.th[c] = theta[c];
+        P.out[c] = theta1[c];
+      }
+      if (d.dim == 2) k_polymer<T, 2><<<blocks_for(nc), 128, 0, st>>>(P, d, p, 1);
+      else k_polymer<T, 3><<<blocks_for(nc), 128, 0, st>>>(P, d, p, 1);
+      for (int c = 0; c < ncomp; ++c) {
+        P.th[c] = theta1[c];
+        P.base[c] = theta[c];
+        P.out[c] = theta[c];
+        P.tau[c] = tau[fo][c];
+      }
+      if (d.dim == 2) k_polymer<T, 2><<<blocks_for(nc), 128, 0, st>>>(P, d, p, 2);
+      else k_polymer<T, 3><<<blocks_for(nc), 128, 0, st>>>(P, d, p, 2);
+    }
+  }
+
+  // ------------------------------------------------------------------ API
+  void set_params(const pf_params& q) override {
+    p = derive(q, g);
+    sigma = q.sigma;
+    have_params = true;
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    graphs.clear();
+  }
+
+  void field_info(int f, size_t* count, size_t* eb) const override {
+    const size_t nf = (size_t)d.fnx * d.fny * d.fnz;
+    const size_t nc = (size_t)d.nx * d.ny * d.nz;
+    const size_t ncw = (size_t)d.nx * d.ny * (d.nz + 1);
+    size_t c = 0;
+    switch (f) {
+      case PF_PHI: case PF_PHI_OLD: case PF_G: c = nf; break;
+      case PF_U: case PF_U_OLD: case PF_P: case PF_P_OLD: c = nc; break;
+      case PF_V: case PF_V_OLD: c = d.dim == 3 ? nc : 0; break;
+      case PF_W: case PF_W_OLD: c = ncw; break;
+      case PF_THETA: case PF_TAU: case PF_TAU_OLD: c = nc * ncomp; break;
+      default: throw ApiError(PF_ERR_ARG, "unknown field id " + std::to_string(f));
+    }
+    *count = c;
+    *eb = sizeof(T);
+  }
+
+  // pointers of a field's storage (components contiguous in the caller's view)
+  std::vector<T*> field_ptrs(int f) {
+    const int po = pc ^ 1, fo = fc ^ 1;
+    switch (f) {
+      case PF_PHI: return {phi[pc]};
+      case PF_PHI_OLD: return {phi[po]};
+      case PF_U: return {u[fc]};
+      case PF_U_OLD: return {u[fo]};
+      case PF_V: return {v[fc]};
+      case PF_V_OLD: return {v[fo]};
+      case PF_W: return {w[fc]};
+      case PF_W_OLD: return {w[fo]};
+      case PF_P: return {pr[fc]};
+      case PF_P_OLD: return {pr[fo]};
+      case PF_G: return {G};
+      case PF_THETA: return std::vector<T*>(theta, theta + ncomp);
+      case PF_TAU: return std::vector<T*>(tau[fc], tau[fc] + ncomp);
+      case PF_TAU_OLD: return std::vector<T*>(tau[fo], tau[fo] + ncomp);
+    }
+    throw ApiError(PF_ERR_ARG, "unknown field id");
+  }
+
+  void copy_field(int f, const void* src, size_t bytes, int on_dev) {
+    size_t cnt, eb;
+    field_info(f, &cnt, &eb);
+    if (bytes != cnt * eb) throw ApiError(PF_ERR_ARG, "byte count does not match the field size");
+    auto ptrs = field_ptrs(f);
+    const size_t per = cnt / ptrs.size();
+    for (size_t q = 0; q < ptrs.size(); ++q)
+      PF_CUDA_TRY(cudaMemcpyAsync(ptrs[q], static_cast<const char*>(src) + q * per * eb, per * eb,
+                                  on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  }
+
+  void set_field(int f, const void* src, size_t bytes, int on_dev) override {
+    if (f == PF_G) throw ApiError(PF_ERR_ARG, "PF_G is read-only");
+    copy_field(f, src, bytes, on_dev);
+    int twin = -1;
+    if (f == PF_PHI) twin = PF_PHI_OLD;
+    if (f == PF_U) twin = PF_U_OLD;
+    if (f == PF_V) twin = PF_V_OLD;
+    if (f == PF_W) twin = PF_W_OLD;
+    if (f == PF_P) twin = PF_P_OLD;
+    if (f == PF_TAU) twin = PF_TAU_OLD;
+    if (twin >= 0) copy_field(twin, src, bytes, on_dev);
+    if (!on_dev) PF_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+
+  void get_field(int f, void* dst, size_t bytes, int on_dev) override {
+    size_t cnt, eb;
+    field_info(f, &cnt, &eb);
+    if (bytes != cnt * eb) throw ApiError(PF_ERR_ARG, "byte count does not match the field size");
+    auto ptrs = field_ptrs(f);
+    const size_t per = cnt / ptrs.size();
+    for (size_t q = 0; q < ptrs.size(); ++q)
+      PF_CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(dst) + q * per * eb, ptrs[q], per * eb,
+                                  on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    PF_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+
+  void check_launch() {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) throw CudaError(e, "kernel launch", __FILE__, __LINE__);
+  }
+
+  void run_one(int flags) {
+    if (flags & PF_STEP_NO_GRAPH) {
+      launch_step(flags);
+      check_launch();
+      return;
+    }
+    auto key = std::make_tuple(pc, fc, flags & PF_STEP_CH_ONLY);
+    auto it = graphs.find(key);
+    if (it == graphs.end()) {
+      cudaGraph_t gr;
+      PF_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      launch_step(flags);
+      cudaError_t le = cudaGetLastError();
+      cudaError_t ce = cudaStreamEndCapture(st, &gr);
+      if (le != cudaSuccess) throw CudaError(le, "kernel launch during capture", __FILE__, __LINE__);
+      PF_CUDA_TRY(ce);
+      cudaGraphExec_t ex;
+      PF_CUDA_TRY(cudaGraphInstantiate(&ex, gr, 0));
+      cudaGraphDestroy(gr);
+      it = graphs.emplace(key, ex).first;
+    }
+    PF_CUDA_TRY(cudaGraphLaunch(it->second, st));
+  }
+
+  double mass_check() {
+    double out[6];
+    diagnostics(out);
+    return out[0];
+  }
+
+  void step(int nsteps, int flags) override {
+    if (!have_params) throw ApiError(PF_ERR_ARG, "pf_set_params must precede pf_step");
+    if (nsteps < 0) throw ApiError(PF_ERR_ARG, "nsteps < 0");
+    for (int s = 0; s < nsteps; ++s) {
+      run_one(flags);
+      pc ^= 1;
+      if (!(flags & PF_STEP_CH_ONLY)) fc ^= 1;
+      ++steps_done;
+      if (steps_done % 50 == 0 || s == nsteps - 1) {
+        const double m = mass_check();
+        if (!std::isfinite(m)) throw ApiError(PF_ERR_NONFINITE, "phi mass is not finite after step " + std::to_string(steps_done));
+      }
+    }
+  }
+
+  void diagnostics(double out[6]) override {
+    k_reduce<T><<<nred_blocks, 256, 0, st>>>(phi[pc], d, p, sigma, d.dim == 3 ? d.h : g.ly, partial);
+    check_launch();
+    std::vector<double> h((size_t)nred_blocks * RED_N);
+    PF_CUDA_TRY(cudaMemcpyAsync(h.data(), partial, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PF_CUDA_TRY(cudaStreamSynchronize(st));
+    double s[RED_N] = {0};
+    for (int b = 0; b < nred_blocks; ++b)
+      for (int q = 0; q < RED_N; ++q) s[q] += h[(size_t)b * RED_N + q];
+    const double hd = std::pow(d.h, d.dim), hw = std::pow(d.h, d.dim - 1);
+    out[0] = s[0] * hd;
+    out[1] = p.lam * s[1] * hd + s[2] * hw;
+    out[2] = s[3] * hw;
+    out[3] = s[4] / s[7];
+    out[4] = s[5] / s[7];
+    out[5] = s[6] / s[7];
+  }
+};
+
+}  // namespace pf
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+struct pf_ctx {
+  std::unique_ptr<pf::ImplBase> impl;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+};
+
+static std::string g_init_err;
+
+template <class F>
+static int guarded(pf_ctx* ctx, F&& f) {
+  try {
+    f();
+    return PF_OK;
+  } catch (const pf::ApiError& e) {
+    if (ctx) ctx->err = e.what();
+    return e.code;
+  } catch (const pf::CudaError& e) {
+    if (ctx)
+      ctx->err = std::string("CUDA error ") + cudaGetErrorString(e.err) + " in " + e.expr + " (" + e.file + ":" +
+                 std::to_string(e.line) + ")";
+    return PF_ERR_CUDA;
+  } catch (const std::exception& e) {
+    if (ctx) ctx->err = e.what();
+    return PF_ERR_ARG;
+  }
+}
+
+extern "C" {
+
+int pf_init_grid(pf_ctx** out, const pf_grid_desc* g, void* stream) {
+  if (!out || !g) {
+    g_init_err = "null argument";
+    return PF_ERR_ARG;
+  }
+  *out = nullptr;
+  auto ctx = std::make_unique<pf_ctx>();
+  int rc = guarded(ctx.get(), [&] {
+    if (g->nx < 2 || g->ny < 1 || g->nz < 2) throw pf::ApiError(PF_ERR_ARG, "need nx >= 2, ny >= 1, nz >= 2");
+    if (!(g->lx > 0 && g->lz > 0)) throw pf::ApiError(PF_ERR_ARG, "lx and lz must be > 0");
+    const double dx = g->lx / g->nx;
+    if (std::fabs(g->lz / g->nz - dx) > 1e-9 * dx || (g->ny > 1 && std::fabs(g->ly / g->ny - dx) > 1e-9 * dx))
+      throw pf::ApiError(PF_ERR_ARG, "cells must be cubes: lx/nx = ly/ny = lz/nz");
+    if (g->precision != PF_FP64 && g->precision != PF_MIXED) throw pf::ApiError(PF_ERR_ARG, "precision must be PF_FP64 or PF_MIXED");
+    if (g->nx % 2 || (g->ny > 1 && g->ny % 2)) throw pf::ApiError(PF_ERR_UNSUPPORTED, "nx and ny (3D) must be even");
+    for (int n : {g->nx, g->ny, g->nz})
+      if (!pf::smooth(n)) throw pf::ApiError(PF_ERR_UNSUPPORTED, "sizes must be 2^a 3^b 5^c 7^d");
+    if (stream) {
+      ctx->stream = static_cast<cudaStream_t>(stream);
+    } else {
+      PF_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+      ctx->own_stream = true;
+    }
+    if (g->precision == PF_FP64) ctx->impl.reset(new pf::Impl<double, double>(*g, ctx->stream));
+    else ctx->impl.reset(new pf::Impl<float, float>(*g, ctx->stream));
+  });
+  if (rc != PF_OK) {
+    g_init_err = ctx->err;
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    return rc;
+  }
+  *out = ctx.release();
+  return PF_OK;
+}
+
+int pf_set_params(pf_ctx* ctx, const pf_params* prm) {
+  if (!ctx || !prm) return PF_ERR_ARG;
+  return guarded(ctx, [&] { ctx->impl->set_params(*prm); });
+}
+
+int pf_field_info(const pf_ctx* ctx, int field_id, size_t* count, size_t* elem_bytes) {
+  if (!ctx || !count || !elem_bytes) return PF_ERR_ARG;
+  return guarded(const_cast<pf_ctx*>(ctx), [&] { ctx->impl->field_info(field_id, count, elem_bytes); });
+}
+
+int pf_set_fields(pf_ctx* ctx, int field_id, const void* src, size_t bytes, int src_on_device) {
+  if (!ctx || !src) return PF_ERR_ARG;
+  return guarded(ctx, [&] { ctx->impl->set_field(field_id, src, bytes, src_on_device); });
+}
+
+int pf_step_ex(pf_ctx* ctx, int nsteps, int flags) {
+  if (!ctx) return PF_ERR_ARG;
+  return guarded(ctx, [&] { ctx->impl->step(nsteps, flags); });
+}
+
+int pf_step(pf_ctx* ctx, int nsteps) { return pf_step_ex(ctx, nsteps, 0); }
+
+int pf_get_fields(pf_ctx* ctx, int field_id, void* dst, size_t bytes, int dst_on_device) {
+  if (!ctx || !dst) return PF_ERR_ARG;
+  return guarded(ctx, [&] { ctx->impl->get_field(field_id, dst, bytes, dst_on_device); });
+}
+
+int pf_diagnostics(pf_ctx* ctx, double out[6]) {
+  if (!ctx || !out) return PF_ERR_ARG;
+  return guarded(ctx, [&] { ctx->impl->diagnostics(out); });
+}
+
+const char* pf_last_error(const pf_ctx* ctx) { return ctx ? ctx->err.c_str() : g_init_err.c_str(); }
+
+void pf_destroy(pf_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  ctx->impl.reset();
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,161 @@
+"""GPU path vs the CPU oracle, element by element, through the C ABI.
+
+Tolerances (stated for the FP64 GPU path): 1e-10 relative per field (max
+|gpu - oracle| / max |oracle|).  Mixed path: 2e-4 max-abs on phi and 1e-3
+relative on velocity and stress after the stated number of steps.
+Sizes span several FFT/solve tiles, odd radices (3, 5, 7) and ragged tails.
+"""
+import numpy as np
+import pytest
+
+from paper_2111_04577_gb300 import binding, build, workloads as wl
+from oracle import step as ostep, observables as ob
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    binding.load()
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def grid(dim, nx, nz, dual=1, lx=4.0):
+    dx = lx / nx
+    if dim == 2:
+        return wl.Grid(nx, 1, nz, lx, dx, nz * dx, dual)
+    return wl.Grid(nx, nx, nz, lx, lx, nz * dx, dual)
+
+
+def workload(g, **kw):
+    prm = wl.params_from_groups(**kw)
+    prm.theta_top_deg = 75.0
+    return wl.Workload("t", g, prm, 1)
+
+
+CH_CASES = [
+    (2, 16, 8, 1), (2, 24, 12, 1), (2, 20, 10, 0), (2, 28, 6, 1),
+    (3, 16, 8, 1), (3, 12, 6, 1), (3, 10, 4, 0),
+]
+
+
+@pytest.mark.parametrize("dim,nx,nz,dual", CH_CASES)
+def test_ch_step_fp64(dim, nx, nz, dual):
+    g = grid(dim, nx, nz, dual)
+    w = workload(g, theta_deg=60.0)
+    phi0 = wl.initial_phi(w)
+    rng = np.random.default_rng(7)
+    phim = phi0 + 1e-2 * rng.uniform(-1, 1, phi0.shape)
+    vel = wl.random_velocity(g, 3, 0.2)
+    s = binding.Solver(g, w.params, binding.PF_FP64)
+    s.load_state(phi0, vel, phi_old=phim)
+    ref = ostep.State(g, w.params.as_dict(), phi0, vel0=vel)
+    ref.phi_old = phim.copy()
+    for n in range(4):
+        s.step(1, binding.PF_STEP_CH_ONLY)
+        ref.step(with_ns=False)
+        assert rel(s.fine("phi"), ref.phi) < FP64_TOL, n
+    assert rel(s.fine("G"), ref.G) < FP64_TOL
+
+
+@pytest.mark.parametrize("dim,nx,nz,dual", [(2, 16, 8, 1), (3, 12, 6, 1)])
+def test_ch_step_without_graph_matches_graph(dim, nx, nz, dual):
+    g = grid(dim, nx, nz, dual)
+    w = workload(g, theta_deg=45.0)
+    phi0 = wl.initial_phi(w)
+    vel = wl.random_velocity(g, 3, 0.2)
+    a = binding.Solver(g, w.params, binding.PF_FP64)
+    b = binding.Solver(g, w.params, binding.PF_FP64)
+    for s in (a, b):
+        s.load_state(phi0, vel)
+    a.step(3, binding.PF_STEP_CH_ONLY)
+    b.step(3, binding.PF_STEP_CH_ONLY | binding.PF_STEP_NO_GRAPH)
+    assert np.array_equal(a.fine("phi"), b.fine("phi"))
+
+
+FULL_CASES = [
+    # dim, nx, nz, dual, groups
+    (2, 32, 16, 1, dict(ratio_rho=1000.0, ratio_mu=100.0, theta_deg=120.0, Wi=1.0, beta=0.5)),
+    (2, 24, 12, 0, dict(ratio_rho=10.0, ratio_mu=5.0, theta_deg=60.0)),
+    (3, 16, 8, 1, dict(ratio_rho=1000.0, ratio_mu=20.0, theta_deg=90.0, Wi=2.0, beta=0.3)),
+    (3, 12, 6, 1, dict(ratio_rho=1000.0, ratio_mu=50.0, theta_deg=45.0)),
+]
+
+
+@pytest.mark.parametrize("dim,nx,nz,dual,groups", FULL_CASES)
+def test_full_step_fp64(dim, nx, nz, dual, groups):
+    g = grid(dim, nx, nz, dual, lx=4.0 if dim == 2 else 5.0)
+    w = workload(g, **groups)
+    w.params.uw_top = 0.3
+    phi0 = wl.initial_phi(w)
+    vel = wl.random_velocity(g, 5, 0.1)
+    s = binding.Solver(g, w.params, binding.PF_FP64)
+    s.load_state(phi0, vel)
+    ref = ostep.State(g, w.params.as_dict(), phi0, vel0=vel)
+    for n in range(4):
+        s.step(1)
+        ref.step()
+    assert rel(s.fine("phi"), ref.phi) < FP64_TOL
+    assert rel(s.coarse("u"), ref.vel[0]) < FP64_TOL
+    assert rel(s.coarse("w"), ref.vel[2]) < FP64_TOL
+    if dim == 3:
+        assert rel(s.coarse("v"), ref.vel[1]) < FP64_TOL
+    assert rel(s.coarse("p"), ref.p) < FP64_TOL
+    if ref.d.visco:
+        th = s.coarse("theta")
+        idx = [(0, 0), (0, 1), (1, 1)] if dim == 2 else [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+        for q, (a, b) in enumerate(idx):
+            assert rel(th[q], ref.theta[..., a, b]) < 1e-9, q
+
+
+def test_config1_fp64_full_run():
+    """2D sessile droplet, coarse 64x32 / fine 128x64, 200 steps, FP64."""
+    w = wl.config("c1")
+    g = w.grid
+    phi0 = wl.initial_phi(w)
+    s = binding.Solver(g, w.params, binding.PF_FP64)
+    s.load_state(phi0)
+    s.step(w.steps)
+    ref = ostep.run(g, w.params.as_dict(), phi0, w.steps)
+    assert rel(s.fine("phi"), ref.phi) < FP64_TOL
+    assert rel(s.coarse("u"), ref.vel[0]) < FP64_TOL
+    assert rel(s.coarse("w"), ref.vel[2]) < FP64_TOL
+    assert rel(s.coarse("p"), ref.p) < FP64_TOL
+    dg = s.diagnostics()
+    assert abs(dg["mass"] - ob.mass(ref.phi, g)) < 1e-12 * np.sum(np.abs(ref.phi)) * g.h ** 2
+    assert abs(dg["energy"] / ob.energy(ref.phi, ref.d, g) - 1) < 1e-10
+    assert abs(dg["wetted"] / ob.wetted(ref.phi, g) - 1) < 1e-10
+    assert np.allclose(dg["centroid"], ob.centroid(ref.phi, g), rtol=1e-10, atol=1e-12)
+
+
+def test_config1_mixed_full_run():
+    """Mixed path on config 1: 2e-4 max-abs on phi, 1e-3 relative on u, w."""
+    w = wl.config("c1")
+    g = w.grid
+    phi0 = wl.initial_phi(w)
+    s = binding.Solver(g, w.params, binding.PF_MIXED)
+    s.load_state(phi0)
+    s.step(w.steps)
+    ref = ostep.run(g, w.params.as_dict(), phi0, w.steps)
+    assert np.max(np.abs(s.fine("phi") - ref.phi)) < 2e-4
+    assert rel(s.coarse("u"), ref.vel[0]) < 1e-3
+    assert rel(s.coarse("w"), ref.vel[2]) < 1e-3
+
+
+def test_mass_conservation_gpu_fp64_and_mixed():
+    w = wl.scaled(wl.config("c2"), 32, 16)
+    g = w.grid
+    phi0 = wl.initial_phi(w)
+    for prec, tol in ((binding.PF_FP64, 1e-13), (binding.PF_MIXED, 1e-5)):
+        s = binding.Solver(g, w.params, prec)
+        s.load_state(phi0)
+        m0 = s.diagnostics()["mass"]
+        s.step(20)
+        m1 = s.diagnostics()["mass"]
+        assert abs(m1 - m0) < tol * np.sum(np.abs(phi0)) * g.h ** 2, prec
