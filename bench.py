@@ -1,0 +1,373 @@
+"""Benchmark of the dual-resolution phase-field step on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (one GPU): the 3D viscoelastic droplet -- coarse 256x256x128 flow mesh,
+fine 512x512x256 phase-field mesh, Oldroyd-B droplet (Wi = 2, beta = 0.3),
+density ratio 1000, viscosity ratio 20, 90 deg contact angle, mixed precision,
+seeded synthetic initial state.  Metric: fine-mesh cell-steps/s of the whole
+time step (CH + restriction + NS + polymer), inputs resident in HBM; every
+field is larger than L2, so no flush is needed.
+
+Also reported: the same GPU's FP64 path and single-resolution paths (CSR: phi
+on the coarse mesh; RSR: every field on the fine mesh), the mixed path's phi
+error against the FP64 path, the dominant kernel against the measured HBM
+copy bandwidth, the CPU oracle on a bounded sample, an end-to-end figure
+through the C ABI with host buffers, and SM clocks sampled during the run.
+
+With torchrun (N > 1) every rank advances its own independent replica
+(weak scaling); the timed region is bracketed by barriers and the max over
+ranks is taken.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fine-mesh cell-steps/s (dual-res 3D) vs FP64 GPU path at stated error; HBM roof %"
+UNIT = "fine cell-steps/s"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def alg_bytes(grid, esize, visco=True):
+    """Algorithmic bytes per step of each kernel (all its launches in one step).
+
+    Minimal traffic of the operation: each input read once, each output
+    written once (no halos, no re-reads)."""
+    nzf, nyf, nxf = grid.fine_shape
+    nf = nzf * nyf * nxf
+    nz, ny, nx = grid.coarse_shape
+    nc = nz * ny * nx
+    ncw = (nz + 1) * ny * nx
+    d3 = grid.dim == 3
+    E = esize
+    sf = (nxf // 2 + 1) * nyf * nzf          # fine spectral complex elements
+    sc = (nx // 2 + 1) * ny * nz             # coarse spectral complex elements (per component)
+    nvel = 3 if d3 else 2
+    ncomp = 6 if d3 else 3
+    nsolve = nvel + 1                        # velocity components + pressure
+    b = {
+        "ch_mu": 3 * E * nf,
+        "ch_rhs_fftx": 3 * E * nf + 2 * nvel * E * nc + 2 * E * sf,
+        "fft_y_fine": 2 * 2 * (2 * E * sf) if d3 else 0,
+        "zsolve_pair": 2 * 2 * E * sf,
+        "ch_ifftx_finish": 2 * E * sf + 3 * E * nf,
+        "ch_G": 2 * E * nf,
+        "restrict": 2 * E * nf + (11 if d3 else 7) * E * nc,
+        "ns_rhs": (2 * (nvel + 1) + (2 * ncomp if visco else 0) + (11 if d3 else 7) + nvel) * E * nc,
+        "rfft_x_coarse": nsolve * (E * nc + 2 * E * sc),
+        "fft_y_coarse": (2 * nsolve * 2 * (2 * E * sc)) if d3 else 0,
+        "zsolve": nsolve * 2 * (2 * E * sc),
+        "zero_mode": 0,
+        "irfft_x_coarse": nsolve * (2 * E * sc + E * nc),
+        "div": (nvel + 1) * E * nc,
+        "correct": (2 * nvel + 3) * E * nc,
+        "polymer_stage1": (2 * ncomp + nvel) * E * nc,
+        "polymer_stage2": (4 * ncomp + nvel + 1) * E * nc,
+    }
+    return b
+
+
+def clocks_start():
+    f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+    try:
+        p = subprocess.Popen(
+            ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+             "--format=csv,noheader,nounits", "-lms", "200"], stdout=f, stderr=subprocess.DEVNULL)
+    except Exception:
+        return None, f.name
+    return p, f.name
+
+
+def clocks_stop(p, path, gpu_index=0):
+    if p is None:
+        return None
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except Exception:
+        p.kill()
+    sm, mx, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        for line in open(path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9 or parts[0] != str(gpu_index):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+    finally:
+        try:
+            os.unlink(path)
+        except OSError:
+            pass
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload(name="c4"):
+    from paper_2111_04577_gb300 import workloads as wl
+    return wl.config(name)
+
+
+def cpu_sample(w, steps, nx=64):
+    """Time the FP64 oracle on the workload's physics at a reduced resolution."""
+    from paper_2111_04577_gb300 import workloads as wl
+    from oracle import step as ostep
+    ws = wl.scaled(w, nx, nx // 2)
+    phi0 = wl.initial_phi(ws)
+    st = ostep.State(ws.grid, ws.params.as_dict(), phi0)
+    st.step()  # warm caches / FFT plans
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st.step()
+    dt = time.perf_counter() - t0
+    cells = ws.grid.fine_cells()
+    return {"value": cells * steps / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"FP64 NumPy/SciPy oracle, same physics at coarse {nx}x{nx}x{nx // 2} / fine "
+                      f"{2 * nx}x{2 * nx}x{nx}, {steps} steps, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload(args.config)
+    steps, warm = args.steps, args.warmup
+    from paper_2111_04577_gb300 import workloads as wl
+    from oracle import step as ostep
+    nx = 48
+    ws = wl.scaled(w, nx, nx // 2)
+    st = ostep.State(ws.grid, ws.params.as_dict(), wl.initial_phi(ws))
+    for _ in range(warm):
+        st.step()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st.step()
+    dt = time.perf_counter() - t0
+    val = ws.grid.fine_cells() * steps / dt
+    sample = (f"FP64 NumPy/SciPy oracle, workload physics at coarse {nx}x{nx}x{nx // 2} / fine "
+              f"{2 * nx}x{2 * nx}x{nx}, one oracle time step per step")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": steps, "warmup": warm, "ms_per_step": dt / steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name + f" (sampled at {nx}x{nx}x{nx // 2})", "precision": "fp64"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_steps(solver, stream, steps):
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    solver.step(steps)
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / 1e3
+
+
+def side_path(w, grid, precision, steps, warm, stream):
+    """Cell-steps/s of another configuration of the same physics."""
+    import gc
+    import torch
+    from paper_2111_04577_gb300 import binding, workloads as wl
+    s = binding.Solver(grid, w.params, precision, stream=stream.cuda_stream)
+    ww = wl.Workload(w.name, grid, w.params, w.steps, w.R0, w.seed, w.amp)
+    s.load_state(wl.initial_phi(ww).astype(s.dtype))
+    s.step(warm)
+    t = time_steps(s, stream, steps)
+    s.close()
+    del s
+    gc.collect()
+    torch.cuda.synchronize()
+    return grid.fine_cells() * steps / t, t / steps * 1e3
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c4")
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64 / single-resolution legs")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_2111_04577_gb300 import binding, build, workloads as wl
+    build.build()
+    w = workload(args.config)
+    g = w.grid
+    stream = torch.cuda.Stream()
+    prec = binding.PF_MIXED
+    solver = binding.Solver(g, w.params, prec, stream=stream.cuda_stream)
+    phi0 = wl.initial_phi(w)
+    phi0_f = phi0.astype(np.float32)
+    solver.load_state(phi0_f)
+    solver.step(args.warmup)
+    torch.cuda.synchronize()
+
+    # ---------------- timed region (device-resident inputs) ----------------
+    clk, clk_path = clocks_start() if rank == 0 else (None, None)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    elapsed = time_steps(solver, stream, args.steps)
+    torch.cuda.synchronize()
+    if dist:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+        dist.barrier()
+    clocks = clocks_stop(clk, clk_path) if rank == 0 else None
+    ms_per_step = elapsed / args.steps * 1e3
+    value = g.fine_cells() * args.steps * world / elapsed
+
+    # ---------------- per-kernel profile and roofline ----------------
+    prof, per_step = solver.profile(3)
+    esize = 4
+    ab = alg_bytes(g, esize, visco=True)
+    peak, peak_kind = peaks()
+    rows = []
+    for name, ms, cnt in prof:
+        byt = ab.get(name, 0)
+        rows.append({"kernel": name, "launches": cnt, "ms": ms, "alg_bytes": byt,
+                     "gbs": byt / (ms * 1e-3) / 1e9 if ms > 0 else 0.0})
+    dom = max(rows, key=lambda r: r["ms"])
+    total_ms = sum(r["ms"] for r in rows)
+    roofline = {"bound": "hbm", "kernel": dom["kernel"], "achieved": dom["gbs"], "peak": peak, "unit": "GB/s",
+                "frac": dom["gbs"] / peak, "traffic": None, "peak_kind": peak_kind,
+                "alg_bytes_per_launch": dom["alg_bytes"] / max(1, dom["launches"]),
+                "launch_ms": dom["ms"] / max(1, dom["launches"])}
+    step_bytes = sum(ab.values())
+
+    # ---------------- end to end through the C ABI with host buffers ----------------
+    pin_in = torch.from_numpy(phi0_f).pin_memory()
+    pin_out = torch.empty(phi0_f.size, dtype=torch.float32).pin_memory()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    solver.set("phi", pin_in)
+    solver.step(args.steps)
+    solver.get("phi", out=pin_out)
+    diag = solver.diagnostics()
+    t_e2e = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([t_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    h2d = 2 * phi0_f.nbytes  # phi^n and its start-up twin phi^{n-1}
+    d2h = phi0_f.nbytes + 6 * 8
+    e2e = {"value": g.fine_cells() * args.steps * world / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+           "note": "pf_set_fields(phi from pinned host) + pf_step(K) + pf_get_fields(phi) + pf_diagnostics"}
+    launches = per_step * args.steps + (args.steps // 50 + 1)
+
+    extra = {}
+    if rank == 0 and not args.no_compare:
+        # accuracy of the mixed path against the FP64 GPU path on the same input
+        nst = 20
+        sm = binding.Solver(g, w.params, binding.PF_MIXED, stream=stream.cuda_stream)
+        sm.load_state(phi0_f)
+        sm.step(nst)
+        phim = sm.get("phi").astype(np.float64)
+        sm.close()
+        del sm
+        sd = binding.Solver(g, w.params, binding.PF_FP64, stream=stream.cuda_stream)
+        sd.load_state(phi0)
+        sd.step(nst)
+        phid = sd.get("phi")
+        ud = sd.coarse("u")
+        sd.step(2)
+        t64 = time_steps(sd, stream, 5)
+        sd.close()
+        del sd
+        torch.cuda.empty_cache()
+        extra["fp64_path"] = {"value": g.fine_cells() * 5 / t64, "ms_per_step": t64 / 5 * 1e3,
+                              "speedup_mixed_over_fp64": (value / world) / (g.fine_cells() * 5 / t64),
+                              "mixed_phi_maxabs_err_vs_fp64_after_steps": float(np.max(np.abs(phim - phid))),
+                              "steps_compared": nst}
+        # single resolution: CSR (phi on the coarse mesh) and RSR (all fields on the fine mesh)
+        csr = wl.Grid(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, 0)
+        rsr = wl.Grid(2 * g.nx, 2 * g.ny, 2 * g.nz, g.lx, g.ly, g.lz, 0)
+        v_csr, ms_csr = side_path(w, csr, binding.PF_MIXED, 10, 2, stream)
+        v_rsr, ms_rsr = side_path(w, rsr, binding.PF_MIXED, 5, 2, stream)
+        extra["single_res"] = {
+            "csr": {"grid": f"{csr.nx}x{csr.ny}x{csr.nz} (phi coarse)", "cell_steps_per_s": v_csr,
+                    "ms_per_step": ms_csr},
+            "rsr": {"grid": f"{rsr.nx}x{rsr.ny}x{rsr.nz} (all fine)", "cell_steps_per_s": v_rsr,
+                    "ms_per_step": ms_rsr,
+                    "dual_speedup_at_same_phi_resolution": ms_rsr / ms_per_step},
+        }
+    cpu = cpu_sample(w, 2, 64) if rank == 0 else None
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (FP64 contact-line flux, zero mode, reductions)",
+            "data": "synthetic",
+            "config": {"workload": w.name + " (coarse 256x256x128 / fine 512x512x256, mixed)",
+                       "fine_cells": g.fine_cells(), "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks,
+            "kernels": rows, "alg_bytes_per_fine_cell_step": step_bytes / g.fine_cells(),
+            "step_roof_frac": (step_bytes / (ms_per_step * 1e-3) / 1e9) / peak,
+            "profile_sum_ms": total_ms, "diagnostics": diag,
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

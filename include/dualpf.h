@@ -14,8 +14,10 @@
  *  - Return value: 0 on success, a negative PF_ERR_* code otherwise; the
  *    message of the last failure is returned by pf_last_error().
  *  - Streams: all device work is enqueued on the cudaStream_t given to
- *    pf_init_grid (NULL = legacy default stream).  pf_get_fields and
- *    pf_diagnostics synchronise that stream before returning.
+ *    pf_init_grid; given NULL, the context creates and owns a non-blocking
+ *    stream (the legacy default stream cannot be captured into a graph).
+ *    pf_set_fields from host memory, pf_get_fields, pf_diagnostics and
+ *    pf_profile synchronise that stream before returning.
  *  - Ownership: the library allocates and owns every field buffer of a
  *    context; callers own the src/dst buffers they pass in.  Nothing is
  *    retained after a call returns.
@@ -110,7 +112,7 @@ typedef struct {
 } pf_params;
 
 /* Create a context for grid *g and allocate all fields on the current CUDA
- * device (all zero).  stream: a cudaStream_t or NULL.  On success *out owns
+ * device (all zero).  stream: a cudaStream_t, or NULL for a private one.  On success *out owns
  * the context; release it with pf_destroy.  Errors: PF_ERR_ARG (bad sizes,
  * non-cubic cells), PF_ERR_UNSUPPORTED (a size with a prime factor > 7),
  * PF_ERR_NOMEM, PF_ERR_CUDA. */
@@ -152,6 +154,19 @@ int pf_get_fields(pf_ctx* ctx, int field_id, void* dst, size_t bytes, int dst_on
  * out[3..5] centroid of (1+phi)/2 in x, y, z.
  * phi_w = 1.5 phi_0 - 0.5 phi_1 is the wall value of the contact-angle law. */
 int pf_diagnostics(pf_ctx* ctx, double out[6]);
+
+/* Per-kernel profile: run nsteps steps launching kernels directly (no graph)
+ * with a CUDA event before each launch, and report for each distinct kernel
+ * its name (NUL-terminated, PF_PROFILE_NAME bytes per entry in `names`), its
+ * summed device time per step in milliseconds (`avg_ms`, averaged over the
+ * steps) and its number of launches per step (`counts`), in launch order.
+ * *n_entries receives the number of entries written (<= max_entries) and
+ * *launches_per_step the number of kernel launches one step makes.  The
+ * state advances by nsteps steps exactly as pf_step_ex would.  Synchronises.
+ * Errors: PF_ERR_ARG, PF_ERR_CUDA. */
+#define PF_PROFILE_NAME 48
+int pf_profile(pf_ctx* ctx, int nsteps, int flags, int max_entries, char* names, double* avg_ms,
+               int* counts, int* n_entries, int* launches_per_step);
 
 /* Message of the last failed call on ctx (or of the last failed
  * pf_init_grid when ctx is NULL).  Valid until the next call. */

@@ -24,7 +24,8 @@ ERRORS = {-1: "PF_ERR_ARG", -2: "PF_ERR_DISCRIMINANT", -3: "PF_ERR_UNSUPPORTED",
           -5: "PF_ERR_TIMEOUT", -6: "PF_ERR_CUDA", -7: "PF_ERR_NOMEM"}
 
 EXPORTS = ["pf_init_grid", "pf_set_params", "pf_field_info", "pf_set_fields", "pf_step", "pf_step_ex",
-           "pf_get_fields", "pf_diagnostics", "pf_last_error", "pf_destroy"]
+           "pf_get_fields", "pf_diagnostics", "pf_profile", "pf_last_error", "pf_destroy"]
+PROFILE_NAME = 48
 
 
 class GridDesc(C.Structure):
@@ -62,12 +63,14 @@ def load(path: str = LIB_PATH):
         lib.pf_step.argtypes = [vp, C.c_int]
         lib.pf_step_ex.argtypes = [vp, C.c_int, C.c_int]
         lib.pf_diagnostics.argtypes = [vp, C.POINTER(C.c_double)]
+        lib.pf_profile.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_char_p, C.POINTER(C.c_double),
+                                   C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
         lib.pf_last_error.argtypes = [vp]
         lib.pf_last_error.restype = C.c_char_p
         lib.pf_destroy.argtypes = [vp]
         lib.pf_destroy.restype = None
         for f in ("pf_init_grid", "pf_set_params", "pf_field_info", "pf_set_fields", "pf_get_fields",
-                  "pf_step", "pf_step_ex", "pf_diagnostics"):
+                  "pf_step", "pf_step_ex", "pf_diagnostics", "pf_profile"):
             getattr(lib, f).restype = C.c_int
         _lib = lib
     return _lib
@@ -145,6 +148,22 @@ class Solver:
         out = (C.c_double * 6)()
         self._chk(self.lib.pf_diagnostics(self.h, out))
         return dict(mass=out[0], energy=out[1], wetted=out[2], centroid=(out[3], out[4], out[5]))
+
+    def profile(self, nsteps=3, flags=0, max_entries=64):
+        """Per-kernel device ms per step (direct launches, CUDA events).
+        Returns (list of (name, ms_per_step, launches_per_step), total launches
+        per step).  Advances the state by nsteps."""
+        names = C.create_string_buffer(max_entries * PROFILE_NAME)
+        ms = (C.c_double * max_entries)()
+        cnt = (C.c_int * max_entries)()
+        n, per = C.c_int(), C.c_int()
+        self._chk(self.lib.pf_profile(self.h, int(nsteps), int(flags), max_entries, names, ms, cnt, C.byref(n),
+                                      C.byref(per)))
+        out = []
+        for i in range(n.value):
+            raw = names.raw[i * PROFILE_NAME:(i + 1) * PROFILE_NAME]
+            out.append((raw.split(b"\0", 1)[0].decode(), ms[i], cnt[i]))
+        return out, per.value
 
     def close(self):
         if getattr(self, "h", None):

@@ -102,6 +102,7 @@ struct CoarseVel {
 // Producer of the increment-form right side R for the x-transform kernel.
 template <class T>
 struct ChRhs {
+  static constexpr const char* name = "ch_rhs_fftx";
   FineView<T> f;
   const T* mu;
   CoarseVel<T> vel;
@@ -137,6 +138,7 @@ struct ChRhs {
 // phi^{n+1} = phi* + delta, written over phi^{n-1} (same index, no hazard).
 template <class T>
 struct ChFinish {
+  static constexpr const char* name = "ch_ifftx_finish";
   const T* pn;
   T* po_new;  // holds phi^{n-1} on entry, phi^{n+1} on exit
   int fnx;

@@ -81,12 +81,14 @@ struct Arena {
 // producers / consumers for the x transforms of plain arrays
 template <class T>
 struct ArrPro {
+  static constexpr const char* name = "rfft_x_coarse";
   const T* a;
   int n;
   __device__ __forceinline__ T operator()(int line, int x) const { return a[(size_t)line * n + x]; }
 };
 template <class T>
 struct ArrEpi {
+  static constexpr const char* name = "irfft_x_coarse";
   T* a;
   int n;
   __device__ __forceinline__ void operator()(int line, int x, T v) const { a[(size_t)line * n + x] = v; }
@@ -100,6 +102,8 @@ struct ImplBase {
   virtual void get_field(int f, void* dst, size_t bytes, int on_dev) = 0;
   virtual void step(int nsteps, int flags) = 0;
   virtual void diagnostics(double out[6]) = 0;
+  virtual void profile(int nsteps, int flags, std::vector<std::string>& names, std::vector<double>& ms,
+                       std::vector<int>& counts, int& per_step) = 0;
 };
 
 static Phys derive(const pf_params& q, const pf_grid_desc& g) {
@@ -175,6 +179,23 @@ struct Impl : ImplBase {
   int pc = 0, fc = 0;  // parities: phi^n = phi[pc]; u^n = u[fc], ...
   std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;
   long long steps_done = 0;
+  // per-kernel timing (pf_profile): one event before every launch of a step
+  bool prof = false;
+  int nlaunch = 0;
+  std::vector<const char*> mark_names;
+  std::vector<cudaEvent_t> mark_ev;
+  void mark(const char* name) {
+    ++nlaunch;
+    if (!prof) return;
+    const size_t i = mark_names.size();
+    if (i >= mark_ev.size()) {
+      cudaEvent_t e;
+      PF_CUDA_TRY(cudaEventCreate(&e));
+      mark_ev.push_back(e);
+    }
+    PF_CUDA_TRY(cudaEventRecord(mark_ev[i], st));
+    mark_names.push_back(name);
+  }
 
   Impl(const pf_grid_desc& gd, cudaStream_t s) : g(gd), st(s) {
     d.nx = g.nx;
@@ -251,6 +272,7 @@ struct Impl : ImplBase {
 
   ~Impl() override {
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    for (auto e : mark_ev) cudaEventDestroy(e);
   }
 
   cpx<T>* twiddles(int n) {
@@ -296,6 +318,7 @@ struct Impl : ImplBase {
     const int pairs = (nlines + 1) / 2;
     const int grid = (pairs + npair - 1) / npair;
     const size_t sm = 2 * (size_t)npair * n * sizeof(cpx<T>);
+    mark(Pro::name);
     k_rfft_x<T, Pro><<<grid, 256, sm, st>>>(pro, out, n, nlines, pitch, pl, tw, npair);
   }
   template <class Epi>
@@ -304,12 +327,14 @@ struct Impl : ImplBase {
     const int pairs = (nlines + 1) / 2;
     const int grid = (pairs + npair - 1) / npair;
     const size_t sm = 2 * (size_t)npair * n * sizeof(cpx<T>);
+    mark(Epi::name);
     k_irfft_x<T, Epi><<<grid, 256, sm, st>>>(in, epi, n, nlines, pitch, pl, tw, npair, scale);
   }
   void fft_y(cpx<T>* data, int ny, int pitch, int ncol, int levels, const FftPlan& pl, const cpx<T>* tw, int sign) {
     const int tx = sizeof(T) == 4 ? 8 : 4;
     dim3 grid((ncol + tx - 1) / tx, levels);
     const size_t sm = 2 * (size_t)ny * tx * sizeof(cpx<T>);
+    mark(ny == d.fny && levels == d.fnz && d.r > 1 ? "fft_y_fine" : "fft_y_coarse");
     k_fft_y<T><<<grid, 256, sm, st>>>(data, ny, pitch, ncol, pl, tw, sign, tx);
   }
   void zsolve(cpx<T>* data, int rows, int ny, int pitch, int ncol, const double* ex, const double* ey, int bc,
@@ -330,8 +355,12 @@ struct Impl : ImplBase {
     const int tx = 16;
     const size_t sm = (size_t)rows * tx * sizeof(TC) * (zs.same ? 3 : 4);
     dim3 grid((ncol + tx - 1) / tx, ny);
+    mark(two ? "zsolve_pair" : "zsolve");
     k_zsolve<T, TC><<<grid, 2 * tx, sm, st>>>(data, ex, ey, zs, tx);
-    if (poisson) k_zero_mode<T><<<1, 32, 0, st>>>(data, rows, ny, pitch, h2, scale, zwork);
+    if (poisson) {
+      mark("zero_mode");
+      k_zero_mode<T><<<1, 32, 0, st>>>(data, rows, ny, pitch, h2, scale, zwork);
+    }
   }
 
   // one transform solve on the coarse mesh: rhs (real, lines of nx) -> out
@@ -351,6 +380,7 @@ struct Impl : ImplBase {
     const size_t nf = (size_t)d.fnx * d.fny * d.fnz;
     // ---- Cahn-Hilliard on the fine mesh ----
     FineView<T> fv{phi[pc], phi[po]};
+    mark("ch_mu");
     k_ch_mu<T><<<blocks_for(nf), nb, 0, st>>>(fv, mu, gwall, d, p);
     ChRhs<T> rhs;
     rhs.f = fv;
@@ -368,11 +398,13 @@ struct Impl : ImplBase {
            1.0 / ((double)d.fnx * d.fny), false);
     if (d.dim == 3) fft_y(spF, d.fny, pF, d.fnx / 2 + 1, d.fnz, plFy, twFy, +1);
     irfft_x(spF, ChFinish<T>{phi[pc], phi[po], d.fnx}, d.fnx, nlf, pF, plFx, twFx, (T)1);
+    mark("ch_G");
     k_ch_G<T><<<blocks_for(nf), nb, 0, st>>>(phi[po], gwall, G, d, p);
     if (flags & PF_STEP_CH_ONLY) return;
     // ---- restriction to the coarse mesh ----
     const size_t ncw = (size_t)d.nx * d.ny * (d.nz + 1);
     const size_t nc = (size_t)d.nx * d.ny * d.nz;
+    mark("restrict");
     k_restrict<T><<<blocks_for(ncw), nb, 0, st>>>(phi[po], G, rs, d);
     // ---- Navier-Stokes ----
     NsAcc<T> A;
@@ -391,14 +423,17 @@ struct Impl : ImplBase {
     A.a.rs = rs;
     A.d = d;
     A.p = p;
+    mark("ns_rhs");
     k_ns_rhs<T><<<blocks_for(nc), nb, 0, st>>>(A, ru, rv, rw, p.visco);
     const double kk = p.gamma0 / (p.dt * p.nu_m);
     // u~, v~ land in the n-1 buffers (free once the right sides exist)
     coarse_solve(ru, u[fo], spU, d.nz, Z_DIRICH, kk, false);
     if (d.dim == 3) coarse_solve(rv, v[fo], spV, d.nz, Z_DIRICH, kk, false);
     coarse_solve(rw, wt, spW, d.nz - 1, Z_FACES, kk, false);
+    mark("div");
     k_div<T><<<blocks_for(nc), nb, 0, st>>>(u[fo], v[fo], wt, dv, d, (T)(p.gamma0 * p.rho0 / p.dt));
     coarse_solve(dv, pp, spP, d.nz, Z_NEUMANN, 0.0, true);
+    mark("correct");
     k_correct<T><<<blocks_for(ncw), nb, 0, st>>>(u[fo], v[fo], wt, w[fo], pp, pr[fc], pr[fo], d,
                                                   (T)(p.dt / (p.gamma0 * p.rho0)));
     // ---- polymer ----
@@ -412,6 +447,7 @@ struct Impl : ImplBase {
         P.th[c] = theta[c];
         P.out[c] = theta1[c];
       }
+      mark("polymer_stage1");
       if (d.dim == 2) k_polymer<T, 2><<<blocks_for(nc), 128, 0, st>>>(P, d, p, 1);
       else k_polymer<T, 3><<<blocks_for(nc), 128, 0, st>>>(P, d, p, 1);
       for (int c = 0; c < ncomp; ++c) {
@@ -420,6 +456,7 @@ struct Impl : ImplBase {
         P.out[c] = theta[c];
         P.tau[c] = tau[fo][c];
       }
+      mark("polymer_stage2");
       if (d.dim == 2) k_polymer<T, 2><<<blocks_for(nc), 128, 0, st>>>(P, d, p, 2);
       else k_polymer<T, 3><<<blocks_for(nc), 128, 0, st>>>(P, d, p, 2);
     }
@@ -537,6 +574,60 @@ struct Impl : ImplBase {
       it = graphs.emplace(key, ex).first;
     }
     PF_CUDA_TRY(cudaGraphLaunch(it->second, st));
+  }
+
+  // per-kernel average device time over nsteps direct (non-graph) steps
+  void profile(int nsteps, int flags, std::vector<std::string>& names, std::vector<double>& ms,
+               std::vector<int>& counts, int& per_step) override {
+    if (!have_params) throw ApiError(PF_ERR_ARG, "pf_set_params must precede pf_profile");
+    std::map<std::string, double> acc;
+    std::map<std::string, int> cnt;
+    std::vector<std::string> order;
+    cudaEvent_t last;
+    PF_CUDA_TRY(cudaEventCreate(&last));
+    per_step = 0;
+    for (int s = 0; s < nsteps; ++s) {
+      prof = true;
+      nlaunch = 0;
+      mark_names.clear();
+      launch_step(flags);
+      check_launch();
+      PF_CUDA_TRY(cudaEventRecord(last, st));
+      prof = false;
+      PF_CUDA_TRY(cudaEventSynchronize(last));
+      per_step = nlaunch;
+      for (size_t i = 0; i < mark_names.size(); ++i) {
+        float t = 0;
+        PF_CUDA_TRY(cudaEventElapsedTime(&t, mark_ev[i], i + 1 < mark_names.size() ? mark_ev[i + 1] : last));
+        if (!acc.count(mark_names[i])) order.push_back(mark_names[i]);
+        acc[mark_names[i]] += t;
+        if (s == 0) cnt[mark_names[i]] += 1;
+      }
+      pc ^= 1;
+      if (!(flags & PF_STEP_CH_ONLY)) fc ^= 1;
+      ++steps_done;
+    }
+    cudaEventDestroy(last);
+    names = order;
+    ms.clear();
+    counts.clear();
+    for (auto& n : order) {
+      ms.push_back(acc[n] / std::max(1, nsteps));
+      counts.push_back(cnt[n]);
+    }
+  }
+
+  int launches_per_step(int flags) {
+    prof = false;
+    nlaunch = 0;
+    // count without launching: replay the launch sequence into a throwaway capture
+    cudaGraph_t gr;
+    PF_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    launch_step(flags);
+    cudaGetLastError();
+    PF_CUDA_TRY(cudaStreamEndCapture(st, &gr));
+    cudaGraphDestroy(gr);
+    return nlaunch;
   }
 
   double mass_check() {
@@ -679,6 +770,28 @@ int pf_get_fields(pf_ctx* ctx, int field_id, void* dst, size_t bytes, int dst_on
 int pf_diagnostics(pf_ctx* ctx, double out[6]) {
   if (!ctx || !out) return PF_ERR_ARG;
   return guarded(ctx, [&] { ctx->impl->diagnostics(out); });
+}
+
+int pf_profile(pf_ctx* ctx, int nsteps, int flags, int max_entries, char* names, double* avg_ms, int* counts,
+               int* n_entries, int* launches_per_step) {
+  if (!ctx || nsteps < 1 || max_entries < 1 || !names || !avg_ms || !counts || !n_entries || !launches_per_step)
+    return PF_ERR_ARG;
+  return guarded(ctx, [&] {
+    std::vector<std::string> nm;
+    std::vector<double> ms;
+    std::vector<int> cn;
+    int per = 0;
+    ctx->impl->profile(nsteps, flags, nm, ms, cn, per);
+    const int n = std::min<int>(max_entries, (int)nm.size());
+    for (int i = 0; i < n; ++i) {
+      std::strncpy(names + (size_t)i * PF_PROFILE_NAME, nm[i].c_str(), PF_PROFILE_NAME - 1);
+      names[(size_t)i * PF_PROFILE_NAME + PF_PROFILE_NAME - 1] = 0;
+      avg_ms[i] = ms[i];
+      counts[i] = cn[i];
+    }
+    *n_entries = n;
+    *launches_per_step = per;
+  });
 }
 
 const char* pf_last_error(const pf_ctx* ctx) { return ctx ? ctx->err.c_str() : g_init_err.c_str(); }
