@@ -223,6 +223,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c4")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 / single-resolution legs")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--nx", type=int, default=0,
+                    help="run the workload's physics at another coarse nx (ny = nx, nz = nx/2); profiling only")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -241,6 +244,8 @@ def main():
     from paper_2111_04577_gb300 import binding, build, workloads as wl
     build.build()
     w = workload(args.config)
+    if args.nx:
+        w = wl.scaled(w, args.nx, args.nx // 2)
     g = w.grid
     stream = torch.cuda.Stream()
     prec = binding.PF_MIXED
@@ -344,7 +349,7 @@ def main():
                     "ms_per_step": ms_rsr,
                     "dual_speedup_at_same_phi_resolution": ms_rsr / ms_per_step},
         }
-    cpu = cpu_sample(w, 2, 64) if rank == 0 else None
+    cpu = cpu_sample(workload(args.config), 2, 64) if (rank == 0 and not args.no_cpu) else None
 
     if rank == 0:
         line = {
@@ -352,7 +357,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 (FP64 contact-line flux, zero mode, reductions)",
             "data": "synthetic",
-            "config": {"workload": w.name + " (coarse 256x256x128 / fine 512x512x256, mixed)",
+            "config": {"workload": w.name + f" (coarse {g.nx}x{g.ny}x{g.nz} / fine "
+                                   f"{g.fine_shape[2]}x{g.fine_shape[1]}x{g.fine_shape[0]}, mixed)",
                        "fine_cells": g.fine_cells(), "l2": "inputs larger than L2 (no flush)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,

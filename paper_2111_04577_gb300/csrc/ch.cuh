@@ -36,34 +36,31 @@ __device__ __forceinline__ double wall_g(double cth, double p0, double p1, doubl
 
 // mu* = f(phi*) - (L_N phi* + B(g)); also stores g per wall column.
 template <class T>
-__global__ void k_ch_mu(FineView<T> f, T* __restrict__ mu, double* __restrict__ gwall, Dims d, Phys p) {
-  const size_t n = (size_t)d.fnx * d.fny * d.fnz;
-  const T ih2 = (T)(1.0 / (d.h * d.h));
-  const T ie2 = (T)(1.0 / (p.eta * p.eta));
-  for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < n; id += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(id % d.fnx);
-    const int j = (int)((id / d.fnx) % d.fny);
-    const int k = (int)(id / ((size_t)d.fnx * d.fny));
-    const T c0 = f.star(id);
-    T lap = f.star(fidx(d, wrap(i + 1, d.fnx), j, k)) + f.star(fidx(d, wrap(i - 1, d.fnx), j, k)) - 2 * c0;
-    if (d.dim == 3) lap += f.star(fidx(d, i, wrap(j + 1, d.fny), k)) + f.star(fidx(d, i, wrap(j - 1, d.fny), k)) - 2 * c0;
-    const T zp = (k + 1 < d.fnz) ? f.star(fidx(d, i, j, k + 1)) : c0;
-    const T zm = (k > 0) ? f.star(fidx(d, i, j, k - 1)) : c0;
-    lap = (lap + zp + zm - 2 * c0) * ih2;
-    double B = 0.0;
-    const size_t col = (size_t)j * d.fnx + i;
-    if (k == 0) {
-      const double g = wall_g(p.cos_bot, (double)c0, (double)zp, p.eta);
-      gwall[col] = g;
-      B += g / d.h;
-    }
-    if (k == d.fnz - 1) {
-      const double g = wall_g(p.cos_top, (double)c0, (double)zm, p.eta);
-      gwall[(size_t)d.fnx * d.fny + col] = g;
-      B += g / d.h;
-    }
-    mu[id] = c0 * (c0 * c0 - 1) * ie2 - (lap + (T)B);
+__global__ void k_ch_mu(FineView<T> f, T* __restrict__ mu, double* __restrict__ gwall, Dims d, Phys p, PhysT<T> q) {
+  RowIdx x;
+  if (!row_index(d.fnx, d.fny, x)) return;
+  const int i = x.i, j = x.j, k = x.k;
+  const size_t id = (size_t)x.row * d.fnx + i;
+  const T c0 = f.star(id);
+  T lap = f.star(id - i + wrap(i + 1, d.fnx)) + f.star(id - i + wrap(i - 1, d.fnx)) - 2 * c0;
+  if (d.dim == 3) lap += f.star(fidx(d, i, wrap(j + 1, d.fny), k)) + f.star(fidx(d, i, wrap(j - 1, d.fny), k)) - 2 * c0;
+  const size_t plane = (size_t)d.fnx * d.fny;
+  const T zp = (k + 1 < d.fnz) ? f.star(id + plane) : c0;
+  const T zm = (k > 0) ? f.star(id - plane) : c0;
+  lap = (lap + zp + zm - 2 * c0) * q.ih2;
+  T B = 0;
+  const size_t col = (size_t)j * d.fnx + i;
+  if (k == 0) {
+    const double g = wall_g(p.cos_bot, (double)c0, (double)zp, p.eta);
+    gwall[col] = g;
+    B += (T)(g / d.h);
   }
+  if (k == d.fnz - 1) {
+    const double g = wall_g(p.cos_top, (double)c0, (double)zm, p.eta);
+    gwall[plane + col] = g;
+    B += (T)(g / d.h);
+  }
+  mu[id] = c0 * (c0 * c0 - 1) * q.ie2 - (lap + B);
 }
 
 // Prolonged extrapolated velocity (Eq. dual1) on the fine faces.
@@ -75,26 +72,26 @@ struct CoarseVel {
   __device__ __forceinline__ T ws(size_t i) const { return (T)2 * wn[i] - wo[i]; }
   // fine x-face I (left face of fine cell I), fine row (J, K)
   __device__ __forceinline__ T uface(const Dims& d, int I, int J, int K) const {
-    const int jc = J / d.ry, kc = K / d.r;
-    const int ic = I / d.r;
+    const int jc = J >> d.rys, kc = K >> d.rs;
+    const int ic = I >> d.rs;
     const size_t b = ((size_t)kc * d.ny + jc) * d.nx;
-    if (I % d.r == 0) return us(b + ic);
+    if ((I & (d.r - 1)) == 0) return us(b + ic);
     return (T)0.5 * (us(b + ic) + us(b + wrap(ic + 1, d.nx)));
   }
   __device__ __forceinline__ T vface(const Dims& d, int I, int J, int K) const {
-    const int ic = I / d.r, kc = K / d.r;
-    const int jc = J / d.ry;
+    const int ic = I >> d.rs, kc = K >> d.rs;
+    const int jc = J >> d.rys;
     const size_t b = (size_t)kc * d.ny * d.nx + ic;
-    if (J % d.ry == 0) return vs(b + (size_t)jc * d.nx);
+    if ((J & (d.ry - 1)) == 0) return vs(b + (size_t)jc * d.nx);
     return (T)0.5 * (vs(b + (size_t)jc * d.nx) + vs(b + (size_t)wrap(jc + 1, d.ny) * d.nx));
   }
   // fine z-face K (0..fnz), K = 0 and fnz are walls
   __device__ __forceinline__ T wface(const Dims& d, int I, int J, int K) const {
-    const int ic = I / d.r, jc = J / d.ry;
+    const int ic = I >> d.rs, jc = J >> d.rys;
     const size_t col = (size_t)jc * d.nx + ic;
     const size_t plane = (size_t)d.ny * d.nx;
-    const int kc = K / d.r;
-    if (K % d.r == 0) return ws(kc * plane + col);
+    const int kc = K >> d.rs;
+    if ((K & (d.r - 1)) == 0) return ws(kc * plane + col);
     return (T)0.5 * (ws(kc * plane + col) + ws((kc + 1) * plane + col));
   }
 };
@@ -151,27 +148,23 @@ struct ChFinish {
 // G = lambda (-(L_N phi + B(g)) + f(phi))  (Eq. NS5 with the wetting ghost)
 template <class T>
 __global__ void k_ch_G(const T* __restrict__ phi, const double* __restrict__ gwall, T* __restrict__ G, Dims d,
-                       Phys p) {
-  const size_t n = (size_t)d.fnx * d.fny * d.fnz;
-  const T ih2 = (T)(1.0 / (d.h * d.h));
-  const T ie2 = (T)(1.0 / (p.eta * p.eta));
-  const T lam = (T)p.lam;
-  for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < n; id += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(id % d.fnx);
-    const int j = (int)((id / d.fnx) % d.fny);
-    const int k = (int)(id / ((size_t)d.fnx * d.fny));
-    const T c0 = phi[id];
-    T lap = phi[fidx(d, wrap(i + 1, d.fnx), j, k)] + phi[fidx(d, wrap(i - 1, d.fnx), j, k)] - 2 * c0;
-    if (d.dim == 3) lap += phi[fidx(d, i, wrap(j + 1, d.fny), k)] + phi[fidx(d, i, wrap(j - 1, d.fny), k)] - 2 * c0;
-    const T zp = (k + 1 < d.fnz) ? phi[fidx(d, i, j, k + 1)] : c0;
-    const T zm = (k > 0) ? phi[fidx(d, i, j, k - 1)] : c0;
-    lap = (lap + zp + zm - 2 * c0) * ih2;
-    double B = 0.0;
-    const size_t col = (size_t)j * d.fnx + i;
-    if (k == 0) B += gwall[col] / d.h;
-    if (k == d.fnz - 1) B += gwall[(size_t)d.fnx * d.fny + col] / d.h;
-    G[id] = lam * (-(lap + (T)B) + c0 * (c0 * c0 - 1) * ie2);
-  }
+                       PhysT<T> q) {
+  RowIdx x;
+  if (!row_index(d.fnx, d.fny, x)) return;
+  const int i = x.i, j = x.j, k = x.k;
+  const size_t id = (size_t)x.row * d.fnx + i;
+  const size_t plane = (size_t)d.fnx * d.fny;
+  const T c0 = phi[id];
+  T lap = phi[id - i + wrap(i + 1, d.fnx)] + phi[id - i + wrap(i - 1, d.fnx)] - 2 * c0;
+  if (d.dim == 3) lap += phi[fidx(d, i, wrap(j + 1, d.fny), k)] + phi[fidx(d, i, wrap(j - 1, d.fny), k)] - 2 * c0;
+  const T zp = (k + 1 < d.fnz) ? phi[id + plane] : c0;
+  const T zm = (k > 0) ? phi[id - plane] : c0;
+  lap = (lap + zp + zm - 2 * c0) * q.ih2;
+  T B = 0;
+  const size_t col = (size_t)j * d.fnx + i;
+  if (k == 0) B += (T)gwall[col] * q.ih;
+  if (k == d.fnz - 1) B += (T)gwall[plane + col] * q.ih;
+  G[id] = q.lam * (-(lap + B) + c0 * (c0 * c0 - 1) * q.ie2);
 }
 
 // Coarse samples of the restricted phi and G (Eq. dual2).
@@ -187,44 +180,49 @@ struct Restricted {
 // Mean of a fine field over x in [x0, x0+nx_), y in [y0, ..), z in [z0, ..);
 // periodic wrap in x, y; mirror ghost (cell -1 -> 0, fnz -> fnz-1) in z.
 template <class T>
-__device__ __forceinline__ double box_mean(const T* a, const Dims& d, int x0, int nxr, int y0, int nyr, int z0,
-                                           int nzr) {
-  double s = 0;
+__device__ __forceinline__ T box_mean(const T* a, const Dims& d, int x0, int nxr, int y0, int nyr, int z0, int nzr,
+                                      T inv) {
+  T s = 0;
   for (int kk = 0; kk < nzr; ++kk) {
     int z = z0 + kk;
     z = z < 0 ? 0 : (z >= d.fnz ? d.fnz - 1 : z);
     for (int jj = 0; jj < nyr; ++jj) {
       const int y = wrap(y0 + jj, d.fny);
-      for (int ii = 0; ii < nxr; ++ii) s += (double)a[fidx(d, wrap(x0 + ii, d.fnx), y, z)];
+      const T* rowp = a + ((size_t)z * d.fny + y) * d.fnx;
+      for (int ii = 0; ii < nxr; ++ii) s += rowp[wrap(x0 + ii, d.fnx)];
     }
   }
-  return s / (double)(nxr * nyr * nzr);
+  return s * inv;
 }
 
+// one thread per coarse (i, j, k), k = 0..nz (the last layer only for z-faces/edges)
 template <class T>
 __global__ void k_restrict(const T* __restrict__ phi, const T* __restrict__ G, Restricted<T> out, Dims d) {
-  const size_t n = (size_t)d.nx * d.ny * (d.nz + 1);
+  RowIdx x;
+  if (!row_index(d.nx, d.ny, x)) return;
+  const int i = x.i, j = x.j, k = x.k;
+  const size_t id = (size_t)x.row * d.nx + i;
   const int r = d.r, ry = d.ry;
-  for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < n; id += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(id % d.nx);
-    const int j = (int)((id / d.nx) % d.ny);
-    const int k = (int)(id / ((size_t)d.nx * d.ny));
-    // z-faces and z-edges exist for k = 0..nz
-    out.phifz[id] = (T)box_mean(phi, d, r * i, r, ry * j, ry, r * k - 1, 2);
-    out.Gfz[id] = (T)box_mean(G, d, r * i, r, ry * j, ry, r * k - 1, 2);
-    out.phiexz[id] = (T)box_mean(phi, d, r * i - 1, 2, ry * j, ry, r * k - 1, 2);
-    if (d.dim == 3) out.phieyz[id] = (T)box_mean(phi, d, r * i, r, ry * j - 1, 2, r * k - 1, 2);
-    if (k == d.nz) continue;
-    out.phic[id] = (T)box_mean(phi, d, r * i, r, ry * j, ry, r * k, r);
-    out.Gc[id] = (T)box_mean(G, d, r * i, r, ry * j, ry, r * k, r);
-    out.phifx[id] = (T)box_mean(phi, d, r * i - 1, 2, ry * j, ry, r * k, r);
-    out.Gfx[id] = (T)box_mean(G, d, r * i - 1, 2, ry * j, ry, r * k, r);
-    if (d.dim == 3) {
-      out.phify[id] = (T)box_mean(phi, d, r * i, r, ry * j - 1, 2, r * k, r);
-      out.Gfy[id] = (T)box_mean(G, d, r * i, r, ry * j - 1, 2, r * k, r);
-      out.phiexy[id] = (T)box_mean(phi, d, r * i - 1, 2, ry * j - 1, 2, r * k, r);
-    }
+  const T i2 = (T)0.5, i4 = (T)0.25;
+  const T irr = (T)1 / (T)(r * ry), irrr = (T)1 / (T)(r * ry * r), i2rr = (T)1 / (T)(2 * r * ry);
+  const T i4r = (T)1 / (T)(4 * (d.dim == 3 ? r : 1));
+  (void)i2; (void)i4;
+  // z-faces and z-edges exist for k = 0..nz
+  out.phifz[id] = box_mean(phi, d, r * i, r, ry * j, ry, r * k - 1, 2, i2rr);
+  out.Gfz[id] = box_mean(G, d, r * i, r, ry * j, ry, r * k - 1, 2, i2rr);
+  out.phiexz[id] = box_mean(phi, d, r * i - 1, 2, ry * j, ry, r * k - 1, 2, (T)1 / (T)(4 * ry));
+  if (d.dim == 3) out.phieyz[id] = box_mean(phi, d, r * i, r, ry * j - 1, 2, r * k - 1, 2, (T)1 / (T)(4 * r));
+  if (k == d.nz) return;
+  out.phic[id] = box_mean(phi, d, r * i, r, ry * j, ry, r * k, r, irrr);
+  out.Gc[id] = box_mean(G, d, r * i, r, ry * j, ry, r * k, r, irrr);
+  out.phifx[id] = box_mean(phi, d, r * i - 1, 2, ry * j, ry, r * k, r, i2rr);
+  out.Gfx[id] = box_mean(G, d, r * i - 1, 2, ry * j, ry, r * k, r, i2rr);
+  if (d.dim == 3) {
+    out.phify[id] = box_mean(phi, d, r * i, r, ry * j - 1, 2, r * k, r, (T)1 / (T)(2 * r * r));
+    out.Gfy[id] = box_mean(G, d, r * i, r, ry * j - 1, 2, r * k, r, (T)1 / (T)(2 * r * r));
+    out.phiexy[id] = box_mean(phi, d, r * i - 1, 2, ry * j - 1, 2, r * k, r, i4r);
   }
+  (void)irr;
 }
 
 }  // namespace pf

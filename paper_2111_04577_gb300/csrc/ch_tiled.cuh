@@ -1,0 +1,243 @@
+// Shared-memory tiled Cahn-Hilliard stencils (fine mesh).
+//
+// k_ch_rhs: one pass from (phi^n, phi^{n-1}, coarse u^n, u^{n-1}) to the
+//   increment-form right side R of the Psi solve (see ch.cuh):
+//     phi* = 2 phi^n - phi^{n-1}                       (Eq. NS32)
+//     mu*  = f(phi*) - (L_N phi* + B(g))               (Eqs. NS6, NS34)
+//     R    = (phi^{n-1} - phi^n)/(M lambda dt) - div(u* phi*)/(M lambda) + L_N mu*
+//   A CTA owns a TX x TY x TZ block of fine cells: phi* is staged with a halo of
+//   2 cells, mu* is formed in shared memory on the block plus one cell, and R
+//   on the block, so mu* never goes to HBM.  g, the contact-angle flux of the
+//   wall columns, is evaluated in FP64 and stored for the chemical potential.
+// k_ch_G_restrict: from phi^{n+1} (and g) to the chemical potential
+//   G = lambda(-(L_N phi + B(g)) + f(phi)) (Eq. NS5) on a fine block with a
+//   one-cell halo in shared memory, then every coarse sample of phi and G that
+//   Eqs. dual2/dual3 need (centres, faces, edges), without writing fine G.
+#pragma once
+#include "ch.cuh"
+
+namespace pf {
+
+__device__ __forceinline__ int pmod(int x, int n) {
+  x %= n;
+  return x < 0 ? x + n : x;
+}
+__device__ __forceinline__ int clampi(int x, int lo, int hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+template <int DIM>
+struct RhsTile {
+  static constexpr int TX = 64, TY = DIM == 3 ? 8 : 1, TZ = DIM == 3 ? 8 : 16;
+  static constexpr int HY = DIM == 3 ? 2 : 0;
+  static constexpr int SX = TX + 4, SY = TY + 2 * HY, SZ = TZ + 4;
+  static constexpr int MX = TX + 2, MY = TY + (DIM == 3 ? 2 : 0), MZ = TZ + 2;
+  static constexpr int NS = SX * SY * SZ, NM = MX * MY * MZ;
+};
+
+template <class T, int DIM>
+__global__ void __launch_bounds__(256) k_ch_rhs(const FineView<T> f, const CoarseVel<T> vel, T* __restrict__ R,
+                                                double* __restrict__ gwall, const Dims d, const Phys p,
+                                                const PhysT<T> q, const T inv_mldt, const T inv_ml) {
+  using TL = RhsTile<DIM>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* ps = reinterpret_cast<T*>(smraw);  // phi*, [SZ][SY][SX]
+  T* ms = ps + TL::NS;                  // mu*,  [MZ][MY][MX]
+  const int x0 = blockIdx.x * TL::TX, y0 = blockIdx.y * TL::TY, z0 = blockIdx.z * TL::TZ;
+  const int fnx = d.fnx, fny = d.fny, fnz = d.fnz;
+  const size_t plane = (size_t)fnx * fny;
+  // ---- stage phi* with a 2-cell halo (x, y periodic; z clamped, never read past a wall) ----
+  {
+    const float isx = 1.0f / TL::SX, isy = 1.0f / TL::SY;
+    for (int e = threadIdx.x; e < TL::NS; e += blockDim.x) {
+      const int zz = qdiv(e, TL::SX * TL::SY, isx * isy);
+      const int rem = e - zz * TL::SX * TL::SY;
+      const int yy = qdiv(rem, TL::SX, isx), xx = rem - yy * TL::SX;
+      const int gx = pmod(x0 - 2 + xx, fnx);
+      const int gy = DIM == 3 ? pmod(y0 - TL::HY + yy, fny) : 0;
+      const int gz = clampi(z0 - 2 + zz, 0, fnz - 1);
+      const size_t o = (size_t)gz * plane + (size_t)gy * fnx + gx;
+      ps[e] = (T)2 * f.pn[o] - f.po[o];
+    }
+  }
+  __syncthreads();
+  auto P = [&](int sz, int sy, int sx) -> T { return ps[(sz * TL::SY + sy) * TL::SX + sx]; };
+  // ---- mu* on the block plus one cell ----
+  {
+    const float imx = 1.0f / TL::MX, imy = 1.0f / TL::MY;
+    for (int e = threadIdx.x; e < TL::NM; e += blockDim.x) {
+      const int mz = qdiv(e, TL::MX * TL::MY, imx * imy);
+      const int rem = e - mz * TL::MX * TL::MY;
+      const int my = qdiv(rem, TL::MX, imx), mx = rem - my * TL::MX;
+      const int gz = z0 - 1 + mz;
+      if (gz < 0 || gz >= fnz) {
+        ms[e] = (T)0;
+        continue;
+      }
+      const int sx = mx + 1, sy = my + (DIM == 3 ? 1 : 0), sz = mz + 1;
+      const T c0 = P(sz, sy, sx);
+      T lap = P(sz, sy, sx + 1) + P(sz, sy, sx - 1) - 2 * c0;
+      if (DIM == 3) lap += P(sz, sy + 1, sx) + P(sz, sy - 1, sx) - 2 * c0;
+      const T czp = gz + 1 < fnz ? P(sz + 1, sy, sx) : c0;
+      const T czm = gz > 0 ? P(sz - 1, sy, sx) : c0;
+      lap = (lap + czp + czm - 2 * c0) * q.ih2;
+      T B = 0;
+      const bool own = mx >= 1 && mx <= TL::TX && (DIM == 2 || (my >= 1 && my <= TL::TY));
+      const int gx = x0 - 1 + mx, gy = DIM == 3 ? y0 - 1 + my : 0;
+      if (gz == 0) {
+        const double g = wall_g(p.cos_bot, (double)c0, (double)czp, p.eta);
+        if (own && gx < fnx && gy < fny) gwall[(size_t)gy * fnx + gx] = g;
+        B += (T)(g / d.h);
+      }
+      if (gz == fnz - 1) {
+        const double g = wall_g(p.cos_top, (double)c0, (double)czm, p.eta);
+        if (own && gx < fnx && gy < fny) gwall[plane + (size_t)gy * fnx + gx] = g;
+        B += (T)(g / d.h);
+      }
+      ms[e] = c0 * (c0 * c0 - 1) * q.ie2 - (lap + B);
+    }
+  }
+  __syncthreads();
+  auto M = [&](int mz, int my, int mx) -> T { return ms[(mz * TL::MY + my) * TL::MX + mx]; };
+  // ---- R on the block ----
+  const float itx = 1.0f / TL::TX, ity = 1.0f / TL::TY;
+  for (int e = threadIdx.x; e < TL::TX * TL::TY * TL::TZ; e += blockDim.x) {
+    const int tz = qdiv(e, TL::TX * TL::TY, itx * ity);
+    const int rem = e - tz * TL::TX * TL::TY;
+    const int ty = qdiv(rem, TL::TX, itx), tx = rem - ty * TL::TX;
+    const int gx = x0 + tx, gy = y0 + ty, gz = z0 + tz;
+    if (gx >= fnx || gy >= fny || gz >= fnz) continue;
+    const int sx = tx + 2, sy = ty + TL::HY, sz = tz + 2;
+    const T c0 = P(sz, sy, sx);
+    const int gxp = gx + 1 == fnx ? 0 : gx + 1;
+    T adv = vel.uface(d, gxp, gy, gz) * (c0 + P(sz, sy, sx + 1)) - vel.uface(d, gx, gy, gz) * (P(sz, sy, sx - 1) + c0);
+    if (DIM == 3) {
+      const int gyp = gy + 1 == fny ? 0 : gy + 1;
+      adv += vel.vface(d, gx, gyp, gz) * (c0 + P(sz, sy + 1, sx)) - vel.vface(d, gx, gy, gz) * (P(sz, sy - 1, sx) + c0);
+    }
+    if (gz + 1 < fnz) adv += vel.wface(d, gx, gy, gz + 1) * (c0 + P(sz + 1, sy, sx));
+    if (gz > 0) adv -= vel.wface(d, gx, gy, gz) * (P(sz - 1, sy, sx) + c0);
+    adv *= (T)0.5 * q.ih;
+    const int mx = tx + 1, my = ty + (DIM == 3 ? 1 : 0), mz = tz + 1;
+    const T m0 = M(mz, my, mx);
+    T lap = M(mz, my, mx + 1) + M(mz, my, mx - 1) - 2 * m0;
+    if (DIM == 3) lap += M(mz, my + 1, mx) + M(mz, my - 1, mx) - 2 * m0;
+    const T mzp = gz + 1 < fnz ? M(mz + 1, my, mx) : m0;
+    const T mzm = gz > 0 ? M(mz - 1, my, mx) : m0;
+    lap = (lap + mzp + mzm - 2 * m0) * q.ih2;
+    const size_t o = (size_t)gz * plane + (size_t)gy * fnx + gx;
+    R[o] = (f.po[o] - f.pn[o]) * inv_mldt - adv * inv_ml + lap;
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <int DIM>
+struct GrTile {
+  // coarse block; the fine block is r times larger plus a halo
+  static constexpr int CX = DIM == 3 ? 16 : 64, CY = DIM == 3 ? 4 : 1, CZ = 4;
+};
+
+template <class T, int DIM>
+__global__ void __launch_bounds__(256) k_ch_G_restrict(const T* __restrict__ phi, const double* __restrict__ gwall,
+                                                       Restricted<T> out, const Dims d, const PhysT<T> q) {
+  using TL = GrTile<DIM>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int r = d.r, ry = d.ry;
+  // fine G block: x in [r*cx0 - 1, r*(cx0+CX)), likewise y (3D) and z
+  const int GX = r * TL::CX + 1, GY = DIM == 3 ? ry * TL::CY + 1 : 1, GZ = r * TL::CZ + 1;
+  const int PX = GX + 2, PY = DIM == 3 ? GY + 2 : 1, PZ = GZ + 2;  // phi block with one more cell each side
+  T* ph = reinterpret_cast<T*>(smraw);  // [PZ][PY][PX]
+  T* gs = ph + PX * PY * PZ;            // [GZ][GY][GX]
+  const int cx0 = blockIdx.x * TL::CX, cy0 = blockIdx.y * TL::CY, cz0 = blockIdx.z * TL::CZ;
+  const int fnx = d.fnx, fny = d.fny, fnz = d.fnz;
+  const size_t plane = (size_t)fnx * fny;
+  const int fx0 = r * cx0 - 1, fy0 = DIM == 3 ? ry * cy0 - 1 : 0, fz0 = r * cz0 - 1;  // origin of the G block
+  {
+    const int n = PX * PY * PZ;
+    const float ipx = 1.0f / PX, ipy = 1.0f / PY;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const int zz = qdiv(e, PX * PY, ipx * ipy);
+      const int rem = e - zz * PX * PY;
+      const int yy = qdiv(rem, PX, ipx), xx = rem - yy * PX;
+      const int gx = pmod(fx0 - 1 + xx, fnx);
+      const int gy = DIM == 3 ? pmod(fy0 - 1 + yy, fny) : 0;
+      const int gz = clampi(fz0 - 1 + zz, 0, fnz - 1);
+      ph[e] = phi[(size_t)gz * plane + (size_t)gy * fnx + gx];
+    }
+  }
+  __syncthreads();
+  auto PH = [&](int z, int y, int x) -> T { return ph[(z * PY + y) * PX + x]; };
+  {
+    const int n = GX * GY * GZ;
+    const float igx = 1.0f / GX, igy = 1.0f / GY;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      const int gzl = qdiv(e, GX * GY, igx * igy);
+      const int rem = e - gzl * GX * GY;
+      const int gyl = qdiv(rem, GX, igx), gxl = rem - gyl * GX;
+      // the real fine cell this sample stands for (mirror ghost in z)
+      const int gz = clampi(fz0 + gzl, 0, fnz - 1);
+      const int pz = gz - (fz0 - 1);  // index in the phi block
+      const int py = DIM == 3 ? gyl + 1 : 0, px = gxl + 1;
+      const T c0 = PH(pz, py, px);
+      T lap = PH(pz, py, px + 1) + PH(pz, py, px - 1) - 2 * c0;
+      if (DIM == 3) lap += PH(pz, py + 1, px) + PH(pz, py - 1, px) - 2 * c0;
+      const T czp = gz + 1 < fnz ? PH(pz + 1, py, px) : c0;
+      const T czm = gz > 0 ? PH(pz - 1, py, px) : c0;
+      lap = (lap + czp + czm - 2 * c0) * q.ih2;
+      T B = 0;
+      if (gz == 0 || gz == fnz - 1) {
+        const int gx = pmod(fx0 + gxl, fnx), gy = DIM == 3 ? pmod(fy0 + gyl, fny) : 0;
+        const size_t col = (size_t)gy * fnx + gx;
+        if (gz == 0) B += (T)gwall[col] * q.ih;
+        if (gz == fnz - 1) B += (T)gwall[plane + col] * q.ih;
+      }
+      gs[e] = q.lam * (-(lap + B) + c0 * (c0 * c0 - 1) * q.ie2);
+    }
+  }
+  __syncthreads();
+  // phi at the same fine samples as G: block origin shift of one cell
+  auto PHs = [&](int z, int y, int x) -> T {  // (z, y, x) in G-block coordinates, z mirrored
+    const int gz = clampi(fz0 + z, 0, fnz - 1);
+    return PH(gz - (fz0 - 1), DIM == 3 ? y + 1 : 0, x + 1);
+  };
+  auto GS = [&](int z, int y, int x) -> T {
+    const int gz = clampi(fz0 + z, 0, fnz - 1);
+    return gs[((gz - fz0) * GY + y) * GX + x];
+  };
+  // one thread per coarse cell of the block (and the top z-face layer)
+  const int ncell = TL::CX * TL::CY * (TL::CZ + 1);
+  const float icx = 1.0f / TL::CX, icy = 1.0f / TL::CY;
+  for (int e = threadIdx.x; e < ncell; e += blockDim.x) {
+    const int lz = qdiv(e, TL::CX * TL::CY, icx * icy);
+    const int rem = e - lz * TL::CX * TL::CY;
+    const int ly = qdiv(rem, TL::CX, icx), lx = rem - ly * TL::CX;
+    const int i = cx0 + lx, j = cy0 + ly, k = cz0 + lz;
+    if (i >= d.nx || j >= d.ny || k > d.nz) continue;
+    if (lz == TL::CZ && k != d.nz) continue;  // the extra layer only for the top wall face
+    const size_t id = ((size_t)k * d.ny + j) * d.nx + i;
+    // block-local fine coordinates of this coarse cell's first fine cell (+1 for the halo)
+    const int bx = r * lx + 1, by = DIM == 3 ? ry * ly + 1 : 0, bz = r * lz + 1;
+    auto mean = [&](auto&& F, int xa, int nxr, int ya, int nyr, int za, int nzr) -> T {
+      T s = 0;
+      for (int zz = 0; zz < nzr; ++zz)
+        for (int yy = 0; yy < nyr; ++yy)
+          for (int xx = 0; xx < nxr; ++xx) s += F(za + zz, ya + yy, xa + xx);
+      return s / (T)(nxr * nyr * nzr);
+    };
+    // z-faces and z-edges: fine z cells (r k - 1, r k)
+    out.phifz[id] = mean(PHs, bx, r, by, ry, bz - 1, 2);
+    out.Gfz[id] = mean(GS, bx, r, by, ry, bz - 1, 2);
+    out.phiexz[id] = mean(PHs, bx - 1, 2, by, ry, bz - 1, 2);
+    if (DIM == 3) out.phieyz[id] = mean(PHs, bx, r, by - 1, 2, bz - 1, 2);
+    if (k == d.nz) continue;
+    out.phic[id] = mean(PHs, bx, r, by, ry, bz, r);
+    out.Gc[id] = mean(GS, bx, r, by, ry, bz, r);
+    out.phifx[id] = mean(PHs, bx - 1, 2, by, ry, bz, r);
+    out.Gfx[id] = mean(GS, bx - 1, 2, by, ry, bz, r);
+    if (DIM == 3) {
+      out.phify[id] = mean(PHs, bx, r, by - 1, 2, bz, r);
+      out.Gfy[id] = mean(GS, bx, r, by - 1, 2, bz, r);
+      out.phiexy[id] = mean(PHs, bx - 1, 2, by - 1, 2, bz, r);
+    }
+  }
+}
+
+}  // namespace pf

@@ -46,6 +46,7 @@ __host__ __device__ __forceinline__ cpx<T> mul_si(cpx<T> a, int sign) {
 struct Dims {
   int nx, ny, nz;      // coarse cells
   int r, ry;           // refinement in x/z and in y (ry = 1 in 2D)
+  int rs, rys;         // log2(r), log2(ry)
   int fnx, fny, fnz;   // fine cells
   int dim;             // 2 or 3
   double dx, h;        // coarse and fine spacing
@@ -60,6 +61,44 @@ struct Phys {
   double uw_bot, uw_top, gx, gy, gz;
   int visco;
 };
+
+// Scheme constants converted once to the arithmetic type of the kernels, so
+// that no FP64 operation is issued per cell on the FP32 path.
+template <class T>
+struct PhysT {
+  T idt, irho0, inum, num;            // 1/dt, 1/rho0, 1/nu_m, nu_m
+  T rho1, rho2, mu_s1, mu_s2;
+  T uw2_bot, uw2_top;                 // 2 u_w (no-slip ghost)
+  T cj_dx;                            // -(rho1 - rho2)/2 M / dx  (J per unit G difference)
+  T gx, gy, gz;
+  T ih, ih2, iD, iD2;                 // fine and coarse inverse spacings
+  T ie2, lam;                         // 1/eta^2, lambda
+  T dt, ilh, wtau;                    // dt, 1/lambda_H, mu_p/lambda_H
+};
+
+// Kernels over rows of a mesh use a 2D grid: blockIdx.x = row (y, z pair),
+// blockIdx.y * blockDim.x + threadIdx.x = x.  No 64-bit index division.
+struct RowIdx {
+  int i, j, k, row;
+};
+__device__ __forceinline__ bool row_index(int nxrow, int nyrow, RowIdx& r) {
+  r.row = blockIdx.x;
+  r.i = blockIdx.y * blockDim.x + threadIdx.x;
+  if (r.i >= nxrow) return false;
+  r.k = r.row / nyrow;
+  r.j = r.row - r.k * nyrow;
+  return true;
+}
+
+// Exact quotient of 0 <= x < 2^22 by 1 <= d using a float reciprocal (one
+// correction step); avoids the long integer-division sequence in index math.
+__device__ __forceinline__ int qdiv(int x, int d, float invd) {
+  int q = __float2int_rz((float)x * invd);
+  const int r = x - q * d;
+  if (r < 0) --q;
+  else if (r >= d) ++q;
+  return q;
+}
 
 // fine index helpers (x fastest)
 __host__ __device__ __forceinline__ size_t fidx(const Dims& d, int i, int j, int k) {
@@ -76,7 +115,8 @@ __host__ __device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + 
 struct FftPlan {
   int n;
   int ns;
-  int radix[24];
+  unsigned long long code;  // radix of stage s in bits [3s, 3s+3)
+  __host__ __device__ __forceinline__ int radix(int s) const { return (int)((code >> (3 * s)) & 7ull); }
 };
 
 }  // namespace pf

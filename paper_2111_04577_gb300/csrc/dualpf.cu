@@ -19,7 +19,9 @@
 
 #include "../../include/dualpf.h"
 #include "ch.cuh"
+#include "ch_tiled.cuh"
 #include "ns.cuh"
+#include "ns_rhs.cuh"
 #include "polymer.cuh"
 #include "reduce.cuh"
 #include "spectral.cuh"
@@ -47,9 +49,10 @@ static FftPlan make_plan(int n) {
   while (m % 2 == 0) { r.push_back(2); m /= 2; }
   for (int p : {3, 5, 7})
     while (m % p == 0) { r.push_back(p); m /= p; }
-  if (m != 1 || r.size() > 24) throw ApiError(PF_ERR_UNSUPPORTED, "FFT length " + std::to_string(n) + " is not 2^a 3^b 5^c 7^d");
+  if (m != 1 || r.size() > 21) throw ApiError(PF_ERR_UNSUPPORTED, "FFT length " + std::to_string(n) + " is not 2^a 3^b 5^c 7^d");
   pl.ns = (int)r.size();
-  for (size_t i = 0; i < r.size(); ++i) pl.radix[i] = r[i];
+  pl.code = 0;
+  for (size_t i = 0; i < r.size(); ++i) pl.code |= (unsigned long long)r[i] << (3 * i);
   return pl;
 }
 
@@ -82,6 +85,13 @@ struct Arena {
 template <class T>
 struct ArrPro {
   static constexpr const char* name = "rfft_x_coarse";
+  const T* a;
+  int n;
+  __device__ __forceinline__ T operator()(int line, int x) const { return a[(size_t)line * n + x]; }
+};
+template <class T>
+struct FineArrPro {
+  static constexpr const char* name = "rfft_x_fine";
   const T* a;
   int n;
   __device__ __forceinline__ T operator()(int line, int x) const { return a[(size_t)line * n + x]; }
@@ -156,6 +166,7 @@ struct Impl : ImplBase {
   pf_grid_desc g;
   Dims d{};
   Phys p{};
+  PhysT<T> q{};
   double sigma = 1.0;
   bool have_params = false;
   cudaStream_t st;
@@ -204,6 +215,8 @@ struct Impl : ImplBase {
     d.dim = g.ny == 1 ? 2 : 3;
     d.r = g.dual ? 2 : 1;
     d.ry = d.dim == 3 ? d.r : 1;
+    d.rs = d.r == 2 ? 1 : 0;
+    d.rys = d.ry == 2 ? 1 : 0;
     d.fnx = d.r * g.nx;
     d.fny = d.ry * g.ny;
     d.fnz = d.r * g.nz;
@@ -302,15 +315,27 @@ struct Impl : ImplBase {
     PF_CUDA_TRY(cudaFuncSetAttribute(k_zsolve<T, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_rfft_x<T, ChRhs<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_rfft_x<T, ArrPro<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PF_CUDA_TRY(cudaFuncSetAttribute(k_rfft_x<T, FineArrPro<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_irfft_x<T, ChFinish<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_irfft_x<T, ArrEpi<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
   }
 
   // ------------------------------------------------------------------ launches
-  static int blocks_for(size_t n, int bs = 256) {
-    size_t b = (n + bs - 1) / bs;
-    const size_t cap = 152 * 16;
-    return (int)(b < cap ? (b == 0 ? 1 : b) : cap);
+  // row grids: blockIdx.x = row, (blockIdx.y, threadIdx.x) = x
+  struct RowLaunch {
+    dim3 grid, block;
+  };
+  static RowLaunch rows(int nrows, int nxrow, int maxbs = 256) {
+    int bs = ((nxrow + 31) / 32) * 32;
+    if (bs > maxbs) bs = maxbs;
+    RowLaunch r;
+    r.block = dim3(bs);
+    r.grid = dim3(nrows, (nxrow + bs - 1) / bs);
+    return r;
   }
   template <class Pro>
   void rfft_x(Pro pro, cpx<T>* out, int n, int nlines, int pitch, const FftPlan& pl, const cpx<T>* tw) {
@@ -352,11 +377,11 @@ struct Impl : ImplBase {
     zs.shift1 = s1;
     zs.shift2 = s2;
     zs.scale = scale;
-    const int tx = 16;
-    const size_t sm = (size_t)rows * tx * sizeof(TC) * (zs.same ? 3 : 4);
+    const int tx = sizeof(T) == 4 ? 32 : 16;
+    const size_t sm = (size_t)rows * tx * (sizeof(cpx<T>) + sizeof(TC) * (zs.same ? 1 : 2));
     dim3 grid((ncol + tx - 1) / tx, ny);
     mark(two ? "zsolve_pair" : "zsolve");
-    k_zsolve<T, TC><<<grid, 2 * tx, sm, st>>>(data, ex, ey, zs, tx);
+    k_zsolve<T, TC><<<grid, 256, sm, st>>>(data, ex, ey, zs, tx);
     if (poisson) {
       mark("zero_mode");
       k_zero_mode<T><<<1, 32, 0, st>>>(data, rows, ny, pitch, h2, scale, zwork);
@@ -376,65 +401,73 @@ struct Impl : ImplBase {
 
   void launch_step(int flags) {
     const int po = pc ^ 1, fo = fc ^ 1;
-    const int nb = 256;
     const size_t nf = (size_t)d.fnx * d.fny * d.fnz;
     // ---- Cahn-Hilliard on the fine mesh ----
     FineView<T> fv{phi[pc], phi[po]};
-    mark("ch_mu");
-    k_ch_mu<T><<<blocks_for(nf), nb, 0, st>>>(fv, mu, gwall, d, p);
-    ChRhs<T> rhs;
-    rhs.f = fv;
-    rhs.mu = mu;
-    rhs.vel = CoarseVel<T>{u[fc], u[fo], v[fc], v[fo], w[fc], w[fo]};
-    rhs.d = d;
-    rhs.inv_mldt = (T)(1.0 / (p.Ml * p.dt));
-    rhs.inv_ml = (T)(1.0 / p.Ml);
-    rhs.ih = (T)(1.0 / d.h);
-    rhs.ih2 = (T)(1.0 / (d.h * d.h));
+    const CoarseVel<T> vel{u[fc], u[fo], v[fc], v[fo], w[fc], w[fo]};
+    const T inv_mldt = (T)(1.0 / (p.Ml * p.dt)), inv_ml = (T)(1.0 / p.Ml);
+    mark("ch_rhs");
+    if (d.dim == 2) {
+      using TL = RhsTile<2>;
+      dim3 grid((d.fnx + TL::TX - 1) / TL::TX, 1, (d.fnz + TL::TZ - 1) / TL::TZ);
+      k_ch_rhs<T, 2><<<grid, 256, (TL::NS + TL::NM) * sizeof(T), st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml);
+    } else {
+      using TL = RhsTile<3>;
+      dim3 grid((d.fnx + TL::TX - 1) / TL::TX, (d.fny + TL::TY - 1) / TL::TY, (d.fnz + TL::TZ - 1) / TL::TZ);
+      k_ch_rhs<T, 3><<<grid, 256, (TL::NS + TL::NM) * sizeof(T), st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml);
+    }
     const int nlf = d.fny * d.fnz;
-    rfft_x(rhs, spF, d.fnx, nlf, pF, plFx, twFx);
+    rfft_x(FineArrPro<T>{mu, d.fnx}, spF, d.fnx, nlf, pF, plFx, twFx);
     if (d.dim == 3) fft_y(spF, d.fny, pF, d.fnx / 2 + 1, d.fnz, plFy, twFy, -1);
     zsolve(spF, d.fnz, d.fny, pF, d.fnx / 2 + 1, eFx, eFy, Z_NEUMANN, d.h * d.h, p.c, -p.alpha, true,
            1.0 / ((double)d.fnx * d.fny), false);
     if (d.dim == 3) fft_y(spF, d.fny, pF, d.fnx / 2 + 1, d.fnz, plFy, twFy, +1);
     irfft_x(spF, ChFinish<T>{phi[pc], phi[po], d.fnx}, d.fnx, nlf, pF, plFx, twFx, (T)1);
-    mark("ch_G");
-    k_ch_G<T><<<blocks_for(nf), nb, 0, st>>>(phi[po], gwall, G, d, p);
     if (flags & PF_STEP_CH_ONLY) return;
-    // ---- restriction to the coarse mesh ----
-    const size_t ncw = (size_t)d.nx * d.ny * (d.nz + 1);
-    const size_t nc = (size_t)d.nx * d.ny * d.nz;
-    mark("restrict");
-    k_restrict<T><<<blocks_for(ncw), nb, 0, st>>>(phi[po], G, rs, d);
-    // ---- Navier-Stokes ----
-    NsAcc<T> A;
-    A.a.un = u[fc];
-    A.a.uo = u[fo];
-    A.a.vn = v[fc];
-    A.a.vo = v[fo];
-    A.a.wn = w[fc];
-    A.a.wo = w[fo];
-    A.a.pn = pr[fc];
-    A.a.po = pr[fo];
-    for (int c = 0; c < 6; ++c) {
-      A.a.tn[c] = tau[fc][c];
-      A.a.to[c] = tau[fo][c];
+    // ---- chemical potential and restriction to the coarse mesh ----
+    mark("ch_G_restrict");
+    if (d.dim == 2) {
+      using TL = GrTile<2>;
+      const size_t sm = ((size_t)(d.r * TL::CX + 3) * 1 * (d.r * TL::CZ + 3) + (size_t)(d.r * TL::CX + 1) * 1 * (d.r * TL::CZ + 1)) * sizeof(T);
+      dim3 grid((d.nx + TL::CX - 1) / TL::CX, 1, (d.nz + TL::CZ - 1) / TL::CZ);
+      k_ch_G_restrict<T, 2><<<grid, 256, sm, st>>>(phi[po], gwall, rs, d, q);
+    } else {
+      using TL = GrTile<3>;
+      const size_t sm = ((size_t)(d.r * TL::CX + 3) * (d.ry * TL::CY + 3) * (d.r * TL::CZ + 3) +
+                         (size_t)(d.r * TL::CX + 1) * (d.ry * TL::CY + 1) * (d.r * TL::CZ + 1)) * sizeof(T);
+      dim3 grid((d.nx + TL::CX - 1) / TL::CX, (d.ny + TL::CY - 1) / TL::CY, (d.nz + TL::CZ - 1) / TL::CZ);
+      k_ch_G_restrict<T, 3><<<grid, 256, sm, st>>>(phi[po], gwall, rs, d, q);
     }
-    A.a.rs = rs;
-    A.d = d;
-    A.p = p;
+    const RowLaunch lw = rows(d.ny * (d.nz + 1), d.nx);
+    const RowLaunch lc = rows(d.ny * d.nz, d.nx);
+    // ---- Navier-Stokes ----
+    NsIn<T> A;
+    A.un = u[fc];
+    A.uo = u[fo];
+    A.vn = v[fc];
+    A.vo = v[fo];
+    A.wn = w[fc];
+    A.wo = w[fo];
+    A.pn = pr[fc];
+    A.po = pr[fo];
+    for (int c = 0; c < 6; ++c) {
+      A.tn[c] = tau[fc][c];
+      A.to[c] = tau[fo][c];
+    }
+    A.rs = rs;
     mark("ns_rhs");
-    k_ns_rhs<T><<<blocks_for(nc), nb, 0, st>>>(A, ru, rv, rw, p.visco);
+    if (d.dim == 2) k_ns_rhs_v2<T, 2><<<lc.grid, lc.block, 0, st>>>(A, d, q, ru, rv, rw, p.visco);
+    else k_ns_rhs_v2<T, 3><<<lc.grid, lc.block, 0, st>>>(A, d, q, ru, rv, rw, p.visco);
     const double kk = p.gamma0 / (p.dt * p.nu_m);
     // u~, v~ land in the n-1 buffers (free once the right sides exist)
     coarse_solve(ru, u[fo], spU, d.nz, Z_DIRICH, kk, false);
     if (d.dim == 3) coarse_solve(rv, v[fo], spV, d.nz, Z_DIRICH, kk, false);
     coarse_solve(rw, wt, spW, d.nz - 1, Z_FACES, kk, false);
     mark("div");
-    k_div<T><<<blocks_for(nc), nb, 0, st>>>(u[fo], v[fo], wt, dv, d, (T)(p.gamma0 * p.rho0 / p.dt));
+    k_div<T><<<lc.grid, lc.block, 0, st>>>(u[fo], v[fo], wt, dv, d, (T)(p.gamma0 * p.rho0 / p.dt));
     coarse_solve(dv, pp, spP, d.nz, Z_NEUMANN, 0.0, true);
     mark("correct");
-    k_correct<T><<<blocks_for(ncw), nb, 0, st>>>(u[fo], v[fo], wt, w[fo], pp, pr[fc], pr[fo], d,
+    k_correct<T><<<lw.grid, lw.block, 0, st>>>(u[fo], v[fo], wt, w[fo], pp, pr[fc], pr[fo], d,
                                                   (T)(p.dt / (p.gamma0 * p.rho0)));
     // ---- polymer ----
     if (p.visco) {
@@ -448,8 +481,9 @@ struct Impl : ImplBase {
         P.out[c] = theta1[c];
       }
       mark("polymer_stage1");
-      if (d.dim == 2) k_polymer<T, 2><<<blocks_for(nc), 128, 0, st>>>(P, d, p, 1);
-      else k_polymer<T, 3><<<blocks_for(nc), 128, 0, st>>>(P, d, p, 1);
+      const RowLaunch lp = rows(d.ny * d.nz, d.nx, 128);
+      if (d.dim == 2) k_polymer<T, 2><<<lp.grid, lp.block, 0, st>>>(P, d, q, 1);
+      else k_polymer<T, 3><<<lp.grid, lp.block, 0, st>>>(P, d, q, 1);
       for (int c = 0; c < ncomp; ++c) {
         P.th[c] = theta1[c];
         P.base[c] = theta[c];
@@ -457,15 +491,38 @@ struct Impl : ImplBase {
         P.tau[c] = tau[fo][c];
       }
       mark("polymer_stage2");
-      if (d.dim == 2) k_polymer<T, 2><<<blocks_for(nc), 128, 0, st>>>(P, d, p, 2);
-      else k_polymer<T, 3><<<blocks_for(nc), 128, 0, st>>>(P, d, p, 2);
+      if (d.dim == 2) k_polymer<T, 2><<<lp.grid, lp.block, 0, st>>>(P, d, q, 2);
+      else k_polymer<T, 3><<<lp.grid, lp.block, 0, st>>>(P, d, q, 2);
     }
   }
 
   // ------------------------------------------------------------------ API
-  void set_params(const pf_params& q) override {
-    p = derive(q, g);
-    sigma = q.sigma;
+  void set_params(const pf_params& prm) override {
+    p = derive(prm, g);
+    sigma = prm.sigma;
+    q.idt = (T)(1.0 / p.dt);
+    q.irho0 = (T)(1.0 / p.rho0);
+    q.inum = (T)(1.0 / p.nu_m);
+    q.num = (T)p.nu_m;
+    q.rho1 = (T)p.rho1;
+    q.rho2 = (T)p.rho2;
+    q.mu_s1 = (T)p.mu_s1;
+    q.mu_s2 = (T)p.mu_s2;
+    q.uw2_bot = (T)(2 * p.uw_bot);
+    q.uw2_top = (T)(2 * p.uw_top);
+    q.cj_dx = (T)(-0.5 * (p.rho1 - p.rho2) * p.mob / d.dx);
+    q.gx = (T)p.gx;
+    q.gy = (T)p.gy;
+    q.gz = (T)p.gz;
+    q.ih = (T)(1.0 / d.h);
+    q.ih2 = (T)(1.0 / (d.h * d.h));
+    q.iD = (T)(1.0 / d.dx);
+    q.iD2 = (T)(1.0 / (d.dx * d.dx));
+    q.ie2 = (T)(1.0 / (p.eta * p.eta));
+    q.lam = (T)p.lam;
+    q.dt = (T)p.dt;
+    q.ilh = p.visco ? (T)(1.0 / p.lam_h) : (T)0;
+    q.wtau = p.visco ? (T)(p.mu_p1 / p.lam_h) : (T)0;
     have_params = true;
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
     graphs.clear();
@@ -538,6 +595,11 @@ struct Impl : ImplBase {
   void get_field(int f, void* dst, size_t bytes, int on_dev) override {
     size_t cnt, eb;
     field_info(f, &cnt, &eb);
+    if (f == PF_G) {  // chemical potential of phi^n, formed on request
+      const RowLaunch lf = rows(d.fny * d.fnz, d.fnx);
+      k_ch_G<T><<<lf.grid, lf.block, 0, st>>>(phi[pc], gwall, G, d, q);
+      check_launch();
+    }
     if (bytes != cnt * eb) throw ApiError(PF_ERR_ARG, "byte count does not match the field size");
     auto ptrs = field_ptrs(f);
     const size_t per = cnt / ptrs.size();

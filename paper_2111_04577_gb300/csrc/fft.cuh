@@ -87,16 +87,17 @@ __device__ void fft_stage(const cpx<T>* __restrict__ in, cpx<T>* __restrict__ ou
   const int M = n / (L * P);
   const int nbf = n / P;
   const int total = nbf * nl;
+  const float iM = 1.0f / (float)M, inbf = 1.0f / (float)nbf, inl = 1.0f / (float)nl;
   for (int id = tid; id < total; id += nth) {
     int l, bf;
     if (es == 1) {
-      bf = id % nbf;
-      l = id / nbf;
+      l = qdiv(id, nbf, inbf);
+      bf = id - l * nbf;
     } else {
-      l = id % nl;
-      bf = id / nl;
+      bf = qdiv(id, nl, inl);
+      l = id - bf * nl;
     }
-    const int j = bf / M, k = bf - (bf / M) * M;
+    const int j = qdiv(bf, M, iM), k = bf - j * M;
     const cpx<T>* src = in + (size_t)l * ls;
     cpx<T>* dst = out + (size_t)l * ls;
     cpx<T> z[P];
@@ -126,7 +127,7 @@ __device__ cpx<T>* fft_lines(cpx<T>* a, cpx<T>* b, const FftPlan& pl, const cpx<
   cpx<T>* in = a;
   cpx<T>* out = b;
   for (int s = 0; s < pl.ns; ++s) {
-    const int p = pl.radix[s];
+    const int p = pl.radix(s);
     switch (p) {
       case 2: fft_stage<T, 2>(in, out, pl.n, L, tw, sign, nl, es, ls, tid, nth); break;
       case 3: fft_stage<T, 3>(in, out, pl.n, L, tw, sign, nl, es, ls, tid, nth); break;

@@ -105,21 +105,21 @@ __device__ __forceinline__ int comp_of(int a, int b) {
 }
 
 template <class T, int N>
-__global__ void k_polymer(PolyIn<T> P, Dims d, Phys p, int stage) {
+__global__ void k_polymer(PolyIn<T> P, Dims d, PhysT<T> q, int stage) {
   const size_t plane = (size_t)d.nx * d.ny;
-  const size_t n = plane * d.nz;
-  const T iD = (T)(1.0 / d.dx);
-  const T dt = (T)p.dt, ilh = (T)(1.0 / p.lam_h);
+  const T iD = q.iD;
+  const T dt = q.dt, ilh = q.ilh;
   constexpr int NC = N == 2 ? 3 : 6;
-  for (size_t id = blockIdx.x * (size_t)blockDim.x + threadIdx.x; id < n; id += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(id % d.nx);
-    const int j = (int)((id / d.nx) % d.ny);
-    const int k = (int)(id / plane);
+  RowIdx x;
+  if (!row_index(d.nx, d.ny, x)) return;
+  {
+    const int i = x.i, j = x.j, k = x.k;
+    const size_t id = (size_t)x.row * d.nx + i;
     auto C = [&](int ii, int jj, int kk) { return ((size_t)kk * d.ny + wrap(jj, d.ny)) * d.nx + wrap(ii, d.nx); };
     // velocity gradient L[a][b] = du_a/dx_b (Eq. NS23 uses its transpose convention)
     auto uc = [&](int ii, int jj, int kk) -> T {  // centre-averaged u, ghosts at walls
-      if (kk < 0) return (T)(2 * p.uw_bot) - (T)0.5 * (P.u[C(ii, jj, 0)] + P.u[C(ii + 1, jj, 0)]);
-      if (kk >= d.nz) return (T)(2 * p.uw_top) - (T)0.5 * (P.u[C(ii, jj, d.nz - 1)] + P.u[C(ii + 1, jj, d.nz - 1)]);
+      if (kk < 0) return q.uw2_bot - (T)0.5 * (P.u[C(ii, jj, 0)] + P.u[C(ii + 1, jj, 0)]);
+      if (kk >= d.nz) return q.uw2_top - (T)0.5 * (P.u[C(ii, jj, d.nz - 1)] + P.u[C(ii + 1, jj, d.nz - 1)]);
       return (T)0.5 * (P.u[C(ii, jj, kk)] + P.u[C(ii + 1, jj, kk)]);
     };
     auto vc = [&](int ii, int jj, int kk) -> T {
@@ -154,16 +154,16 @@ __global__ void k_polymer(PolyIn<T> P, Dims d, Phys p, int stage) {
       const T wb = P.w[id], wt = P.w[id + plane];
       const size_t xm = C(i - 1, j, k), xp = C(i + 1, j, k);
 #pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        const T t0 = P.th[q][id];
-        T a = (ur * (t0 + P.th[q][xp]) - ul * (P.th[q][xm] + t0));
-        if (k + 1 < d.nz) a += wt * (t0 + P.th[q][id + plane]);
-        if (k > 0) a -= wb * (P.th[q][id - plane] + t0);
+      for (int cq = 0; cq < NC; ++cq) {
+        const T t0 = P.th[cq][id];
+        T a = (ur * (t0 + P.th[cq][xp]) - ul * (P.th[cq][xm] + t0));
+        if (k + 1 < d.nz) a += wt * (t0 + P.th[cq][id + plane]);
+        if (k > 0) a -= wb * (P.th[cq][id - plane] + t0);
         if (N == 3) {
           const T vl = P.v[id], vr = P.v[C(i, j + 1, k)];
-          a += vr * (t0 + P.th[q][C(i, j + 1, k)]) - vl * (P.th[q][C(i, j - 1, k)] + t0);
+          a += vr * (t0 + P.th[cq][C(i, j + 1, k)]) - vl * (P.th[cq][C(i, j - 1, k)] + t0);
         }
-        adv[q] = (T)0.5 * iD * a;
+        adv[cq] = (T)0.5 * iD * a;
       }
     }
     // eigen-decomposition of Theta at the cell
@@ -227,13 +227,13 @@ __global__ void k_polymer(PolyIn<T> P, Dims d, Phys p, int stage) {
         T s = 0;
 #pragma unroll
         for (int c = 0; c < N; ++c) s += R[a][c] * HR[c][b];
-        const int q = comp_of<N>(a, b);
-        const T rh = s - adv[q];
-        const T t0 = P.th[q][id];
-        newth[q] = stage == 1 ? t0 + dt * rh : (T)0.5 * P.base[q][id] + (T)0.5 * (t0 + dt * rh);
+        const int cq = comp_of<N>(a, b);
+        const T rh = s - adv[cq];
+        const T t0 = P.th[cq][id];
+        newth[cq] = stage == 1 ? t0 + dt * rh : (T)0.5 * P.base[cq][id] + (T)0.5 * (t0 + dt * rh);
       }
 #pragma unroll
-    for (int q = 0; q < NC; ++q) P.out[q][id] = newth[q];
+    for (int cq = 0; cq < NC; ++cq) P.out[cq][id] = newth[cq];
     if (stage == 2) {
       // tau = (1 + phi)/2 (mu_p/lambda_H) (R e^theta R^T - I)
 #pragma unroll
@@ -241,7 +241,7 @@ __global__ void k_polymer(PolyIn<T> P, Dims d, Phys p, int stage) {
 #pragma unroll
         for (int b = 0; b < N; ++b) A[a][b] = newth[comp_of<N>(a, b)];
       eig_sym<T, N>(A, th, R);
-      const T wgt = (T)0.5 * ((T)1 + P.phic[id]) * (T)(p.mu_p1 / p.lam_h);
+      const T wgt = (T)0.5 * ((T)1 + P.phic[id]) * q.wtau;
 #pragma unroll
       for (int a = 0; a < N; ++a)
 #pragma unroll

@@ -22,6 +22,27 @@ namespace pf {
 
 enum ZBc { Z_NEUMANN = 0, Z_DIRICH = 1, Z_FACES = 2 };
 
+// Copy n elements global -> shared (or back) with U independent loads in
+// flight per thread before the first store.
+template <int U, class V, class Src, class Dst>
+__device__ __forceinline__ void staged_copy(int n, Src src, Dst dst) {
+  const int nth = blockDim.x;
+  for (int b = threadIdx.x; b < n; b += nth * U) {
+    V tmp[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = b + u * nth;
+      if (e < n) tmp[u] = src(e);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = b + u * nth;
+      if (e < n) dst(e, tmp[u]);
+    }
+  }
+}
+
+
 // ---------------------------------------------------------------------------
 // forward real FFT along x: two real lines per complex transform
 // Pro: T operator()(int line, int x) const  -- produces the input sample
@@ -33,27 +54,29 @@ __global__ void k_rfft_x(Pro pro, cpx<T>* __restrict__ out, int n, int nlines, i
   cpx<T>* a = reinterpret_cast<cpx<T>*>(smraw);
   cpx<T>* b = a + (size_t)npair * n;
   const int pair0 = blockIdx.x * npair;
-  for (int e = threadIdx.x; e < npair * n; e += blockDim.x) {
-    const int m = e / n, x = e - (e / n) * n;
+  for (int m = 0; m < npair; ++m) {
     const int l0 = 2 * (pair0 + m), l1 = l0 + 1;
-    T va = 0, vb = 0;
-    if (l0 < nlines) va = pro(l0, x);
-    if (l1 < nlines) vb = pro(l1, x);
-    a[e] = mk(va, vb);
+    for (int x = threadIdx.x; x < n; x += blockDim.x) {
+      T va = 0, vb = 0;
+      if (l0 < nlines) va = pro(l0, x);
+      if (l1 < nlines) vb = pro(l1, x);
+      a[m * n + x] = mk(va, vb);
+    }
   }
   __syncthreads();
   cpx<T>* z = fft_lines<T>(a, b, pl, tw, -1, npair, 1, n);
   const int nh = n / 2 + 1;
-  for (int e = threadIdx.x; e < npair * nh; e += blockDim.x) {
-    const int m = e / nh, k = e - (e / nh) * nh;
+  for (int m = 0; m < npair; ++m) {
     const int l0 = 2 * (pair0 + m), l1 = l0 + 1;
-    if (l0 >= nlines) continue;
-    const cpx<T> zk = z[m * n + k];
-    const cpx<T> zn = conjg(z[m * n + (k == 0 ? 0 : n - k)]);
-    const cpx<T> A = scal(zk + zn, (T)0.5);
-    const cpx<T> d = zk - zn;  // B = -i/2 d
-    out[(size_t)l0 * pitch + k] = A;
-    if (l1 < nlines) out[(size_t)l1 * pitch + k] = mk(d.im * (T)0.5, -d.re * (T)0.5);
+    if (l0 >= nlines) break;
+    for (int k = threadIdx.x; k < nh; k += blockDim.x) {
+      const cpx<T> zk = z[m * n + k];
+      const cpx<T> zn = conjg(z[m * n + (k == 0 ? 0 : n - k)]);
+      const cpx<T> A = scal(zk + zn, (T)0.5);
+      const cpx<T> dd = zk - zn;  // B = -i/2 dd
+      out[(size_t)l0 * pitch + k] = A;
+      if (l1 < nlines) out[(size_t)l1 * pitch + k] = mk(dd.im * (T)0.5, -dd.re * (T)0.5);
+    }
   }
 }
 
@@ -69,27 +92,30 @@ __global__ void k_irfft_x(const cpx<T>* __restrict__ in, Epi epi, int n, int nli
   cpx<T>* b = a + (size_t)npair * n;
   const int pair0 = blockIdx.x * npair;
   const int nh = n / 2;
-  for (int e = threadIdx.x; e < npair * n; e += blockDim.x) {
-    const int m = e / n, x = e - (e / n) * n;
+  for (int m = 0; m < npair; ++m) {
     const int l0 = 2 * (pair0 + m), l1 = l0 + 1;
-    const int k = x <= nh ? x : n - x;
-    cpx<T> A = mk<T>(0, 0), B = mk<T>(0, 0);
-    if (l0 < nlines) A = in[(size_t)l0 * pitch + k];
-    if (l1 < nlines) B = in[(size_t)l1 * pitch + k];
-    if (x > nh) {
-      A = conjg(A);
-      B = conjg(B);
+    for (int x = threadIdx.x; x < n; x += blockDim.x) {
+      const int k = x <= nh ? x : n - x;
+      cpx<T> A = mk<T>(0, 0), B = mk<T>(0, 0);
+      if (l0 < nlines) A = in[(size_t)l0 * pitch + k];
+      if (l1 < nlines) B = in[(size_t)l1 * pitch + k];
+      if (x > nh) {
+        A = conjg(A);
+        B = conjg(B);
+      }
+      a[m * n + x] = mk(A.re - B.im, A.im + B.re);  // A + i B
     }
-    a[e] = mk(A.re - B.im, A.im + B.re);  // A + i B
   }
   __syncthreads();
   cpx<T>* z = fft_lines<T>(a, b, pl, tw, +1, npair, 1, n);
-  for (int e = threadIdx.x; e < npair * n; e += blockDim.x) {
-    const int m = e / n, x = e - (e / n) * n;
+  for (int m = 0; m < npair; ++m) {
     const int l0 = 2 * (pair0 + m), l1 = l0 + 1;
-    const cpx<T> v = z[e];
-    if (l0 < nlines) epi(l0, x, v.re * scale);
-    if (l1 < nlines) epi(l1, x, v.im * scale);
+    if (l0 >= nlines) break;
+    for (int x = threadIdx.x; x < n; x += blockDim.x) {
+      const cpx<T> v = z[m * n + x];
+      epi(l0, x, v.re * scale);
+      if (l1 < nlines) epi(l1, x, v.im * scale);
+    }
   }
 }
 
@@ -104,21 +130,27 @@ __global__ void k_fft_y(cpx<T>* __restrict__ data, int ny, int pitch, int ncol, 
   cpx<T>* b = a + (size_t)ny * tx;
   const int c0 = blockIdx.x * tx;
   cpx<T>* base = data + (size_t)blockIdx.y * ny * pitch;
-  for (int e = threadIdx.x; e < ny * tx; e += blockDim.x) {
-    const int y = e / tx, c = e - (e / tx) * tx;
-    a[e] = (c0 + c < ncol) ? base[(size_t)y * pitch + c0 + c] : mk<T>(0, 0);
-  }
+  const float itx = 1.0f / (float)tx;
+  staged_copy<8, cpx<T>>(
+      ny * tx,
+      [&](int e) {
+        const int y = qdiv(e, tx, itx), c = e - y * tx;
+        return (c0 + c < ncol) ? base[(size_t)y * pitch + c0 + c] : mk<T>(0, 0);
+      },
+      [&](int e, cpx<T> v) { a[e] = v; });
   __syncthreads();
   cpx<T>* z = fft_lines<T>(a, b, pl, tw, sign, tx, tx, 1);
   for (int e = threadIdx.x; e < ny * tx; e += blockDim.x) {
-    const int y = e / tx, c = e - (e / tx) * tx;
+    const int y = qdiv(e, tx, itx), c = e - y * tx;
     if (c0 + c < ncol) base[(size_t)y * pitch + c0 + c] = z[e];
   }
 }
 
 // ---------------------------------------------------------------------------
-// z solves.  One CTA: TX kx-columns at one ky; thread t handles column t/2,
-// component t%2 (real and imaginary parts are independent real systems).
+// z solves.  One CTA: a tile of TX kx-columns x all z rows at one ky, staged
+// in shared memory with coalesced row loads; thread t < 2 TX then solves column
+// t/2, component t%2 (real and imaginary parts are independent real systems)
+// sequentially along z in shared memory, and the tile is stored back.
 // Solve 1: (L - shift1) x = scale * rhs, eliminated bottom-up then substituted
 // top-down.  With `two`, the result x feeds solve 2, (L - shift2) y = x, whose
 // elimination runs top-down while solve 1 substitutes, so the pair costs three
@@ -137,6 +169,11 @@ struct ZSolve {
 };
 
 template <class TC>
+__device__ __forceinline__ TC recip(TC x) { return (TC)1 / x; }
+template <>
+__device__ __forceinline__ float recip<float>(float x) { return __frcp_rn(x); }
+
+template <class TC>
 __device__ __forceinline__ TC zdiag(int k, int rows, int bc, TC sig) {
   if (bc == Z_FACES || (k > 0 && k < rows - 1)) return (TC)-2 - sig;
   return (bc == Z_NEUMANN ? (TC)-1 : (TC)-3) - sig;
@@ -145,71 +182,101 @@ __device__ __forceinline__ TC zdiag(int k, int rows, int bc, TC sig) {
 template <class T, class TC>
 __global__ void k_zsolve(cpx<T>* __restrict__ data, const double* __restrict__ eigx,
                          const double* __restrict__ eigy, ZSolve zs, int tx) {
-  extern __shared__ unsigned char smraw[];
+  // shared memory: the tile (R rows x tx complex), then the factors
+  extern __shared__ __align__(16) unsigned char smraw[];
   const int R = zs.rows;
-  const int nt = 2 * tx;
-  TC* cp = reinterpret_cast<TC*>(smraw);            // R x tx  (factor 1/b')
-  TC* dp = cp + (size_t)R * tx;                      // R x nt  (modified rhs)
-  TC* cq = dp + (size_t)R * nt;                      // R x tx  (solve-2 factors, if !same)
+  cpx<T>* tile = reinterpret_cast<cpx<T>*>(smraw);   // R x tx, row k at tile + k*tx
+  TC* cp = reinterpret_cast<TC*>(tile + (size_t)R * tx);  // R x tx  (1/b' of solve 1)
+  TC* cq = cp + (size_t)R * tx;                            // R x tx  (solve-2 factors, if !same)
+  const int ky = blockIdx.y;
+  const int col0 = blockIdx.x * tx;
+  const int ncol = min(tx, zs.ncol - col0);
+  cpx<T>* gbase = data + (size_t)ky * zs.pitch + col0;
+  const size_t zstride = (size_t)zs.ny * zs.pitch;
+  // stage the tile: rows of tx contiguous complex values (coalesced)
+  const float itx = 1.0f / (float)tx;
+  staged_copy<8, cpx<T>>(
+      R * tx,
+      [&](int e) {
+        const int k = qdiv(e, tx, itx), c = e - k * tx;
+        return c < ncol ? gbase[(size_t)k * zstride + c] : mk<T>(0, 0);
+      },
+      [&](int e, cpx<T> v) { tile[e] = v; });
+  __syncthreads();
   const int t = threadIdx.x;
   const int c = t >> 1, part = t & 1;
-  const int ky = blockIdx.y;
-  int col = blockIdx.x * tx + c;
-  // inactive lanes keep participating in __syncwarp but touch no memory
-  const bool active = col < zs.ncol && !(zs.skip_zero && col == 0 && ky == 0);
-  if (!active) col = 0;
-  const size_t zstride = (size_t)zs.ny * zs.pitch * 2;  // in T units
-  T* base = reinterpret_cast<T*>(data) + ((size_t)ky * zs.pitch + col) * 2 + part;
-  const TC k2 = (TC)(-(eigx[col] + eigy[ky]));
-  const TC h2 = (TC)zs.h2;
-  const TC sg1 = (k2 + (TC)zs.shift1) * h2;
-  const TC rs = (TC)(zs.h2 * zs.scale);
-  // phase A: bottom-up elimination of solve 1
-  TC cprev = 0, dprev = 0;
-  for (int k = 0; k < R; ++k) {
-    const TC r = active ? (TC)base[(size_t)k * zstride] * rs : (TC)0;
-    const TC bk = zdiag<TC>(k, R, zs.bc, sg1) - cprev;
-    const TC m = (TC)1 / bk;
-    const TC dk = (r - dprev) * m;
-    if (part == 0) cp[(size_t)k * tx + c] = m;
-    dp[(size_t)k * nt + t] = dk;
-    cprev = m;
-    dprev = dk;
-  }
-  if (!zs.two) {
-    __syncwarp();
-    TC x = 0;
-    for (int k = R - 1; k >= 0; --k) {
-      x = dp[(size_t)k * nt + t] - (k < R - 1 ? cp[(size_t)k * tx + c] * x : (TC)0);
-      if (active) base[(size_t)k * zstride] = (T)x;
-    }
-    return;
-  }
-  TC* c2 = cp;
-  if (!zs.same) {
-    const TC sg2 = (k2 + (TC)zs.shift2) * h2;
-    TC cc = 0;
+  const int col = col0 + c;
+  const bool active = c < ncol && !(zs.skip_zero && col == 0 && ky == 0);
+  if (t < 2 * tx) {
+    T* v = reinterpret_cast<T*>(tile + c) + part;  // component `part` of column c; row stride 2*tx
+    const int vs = 2 * tx;
+    const TC k2 = (TC)(-(eigx[active ? col : 0] + eigy[ky]));
+    const TC h2 = (TC)zs.h2;
+    const TC sg1 = (k2 + (TC)zs.shift1) * h2;
+    const TC rs = (TC)(zs.h2 * zs.scale);
+    // phase A: elimination of solve 1 (top row k = 0 first), modified rhs in place.
+    // The factor recurrence m_k = 1/(b - m_{k-1}) is stationary once two
+    // successive values agree bit for bit (constant interior diagonal), so
+    // from there on it is reused without recomputation -- exactly.
+    TC cprev = 0, dprev = 0;
+    bool stat = false;
+#pragma unroll 4
     for (int k = 0; k < R; ++k) {
-      const TC m = (TC)1 / (zdiag<TC>(k, R, zs.bc, sg2) - cc);
-      if (part == 0) cq[(size_t)k * tx + c] = m;
-      cc = m;
+      const TC r = (TC)v[(size_t)k * vs] * rs;
+      TC m = cprev;
+      if (!stat || k == R - 1) {
+        m = recip<TC>(zdiag<TC>(k, R, zs.bc, sg1) - cprev);
+        stat = (k > 0 && k < R - 1 && m == cprev);
+      }
+      const TC dk = (r - dprev) * m;
+      if (part == 0) cp[(size_t)k * tx + c] = m;
+      v[(size_t)k * vs] = (T)dk;
+      cprev = m;
+      dprev = dk;
     }
-    c2 = cq;
+    TC* c2 = cp;
+    if (zs.two && !zs.same) {
+      const TC sg2 = (k2 + (TC)zs.shift2) * h2;
+      TC cc = 0;
+      for (int k = 0; k < R; ++k) {
+        const TC m = recip<TC>(zdiag<TC>(k, R, zs.bc, sg2) - cc);
+        if (part == 0) cq[(size_t)k * tx + c] = m;
+        cc = m;
+      }
+      c2 = cq;
+    }
+    __syncwarp();
+    if (!zs.two) {
+      TC x = 0;
+#pragma unroll 4
+      for (int k = R - 1; k >= 0; --k) {
+        x = (TC)v[(size_t)k * vs] - (k < R - 1 ? cp[(size_t)k * tx + c] * x : (TC)0);
+        v[(size_t)k * vs] = (T)x;
+      }
+    } else {
+      // phase B: back substitution of solve 1 (bottom-up); solve 2 eliminated in the same order
+      TC x = 0, qv = 0;
+#pragma unroll 4
+      for (int k = R - 1; k >= 0; --k) {
+        x = (TC)v[(size_t)k * vs] - (k < R - 1 ? cp[(size_t)k * tx + c] * x : (TC)0);
+        const TC m2 = c2[(size_t)(R - 1 - k) * tx + c];
+        qv = (x * h2 - (k < R - 1 ? qv : (TC)0)) * m2;
+        v[(size_t)k * vs] = (T)qv;
+      }
+      // phase C: back substitution of solve 2 (top-down)
+      TC y = 0;
+#pragma unroll 4
+      for (int k = 0; k < R; ++k) {
+        y = (TC)v[(size_t)k * vs] - (k > 0 ? c2[(size_t)(R - 1 - k) * tx + c] * y : (TC)0);
+        v[(size_t)k * vs] = (T)y;
+      }
+    }
   }
-  __syncwarp();
-  // phase B: substitute solve 1 top-down; eliminate solve 2 in the same order
-  TC x = 0, q = 0;
-  for (int k = R - 1; k >= 0; --k) {
-    x = dp[(size_t)k * nt + t] - (k < R - 1 ? cp[(size_t)k * tx + c] * x : (TC)0);
-    const TC m2 = c2[(size_t)(R - 1 - k) * tx + c];
-    q = (x * h2 - (k < R - 1 ? q : (TC)0)) * m2;
-    dp[(size_t)k * nt + t] = q;
-  }
-  // phase C: substitute solve 2 bottom-up
-  TC y = 0;
-  for (int k = 0; k < R; ++k) {
-    y = dp[(size_t)k * nt + t] - (k > 0 ? c2[(size_t)(R - 1 - k) * tx + c] * y : (TC)0);
-    if (active) base[(size_t)k * zstride] = (T)y;
+  __syncthreads();
+  for (int e = threadIdx.x; e < R * tx; e += blockDim.x) {
+    const int k = qdiv(e, tx, itx), cc = e - k * tx;
+    const int colc = col0 + cc;
+    if (cc < ncol && !(zs.skip_zero && colc == 0 && ky == 0)) gbase[(size_t)k * zstride + cc] = tile[e];
   }
 }
 
