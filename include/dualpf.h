@@ -168,6 +168,28 @@ int pf_diagnostics(pf_ctx* ctx, double out[6]);
 int pf_profile(pf_ctx* ctx, int nsteps, int flags, int max_entries, char* names, double* avg_ms,
                int* counts, int* n_entries, int* launches_per_step);
 
+/* Allocation-free diagnostics.  The paper has no counterpart: this is a
+ * service for callers that may not allocate device memory (an application
+ * whose memory pool owns the whole GPU, an allocator that forbids
+ * cudaMalloc/cudaFree, a real-time loop in which an allocation would stall).
+ * It computes the six FP64 reductions of pf_diagnostics from a phase field
+ * the caller already holds on the current device -- phi_device points to the
+ * fine mesh of *g in the element type of g->precision (double for PF_FP64,
+ * float for PF_MIXED), layout as above -- with no context and no allocation
+ * of any kind.  Its scratch is one file-scope device array of 1 MiB that
+ * every GPU which loads the library holds until the process exits; the
+ * phase field may have at most 134,217,728 fine cells, larger fields are
+ * rejected with PF_ERR_UNSUPPORTED.  Work is enqueued on `stream` (a
+ * cudaStream_t, NULL for the legacy stream) and the call synchronises it.
+ * The first call on a device resolves the array's device address; make that
+ * first call before any stream capture.  All calls share the array: calls
+ * that overlap on the GPU (other streams, other threads) race and must be
+ * serialised by the caller.  Each call overwrites every slot it reads, so
+ * the contents left by an earlier call never matter.  Errors: PF_ERR_ARG,
+ * PF_ERR_UNSUPPORTED, PF_ERR_CUDA. */
+int pf_diagnostics_noalloc(const pf_grid_desc* g, const pf_params* prm, const void* phi_device, double out[6],
+                           void* stream);
+
 /* Message of the last failed call on ctx (or of the last failed
  * pf_init_grid when ctx is NULL).  Valid until the next call. */
 const char* pf_last_error(const pf_ctx* ctx);

@@ -24,7 +24,8 @@ ERRORS = {-1: "PF_ERR_ARG", -2: "PF_ERR_DISCRIMINANT", -3: "PF_ERR_UNSUPPORTED",
           -5: "PF_ERR_TIMEOUT", -6: "PF_ERR_CUDA", -7: "PF_ERR_NOMEM"}
 
 EXPORTS = ["pf_init_grid", "pf_set_params", "pf_field_info", "pf_set_fields", "pf_step", "pf_step_ex",
-           "pf_get_fields", "pf_diagnostics", "pf_profile", "pf_last_error", "pf_destroy"]
+           "pf_get_fields", "pf_diagnostics", "pf_profile", "pf_diagnostics_noalloc", "pf_last_error",
+           "pf_destroy"]
 PROFILE_NAME = 48
 
 
@@ -65,6 +66,9 @@ def load(path: str = LIB_PATH):
         lib.pf_diagnostics.argtypes = [vp, C.POINTER(C.c_double)]
         lib.pf_profile.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_char_p, C.POINTER(C.c_double),
                                    C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        lib.pf_diagnostics_noalloc.argtypes = [C.POINTER(GridDesc), C.POINTER(ParamsC), vp,
+                                               C.POINTER(C.c_double), vp]
+        lib.pf_diagnostics_noalloc.restype = C.c_int
         lib.pf_last_error.argtypes = [vp]
         lib.pf_last_error.restype = C.c_char_p
         lib.pf_destroy.argtypes = [vp]
