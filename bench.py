@@ -66,13 +66,12 @@ def alg_bytes(grid, esize, visco=True):
     ncomp = 6 if d3 else 3
     nsolve = nvel + 1                        # velocity components + pressure
     b = {
-        "ch_mu": 3 * E * nf,
-        "ch_rhs_fftx": 3 * E * nf + 2 * nvel * E * nc + 2 * E * sf,
+        "ch_rhs": 3 * E * nf + 2 * nvel * E * nc,
+        "rfft_x_fine": E * nf + 2 * E * sf,
         "fft_y_fine": 2 * 2 * (2 * E * sf) if d3 else 0,
         "zsolve_pair": 2 * 2 * E * sf,
         "ch_ifftx_finish": 2 * E * sf + 3 * E * nf,
-        "ch_G": 2 * E * nf,
-        "restrict": 2 * E * nf + (11 if d3 else 7) * E * nc,
+        "ch_G_restrict": E * nf + (11 if d3 else 7) * E * nc,
         "ns_rhs": (2 * (nvel + 1) + (2 * ncomp if visco else 0) + (11 if d3 else 7) + nvel) * E * nc,
         "rfft_x_coarse": nsolve * (E * nc + 2 * E * sc),
         "fft_y_coarse": (2 * nsolve * 2 * (2 * E * sc)) if d3 else 0,

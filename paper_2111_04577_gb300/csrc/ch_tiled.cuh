@@ -14,6 +14,8 @@
 //   one-cell halo in shared memory, then every coarse sample of phi and G that
 //   Eqs. dual2/dual3 need (centres, faces, edges), without writing fine G.
 #pragma once
+#include <type_traits>
+
 #include "ch.cuh"
 
 namespace pf {
@@ -24,26 +26,40 @@ __device__ __forceinline__ int pmod(int x, int n) {
 }
 __device__ __forceinline__ int clampi(int x, int lo, int hi) { return x < lo ? lo : (x > hi ? hi : x); }
 
-template <int DIM>
+// wrap into [0, n) for -n <= x < 2n
+__device__ __forceinline__ int wrap1(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
+
+template <int DIM, int ES>
 struct RhsTile {
-  static constexpr int TX = 64, TY = DIM == 3 ? 8 : 1, TZ = DIM == 3 ? 8 : 16;
+  // ES: element size; FP64 tiles are half as deep to stay within shared memory
+  static constexpr int TX = 64, TY = DIM == 3 ? 8 : 1, TZ = DIM == 3 ? (ES == 8 ? 4 : 8) : 16;
   static constexpr int HY = DIM == 3 ? 2 : 0;
   static constexpr int SX = TX + 4, SY = TY + 2 * HY, SZ = TZ + 4;
   static constexpr int MX = TX + 2, MY = TY + (DIM == 3 ? 2 : 0), MZ = TZ + 2;
   static constexpr int NS = SX * SY * SZ, NM = MX * MY * MZ;
+  // coarse velocity box: x, y with one cell of halo on each side, z with one extra face
+  __host__ __device__ static constexpr int VX(int rs) { return (TX >> rs) + 2; }
+  __host__ __device__ static constexpr int VY(int rys) { return DIM == 3 ? (TY >> rys) + 2 : 1; }
+  __host__ __device__ static constexpr int VZ(int rs) { return (TZ >> rs) + 1; }
+  __host__ __device__ static constexpr int NV(int rs, int rys) { return VX(rs) * VY(rys) * VZ(rs); }
 };
 
 template <class T, int DIM>
 __global__ void __launch_bounds__(256) k_ch_rhs(const FineView<T> f, const CoarseVel<T> vel, T* __restrict__ R,
                                                 double* __restrict__ gwall, const Dims d, const Phys p,
                                                 const PhysT<T> q, const T inv_mldt, const T inv_ml) {
-  using TL = RhsTile<DIM>;
+  using TL = RhsTile<DIM, sizeof(T)>;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* ps = reinterpret_cast<T*>(smraw);  // phi*, [SZ][SY][SX]
   T* ms = ps + TL::NS;                  // mu*,  [MZ][MY][MX]
+  const int VX = TL::VX(d.rs), VY = TL::VY(d.rys), VZ = TL::VZ(d.rs), NV = VX * VY * VZ;
+  T* us = ms + TL::NM;                  // u*, v*, w* on the coarse box [VZ][VY][VX]
+  T* vs = us + NV;
+  T* wsm = vs + NV;
   const int x0 = blockIdx.x * TL::TX, y0 = blockIdx.y * TL::TY, z0 = blockIdx.z * TL::TZ;
   const int fnx = d.fnx, fny = d.fny, fnz = d.fnz;
   const size_t plane = (size_t)fnx * fny;
+  const bool smallx = fnx < TL::SX, smally = fny < TL::SY;  // tile wider than the domain
   // ---- stage phi* with a 2-cell halo (x, y periodic; z clamped, never read past a wall) ----
   {
     const float isx = 1.0f / TL::SX, isy = 1.0f / TL::SY;
@@ -51,14 +67,51 @@ __global__ void __launch_bounds__(256) k_ch_rhs(const FineView<T> f, const Coars
       const int zz = qdiv(e, TL::SX * TL::SY, isx * isy);
       const int rem = e - zz * TL::SX * TL::SY;
       const int yy = qdiv(rem, TL::SX, isx), xx = rem - yy * TL::SX;
-      const int gx = pmod(x0 - 2 + xx, fnx);
-      const int gy = DIM == 3 ? pmod(y0 - TL::HY + yy, fny) : 0;
+      const int gx = smallx ? pmod(x0 - 2 + xx, fnx) : wrap1(x0 - 2 + xx, fnx);
+      const int gy = DIM == 3 ? (smally ? pmod(y0 - TL::HY + yy, fny) : wrap1(y0 - TL::HY + yy, fny)) : 0;
       const int gz = clampi(z0 - 2 + zz, 0, fnz - 1);
       const size_t o = (size_t)gz * plane + (size_t)gy * fnx + gx;
       ps[e] = (T)2 * f.pn[o] - f.po[o];
     }
   }
+  // ---- stage the extrapolated coarse velocities of the block (Eq. dual1 reads them) ----
+  const int cx0 = (x0 >> d.rs) - 1, cy0 = DIM == 3 ? (y0 >> d.rys) - 1 : 0, cz0 = z0 >> d.rs;
+  {
+    const float ivx = 1.0f / VX, ivy = 1.0f / VY;
+    const int cplane = d.nx * d.ny;
+    for (int e = threadIdx.x; e < NV; e += blockDim.x) {
+      const int zz = qdiv(e, VX * VY, ivx * ivy);
+      const int rem = e - zz * VX * VY;
+      const int yy = qdiv(rem, VX, ivx), xx = rem - yy * VX;
+      const int cx = pmod(cx0 + xx, d.nx);
+      const int cy = DIM == 3 ? pmod(cy0 + yy, d.ny) : 0;
+      const int cz = cz0 + zz;
+      const int czc = cz < d.nz ? cz : d.nz - 1;  // u, v live on cells (the extra layer is unused)
+      const int czw = cz <= d.nz ? cz : d.nz;     // w on faces 0..nz
+      const int oc = czc * cplane + cy * d.nx + cx, ow = czw * cplane + cy * d.nx + cx;
+      us[e] = vel.us(oc);
+      vs[e] = DIM == 3 ? vel.vs(oc) : (T)0;
+      wsm[e] = vel.ws(ow);
+    }
+  }
   __syncthreads();
+  // prolonged face velocities (Eq. dual1) from the staged coarse box
+  auto V = [&](const T* a, int cx, int cy, int cz) -> T { return a[((cz - cz0) * VY + (cy - cy0)) * VX + (cx - cx0)]; };
+  auto uface = [&](int I, int J, int K) -> T {  // fine x-face I (may be fnx: periodic image)
+    const int ic = I >> d.rs, jc = DIM == 3 ? J >> d.rys : 0, kc = K >> d.rs;
+    const T a = V(us, ic, jc, kc);
+    return (I & (d.r - 1)) == 0 ? a : (T)0.5 * (a + V(us, ic + 1, jc, kc));
+  };
+  auto vface = [&](int I, int J, int K) -> T {
+    const int ic = I >> d.rs, jc = J >> d.rys, kc = K >> d.rs;
+    const T a = V(vs, ic, jc, kc);
+    return (J & (d.ry - 1)) == 0 ? a : (T)0.5 * (a + V(vs, ic, jc + 1, kc));
+  };
+  auto wface = [&](int I, int J, int K) -> T {
+    const int ic = I >> d.rs, jc = DIM == 3 ? J >> d.rys : 0, kc = K >> d.rs;
+    const T a = V(wsm, ic, jc, kc);
+    return (K & (d.r - 1)) == 0 ? a : (T)0.5 * (a + V(wsm, ic, jc, kc + 1));
+  };
   auto P = [&](int sz, int sy, int sx) -> T { return ps[(sz * TL::SY + sy) * TL::SX + sx]; };
   // ---- mu* on the block plus one cell ----
   {
@@ -107,14 +160,11 @@ __global__ void __launch_bounds__(256) k_ch_rhs(const FineView<T> f, const Coars
     if (gx >= fnx || gy >= fny || gz >= fnz) continue;
     const int sx = tx + 2, sy = ty + TL::HY, sz = tz + 2;
     const T c0 = P(sz, sy, sx);
-    const int gxp = gx + 1 == fnx ? 0 : gx + 1;
-    T adv = vel.uface(d, gxp, gy, gz) * (c0 + P(sz, sy, sx + 1)) - vel.uface(d, gx, gy, gz) * (P(sz, sy, sx - 1) + c0);
-    if (DIM == 3) {
-      const int gyp = gy + 1 == fny ? 0 : gy + 1;
-      adv += vel.vface(d, gx, gyp, gz) * (c0 + P(sz, sy + 1, sx)) - vel.vface(d, gx, gy, gz) * (P(sz, sy - 1, sx) + c0);
-    }
-    if (gz + 1 < fnz) adv += vel.wface(d, gx, gy, gz + 1) * (c0 + P(sz + 1, sy, sx));
-    if (gz > 0) adv -= vel.wface(d, gx, gy, gz) * (P(sz - 1, sy, sx) + c0);
+    // faces are addressed by unwrapped fine indices: the staged box holds the periodic images
+    T adv = uface(gx + 1, gy, gz) * (c0 + P(sz, sy, sx + 1)) - uface(gx, gy, gz) * (P(sz, sy, sx - 1) + c0);
+    if (DIM == 3) adv += vface(gx, gy + 1, gz) * (c0 + P(sz, sy + 1, sx)) - vface(gx, gy, gz) * (P(sz, sy - 1, sx) + c0);
+    if (gz + 1 < fnz) adv += wface(gx, gy, gz + 1) * (c0 + P(sz + 1, sy, sx));
+    if (gz > 0) adv -= wface(gx, gy, gz) * (P(sz - 1, sy, sx) + c0);
     adv *= (T)0.5 * q.ih;
     const int mx = tx + 1, my = ty + (DIM == 3 ? 1 : 0), mz = tz + 1;
     const T m0 = M(mz, my, mx);
@@ -133,32 +183,44 @@ template <int DIM>
 struct GrTile {
   // coarse block; the fine block is r times larger plus a halo
   static constexpr int CX = DIM == 3 ? 16 : 64, CY = DIM == 3 ? 4 : 1, CZ = 4;
+  // fine G block [GZ][GY][GX] starting one fine cell before the coarse block
+  // (the extra top layer serves the z-face at the top wall), phi block one
+  // more cell each side
+  __host__ __device__ static constexpr int GX(int r) { return r * CX + 1; }
+  __host__ __device__ static constexpr int GY(int ry) { return DIM == 3 ? ry * CY + 1 : 1; }
+  __host__ __device__ static constexpr int GZ(int r) { return r * CZ + 2; }
+  __host__ __device__ static constexpr int PX(int r) { return GX(r) + 2; }
+  __host__ __device__ static constexpr int PY(int ry) { return DIM == 3 ? GY(ry) + 2 : 1; }
+  __host__ __device__ static constexpr int PZ(int r) { return GZ(r) + 2; }
+  __host__ __device__ static constexpr int smem_elems(int r, int ry) {
+    return PX(r) * PY(ry) * PZ(r) + GX(r) * GY(ry) * GZ(r);
+  }
 };
 
-template <class T, int DIM>
+template <class T, int DIM, int R>
 __global__ void __launch_bounds__(256) k_ch_G_restrict(const T* __restrict__ phi, const double* __restrict__ gwall,
                                                        Restricted<T> out, const Dims d, const PhysT<T> q) {
   using TL = GrTile<DIM>;
+  constexpr int RY = DIM == 3 ? R : 1;
+  constexpr int GX = TL::GX(R), GY = TL::GY(RY), GZ = TL::GZ(R);
+  constexpr int PX = TL::PX(R), PY = TL::PY(RY), PZ = TL::PZ(R);
+  constexpr int HY = DIM == 3 ? 1 : 0;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int r = d.r, ry = d.ry;
-  // fine G block: x in [r*cx0 - 1, r*(cx0+CX)), likewise y (3D) and z
-  const int GX = r * TL::CX + 1, GY = DIM == 3 ? ry * TL::CY + 1 : 1, GZ = r * TL::CZ + 1;
-  const int PX = GX + 2, PY = DIM == 3 ? GY + 2 : 1, PZ = GZ + 2;  // phi block with one more cell each side
-  T* ph = reinterpret_cast<T*>(smraw);  // [PZ][PY][PX]
-  T* gs = ph + PX * PY * PZ;            // [GZ][GY][GX]
+  T* ph = reinterpret_cast<T*>(smraw);  // [PZ][PY][PX], z clamped at the walls (mirror ghosts)
+  T* gs = ph + PX * PY * PZ;            // [GZ][GY][GX], G of the (mirrored) sample
   const int cx0 = blockIdx.x * TL::CX, cy0 = blockIdx.y * TL::CY, cz0 = blockIdx.z * TL::CZ;
   const int fnx = d.fnx, fny = d.fny, fnz = d.fnz;
   const size_t plane = (size_t)fnx * fny;
-  const int fx0 = r * cx0 - 1, fy0 = DIM == 3 ? ry * cy0 - 1 : 0, fz0 = r * cz0 - 1;  // origin of the G block
+  const int fx0 = R * cx0 - 1, fy0 = DIM == 3 ? RY * cy0 - 1 : 0, fz0 = R * cz0 - 1;  // G-block origin
+  const bool smallx = fnx < PX, smally = fny < PY;
   {
-    const int n = PX * PY * PZ;
     const float ipx = 1.0f / PX, ipy = 1.0f / PY;
-    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    for (int e = threadIdx.x; e < PX * PY * PZ; e += blockDim.x) {
       const int zz = qdiv(e, PX * PY, ipx * ipy);
       const int rem = e - zz * PX * PY;
       const int yy = qdiv(rem, PX, ipx), xx = rem - yy * PX;
-      const int gx = pmod(fx0 - 1 + xx, fnx);
-      const int gy = DIM == 3 ? pmod(fy0 - 1 + yy, fny) : 0;
+      const int gx = smallx ? pmod(fx0 - 1 + xx, fnx) : wrap1(fx0 - 1 + xx, fnx);
+      const int gy = DIM == 3 ? (smally ? pmod(fy0 - 1 + yy, fny) : wrap1(fy0 - 1 + yy, fny)) : 0;
       const int gz = clampi(fz0 - 1 + zz, 0, fnz - 1);
       ph[e] = phi[(size_t)gz * plane + (size_t)gy * fnx + gx];
     }
@@ -166,16 +228,13 @@ __global__ void __launch_bounds__(256) k_ch_G_restrict(const T* __restrict__ phi
   __syncthreads();
   auto PH = [&](int z, int y, int x) -> T { return ph[(z * PY + y) * PX + x]; };
   {
-    const int n = GX * GY * GZ;
     const float igx = 1.0f / GX, igy = 1.0f / GY;
-    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    for (int e = threadIdx.x; e < GX * GY * GZ; e += blockDim.x) {
       const int gzl = qdiv(e, GX * GY, igx * igy);
       const int rem = e - gzl * GX * GY;
       const int gyl = qdiv(rem, GX, igx), gxl = rem - gyl * GX;
-      // the real fine cell this sample stands for (mirror ghost in z)
-      const int gz = clampi(fz0 + gzl, 0, fnz - 1);
-      const int pz = gz - (fz0 - 1);  // index in the phi block
-      const int py = DIM == 3 ? gyl + 1 : 0, px = gxl + 1;
+      const int gz = clampi(fz0 + gzl, 0, fnz - 1);  // the real cell this sample stands for
+      const int pz = gz - (fz0 - 1), py = gyl + HY, px = gxl + 1;
       const T c0 = PH(pz, py, px);
       T lap = PH(pz, py, px + 1) + PH(pz, py, px - 1) - 2 * c0;
       if (DIM == 3) lap += PH(pz, py + 1, px) + PH(pz, py - 1, px) - 2 * c0;
@@ -193,16 +252,9 @@ __global__ void __launch_bounds__(256) k_ch_G_restrict(const T* __restrict__ phi
     }
   }
   __syncthreads();
-  // phi at the same fine samples as G: block origin shift of one cell
-  auto PHs = [&](int z, int y, int x) -> T {  // (z, y, x) in G-block coordinates, z mirrored
-    const int gz = clampi(fz0 + z, 0, fnz - 1);
-    return PH(gz - (fz0 - 1), DIM == 3 ? y + 1 : 0, x + 1);
-  };
-  auto GS = [&](int z, int y, int x) -> T {
-    const int gz = clampi(fz0 + z, 0, fnz - 1);
-    return gs[((gz - fz0) * GY + y) * GX + x];
-  };
-  // one thread per coarse cell of the block (and the top z-face layer)
+  // phi and G at G-block coordinates (z mirrored through the clamped loads)
+  auto PHs = [&](int z, int y, int x) -> T { return ph[((z + 1) * PY + (y + HY)) * PX + (x + 1)]; };
+  auto GS = [&](int z, int y, int x) -> T { return gs[(z * GY + y) * GX + x]; };
   const int ncell = TL::CX * TL::CY * (TL::CZ + 1);
   const float icx = 1.0f / TL::CX, icy = 1.0f / TL::CY;
   for (int e = threadIdx.x; e < ncell; e += blockDim.x) {
@@ -213,29 +265,37 @@ __global__ void __launch_bounds__(256) k_ch_G_restrict(const T* __restrict__ phi
     if (i >= d.nx || j >= d.ny || k > d.nz) continue;
     if (lz == TL::CZ && k != d.nz) continue;  // the extra layer only for the top wall face
     const size_t id = ((size_t)k * d.ny + j) * d.nx + i;
-    // block-local fine coordinates of this coarse cell's first fine cell (+1 for the halo)
-    const int bx = r * lx + 1, by = DIM == 3 ? ry * ly + 1 : 0, bz = r * lz + 1;
-    auto mean = [&](auto&& F, int xa, int nxr, int ya, int nyr, int za, int nzr) -> T {
+    // G-block coordinates of this coarse cell's first fine cell
+    const int bx = R * lx + 1, by = DIM == 3 ? RY * ly + 1 : 0, bz = R * lz + 1;
+    auto mean = [&](auto&& F, int xa, auto nxr, int ya, auto nyr, int za, auto nzr) -> T {
+      constexpr int NX = decltype(nxr)::value, NY = decltype(nyr)::value, NZ = decltype(nzr)::value;
       T s = 0;
-      for (int zz = 0; zz < nzr; ++zz)
-        for (int yy = 0; yy < nyr; ++yy)
-          for (int xx = 0; xx < nxr; ++xx) s += F(za + zz, ya + yy, xa + xx);
-      return s / (T)(nxr * nyr * nzr);
+#pragma unroll
+      for (int zz = 0; zz < NZ; ++zz)
+#pragma unroll
+        for (int yy = 0; yy < NY; ++yy)
+#pragma unroll
+          for (int xx = 0; xx < NX; ++xx) s += F(za + zz, ya + yy, xa + xx);
+      return s * ((T)1 / (T)(NX * NY * NZ));
     };
-    // z-faces and z-edges: fine z cells (r k - 1, r k)
-    out.phifz[id] = mean(PHs, bx, r, by, ry, bz - 1, 2);
-    out.Gfz[id] = mean(GS, bx, r, by, ry, bz - 1, 2);
-    out.phiexz[id] = mean(PHs, bx - 1, 2, by, ry, bz - 1, 2);
-    if (DIM == 3) out.phieyz[id] = mean(PHs, bx, r, by - 1, 2, bz - 1, 2);
+    using C1 = std::integral_constant<int, 1>;
+    using C2 = std::integral_constant<int, 2>;
+    using CR = std::integral_constant<int, R>;
+    using CRY = std::integral_constant<int, RY>;
+    (void)C1{};
+    out.phifz[id] = mean(PHs, bx, CR{}, by, CRY{}, bz - 1, C2{});
+    out.Gfz[id] = mean(GS, bx, CR{}, by, CRY{}, bz - 1, C2{});
+    out.phiexz[id] = mean(PHs, bx - 1, C2{}, by, CRY{}, bz - 1, C2{});
+    if (DIM == 3) out.phieyz[id] = mean(PHs, bx, CR{}, by - 1, C2{}, bz - 1, C2{});
     if (k == d.nz) continue;
-    out.phic[id] = mean(PHs, bx, r, by, ry, bz, r);
-    out.Gc[id] = mean(GS, bx, r, by, ry, bz, r);
-    out.phifx[id] = mean(PHs, bx - 1, 2, by, ry, bz, r);
-    out.Gfx[id] = mean(GS, bx - 1, 2, by, ry, bz, r);
+    out.phic[id] = mean(PHs, bx, CR{}, by, CRY{}, bz, CR{});
+    out.Gc[id] = mean(GS, bx, CR{}, by, CRY{}, bz, CR{});
+    out.phifx[id] = mean(PHs, bx - 1, C2{}, by, CRY{}, bz, CR{});
+    out.Gfx[id] = mean(GS, bx - 1, C2{}, by, CRY{}, bz, CR{});
     if (DIM == 3) {
-      out.phify[id] = mean(PHs, bx, r, by - 1, 2, bz, r);
-      out.Gfy[id] = mean(GS, bx, r, by - 1, 2, bz, r);
-      out.phiexy[id] = mean(PHs, bx - 1, 2, by - 1, 2, bz, r);
+      out.phify[id] = mean(PHs, bx, CR{}, by - 1, C2{}, bz, CR{});
+      out.Gfy[id] = mean(GS, bx, CR{}, by - 1, C2{}, bz, CR{});
+      out.phiexy[id] = mean(PHs, bx - 1, C2{}, by - 1, C2{}, bz, CR{});
     }
   }
 }

@@ -318,8 +318,10 @@ struct Impl : ImplBase {
     PF_CUDA_TRY(cudaFuncSetAttribute(k_rfft_x<T, FineArrPro<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
-    PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
-    PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict<T, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict<T, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict<T, 3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict<T, 3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_irfft_x<T, ChFinish<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_irfft_x<T, ArrEpi<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
   }
@@ -408,13 +410,15 @@ struct Impl : ImplBase {
     const T inv_mldt = (T)(1.0 / (p.Ml * p.dt)), inv_ml = (T)(1.0 / p.Ml);
     mark("ch_rhs");
     if (d.dim == 2) {
-      using TL = RhsTile<2>;
+      using TL = RhsTile<2, sizeof(T)>;
       dim3 grid((d.fnx + TL::TX - 1) / TL::TX, 1, (d.fnz + TL::TZ - 1) / TL::TZ);
-      k_ch_rhs<T, 2><<<grid, 256, (TL::NS + TL::NM) * sizeof(T), st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml);
+      const size_t sm = (TL::NS + TL::NM + 3 * TL::NV(d.rs, d.rys)) * sizeof(T);
+      k_ch_rhs<T, 2><<<grid, 256, sm, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml);
     } else {
-      using TL = RhsTile<3>;
+      using TL = RhsTile<3, sizeof(T)>;
       dim3 grid((d.fnx + TL::TX - 1) / TL::TX, (d.fny + TL::TY - 1) / TL::TY, (d.fnz + TL::TZ - 1) / TL::TZ);
-      k_ch_rhs<T, 3><<<grid, 256, (TL::NS + TL::NM) * sizeof(T), st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml);
+      const size_t sm = (TL::NS + TL::NM + 3 * TL::NV(d.rs, d.rys)) * sizeof(T);
+      k_ch_rhs<T, 3><<<grid, 256, sm, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml);
     }
     const int nlf = d.fny * d.fnz;
     rfft_x(FineArrPro<T>{mu, d.fnx}, spF, d.fnx, nlf, pF, plFx, twFx);
@@ -428,15 +432,16 @@ struct Impl : ImplBase {
     mark("ch_G_restrict");
     if (d.dim == 2) {
       using TL = GrTile<2>;
-      const size_t sm = ((size_t)(d.r * TL::CX + 3) * 1 * (d.r * TL::CZ + 3) + (size_t)(d.r * TL::CX + 1) * 1 * (d.r * TL::CZ + 1)) * sizeof(T);
+      const size_t sm = TL::smem_elems(d.r, 1) * sizeof(T);
       dim3 grid((d.nx + TL::CX - 1) / TL::CX, 1, (d.nz + TL::CZ - 1) / TL::CZ);
-      k_ch_G_restrict<T, 2><<<grid, 256, sm, st>>>(phi[po], gwall, rs, d, q);
+      if (d.r == 2) k_ch_G_restrict<T, 2, 2><<<grid, 256, sm, st>>>(phi[po], gwall, rs, d, q);
+      else k_ch_G_restrict<T, 2, 1><<<grid, 256, sm, st>>>(phi[po], gwall, rs, d, q);
     } else {
       using TL = GrTile<3>;
-      const size_t sm = ((size_t)(d.r * TL::CX + 3) * (d.ry * TL::CY + 3) * (d.r * TL::CZ + 3) +
-                         (size_t)(d.r * TL::CX + 1) * (d.ry * TL::CY + 1) * (d.r * TL::CZ + 1)) * sizeof(T);
+      const size_t sm = TL::smem_elems(d.r, d.ry) * sizeof(T);
       dim3 grid((d.nx + TL::CX - 1) / TL::CX, (d.ny + TL::CY - 1) / TL::CY, (d.nz + TL::CZ - 1) / TL::CZ);
-      k_ch_G_restrict<T, 3><<<grid, 256, sm, st>>>(phi[po], gwall, rs, d, q);
+      if (d.r == 2) k_ch_G_restrict<T, 3, 2><<<grid, 256, sm, st>>>(phi[po], gwall, rs, d, q);
+      else k_ch_G_restrict<T, 3, 1><<<grid, 256, sm, st>>>(phi[po], gwall, rs, d, q);
     }
     const RowLaunch lw = rows(d.ny * (d.nz + 1), d.nx);
     const RowLaunch lc = rows(d.ny * d.nz, d.nx);

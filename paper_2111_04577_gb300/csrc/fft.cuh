@@ -78,6 +78,96 @@ __device__ __forceinline__ void dft_small(cpx<T>* z, int sign) {
   }
 }
 
+// length-8 DFT (split into two length-4 DFTs of the even and odd samples)
+template <class T>
+__device__ __forceinline__ void dft8(cpx<T>* z, int sign) {
+  cpx<T> e[4] = {z[0], z[2], z[4], z[6]};
+  cpx<T> o[4] = {z[1], z[3], z[5], z[7]};
+  dft_small<T, 4>(e, sign);
+  dft_small<T, 4>(o, sign);
+  const T r = (T)0.70710678118654752440;
+  // w^q = exp(sign * 2 pi i q/8), q = 1, 2, 3
+  const cpx<T> o1 = mk<T>(r * (o[1].re - sign * o[1].im), r * (o[1].im + sign * o[1].re));
+  const cpx<T> o2 = mul_si(o[2], sign);
+  const cpx<T> o3 = mk<T>(r * (-o[3].re - sign * o[3].im), r * (-o[3].im + sign * o[3].re));
+  z[0] = e[0] + o[0];
+  z[4] = e[0] - o[0];
+  z[1] = e[1] + o1;
+  z[5] = e[1] - o1;
+  z[2] = e[2] + o2;
+  z[6] = e[2] - o2;
+  z[3] = e[3] + o3;
+  z[7] = e[3] - o3;
+}
+
+// Stockham stage with compile-time size, radix and sub-transform length (all
+// powers of two): index arithmetic reduces to shifts and masks.
+template <class T, int N, int P, int L>
+__device__ __forceinline__ void fft_stage_c(const cpx<T>* __restrict__ in, cpx<T>* __restrict__ out,
+                                            const cpx<T>* __restrict__ tw, int sign, int nl, int es, int ls,
+                                            int tid, int nth) {
+  constexpr int M = N / (L * P);
+  constexpr int NBF = N / P;
+  const int total = NBF * nl;
+  const float inl = 1.0f / (float)nl;
+  for (int id = tid; id < total; id += nth) {
+    int l, bf;
+    if (es == 1) {
+      l = id / NBF;
+      bf = id - l * NBF;
+    } else {
+      bf = qdiv(id, nl, inl);
+      l = id - bf * nl;
+    }
+    const int j = bf / M, k = bf - j * M;
+    const cpx<T>* src = in + (size_t)l * ls;
+    cpx<T>* dst = out + (size_t)l * ls;
+    cpx<T> z[P];
+#pragma unroll
+    for (int c = 0; c < P; ++c) {
+      cpx<T> v = src[(size_t)(j * M * P + k + c * M) * es];
+      if (L > 1 && c > 0) {
+        cpx<T> w = tw[c * j * M];
+        if (sign > 0) w.im = -w.im;
+        v = v * w;
+      }
+      z[c] = v;
+    }
+    if constexpr (P == 8) dft8<T>(z, sign);
+    else dft_small<T, P>(z, sign);
+#pragma unroll
+    for (int q = 0; q < P; ++q) dst[(size_t)((j + L * q) * M + k) * es] = z[q];
+  }
+}
+
+// radix-8 stages, then one radix-4 or radix-2 stage if N is not a power of 8
+template <class T, int N, int L>
+__device__ __forceinline__ cpx<T>* fft_pow2_run(cpx<T>* in, cpx<T>* out, const cpx<T>* tw, int sign, int nl, int es,
+                                                int ls) {
+  if constexpr (L >= N) {
+    return in;
+  } else {
+    constexpr int REM = N / L;
+    constexpr int P = REM % 8 == 0 ? 8 : (REM % 4 == 0 ? 4 : 2);
+    fft_stage_c<T, N, P, L>(in, out, tw, sign, nl, es, ls, threadIdx.x, blockDim.x);
+    __syncthreads();
+    return fft_pow2_run<T, N, L * P>(out, in, tw, sign, nl, es, ls);
+  }
+}
+
+template <class T>
+__device__ __forceinline__ cpx<T>* fft_pow2(cpx<T>* a, cpx<T>* b, int n, const cpx<T>* tw, int sign, int nl, int es,
+                                            int ls) {
+  switch (n) {
+    case 64: return fft_pow2_run<T, 64, 1>(a, b, tw, sign, nl, es, ls);
+    case 128: return fft_pow2_run<T, 128, 1>(a, b, tw, sign, nl, es, ls);
+    case 256: return fft_pow2_run<T, 256, 1>(a, b, tw, sign, nl, es, ls);
+    case 512: return fft_pow2_run<T, 512, 1>(a, b, tw, sign, nl, es, ls);
+    case 1024: return fft_pow2_run<T, 1024, 1>(a, b, tw, sign, nl, es, ls);
+    default: return nullptr;
+  }
+}
+
 // One Stockham stage of radix P over nl lines.  Element n of line l sits at
 // base[l*ls + n*es].  tw[m] = exp(-2 pi i m/n), m < n.
 template <class T, int P>
@@ -123,6 +213,7 @@ template <class T>
 __device__ cpx<T>* fft_lines(cpx<T>* a, cpx<T>* b, const FftPlan& pl, const cpx<T>* tw, int sign, int nl,
                              int es, int ls) {
   const int tid = threadIdx.x, nth = blockDim.x;
+  if (pl.n >= 64 && pl.n <= 1024 && (pl.n & (pl.n - 1)) == 0) return fft_pow2<T>(a, b, pl.n, tw, sign, nl, es, ls);
   int L = 1;
   cpx<T>* in = a;
   cpx<T>* out = b;

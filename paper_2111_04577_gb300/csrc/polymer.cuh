@@ -33,6 +33,42 @@ __device__ __forceinline__ double dexpm1<double>(double d) {
   return d / expm1(d);
 }
 
+template <class T>
+__device__ __forceinline__ T fexp(T x) { return exp(x); }
+template <>
+__device__ __forceinline__ float fexp<float>(float x) { return __expf(x); }
+
+// one Jacobi rotation zeroing A[p][q] (A symmetric, full storage), V <- V J
+template <class T, int N>
+__device__ __forceinline__ void jacobi_rot(T A[N][N], T V[N][N], int p, int q) {
+  const T apq = A[p][q];
+  if (apq == (T)0) return;
+  const T th = (A[q][q] - A[p][p]) / (2 * apq);
+  const T ath = fabs(th);
+  // t = sgn(th)/(|th| + sqrt(th^2 + 1)), the smaller root; 1/(2 th) when th^2 would overflow
+  T t = ath > (T)1e15 ? (T)0.5 / ath : (T)1 / (ath + sqrt(ath * ath + (T)1));
+  if (th < 0) t = -t;
+  const T c = (T)1 / sqrt(t * t + (T)1), s = t * c;
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    const T arp = A[r][p], arq = A[r][q];
+    A[r][p] = c * arp - s * arq;
+    A[r][q] = s * arp + c * arq;
+  }
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    const T apr = A[p][r], aqr = A[q][r];
+    A[p][r] = c * apr - s * aqr;
+    A[q][r] = s * apr + c * aqr;
+  }
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+    const T vrp = V[r][p], vrq = V[r][q];
+    V[r][p] = c * vrp - s * vrq;
+    V[r][q] = s * vrp + c * vrq;
+  }
+}
+
 // symmetric eigen-decomposition A = V diag(w) V^T by cyclic Jacobi rotations
 template <class T, int N>
 __device__ __forceinline__ void eig_sym(T A[N][N], T w[N], T V[N][N]) {
@@ -40,8 +76,9 @@ __device__ __forceinline__ void eig_sym(T A[N][N], T w[N], T V[N][N]) {
   for (int a = 0; a < N; ++a)
 #pragma unroll
     for (int b = 0; b < N; ++b) V[a][b] = (a == b) ? (T)1 : (T)0;
-  const T eps = sizeof(T) == 4 ? (T)1e-7 : (T)1e-15;
-  for (int sweep = 0; sweep < 10; ++sweep) {
+  const T eps2 = sizeof(T) == 4 ? (T)1e-14 : (T)1e-30;
+#pragma unroll 1
+  for (int sweep = 0; sweep < (sizeof(T) == 4 ? 6 : 10); ++sweep) {
     T off = 0, dia = 0;
 #pragma unroll
     for (int a = 0; a < N; ++a) {
@@ -49,36 +86,13 @@ __device__ __forceinline__ void eig_sym(T A[N][N], T w[N], T V[N][N]) {
 #pragma unroll
       for (int b = a + 1; b < N; ++b) off += A[a][b] * A[a][b];
     }
-    if (off <= eps * eps * dia || off == (T)0) break;
-#pragma unroll
-    for (int p = 0; p < N - 1; ++p) {
-#pragma unroll
-      for (int q = p + 1; q < N; ++q) {
-        const T apq = A[p][q];
-        if (apq == (T)0) continue;
-        const T th = (A[q][q] - A[p][p]) / (2 * apq);
-        const T t = (th >= 0 ? (T)1 : (T)-1) / (fabs(th) + sqrt(th * th + (T)1));
-        const T c = (T)1 / sqrt(t * t + (T)1), s = t * c;
-        // A <- J^T A J with J the (p, q) rotation
-#pragma unroll
-        for (int r = 0; r < N; ++r) {
-          const T arp = A[r][p], arq = A[r][q];
-          A[r][p] = c * arp - s * arq;
-          A[r][q] = s * arp + c * arq;
-        }
-#pragma unroll
-        for (int r = 0; r < N; ++r) {
-          const T apr = A[p][r], aqr = A[q][r];
-          A[p][r] = c * apr - s * aqr;
-          A[q][r] = s * apr + c * aqr;
-        }
-#pragma unroll
-        for (int r = 0; r < N; ++r) {
-          const T vrp = V[r][p], vrq = V[r][q];
-          V[r][p] = c * vrp - s * vrq;
-          V[r][q] = s * vrp + c * vrq;
-        }
-      }
+    if (off <= eps2 * dia || off == (T)0) break;
+    if (N == 2) {
+      jacobi_rot<T, N>(A, V, 0, 1);
+    } else {
+      jacobi_rot<T, N>(A, V, 0, 1);
+      jacobi_rot<T, N>(A, V, 0, N - 1);
+      jacobi_rot<T, N>(A, V, 1, N - 1);
     }
   }
 #pragma unroll
@@ -106,7 +120,7 @@ __device__ __forceinline__ int comp_of(int a, int b) {
 
 template <class T, int N>
 __global__ void k_polymer(PolyIn<T> P, Dims d, PhysT<T> q, int stage) {
-  const size_t plane = (size_t)d.nx * d.ny;
+  const int plane = d.nx * d.ny;
   const T iD = q.iD;
   const T dt = q.dt, ilh = q.ilh;
   constexpr int NC = N == 2 ? 3 : 6;
@@ -114,8 +128,8 @@ __global__ void k_polymer(PolyIn<T> P, Dims d, PhysT<T> q, int stage) {
   if (!row_index(d.nx, d.ny, x)) return;
   {
     const int i = x.i, j = x.j, k = x.k;
-    const size_t id = (size_t)x.row * d.nx + i;
-    auto C = [&](int ii, int jj, int kk) { return ((size_t)kk * d.ny + wrap(jj, d.ny)) * d.nx + wrap(ii, d.nx); };
+    const int id = x.row * d.nx + i;
+    auto C = [&](int ii, int jj, int kk) { return (kk * d.ny + wrap(jj, d.ny)) * d.nx + wrap(ii, d.nx); };
     // velocity gradient L[a][b] = du_a/dx_b (Eq. NS23 uses its transpose convention)
     auto uc = [&](int ii, int jj, int kk) -> T {  // centre-averaged u, ghosts at walls
       if (kk < 0) return q.uw2_bot - (T)0.5 * (P.u[C(ii, jj, 0)] + P.u[C(ii + 1, jj, 0)]);
@@ -152,7 +166,7 @@ __global__ void k_polymer(PolyIn<T> P, Dims d, PhysT<T> q, int stage) {
     {
       const T ul = P.u[id], ur = P.u[C(i + 1, j, k)];
       const T wb = P.w[id], wt = P.w[id + plane];
-      const size_t xm = C(i - 1, j, k), xp = C(i + 1, j, k);
+      const int xm = C(i - 1, j, k), xp = C(i + 1, j, k);
 #pragma unroll
       for (int cq = 0; cq < NC; ++cq) {
         const T t0 = P.th[cq][id];
@@ -197,13 +211,13 @@ __global__ void k_polymer(PolyIn<T> P, Dims d, PhysT<T> q, int stage) {
     T H[N][N];
 #pragma unroll
     for (int a = 0; a < N; ++a) {
-      H[a][a] = 2 * Mt[a][a] + (exp(-th[a]) - (T)1) * ilh;
+      H[a][a] = 2 * Mt[a][a] + (fexp<T>(-th[a]) - (T)1) * ilh;
 #pragma unroll
       for (int b = a + 1; b < N; ++b) {
         const T dd = th[b] - th[a];
         T o;
-        if (dd > 0) o = (Mt[a][b] + exp(-dd) * Mt[b][a]) * dexpm1<T>(-dd);
-        else o = (exp(dd) * Mt[a][b] + Mt[b][a]) * dexpm1<T>(dd);
+        if (dd > 0) o = (Mt[a][b] + fexp<T>(-dd) * Mt[b][a]) * dexpm1<T>(-dd);
+        else o = (fexp<T>(dd) * Mt[a][b] + Mt[b][a]) * dexpm1<T>(dd);
         H[a][b] = o;
         H[b][a] = o;
       }
@@ -248,7 +262,7 @@ __global__ void k_polymer(PolyIn<T> P, Dims d, PhysT<T> q, int stage) {
         for (int b = a; b < N; ++b) {
           T s = 0;
 #pragma unroll
-          for (int c = 0; c < N; ++c) s += R[a][c] * exp(th[c]) * R[b][c];
+          for (int c = 0; c < N; ++c) s += R[a][c] * fexp<T>(th[c]) * R[b][c];
           P.tau[comp_of<N>(a, b)][id] = wgt * (s - (a == b ? (T)1 : (T)0));
         }
     }
