@@ -168,6 +168,29 @@ int pf_diagnostics(pf_ctx* ctx, double out[6]);
 int pf_profile(pf_ctx* ctx, int nsteps, int flags, int max_entries, char* names, double* avg_ms,
                int* counts, int* n_entries, int* launches_per_step);
 
+/* ------------------------------------------------------------------------
+ * Batched sweep: many independent two-dimensional problems of uneven size
+ * (each its own grid and parameters, one precision for all), advanced
+ * together by ONE persistent kernel launch per time step, replayed from a
+ * CUDA graph.  Each problem takes exactly the step of pf_step (same kernels'
+ * device code, same order of Section 3.2); the persistent CTAs walk a
+ * pass-major list of (problem, pass, tile) items and wait, with a bounded
+ * spin, for the previous pass of the same problem.  A wait that runs out
+ * makes pf_batch_step return PF_ERR_TIMEOUT (the status is sticky).
+ * Field access and diagnostics take a problem index 0..nproblems-1 and
+ * behave as pf_set_fields / pf_get_fields / pf_diagnostics on that problem.
+ * ------------------------------------------------------------------------ */
+typedef struct pf_batch pf_batch;
+int pf_batch_create(pf_batch** out, int nproblems, const pf_grid_desc* grids, const pf_params* params,
+                    void* stream);
+int pf_batch_field_info(const pf_batch* b, int problem, int field_id, size_t* count, size_t* elem_bytes);
+int pf_batch_set_fields(pf_batch* b, int problem, int field_id, const void* src, size_t bytes, int src_on_device);
+int pf_batch_get_fields(pf_batch* b, int problem, int field_id, void* dst, size_t bytes, int dst_on_device);
+int pf_batch_step(pf_batch* b, int nsteps);
+int pf_batch_diagnostics(pf_batch* b, int problem, double out[6]);
+const char* pf_batch_last_error(const pf_batch* b);
+void pf_batch_destroy(pf_batch* b);
+
 /* Allocation-free diagnostics.  The paper has no counterpart: this is a
  * service for callers that may not allocate device memory (an application
  * whose memory pool owns the whole GPU, an allocator that forbids

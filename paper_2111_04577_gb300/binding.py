@@ -25,7 +25,8 @@ ERRORS = {-1: "PF_ERR_ARG", -2: "PF_ERR_DISCRIMINANT", -3: "PF_ERR_UNSUPPORTED",
 
 EXPORTS = ["pf_init_grid", "pf_set_params", "pf_field_info", "pf_set_fields", "pf_step", "pf_step_ex",
            "pf_get_fields", "pf_diagnostics", "pf_profile", "pf_diagnostics_noalloc", "pf_last_error",
-           "pf_destroy"]
+           "pf_destroy", "pf_batch_create", "pf_batch_field_info", "pf_batch_set_fields", "pf_batch_get_fields",
+           "pf_batch_step", "pf_batch_diagnostics", "pf_batch_last_error", "pf_batch_destroy"]
 PROFILE_NAME = 48
 
 
@@ -69,6 +70,19 @@ def load(path: str = LIB_PATH):
         lib.pf_diagnostics_noalloc.argtypes = [C.POINTER(GridDesc), C.POINTER(ParamsC), vp,
                                                C.POINTER(C.c_double), vp]
         lib.pf_diagnostics_noalloc.restype = C.c_int
+        lib.pf_batch_create.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(GridDesc), C.POINTER(ParamsC), vp]
+        lib.pf_batch_field_info.argtypes = [vp, C.c_int, C.c_int, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]
+        lib.pf_batch_set_fields.argtypes = [vp, C.c_int, C.c_int, vp, C.c_size_t, C.c_int]
+        lib.pf_batch_get_fields.argtypes = [vp, C.c_int, C.c_int, vp, C.c_size_t, C.c_int]
+        lib.pf_batch_step.argtypes = [vp, C.c_int]
+        lib.pf_batch_diagnostics.argtypes = [vp, C.c_int, C.POINTER(C.c_double)]
+        lib.pf_batch_last_error.argtypes = [vp]
+        lib.pf_batch_last_error.restype = C.c_char_p
+        lib.pf_batch_destroy.argtypes = [vp]
+        lib.pf_batch_destroy.restype = None
+        for f in ("pf_batch_create", "pf_batch_field_info", "pf_batch_set_fields", "pf_batch_get_fields",
+                  "pf_batch_step", "pf_batch_diagnostics"):
+            getattr(lib, f).restype = C.c_int
         lib.pf_last_error.argtypes = [vp]
         lib.pf_last_error.restype = C.c_char_p
         lib.pf_destroy.argtypes = [vp]
@@ -213,3 +227,61 @@ class Solver:
             nc = 3 if g.dim == 2 else 6
             return a.reshape(nc, nz, ny, nx)
         return a.reshape(nz, ny, nx)
+
+
+class Batch:
+    """Many independent 2D problems advanced by one persistent launch per step."""
+
+    def __init__(self, grids, params, precision=PF_MIXED, stream=None):
+        self.lib = load()
+        n = len(grids)
+        self.grids = list(grids)
+        self.dtype = np.float64 if precision == PF_FP64 else np.float32
+        gd = (GridDesc * n)(*[GridDesc(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, precision, g.dual) for g in grids])
+        pr = (ParamsC * n)(*[ParamsC(**p.as_dict()) for p in params])
+        h = C.c_void_p()
+        rc = self.lib.pf_batch_create(C.byref(h), n, gd, pr, C.c_void_p(stream or 0))
+        if rc != 0:
+            raise PFError(rc, self.lib.pf_batch_last_error(None).decode())
+        self.h = h
+
+    def _chk(self, rc):
+        if rc != 0:
+            raise PFError(rc, self.lib.pf_batch_last_error(self.h).decode())
+
+    def info(self, b, name):
+        cnt, eb = C.c_size_t(), C.c_size_t()
+        self._chk(self.lib.pf_batch_field_info(self.h, b, FIELD[name], C.byref(cnt), C.byref(eb)))
+        return cnt.value, eb.value
+
+    def set(self, b, name, arr):
+        cnt, eb = self.info(b, name)
+        a = np.ascontiguousarray(arr, dtype=self.dtype)
+        if a.size != cnt:
+            raise ValueError(f"{name}: {a.size} elements, expected {cnt}")
+        self._chk(self.lib.pf_batch_set_fields(self.h, b, FIELD[name], a.ctypes.data_as(C.c_void_p), cnt * eb, 0))
+
+    def get(self, b, name):
+        cnt, eb = self.info(b, name)
+        a = np.empty(cnt, dtype=self.dtype)
+        self._chk(self.lib.pf_batch_get_fields(self.h, b, FIELD[name], a.ctypes.data_as(C.c_void_p), cnt * eb, 0))
+        return a
+
+    def step(self, n=1):
+        self._chk(self.lib.pf_batch_step(self.h, int(n)))
+
+    def diagnostics(self, b):
+        out = (C.c_double * 6)()
+        self._chk(self.lib.pf_batch_diagnostics(self.h, b, out))
+        return dict(mass=out[0], energy=out[1], wetted=out[2], centroid=(out[3], out[4], out[5]))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pf_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -45,18 +45,15 @@ struct RhsTile {
 };
 
 template <class T, int DIM>
-__global__ void __launch_bounds__(256) k_ch_rhs(const FineView<T> f, const CoarseVel<T> vel, T* __restrict__ R,
-                                                double* __restrict__ gwall, const Dims d, const Phys p,
-                                                const PhysT<T> q, const T inv_mldt, const T inv_ml) {
+__device__ __forceinline__ void k_ch_rhs_b(const FineView<T> f, const CoarseVel<T> vel, T* __restrict__ R, double* __restrict__ gwall, const Dims d, const Phys p, const PhysT<T> q, const T inv_mldt, const T inv_ml, const int3 bid, unsigned char* smraw) {
   using TL = RhsTile<DIM, sizeof(T)>;
-  extern __shared__ __align__(16) unsigned char smraw[];
   T* ps = reinterpret_cast<T*>(smraw);  // phi*, [SZ][SY][SX]
   T* ms = ps + TL::NS;                  // mu*,  [MZ][MY][MX]
   const int VX = TL::VX(d.rs), VY = TL::VY(d.rys), VZ = TL::VZ(d.rs), NV = VX * VY * VZ;
   T* us = ms + TL::NM;                  // u*, v*, w* on the coarse box [VZ][VY][VX]
   T* vs = us + NV;
   T* wsm = vs + NV;
-  const int x0 = blockIdx.x * TL::TX, y0 = blockIdx.y * TL::TY, z0 = blockIdx.z * TL::TZ;
+  const int x0 = bid.x * TL::TX, y0 = bid.y * TL::TY, z0 = bid.z * TL::TZ;
   const int fnx = d.fnx, fny = d.fny, fnz = d.fnz;
   const size_t plane = (size_t)fnx * fny;
   const bool smallx = fnx < TL::SX, smally = fny < TL::SY;  // tile wider than the domain
@@ -178,6 +175,12 @@ __global__ void __launch_bounds__(256) k_ch_rhs(const FineView<T> f, const Coars
   }
 }
 
+template <class T, int DIM>
+__global__ void __launch_bounds__(256) k_ch_rhs(const FineView<T> f, const CoarseVel<T> vel, T* __restrict__ R, double* __restrict__ gwall, const Dims d, const Phys p, const PhysT<T> q, const T inv_mldt, const T inv_ml) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  k_ch_rhs_b<T, DIM>(f, vel, R, gwall, d, p, q, inv_mldt, inv_ml, make_int3(blockIdx.x, blockIdx.y, blockIdx.z), smraw);
+}
+
 // ---------------------------------------------------------------------------
 template <int DIM>
 struct GrTile {
@@ -198,17 +201,15 @@ struct GrTile {
 };
 
 template <class T, int DIM, int R>
-__global__ void __launch_bounds__(256) k_ch_G_restrict(const T* __restrict__ phi, const double* __restrict__ gwall,
-                                                       Restricted<T> out, const Dims d, const PhysT<T> q) {
+__device__ __forceinline__ void k_ch_G_restrict_b(const T* __restrict__ phi, const double* __restrict__ gwall, Restricted<T> out, const Dims d, const PhysT<T> q, const int3 bid, unsigned char* smraw) {
   using TL = GrTile<DIM>;
   constexpr int RY = DIM == 3 ? R : 1;
   constexpr int GX = TL::GX(R), GY = TL::GY(RY), GZ = TL::GZ(R);
   constexpr int PX = TL::PX(R), PY = TL::PY(RY), PZ = TL::PZ(R);
   constexpr int HY = DIM == 3 ? 1 : 0;
-  extern __shared__ __align__(16) unsigned char smraw[];
   T* ph = reinterpret_cast<T*>(smraw);  // [PZ][PY][PX], z clamped at the walls (mirror ghosts)
   T* gs = ph + PX * PY * PZ;            // [GZ][GY][GX], G of the (mirrored) sample
-  const int cx0 = blockIdx.x * TL::CX, cy0 = blockIdx.y * TL::CY, cz0 = blockIdx.z * TL::CZ;
+  const int cx0 = bid.x * TL::CX, cy0 = bid.y * TL::CY, cz0 = bid.z * TL::CZ;
   const int fnx = d.fnx, fny = d.fny, fnz = d.fnz;
   const size_t plane = (size_t)fnx * fny;
   const int fx0 = R * cx0 - 1, fy0 = DIM == 3 ? RY * cy0 - 1 : 0, fz0 = R * cz0 - 1;  // G-block origin
@@ -298,6 +299,12 @@ __global__ void __launch_bounds__(256) k_ch_G_restrict(const T* __restrict__ phi
       out.phiexy[id] = mean(PHs, bx - 1, C2{}, by - 1, C2{}, bz, CR{});
     }
   }
+}
+
+template <class T, int DIM, int R>
+__global__ void __launch_bounds__(256) k_ch_G_restrict(const T* __restrict__ phi, const double* __restrict__ gwall, Restricted<T> out, const Dims d, const PhysT<T> q) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  k_ch_G_restrict_b<T, DIM, R>(phi, gwall, out, d, q, make_int3(blockIdx.x, blockIdx.y, blockIdx.z), smraw);
 }
 
 }  // namespace pf

@@ -81,13 +81,16 @@ struct PhysT {
 struct RowIdx {
   int i, j, k, row;
 };
-__device__ __forceinline__ bool row_index(int nxrow, int nyrow, RowIdx& r) {
-  r.row = blockIdx.x;
-  r.i = blockIdx.y * blockDim.x + threadIdx.x;
+__device__ __forceinline__ bool row_index_b(const int3 bid, int nxrow, int nyrow, RowIdx& r) {
+  r.row = bid.x;
+  r.i = bid.y * blockDim.x + threadIdx.x;
   if (r.i >= nxrow) return false;
   r.k = r.row / nyrow;
   r.j = r.row - r.k * nyrow;
   return true;
+}
+__device__ __forceinline__ bool row_index(int nxrow, int nyrow, RowIdx& r) {
+  return row_index_b(make_int3(blockIdx.x, blockIdx.y, blockIdx.z), nxrow, nyrow, r);
 }
 
 // Exact quotient of 0 <= x < 2^22 by 1 <= d using a float reciprocal (one

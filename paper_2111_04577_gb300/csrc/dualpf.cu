@@ -8,6 +8,7 @@
 // chemical potential and restriction (Eqs. NS5, dual2, dual3), the NS
 // projection step (Eqs. NS35-NS39) and the polymer (Eqs. NS40-NS46).  Time
 // levels rotate by pointer parity, never by copies.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -25,6 +26,7 @@
 #include "polymer.cuh"
 #include "reduce.cuh"
 #include "spectral.cuh"
+#include "batch.cuh"
 
 namespace pf {
 
@@ -313,7 +315,6 @@ struct Impl : ImplBase {
   void set_smem_limits() {
     PF_CUDA_TRY(cudaFuncSetAttribute(k_fft_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_zsolve<T, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
-    PF_CUDA_TRY(cudaFuncSetAttribute(k_rfft_x<T, ChRhs<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_rfft_x<T, ArrPro<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_rfft_x<T, FineArrPro<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
@@ -403,7 +404,6 @@ struct Impl : ImplBase {
 
   void launch_step(int flags) {
     const int po = pc ^ 1, fo = fc ^ 1;
-    const size_t nf = (size_t)d.fnx * d.fny * d.fnz;
     // ---- Cahn-Hilliard on the fine mesh ----
     FineView<T> fv{phi[pc], phi[po]};
     const CoarseVel<T> vel{u[fc], u[fo], v[fc], v[fo], w[fc], w[fo]};
@@ -737,6 +737,247 @@ struct Impl : ImplBase {
   }
 };
 
+
+// ---------------------------------------------------------------------------
+// batched sweep of independent 2D problems (one persistent launch per step)
+// ---------------------------------------------------------------------------
+struct BatchBase {
+  virtual ~BatchBase() {}
+  virtual ImplBase* problem(int i) = 0;
+  virtual int count() const = 0;
+  virtual void step(int nsteps) = 0;
+};
+
+template <class T>
+struct Batch : BatchBase {
+  std::vector<std::unique_ptr<Impl<T, T>>> probs;
+  cudaStream_t st;
+  Arena ar;
+  BatchProb<T>* d_probs = nullptr;
+  BatchItem* d_items = nullptr;
+  int nitems = 0;
+  int* d_done = nullptr;
+  int* d_head = nullptr;
+  size_t smem = 0;
+  int grid = 0;
+  int pc = 0, fc = 0;
+  std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+  static constexpr long long kSpin = 1ll << 24;
+
+  Batch(int n, const pf_grid_desc* g, const pf_params* prm, cudaStream_t s) : st(s) {
+    if (n < 1) throw ApiError(PF_ERR_ARG, "a batch needs at least one problem");
+    for (int i = 0; i < n; ++i) {
+      if (g[i].ny != 1) throw ApiError(PF_ERR_UNSUPPORTED, "batched problems must be two-dimensional (ny = 1)");
+      if (g[i].precision != g[0].precision) throw ApiError(PF_ERR_ARG, "all batched problems share one precision");
+      probs.emplace_back(new Impl<T, T>(g[i], st));
+      probs.back()->set_params(prm[i]);
+    }
+    build();
+  }
+  ~Batch() override {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+  }
+  ImplBase* problem(int i) override { return probs.at(i).get(); }
+  int count() const override { return (int)probs.size(); }
+
+  void build() {
+    const int n = (int)probs.size();
+    std::vector<BatchProb<T>> hp(n);
+    std::vector<BatchItem> items;
+    size_t maxsm = 0;
+    const int tx = sizeof(T) == 4 ? 32 : 16;
+    for (int b = 0; b < n; ++b) {
+      Impl<T, T>& I = *probs[b];
+      BatchProb<T>& B = hp[b];
+      const Dims& d = I.d;
+      B.d = d;
+      B.p = I.p;
+      B.q = I.q;
+      B.inv_mldt = (T)(1.0 / (I.p.Ml * I.p.dt));
+      B.inv_ml = (T)(1.0 / I.p.Ml);
+      B.div_coef = (T)(I.p.gamma0 * I.p.rho0 / I.p.dt);
+      B.corr_coef = (T)(I.p.dt / (I.p.gamma0 * I.p.rho0));
+      for (int k = 0; k < 2; ++k) {
+        B.phi[k] = I.phi[k];
+        B.u[k] = I.u[k];
+        B.v[k] = I.v[k];
+        B.w[k] = I.w[k];
+        B.pr[k] = I.pr[k];
+      }
+      B.R = I.mu;
+      B.ru = I.ru;
+      B.rw = I.rw;
+      B.wt = I.wt;
+      B.pp = I.pp;
+      B.dv = I.dv;
+      B.gwall = I.gwall;
+      B.zwork = I.zwork;
+      B.rs = I.rs;
+      B.spF = I.spF;
+      B.spU = I.spU;
+      B.spW = I.spW;
+      B.spP = I.spP;
+      B.pF = I.pF;
+      B.pC = I.pC;
+      B.npairF = std::max(1, 1024 / d.fnx);
+      B.npairC = std::max(1, 1024 / d.nx);
+      B.tx = tx;
+      B.plFx = I.plFx;
+      B.plCx = I.plCx;
+      B.twFx = I.twFx;
+      B.twCx = I.twCx;
+      B.eFx = I.eFx;
+      B.eFy = I.eFy;
+      B.eCx = I.eCx;
+      B.eCy = I.eCy;
+      B.visco = I.p.visco;
+      auto zs = [&](int rows, int pitch, int ncol, int bc, double h2, double s1, double s2, bool two, double scale,
+                    bool poisson) {
+        ZSolve z{};
+        z.rows = rows;
+        z.ny = 1;
+        z.pitch = pitch;
+        z.ncol = ncol;
+        z.bc = bc;
+        z.two = two ? 1 : 0;
+        z.same = (!two || std::fabs(s1 - s2) <= 1e-14 * std::fabs(s1)) ? 1 : 0;
+        z.skip_zero = poisson ? 1 : 0;
+        z.h2 = h2;
+        z.shift1 = s1;
+        z.shift2 = s2;
+        z.scale = scale;
+        return z;
+      };
+      const double kk = I.p.gamma0 / (I.p.dt * I.p.nu_m);
+      B.zpair = zs(d.fnz, I.pF, d.fnx / 2 + 1, Z_NEUMANN, d.h * d.h, I.p.c, -I.p.alpha, true, 1.0 / d.fnx, false);
+      B.zu = zs(d.nz, I.pC, d.nx / 2 + 1, Z_DIRICH, d.dx * d.dx, kk, kk, false, 1.0 / d.nx, false);
+      B.zw = zs(d.nz - 1, I.pC, d.nx / 2 + 1, Z_FACES, d.dx * d.dx, kk, kk, false, 1.0 / d.nx, false);
+      B.zp = zs(d.nz, I.pC, d.nx / 2 + 1, Z_NEUMANN, d.dx * d.dx, 0.0, 0.0, false, 1.0 / d.nx, true);
+      for (int f = 0; f < 2; ++f) {
+        const int fo = f ^ 1;
+        NsIn<T>& A = B.ns[f];
+        A.un = I.u[f];
+        A.uo = I.u[fo];
+        A.vn = I.v[f];
+        A.vo = I.v[fo];
+        A.wn = I.w[f];
+        A.wo = I.w[fo];
+        A.pn = I.pr[f];
+        A.po = I.pr[fo];
+        for (int c = 0; c < 6; ++c) {
+          A.tn[c] = I.tau[f][c];
+          A.to[c] = I.tau[fo][c];
+        }
+        A.rs = I.rs;
+        for (int stg = 0; stg < 2; ++stg) {
+          PolyIn<T>& P = B.poly[f][stg];
+          P = PolyIn<T>{};
+          P.u = I.u[fo];  // the corrected velocity u^{n+1} lives in the n-1 buffer
+          P.v = I.v[fo];
+          P.w = I.w[fo];
+          P.phic = I.rs.phic;
+          for (int c = 0; c < I.ncomp; ++c) {
+            P.th[c] = stg == 0 ? I.theta[c] : I.theta1[c];
+            P.out[c] = stg == 0 ? I.theta1[c] : I.theta[c];
+            P.base[c] = I.theta[c];
+            P.tau[c] = I.tau[fo][c];
+          }
+        }
+      }
+      // grids of every pass (the launch shapes of the single-problem path)
+      using TR = RhsTile<2, sizeof(T)>;
+      using TG = GrTile<2>;
+      auto cdiv = [](int a, int b) { return (a + b - 1) / b; };
+      const int rowsx = cdiv(d.nx, 256);
+      B.gdim[BP_CH_RHS] = make_int3(cdiv(d.fnx, TR::TX), 1, cdiv(d.fnz, TR::TZ));
+      B.gdim[BP_RFFT_F] = make_int3(cdiv(cdiv(d.fnz, 2), B.npairF), 1, 1);
+      B.gdim[BP_ZPAIR] = make_int3(cdiv(d.fnx / 2 + 1, tx), 1, 1);
+      B.gdim[BP_IFFT_F] = B.gdim[BP_RFFT_F];
+      B.gdim[BP_GRES] = make_int3(cdiv(d.nx, TG::CX), 1, cdiv(d.nz, TG::CZ));
+      B.gdim[BP_NSRHS] = make_int3(d.nz, rowsx, 1);
+      B.gdim[BP_U_RFFT] = make_int3(cdiv(cdiv(d.nz, 2), B.npairC), 1, 1);
+      B.gdim[BP_U_Z] = make_int3(cdiv(d.nx / 2 + 1, tx), 1, 1);
+      B.gdim[BP_U_IFFT] = B.gdim[BP_U_RFFT];
+      B.gdim[BP_W_RFFT] = make_int3(cdiv(cdiv(d.nz - 1, 2), B.npairC), 1, 1);
+      B.gdim[BP_W_Z] = B.gdim[BP_U_Z];
+      B.gdim[BP_W_IFFT] = B.gdim[BP_W_RFFT];
+      B.gdim[BP_DIV] = make_int3(d.nz, rowsx, 1);
+      B.gdim[BP_P_RFFT] = B.gdim[BP_U_RFFT];
+      B.gdim[BP_P_Z] = B.gdim[BP_U_Z];
+      B.gdim[BP_P_ZERO] = make_int3(1, 1, 1);
+      B.gdim[BP_P_IFFT] = B.gdim[BP_U_RFFT];
+      B.gdim[BP_CORR] = make_int3(d.nz + 1, rowsx, 1);
+      B.gdim[BP_POLY1] = B.visco ? make_int3(d.nz, rowsx, 1) : make_int3(0, 1, 1);
+      B.gdim[BP_POLY2] = B.gdim[BP_POLY1];
+      for (int ps = 0; ps < BP_N; ++ps) B.ntiles[ps] = B.gdim[ps].x * B.gdim[ps].y * B.gdim[ps].z;
+      // shared memory of the largest pass
+      auto zsm = [&](const ZSolve& z) { return (size_t)z.rows * tx * (sizeof(cpx<T>) + sizeof(T) * (z.same ? 1 : 2)); };
+      maxsm = std::max(maxsm, (size_t)(TR::NS + TR::NM + 3 * TR::NV(d.rs, 0)) * sizeof(T));
+      maxsm = std::max(maxsm, 2 * (size_t)B.npairF * d.fnx * sizeof(cpx<T>));
+      maxsm = std::max(maxsm, 2 * (size_t)B.npairC * d.nx * sizeof(cpx<T>));
+      maxsm = std::max(maxsm, (size_t)TG::smem_elems(d.r, 1) * sizeof(T));
+      maxsm = std::max({maxsm, zsm(B.zpair), zsm(B.zu), zsm(B.zw), zsm(B.zp)});
+    }
+    // pass-major work list
+    for (int ps = 0; ps < BP_N; ++ps)
+      for (int b = 0; b < n; ++b)
+        for (int t = 0; t < hp[b].ntiles[ps]; ++t) items.push_back(BatchItem{b, ps, t});
+    nitems = (int)items.size();
+    d_probs = ar.get<BatchProb<T>>(n);
+    d_items = ar.get<BatchItem>(items.size());
+    d_done = ar.get<int>((size_t)n * BP_N);
+    d_head = ar.get<int>(2);  // [0] work head (reset every step), [1] sticky status
+    PF_CUDA_TRY(cudaMemcpy(d_probs, hp.data(), n * sizeof(BatchProb<T>), cudaMemcpyHostToDevice));
+    PF_CUDA_TRY(cudaMemcpy(d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice));
+    smem = maxsm;
+    if (smem > 200 * 1024) throw ApiError(PF_ERR_UNSUPPORTED, "batched problem too large for one persistent CTA");
+    PF_CUDA_TRY(cudaFuncSetAttribute(k_batch_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per = 0, dev = 0, nsm = 0;
+    PF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_step<T>, 256, smem));
+    PF_CUDA_TRY(cudaGetDevice(&dev));
+    PF_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    grid = std::max(1, per) * nsm;
+  }
+
+  void launch(int p_c, int f_c) {
+    PF_CUDA_TRY(cudaMemsetAsync(d_done, 0, probs.size() * BP_N * sizeof(int), st));
+    PF_CUDA_TRY(cudaMemsetAsync(d_head, 0, sizeof(int), st));
+    // the kernel's ctl[0] is the work head, ctl[1] the sticky status: both in one array
+    k_batch_step<T><<<grid, 256, smem, st>>>(d_probs, d_items, nitems, d_done, d_head, p_c, f_c, kSpin);
+  }
+
+  void step(int nsteps) override {
+    for (int s = 0; s < nsteps; ++s) {
+      auto key = std::make_pair(pc, fc);
+      auto it = graphs.find(key);
+      if (it == graphs.end()) {
+        cudaGraph_t gr;
+        PF_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        launch(pc, fc);
+        cudaError_t le = cudaGetLastError();
+        cudaError_t ce = cudaStreamEndCapture(st, &gr);
+        if (le != cudaSuccess) throw CudaError(le, "batch launch during capture", __FILE__, __LINE__);
+        PF_CUDA_TRY(ce);
+        cudaGraphExec_t ex;
+        PF_CUDA_TRY(cudaGraphInstantiate(&ex, gr, 0));
+        cudaGraphDestroy(gr);
+        it = graphs.emplace(key, ex).first;
+      }
+      PF_CUDA_TRY(cudaGraphLaunch(it->second, st));
+      pc ^= 1;
+      fc ^= 1;
+      for (auto& I : probs) {
+        I->pc ^= 1;
+        I->fc ^= 1;
+        I->steps_done++;
+      }
+    }
+    int status = 0;
+    PF_CUDA_TRY(cudaMemcpyAsync(&status, d_head + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PF_CUDA_TRY(cudaStreamSynchronize(st));
+    if (status != 0) throw ApiError(status, "a bounded wait of the batched step expired");
+  }
+};
 }  // namespace pf
 
 // ===========================================================================
@@ -862,6 +1103,94 @@ int pf_profile(pf_ctx* ctx, int nsteps, int flags, int max_entries, char* names,
 }
 
 const char* pf_last_error(const pf_ctx* ctx) { return ctx ? ctx->err.c_str() : g_init_err.c_str(); }
+
+}  // extern "C"
+
+struct pf_batch {
+  std::unique_ptr<pf::BatchBase> impl;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+};
+
+template <class F>
+static int bguarded(pf_batch* b, F&& f) {
+  pf_ctx tmp;
+  const int rc = guarded(&tmp, std::forward<F>(f));
+  if (b && rc != PF_OK) b->err = tmp.err;
+  return rc;
+}
+
+extern "C" {
+
+int pf_batch_create(pf_batch** out, int nproblems, const pf_grid_desc* grids, const pf_params* params, void* stream) {
+  if (!out || !grids || !params || nproblems < 1) {
+    g_init_err = "bad arguments to pf_batch_create";
+    return PF_ERR_ARG;
+  }
+  *out = nullptr;
+  auto b = std::make_unique<pf_batch>();
+  int rc = bguarded(b.get(), [&] {
+    for (int i = 0; i < nproblems; ++i) {
+      const pf_grid_desc& g = grids[i];
+      if (g.nx < 2 || g.nz < 2 || g.nx % 2) throw pf::ApiError(PF_ERR_ARG, "need even nx >= 2 and nz >= 2");
+      const double dx = g.lx / g.nx;
+      if (std::fabs(g.lz / g.nz - dx) > 1e-9 * dx) throw pf::ApiError(PF_ERR_ARG, "cells must be squares");
+      for (int n : {g.nx, g.nz})
+        if (!pf::smooth(n)) throw pf::ApiError(PF_ERR_UNSUPPORTED, "sizes must be 2^a 3^b 5^c 7^d");
+    }
+    if (stream) {
+      b->stream = static_cast<cudaStream_t>(stream);
+    } else {
+      PF_CUDA_TRY(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+      b->own_stream = true;
+    }
+    if (grids[0].precision == PF_FP64) b->impl.reset(new pf::Batch<double>(nproblems, grids, params, b->stream));
+    else b->impl.reset(new pf::Batch<float>(nproblems, grids, params, b->stream));
+  });
+  if (rc != PF_OK) {
+    g_init_err = b->err;
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    return rc;
+  }
+  *out = b.release();
+  return PF_OK;
+}
+
+int pf_batch_field_info(const pf_batch* b, int problem, int field_id, size_t* count, size_t* elem_bytes) {
+  if (!b || !count || !elem_bytes) return PF_ERR_ARG;
+  return bguarded(const_cast<pf_batch*>(b), [&] { b->impl->problem(problem)->field_info(field_id, count, elem_bytes); });
+}
+
+int pf_batch_set_fields(pf_batch* b, int problem, int field_id, const void* src, size_t bytes, int src_on_device) {
+  if (!b || !src) return PF_ERR_ARG;
+  return bguarded(b, [&] { b->impl->problem(problem)->set_field(field_id, src, bytes, src_on_device); });
+}
+
+int pf_batch_get_fields(pf_batch* b, int problem, int field_id, void* dst, size_t bytes, int dst_on_device) {
+  if (!b || !dst) return PF_ERR_ARG;
+  return bguarded(b, [&] { b->impl->problem(problem)->get_field(field_id, dst, bytes, dst_on_device); });
+}
+
+int pf_batch_step(pf_batch* b, int nsteps) {
+  if (!b || nsteps < 0) return PF_ERR_ARG;
+  return bguarded(b, [&] { b->impl->step(nsteps); });
+}
+
+int pf_batch_diagnostics(pf_batch* b, int problem, double out[6]) {
+  if (!b || !out) return PF_ERR_ARG;
+  return bguarded(b, [&] { b->impl->problem(problem)->diagnostics(out); });
+}
+
+const char* pf_batch_last_error(const pf_batch* b) { return b ? b->err.c_str() : g_init_err.c_str(); }
+
+void pf_batch_destroy(pf_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  b->impl.reset();
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
 
 void pf_destroy(pf_ctx* ctx) {
   if (!ctx) return;

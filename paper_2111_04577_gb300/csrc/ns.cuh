@@ -28,12 +28,11 @@ struct NsIn {
 
 // (gamma0 rho0/dt) div(u~) at centres; wt holds faces 1..nz-1 as rows 0..nz-2
 template <class T>
-__global__ void k_div(const T* __restrict__ ut, const T* __restrict__ vt, const T* __restrict__ wt, T* __restrict__ out,
-                      Dims d, T coef) {
+__device__ __forceinline__ void k_div_b(const T* __restrict__ ut, const T* __restrict__ vt, const T* __restrict__ wt, T* __restrict__ out, Dims d, T coef, const int3 bid, unsigned char* smraw) {
   const size_t plane = (size_t)d.nx * d.ny;
   const T iD = (T)(1.0 / d.dx);
   RowIdx x;
-  if (!row_index(d.nx, d.ny, x)) return;
+  if (!row_index_b(bid, d.nx, d.ny, x)) return;
   {
     const int i = x.i, j = x.j, k = x.k;
     const size_t id = (size_t)x.row * d.nx + i;
@@ -47,15 +46,20 @@ __global__ void k_div(const T* __restrict__ ut, const T* __restrict__ vt, const 
   }
 }
 
+template <class T>
+__global__ void k_div(const T* __restrict__ ut, const T* __restrict__ vt, const T* __restrict__ wt, T* __restrict__ out, Dims d, T coef) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  k_div_b(ut, vt, wt, out, d, coef, make_int3(blockIdx.x, blockIdx.y, blockIdx.z), smraw);
+}
+
 // u = u~ - cf grad p', p^{n+1} = p^n + p'.  u, v corrected in place (they hold
 // u~ on entry); w written with both walls zero from the face rows wt.
 template <class T>
-__global__ void k_correct(T* __restrict__ u, T* __restrict__ v, const T* __restrict__ wt, T* __restrict__ w,
-                          const T* __restrict__ pp, const T* __restrict__ pn, T* __restrict__ pnew, Dims d, T cf) {
+__device__ __forceinline__ void k_correct_b(T* __restrict__ u, T* __restrict__ v, const T* __restrict__ wt, T* __restrict__ w, const T* __restrict__ pp, const T* __restrict__ pn, T* __restrict__ pnew, Dims d, T cf, const int3 bid, unsigned char* smraw) {
   const size_t plane = (size_t)d.nx * d.ny;
   const T iD = (T)(1.0 / d.dx);
   RowIdx x;
-  if (!row_index(d.nx, d.ny, x)) return;
+  if (!row_index_b(bid, d.nx, d.ny, x)) return;
   {
     const int i = x.i, j = x.j, k = x.k;
     const size_t id = (size_t)x.row * d.nx + i;
@@ -70,6 +74,12 @@ __global__ void k_correct(T* __restrict__ u, T* __restrict__ v, const T* __restr
     if (d.dim == 3) v[id] = v[id] - cf * (pp[id] - pp[((size_t)k * d.ny + wrap(j - 1, d.ny)) * d.nx + i]) * iD;
     pnew[id] = pn[id] + pp[id];
   }
+}
+
+template <class T>
+__global__ void k_correct(T* __restrict__ u, T* __restrict__ v, const T* __restrict__ wt, T* __restrict__ w, const T* __restrict__ pp, const T* __restrict__ pn, T* __restrict__ pnew, Dims d, T cf) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  k_correct_b(u, v, wt, w, pp, pn, pnew, d, cf, make_int3(blockIdx.x, blockIdx.y, blockIdx.z), smraw);
 }
 
 }  // namespace pf

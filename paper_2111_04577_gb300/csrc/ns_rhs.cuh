@@ -13,12 +13,10 @@
 namespace pf {
 
 template <class T, int DIM>
-__global__ void __launch_bounds__(256) k_ns_rhs_v2(const __grid_constant__ NsIn<T> a, const Dims d,
-                                                   const PhysT<T> q, T* __restrict__ ru, T* __restrict__ rv,
-                                                   T* __restrict__ rw, const int have_tau) {
+__device__ __forceinline__ void k_ns_rhs_v2_b(const NsIn<T>& a, const Dims d, const PhysT<T> q, T* __restrict__ ru, T* __restrict__ rv, T* __restrict__ rw, const int have_tau, const int3 bid, unsigned char* smraw) {
   constexpr bool D3 = DIM == 3;
   RowIdx ix;
-  if (!row_index(d.nx, d.ny, ix)) return;
+  if (!row_index_b(bid, d.nx, d.ny, ix)) return;
   const int i = ix.i, j = ix.j, k = ix.k;
   const int nx = d.nx, ny = d.ny, nz = d.nz;
   const int P = nx * ny;
@@ -236,6 +234,12 @@ __global__ void __launch_bounds__(256) k_ns_rhs_v2(const __grid_constant__ NsIn<
                 q.gz;
     rw[c - P] = R * q.inum;  // face rows 0..nz-2 hold faces 1..nz-1
   }
+}
+
+template <class T, int DIM>
+__global__ void __launch_bounds__(256) k_ns_rhs_v2(const __grid_constant__ NsIn<T> a, const Dims d, const PhysT<T> q, T* __restrict__ ru, T* __restrict__ rv, T* __restrict__ rw, const int have_tau) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  k_ns_rhs_v2_b<T, DIM>(a, d, q, ru, rv, rw, have_tau, make_int3(blockIdx.x, blockIdx.y, blockIdx.z), smraw);
 }
 
 }  // namespace pf

@@ -119,13 +119,13 @@ __device__ __forceinline__ int comp_of(int a, int b) {
 }
 
 template <class T, int N>
-__global__ void k_polymer(PolyIn<T> P, Dims d, PhysT<T> q, int stage) {
+__device__ __forceinline__ void k_polymer_b(PolyIn<T> P, Dims d, PhysT<T> q, int stage, const int3 bid, unsigned char* smraw) {
   const int plane = d.nx * d.ny;
   const T iD = q.iD;
   const T dt = q.dt, ilh = q.ilh;
   constexpr int NC = N == 2 ? 3 : 6;
   RowIdx x;
-  if (!row_index(d.nx, d.ny, x)) return;
+  if (!row_index_b(bid, d.nx, d.ny, x)) return;
   {
     const int i = x.i, j = x.j, k = x.k;
     const int id = x.row * d.nx + i;
@@ -267,6 +267,12 @@ __global__ void k_polymer(PolyIn<T> P, Dims d, PhysT<T> q, int stage) {
         }
     }
   }
+}
+
+template <class T, int N>
+__global__ void k_polymer(PolyIn<T> P, Dims d, PhysT<T> q, int stage) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  k_polymer_b<T, N>(P, d, q, stage, make_int3(blockIdx.x, blockIdx.y, blockIdx.z), smraw);
 }
 
 }  // namespace pf

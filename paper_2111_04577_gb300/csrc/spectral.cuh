@@ -48,12 +48,10 @@ __device__ __forceinline__ void staged_copy(int n, Src src, Dst dst) {
 // Pro: T operator()(int line, int x) const  -- produces the input sample
 // ---------------------------------------------------------------------------
 template <class T, class Pro>
-__global__ void k_rfft_x(Pro pro, cpx<T>* __restrict__ out, int n, int nlines, int pitch, FftPlan pl,
-                         const cpx<T>* __restrict__ tw, int npair) {
-  extern __shared__ unsigned char smraw[];
+__device__ __forceinline__ void k_rfft_x_b(Pro pro, cpx<T>* __restrict__ out, int n, int nlines, int pitch, FftPlan pl, const cpx<T>* __restrict__ tw, int npair, const int3 bid, unsigned char* smraw) {
   cpx<T>* a = reinterpret_cast<cpx<T>*>(smraw);
   cpx<T>* b = a + (size_t)npair * n;
-  const int pair0 = blockIdx.x * npair;
+  const int pair0 = bid.x * npair;
   for (int m = 0; m < npair; ++m) {
     const int l0 = 2 * (pair0 + m), l1 = l0 + 1;
     for (int x = threadIdx.x; x < n; x += blockDim.x) {
@@ -80,17 +78,21 @@ __global__ void k_rfft_x(Pro pro, cpx<T>* __restrict__ out, int n, int nlines, i
   }
 }
 
+template <class T, class Pro>
+__global__ void k_rfft_x(Pro pro, cpx<T>* __restrict__ out, int n, int nlines, int pitch, FftPlan pl, const cpx<T>* __restrict__ tw, int npair) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  k_rfft_x_b(pro, out, n, nlines, pitch, pl, tw, npair, make_int3(blockIdx.x, blockIdx.y, blockIdx.z), smraw);
+}
+
 // ---------------------------------------------------------------------------
 // inverse real FFT along x; Epi: void operator()(int line, int x, T value)
 // value already multiplied by `scale`
 // ---------------------------------------------------------------------------
 template <class T, class Epi>
-__global__ void k_irfft_x(const cpx<T>* __restrict__ in, Epi epi, int n, int nlines, int pitch, FftPlan pl,
-                          const cpx<T>* __restrict__ tw, int npair, T scale) {
-  extern __shared__ unsigned char smraw[];
+__device__ __forceinline__ void k_irfft_x_b(const cpx<T>* __restrict__ in, Epi epi, int n, int nlines, int pitch, FftPlan pl, const cpx<T>* __restrict__ tw, int npair, T scale, const int3 bid, unsigned char* smraw) {
   cpx<T>* a = reinterpret_cast<cpx<T>*>(smraw);
   cpx<T>* b = a + (size_t)npair * n;
-  const int pair0 = blockIdx.x * npair;
+  const int pair0 = bid.x * npair;
   const int nh = n / 2;
   for (int m = 0; m < npair; ++m) {
     const int l0 = 2 * (pair0 + m), l1 = l0 + 1;
@@ -119,17 +121,21 @@ __global__ void k_irfft_x(const cpx<T>* __restrict__ in, Epi epi, int n, int nli
   }
 }
 
+template <class T, class Epi>
+__global__ void k_irfft_x(const cpx<T>* __restrict__ in, Epi epi, int n, int nlines, int pitch, FftPlan pl, const cpx<T>* __restrict__ tw, int npair, T scale) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  k_irfft_x_b(in, epi, n, nlines, pitch, pl, tw, npair, scale, make_int3(blockIdx.x, blockIdx.y, blockIdx.z), smraw);
+}
+
 // ---------------------------------------------------------------------------
 // complex FFT along y, in place, tile of TX kx-columns at one z level
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void k_fft_y(cpx<T>* __restrict__ data, int ny, int pitch, int ncol, FftPlan pl,
-                        const cpx<T>* __restrict__ tw, int sign, int tx) {
-  extern __shared__ unsigned char smraw[];
+__device__ __forceinline__ void k_fft_y_b(cpx<T>* __restrict__ data, int ny, int pitch, int ncol, FftPlan pl, const cpx<T>* __restrict__ tw, int sign, int tx, const int3 bid, unsigned char* smraw) {
   cpx<T>* a = reinterpret_cast<cpx<T>*>(smraw);
   cpx<T>* b = a + (size_t)ny * tx;
-  const int c0 = blockIdx.x * tx;
-  cpx<T>* base = data + (size_t)blockIdx.y * ny * pitch;
+  const int c0 = bid.x * tx;
+  cpx<T>* base = data + (size_t)bid.y * ny * pitch;
   const float itx = 1.0f / (float)tx;
   staged_copy<8, cpx<T>>(
       ny * tx,
@@ -144,6 +150,12 @@ __global__ void k_fft_y(cpx<T>* __restrict__ data, int ny, int pitch, int ncol, 
     const int y = qdiv(e, tx, itx), c = e - y * tx;
     if (c0 + c < ncol) base[(size_t)y * pitch + c0 + c] = z[e];
   }
+}
+
+template <class T>
+__global__ void k_fft_y(cpx<T>* __restrict__ data, int ny, int pitch, int ncol, FftPlan pl, const cpx<T>* __restrict__ tw, int sign, int tx) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  k_fft_y_b(data, ny, pitch, ncol, pl, tw, sign, tx, make_int3(blockIdx.x, blockIdx.y, blockIdx.z), smraw);
 }
 
 // ---------------------------------------------------------------------------
@@ -180,16 +192,14 @@ __device__ __forceinline__ TC zdiag(int k, int rows, int bc, TC sig) {
 }
 
 template <class T, class TC>
-__global__ void k_zsolve(cpx<T>* __restrict__ data, const double* __restrict__ eigx,
-                         const double* __restrict__ eigy, ZSolve zs, int tx) {
+__device__ __forceinline__ void k_zsolve_b(cpx<T>* __restrict__ data, const double* __restrict__ eigx, const double* __restrict__ eigy, ZSolve zs, int tx, const int3 bid, unsigned char* smraw) {
   // shared memory: the tile (R rows x tx complex), then the factors
-  extern __shared__ __align__(16) unsigned char smraw[];
   const int R = zs.rows;
   cpx<T>* tile = reinterpret_cast<cpx<T>*>(smraw);   // R x tx, row k at tile + k*tx
   TC* cp = reinterpret_cast<TC*>(tile + (size_t)R * tx);  // R x tx  (1/b' of solve 1)
   TC* cq = cp + (size_t)R * tx;                            // R x tx  (solve-2 factors, if !same)
-  const int ky = blockIdx.y;
-  const int col0 = blockIdx.x * tx;
+  const int ky = bid.y;
+  const int col0 = bid.x * tx;
   const int ncol = min(tx, zs.ncol - col0);
   cpx<T>* gbase = data + (size_t)ky * zs.pitch + col0;
   const size_t zstride = (size_t)zs.ny * zs.pitch;
@@ -280,13 +290,18 @@ __global__ void k_zsolve(cpx<T>* __restrict__ data, const double* __restrict__ e
   }
 }
 
+template <class T, class TC>
+__global__ void k_zsolve(cpx<T>* __restrict__ data, const double* __restrict__ eigx, const double* __restrict__ eigy, ZSolve zs, int tx) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  k_zsolve_b<T, TC>(data, eigx, eigy, zs, tx, make_int3(blockIdx.x, blockIdx.y, blockIdx.z), smraw);
+}
+
 // The (kx, ky) = (0, 0) column of a pure Neumann Poisson problem is singular
 // (constants).  Solved in FP64 with the last row replaced by x = 0, then the
 // mean is removed -- the zero mode set to zero, as in Eq. NS37's solver.
 template <class T>
-__global__ void k_zero_mode(cpx<T>* __restrict__ data, int rows, int ny, int pitch, double h2, double scale,
-                            double* __restrict__ work) {
-  if (threadIdx.x > 1 || blockIdx.x != 0) return;
+__device__ __forceinline__ void k_zero_mode_b(cpx<T>* __restrict__ data, int rows, int ny, int pitch, double h2, double scale, double* __restrict__ work, const int3 bid, unsigned char* smraw) {
+  if (threadIdx.x > 1 || bid.x != 0) return;
   const int part = threadIdx.x;
   const size_t zstride = (size_t)ny * pitch * 2;
   T* base = reinterpret_cast<T*>(data) + part;
@@ -315,6 +330,12 @@ __global__ void k_zero_mode(cpx<T>* __restrict__ data, int rows, int ny, int pit
   }
   const double mean = sum / rows;
   for (int k = 0; k < rows; ++k) base[(size_t)k * zstride] = (T)(dp[k] - mean);
+}
+
+template <class T>
+__global__ void k_zero_mode(cpx<T>* __restrict__ data, int rows, int ny, int pitch, double h2, double scale, double* __restrict__ work) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  k_zero_mode_b(data, rows, ny, pitch, h2, scale, work, make_int3(blockIdx.x, blockIdx.y, blockIdx.z), smraw);
 }
 
 }  // namespace pf
