@@ -214,6 +214,52 @@ def side_path(w, grid, precision, steps, warm, stream):
     return grid.fine_cells() * steps / t, t / steps * 1e3
 
 
+def batch_leg(stream, nprob=64, steps=20):
+    """64 uneven 2D droplets (coarse 64x32 .. 256x128, fine 2x, theta ~ U(30,150),
+    Wi ~ U(0,2), beta = 0.5, mixed precision): one persistent launch per step
+    versus stepping each problem through its own graph."""
+    import gc
+    import torch
+    from paper_2111_04577_gb300 import binding, workloads as wl
+    ws = wl.batch_problems(nprob, seed=0)
+    cells = sum(w.grid.fine_cells() for w in ws)
+    bt = binding.Batch([w.grid for w in ws], [w.params for w in ws], binding.PF_MIXED, stream=stream.cuda_stream)
+    for b, w in enumerate(ws):
+        bt.set(b, "phi", wl.initial_phi(w))
+    bt.step(3)
+    a = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    bt.step(steps)
+    e.record(stream)
+    e.synchronize()
+    t_b = a.elapsed_time(e) / 1e3
+    bt.close()
+    del bt
+    solvers = []
+    for w in ws:
+        s = binding.Solver(w.grid, w.params, binding.PF_MIXED, stream=stream.cuda_stream)
+        s.load_state(wl.initial_phi(w))
+        s.step(3)
+        solvers.append(s)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for s in solvers:
+        s.step(steps)
+    e.record(stream)
+    e.synchronize()
+    t_s = a.elapsed_time(e) / 1e3
+    for s in solvers:
+        s.close()
+    del solvers
+    gc.collect()
+    return {"problems": nprob, "fine_cells": cells, "steps": steps,
+            "cell_steps_per_s": cells * steps / t_b, "ms_per_step": t_b / steps * 1e3,
+            "unbatched_cell_steps_per_s": cells * steps / t_s, "unbatched_ms_per_step": t_s / steps * 1e3,
+            "speedup": t_s / t_b, "launches_per_step": 1}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -223,6 +269,7 @@ def main():
     ap.add_argument("--config", default="c4")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64 / single-resolution legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--no-tune", action="store_true", help="keep the built-in launch shapes")
     ap.add_argument("--nx", type=int, default=0,
                     help="run the workload's physics at another coarse nx (ny = nx, nz = nx/2); profiling only")
     args = ap.parse_args()
@@ -251,6 +298,11 @@ def main():
     solver = binding.Solver(g, w.params, prec, stream=stream.cuda_stream)
     phi0 = wl.initial_phi(w)
     phi0_f = phi0.astype(np.float32)
+    tuning = {}
+    if not args.no_tune:
+        from paper_2111_04577_gb300 import autotune
+        tuning = autotune.tuned(g, w.params, prec, phi0=phi0_f)
+        autotune.apply(solver, tuning)
     solver.load_state(phi0_f)
     solver.step(args.warmup)
     torch.cuda.synchronize()
@@ -348,6 +400,8 @@ def main():
                     "ms_per_step": ms_rsr,
                     "dual_speedup_at_same_phi_resolution": ms_rsr / ms_per_step},
         }
+    if rank == 0 and not args.no_compare:
+        extra["batch_sweep"] = batch_leg(stream)
     cpu = cpu_sample(workload(args.config), 2, 64) if (rank == 0 and not args.no_cpu) else None
 
     if rank == 0:
@@ -364,7 +418,7 @@ def main():
             "clocks": clocks,
             "kernels": rows, "alg_bytes_per_fine_cell_step": step_bytes / g.fine_cells(),
             "step_roof_frac": (step_bytes / (ms_per_step * 1e-3) / 1e9) / peak,
-            "profile_sum_ms": total_ms, "diagnostics": diag,
+            "profile_sum_ms": total_ms, "diagnostics": diag, "tuning": tuning,
         }
         line.update(extra)
         print(json.dumps(line), flush=True)

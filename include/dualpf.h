@@ -213,6 +213,18 @@ void pf_batch_destroy(pf_batch* b);
 int pf_diagnostics_noalloc(const pf_grid_desc* g, const pf_params* prm, const void* phi_device, double out[6],
                            void* stream);
 
+/* Launch-shape knobs picked by the autotuner (paper_2111_04577_gb300/autotune.py);
+ * 0 restores the built-in default.  They change only how the work is tiled,
+ * never the arithmetic of a cell.
+ *   PF_TUNE_XFFT_PAIRS   pairs of x-lines per CTA of the x transforms (1..16)
+ *   PF_TUNE_YFFT_COLS    kx columns per CTA of the y transforms (power of two <= 32)
+ *   PF_TUNE_ZSOLVE_COLS  kx columns per CTA of the z solves (multiple of 16, <= 64)
+ *   PF_TUNE_ROW_BLOCK    threads per CTA of the row kernels (multiple of 32)
+ * Errors: PF_ERR_ARG for an unknown knob or a value that does not fit. */
+enum { PF_TUNE_XFFT_PAIRS = 0, PF_TUNE_YFFT_COLS = 1, PF_TUNE_ZSOLVE_COLS = 2, PF_TUNE_ROW_BLOCK = 3, PF_TUNE_COUNT = 4 };
+int pf_set_tuning(pf_ctx* ctx, int knob, int value);
+int pf_get_tuning(const pf_ctx* ctx, int knob, int* value);
+
 /* Message of the last failed call on ctx (or of the last failed
  * pf_init_grid when ctx is NULL).  Valid until the next call. */
 const char* pf_last_error(const pf_ctx* ctx);

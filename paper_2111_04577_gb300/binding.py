@@ -26,7 +26,8 @@ ERRORS = {-1: "PF_ERR_ARG", -2: "PF_ERR_DISCRIMINANT", -3: "PF_ERR_UNSUPPORTED",
 EXPORTS = ["pf_init_grid", "pf_set_params", "pf_field_info", "pf_set_fields", "pf_step", "pf_step_ex",
            "pf_get_fields", "pf_diagnostics", "pf_profile", "pf_diagnostics_noalloc", "pf_last_error",
            "pf_destroy", "pf_batch_create", "pf_batch_field_info", "pf_batch_set_fields", "pf_batch_get_fields",
-           "pf_batch_step", "pf_batch_diagnostics", "pf_batch_last_error", "pf_batch_destroy"]
+           "pf_batch_step", "pf_batch_diagnostics", "pf_batch_last_error", "pf_batch_destroy", "pf_set_tuning",
+           "pf_get_tuning"]
 PROFILE_NAME = 48
 
 
@@ -83,6 +84,10 @@ def load(path: str = LIB_PATH):
         for f in ("pf_batch_create", "pf_batch_field_info", "pf_batch_set_fields", "pf_batch_get_fields",
                   "pf_batch_step", "pf_batch_diagnostics"):
             getattr(lib, f).restype = C.c_int
+        lib.pf_set_tuning.argtypes = [vp, C.c_int, C.c_int]
+        lib.pf_get_tuning.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
+        lib.pf_set_tuning.restype = C.c_int
+        lib.pf_get_tuning.restype = C.c_int
         lib.pf_last_error.argtypes = [vp]
         lib.pf_last_error.restype = C.c_char_p
         lib.pf_destroy.argtypes = [vp]
@@ -182,6 +187,14 @@ class Solver:
             raw = names.raw[i * PROFILE_NAME:(i + 1) * PROFILE_NAME]
             out.append((raw.split(b"\0", 1)[0].decode(), ms[i], cnt[i]))
         return out, per.value
+
+    def set_tuning(self, knob, value):
+        self._chk(self.lib.pf_set_tuning(self.h, int(knob), int(value)))
+
+    def get_tuning(self, knob):
+        v = C.c_int()
+        self._chk(self.lib.pf_get_tuning(self.h, int(knob), C.byref(v)))
+        return v.value
 
     def close(self):
         if getattr(self, "h", None):

@@ -116,6 +116,8 @@ struct ImplBase {
   virtual void diagnostics(double out[6]) = 0;
   virtual void profile(int nsteps, int flags, std::vector<std::string>& names, std::vector<double>& ms,
                        std::vector<int>& counts, int& per_step) = 0;
+  virtual void set_tuning(int knob, int value) = 0;
+  virtual int get_tuning(int knob) const = 0;
 };
 
 static Phys derive(const pf_params& q, const pf_grid_desc& g) {
@@ -192,6 +194,8 @@ struct Impl : ImplBase {
   int pc = 0, fc = 0;  // parities: phi^n = phi[pc]; u^n = u[fc], ...
   std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;
   long long steps_done = 0;
+  // tuning knobs (pf_set_tuning); 0 = built-in default
+  int tune[PF_TUNE_COUNT] = {0};
   // per-kernel timing (pf_profile): one event before every launch of a step
   bool prof = false;
   int nlaunch = 0;
@@ -332,7 +336,8 @@ struct Impl : ImplBase {
   struct RowLaunch {
     dim3 grid, block;
   };
-  static RowLaunch rows(int nrows, int nxrow, int maxbs = 256) {
+  RowLaunch rows(int nrows, int nxrow, int maxbs = 256) const {
+    if (tune[PF_TUNE_ROW_BLOCK] > 0) maxbs = std::min(maxbs, tune[PF_TUNE_ROW_BLOCK]);
     int bs = ((nxrow + 31) / 32) * 32;
     if (bs > maxbs) bs = maxbs;
     RowLaunch r;
@@ -342,7 +347,7 @@ struct Impl : ImplBase {
   }
   template <class Pro>
   void rfft_x(Pro pro, cpx<T>* out, int n, int nlines, int pitch, const FftPlan& pl, const cpx<T>* tw) {
-    const int npair = std::max(1, 1024 / n);
+    const int npair = tune[PF_TUNE_XFFT_PAIRS] > 0 ? tune[PF_TUNE_XFFT_PAIRS] : std::max(1, 1024 / n);
     const int pairs = (nlines + 1) / 2;
     const int grid = (pairs + npair - 1) / npair;
     const size_t sm = 2 * (size_t)npair * n * sizeof(cpx<T>);
@@ -351,7 +356,7 @@ struct Impl : ImplBase {
   }
   template <class Epi>
   void irfft_x(const cpx<T>* in, Epi epi, int n, int nlines, int pitch, const FftPlan& pl, const cpx<T>* tw, T scale) {
-    const int npair = std::max(1, 1024 / n);
+    const int npair = tune[PF_TUNE_XFFT_PAIRS] > 0 ? tune[PF_TUNE_XFFT_PAIRS] : std::max(1, 1024 / n);
     const int pairs = (nlines + 1) / 2;
     const int grid = (pairs + npair - 1) / npair;
     const size_t sm = 2 * (size_t)npair * n * sizeof(cpx<T>);
@@ -359,7 +364,7 @@ struct Impl : ImplBase {
     k_irfft_x<T, Epi><<<grid, 256, sm, st>>>(in, epi, n, nlines, pitch, pl, tw, npair, scale);
   }
   void fft_y(cpx<T>* data, int ny, int pitch, int ncol, int levels, const FftPlan& pl, const cpx<T>* tw, int sign) {
-    const int tx = sizeof(T) == 4 ? 8 : 4;
+    const int tx = tune[PF_TUNE_YFFT_COLS] > 0 ? tune[PF_TUNE_YFFT_COLS] : (sizeof(T) == 4 ? 8 : 4);
     dim3 grid((ncol + tx - 1) / tx, levels);
     const size_t sm = 2 * (size_t)ny * tx * sizeof(cpx<T>);
     mark(ny == d.fny && levels == d.fnz && d.r > 1 ? "fft_y_fine" : "fft_y_coarse");
@@ -380,7 +385,7 @@ struct Impl : ImplBase {
     zs.shift1 = s1;
     zs.shift2 = s2;
     zs.scale = scale;
-    const int tx = sizeof(T) == 4 ? 32 : 16;
+    const int tx = tune[PF_TUNE_ZSOLVE_COLS] > 0 ? tune[PF_TUNE_ZSOLVE_COLS] : (sizeof(T) == 4 ? 32 : 16);
     const size_t sm = (size_t)rows * tx * (sizeof(cpx<T>) + sizeof(TC) * (zs.same ? 1 : 2));
     dim3 grid((ncol + tx - 1) / tx, ny);
     mark(two ? "zsolve_pair" : "zsolve");
@@ -641,6 +646,29 @@ struct Impl : ImplBase {
       it = graphs.emplace(key, ex).first;
     }
     PF_CUDA_TRY(cudaGraphLaunch(it->second, st));
+  }
+
+  void set_tuning(int knob, int value) override {
+    if (knob < 0 || knob >= PF_TUNE_COUNT) throw ApiError(PF_ERR_ARG, "unknown tuning knob");
+    if (value < 0) throw ApiError(PF_ERR_ARG, "tuning value must be >= 0");
+    auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
+    if (value > 0) {
+      if (knob == PF_TUNE_XFFT_PAIRS && (value > 16 || 2 * (size_t)value * std::max(d.fnx, d.nx) * sizeof(cpx<T>) > (size_t)kMaxSmem))
+        throw ApiError(PF_ERR_ARG, "x-transform line pairs do not fit in shared memory");
+      if (knob == PF_TUNE_YFFT_COLS && (!pow2(value) || value > 32 || 2 * (size_t)value * std::max(d.fny, d.ny) * sizeof(cpx<T>) > (size_t)kMaxSmem))
+        throw ApiError(PF_ERR_ARG, "y-transform columns must be a power of two that fits in shared memory");
+      // two solver lanes per column: whole warps (the solve phase synchronises with __syncwarp)
+      if (knob == PF_TUNE_ZSOLVE_COLS && (value % 16 || value > 64 || (size_t)std::max(d.fnz, d.nz) * value * (sizeof(cpx<T>) + 2 * sizeof(TC)) > (size_t)kMaxSmem))
+        throw ApiError(PF_ERR_ARG, "z-solve columns must be a multiple of 16 that fits in shared memory");
+      if (knob == PF_TUNE_ROW_BLOCK && (value % 32 || value > 1024)) throw ApiError(PF_ERR_ARG, "row block must be a multiple of 32");
+    }
+    tune[knob] = value;
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    graphs.clear();
+  }
+  int get_tuning(int knob) const override {
+    if (knob < 0 || knob >= PF_TUNE_COUNT) throw ApiError(PF_ERR_ARG, "unknown tuning knob");
+    return tune[knob];
   }
 
   // per-kernel average device time over nsteps direct (non-graph) steps
@@ -1100,6 +1128,16 @@ int pf_profile(pf_ctx* ctx, int nsteps, int flags, int max_entries, char* names,
     *n_entries = n;
     *launches_per_step = per;
   });
+}
+
+int pf_set_tuning(pf_ctx* ctx, int knob, int value) {
+  if (!ctx) return PF_ERR_ARG;
+  return guarded(ctx, [&] { ctx->impl->set_tuning(knob, value); });
+}
+
+int pf_get_tuning(const pf_ctx* ctx, int knob, int* value) {
+  if (!ctx || !value) return PF_ERR_ARG;
+  return guarded(const_cast<pf_ctx*>(ctx), [&] { *value = ctx->impl->get_tuning(knob); });
 }
 
 const char* pf_last_error(const pf_ctx* ctx) { return ctx ? ctx->err.c_str() : g_init_err.c_str(); }

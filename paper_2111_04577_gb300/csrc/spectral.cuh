@@ -159,7 +159,9 @@ __global__ void k_fft_y(cpx<T>* __restrict__ data, int ny, int pitch, int ncol, 
 }
 
 // ---------------------------------------------------------------------------
-// z solves.  One CTA: a tile of TX kx-columns x all z rows at one ky, staged
+// z solves.  TX must be a multiple of 16: the 2 TX solver lanes then form whole
+// warps, which the __syncwarp of the solve phase requires.
+// One CTA: a tile of TX kx-columns x all z rows at one ky, staged
 // in shared memory with coalesced row loads; thread t < 2 TX then solves column
 // t/2, component t%2 (real and imaginary parts are independent real systems)
 // sequentially along z in shared memory, and the tile is stored back.
