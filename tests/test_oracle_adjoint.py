@@ -1,0 +1,69 @@
+"""Pins of the differentiable CH restatement (the FP64 CPU adjoint reference).
+
+Its forward must equal the oracle's CH step, and its autograd gradients must
+equal central finite differences of the oracle itself, for the wetted length
+and the z-centroid, with respect to the bottom contact angle, the mobility and
+phi0 (a seeded direction)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2111_04577_gb300 import workloads as wl
+from oracle import ch_torch, step as ostep, observables as ob
+
+
+def tiny():
+    g = wl.Grid(8, 1, 4, 4.0, 0.5, 2.0, 1)
+    prm = wl.params_from_groups(theta_deg=60.0, Pe=50.0, Cn=0.2)
+    prm.theta_top_deg = 80.0
+    w = wl.Workload("tiny", g, prm, 1)
+    return w
+
+
+def oracle_J(w, vel, phi0, steps, which, theta=None, mob=None):
+    prm = w.params.as_dict()
+    if theta is not None:
+        prm["theta_bot_deg"] = theta
+    if mob is not None:
+        prm["mobility"] = mob
+    st = ostep.State(w.grid, prm, phi0, vel0=vel)
+    for _ in range(steps):
+        st.step(with_ns=False)
+    if which == "wetted":
+        return ob.wetted(st.phi, w.grid)
+    return ob.centroid(st.phi, w.grid)[2]
+
+
+def test_forward_equals_oracle():
+    w = tiny()
+    vel = wl.random_velocity(w.grid, 3, 0.3)
+    phi0 = wl.initial_phi(w)
+    J, *_rest, pn = ch_torch.run(w.grid, w.params.as_dict(), vel, phi0, 4, "wetted")
+    st = ostep.State(w.grid, w.params.as_dict(), phi0, vel0=vel)
+    for _ in range(4):
+        st.step(with_ns=False)
+    assert np.max(np.abs(pn.detach().numpy() - st.phi)) < 1e-12
+    assert abs(J.item() - ob.wetted(st.phi, w.grid)) < 1e-12
+
+
+@pytest.mark.parametrize("which", ["wetted", "centroid"])
+def test_gradients_equal_finite_differences(which):
+    w = tiny()
+    vel = wl.random_velocity(w.grid, 3, 0.3)
+    phi0 = wl.initial_phi(w)
+    steps = 4
+    J, ph0, th, mob, _ = ch_torch.run(w.grid, w.params.as_dict(), vel, phi0, steps, which)
+    J.backward()
+    t0, m0 = w.params.theta_bot_deg, w.params.mobility
+    dt_ = 1e-3
+    fd_t = (oracle_J(w, vel, phi0, steps, which, theta=t0 + dt_) - oracle_J(w, vel, phi0, steps, which, theta=t0 - dt_)) / (2 * dt_)
+    dm = 1e-2 * m0  # the FD rounding error dominates below ~1e-3
+    fd_m = (oracle_J(w, vel, phi0, steps, which, mob=m0 + dm) - oracle_J(w, vel, phi0, steps, which, mob=m0 - dm)) / (2 * dm)
+    rng = np.random.default_rng(5)
+    dirn = rng.standard_normal(phi0.shape)
+    eps = 1e-5
+    fd_p = (oracle_J(w, vel, phi0 + eps * dirn, steps, which) - oracle_J(w, vel, phi0 - eps * dirn, steps, which)) / (2 * eps)
+    ad_p = float(np.sum(ph0.grad.numpy() * dirn))
+    assert abs(th.grad.item() - fd_t) <= 1e-6 * max(1e-8, abs(fd_t)) + 1e-10
+    assert abs(mob.grad.item() - fd_m) <= 1e-5 * max(1e-8, abs(fd_m)) + 1e-10
+    assert abs(ad_p - fd_p) <= 1e-6 * max(1e-8, abs(fd_p)) + 1e-10
