@@ -213,6 +213,24 @@ void pf_batch_destroy(pf_batch* b);
 int pf_diagnostics_noalloc(const pf_grid_desc* g, const pf_params* prm, const void* phi_device, double out[6],
                            void* stream);
 
+/* Discrete adjoint of the Cahn-Hilliard step (Section 3.2.1) with the velocity
+ * held fixed (the flow fields of the context are not advanced): gradients of
+ * an objective of phi^N after nsteps steps from the context's current state,
+ * taken as phi^0 with phi^{-1} = phi^0.
+ *   objective PF_OBJ_WETTED:     wetted length/area sum_bottom (1 + phi_w)/2 h^(d-1)
+ *   objective PF_OBJ_CENTROID_Z: z-centroid of (1 + phi)/2
+ * out[0] = J, out[1] = dJ/d theta_bot (per degree), out[2] = dJ/d mobility.
+ * dphi0 (may be NULL) receives dJ/d phi^0 (fine mesh, storage element type;
+ * host memory, or device memory when dphi0_on_device).  The forward sweep
+ * stores the BDF2 state every ckpt_every steps; the reverse sweep recomputes
+ * each segment, then runs the transposed kernels and the same (symmetric)
+ * transform solves.  The context is left at phi^N.  The mobility derivative
+ * follows S when S = 0 selects the bound of Eq. NS30.
+ * Errors: PF_ERR_ARG, PF_ERR_DISCRIMINANT, PF_ERR_CUDA, PF_ERR_NOMEM. */
+enum { PF_OBJ_WETTED = 0, PF_OBJ_CENTROID_Z = 1 };
+int pf_adjoint(pf_ctx* ctx, int nsteps, int ckpt_every, int objective, double out[3], void* dphi0,
+               int dphi0_on_device);
+
 /* Launch-shape knobs picked by the autotuner (paper_2111_04577_gb300/autotune.py);
  * 0 restores the built-in default.  They change only how the work is tiled,
  * never the arithmetic of a cell.

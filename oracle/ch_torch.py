@@ -70,12 +70,15 @@ class CHTorch:
         return A + (Fz[1:] - Fz[:-1]) / h
 
     def step(self, pn, po, theta_bot_deg, mobility):
+        """One step.  `mobility` is a scalar tensor, or a triple (M_a, M_b, M_s) of
+        copies of it entering the 1/(M lambda dt) term, the advection term 1/(M lambda)
+        and S of Eq. NS30 respectively (their gradients add up to dJ/dM)."""
         p = self.prm
         h, eta, dt = self.g.h, p["eta"], p["dt"]
         g0 = 1.5
         lam = 3.0 * p["sigma"] * eta / (2.0 * math.sqrt(2.0))
-        Ml = mobility * lam
-        S = eta ** 2 * torch.sqrt(4.0 * g0 / (Ml * dt))           # Eq. NS30, equality
+        Ma, Mb, Ms = mobility if isinstance(mobility, tuple) else (mobility,) * 3
+        S = eta ** 2 * torch.sqrt(4.0 * g0 / (Ms * lam * dt))      # Eq. NS30, equality
         alpha = -S / (2.0 * eta ** 2)                               # Eq. NS29 at zero discriminant
         c = alpha + S / eta ** 2
         phs = 2 * pn - po
@@ -91,7 +94,7 @@ class CHTorch:
         gt = ct * (1 - wt * wt) / (s2 * eta)
         zero = torch.zeros_like(phs[1:-1])
         B = torch.cat([(gb / h)[None], zero, (gt / h)[None]], 0)
-        R1 = (phh / dt - A) / Ml + self.lapN(hh) - c * B
+        R1 = phh / (dt * Ma * lam) - A / (Mb * lam) + self.lapN(hh) - c * B
         psi = torch.linalg.solve(self.L - c * self.I, R1.reshape(-1)).reshape(self.shape)
         phi = torch.linalg.solve(self.L + alpha * self.I, (psi - B).reshape(-1)).reshape(self.shape)
         return phi
@@ -109,14 +112,21 @@ def objective(phi, grid, which):
     return torch.sum(wgt * z[:, None, None]) / torch.sum(wgt)
 
 
-def run(grid, prm, vel, phi0, steps, which, theta=None, mobility=None):
-    """Objective after `steps` CH steps from phi^{-1} = phi^0; returns (J, tensors)."""
+def run(grid, prm, vel, phi0, steps, which, theta=None, mobility=None, split_mobility=False):
+    """Objective after `steps` CH steps from phi^{-1} = phi^0; returns (J, tensors).
+
+    With split_mobility the returned `mob` is the triple of copies described in
+    CHTorch.step: dJ/dM is the sum of their gradients, and the size of each part
+    shows how much cancellation dJ/dM carries."""
     m = CHTorch(grid, prm, vel)
     ph0 = torch.tensor(phi0, dtype=torch.float64, requires_grad=True)
     th = torch.tensor(float(prm["theta_bot_deg"] if theta is None else theta), dtype=torch.float64,
                       requires_grad=True)
-    mob = torch.tensor(float(prm["mobility"] if mobility is None else mobility), dtype=torch.float64,
-                       requires_grad=True)
+    m0 = float(prm["mobility"] if mobility is None else mobility)
+    if split_mobility:
+        mob = tuple(torch.tensor(m0, dtype=torch.float64, requires_grad=True) for _ in range(3))
+    else:
+        mob = torch.tensor(m0, dtype=torch.float64, requires_grad=True)
     pn, po = ph0, ph0
     for _ in range(steps):
         pn, po = m.step(pn, po, th, mob), pn

@@ -27,7 +27,8 @@ EXPORTS = ["pf_init_grid", "pf_set_params", "pf_field_info", "pf_set_fields", "p
            "pf_get_fields", "pf_diagnostics", "pf_profile", "pf_diagnostics_noalloc", "pf_last_error",
            "pf_destroy", "pf_batch_create", "pf_batch_field_info", "pf_batch_set_fields", "pf_batch_get_fields",
            "pf_batch_step", "pf_batch_diagnostics", "pf_batch_last_error", "pf_batch_destroy", "pf_set_tuning",
-           "pf_get_tuning"]
+           "pf_get_tuning", "pf_adjoint"]
+PF_OBJ_WETTED, PF_OBJ_CENTROID_Z = 0, 1
 PROFILE_NAME = 48
 
 
@@ -84,6 +85,8 @@ def load(path: str = LIB_PATH):
         for f in ("pf_batch_create", "pf_batch_field_info", "pf_batch_set_fields", "pf_batch_get_fields",
                   "pf_batch_step", "pf_batch_diagnostics"):
             getattr(lib, f).restype = C.c_int
+        lib.pf_adjoint.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), vp, C.c_int]
+        lib.pf_adjoint.restype = C.c_int
         lib.pf_set_tuning.argtypes = [vp, C.c_int, C.c_int]
         lib.pf_get_tuning.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
         lib.pf_set_tuning.restype = C.c_int
@@ -187,6 +190,21 @@ class Solver:
             raw = names.raw[i * PROFILE_NAME:(i + 1) * PROFILE_NAME]
             out.append((raw.split(b"\0", 1)[0].decode(), ms[i], cnt[i]))
         return out, per.value
+
+    def adjoint(self, nsteps, ckpt_every=50, objective=PF_OBJ_WETTED, want_phi=True):
+        """(J, dJ/dtheta_bot [per degree], dJ/dmobility, dJ/dphi0 or None) of the CH
+        step with the velocity fixed, from the current state; leaves phi^N."""
+        out = (C.c_double * 3)()
+        g = None
+        ptr = None
+        if want_phi:
+            cnt, _ = self.info("phi")
+            g = np.empty(cnt, dtype=self.dtype)
+            ptr = g.ctypes.data_as(C.c_void_p)
+        self._chk(self.lib.pf_adjoint(self.h, int(nsteps), int(ckpt_every), int(objective), out, ptr, 0))
+        if g is not None:
+            g = g.reshape(self.grid.fine_shape)
+        return out[0], out[1], out[2], g
 
     def set_tuning(self, knob, value):
         self._chk(self.lib.pf_set_tuning(self.h, int(knob), int(value)))

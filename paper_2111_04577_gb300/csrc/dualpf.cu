@@ -27,6 +27,7 @@
 #include "reduce.cuh"
 #include "spectral.cuh"
 #include "batch.cuh"
+#include "adjoint.cuh"
 
 namespace pf {
 
@@ -117,6 +118,7 @@ struct ImplBase {
   virtual void profile(int nsteps, int flags, std::vector<std::string>& names, std::vector<double>& ms,
                        std::vector<int>& counts, int& per_step) = 0;
   virtual void set_tuning(int knob, int value) = 0;
+  virtual void adjoint(int nsteps, int K, int which, double out[3], void* dphi0, int on_dev) = 0;
   virtual int get_tuning(int knob) const = 0;
 };
 
@@ -172,6 +174,7 @@ struct Impl : ImplBase {
   Phys p{};
   PhysT<T> q{};
   double sigma = 1.0;
+  double prm_S = 0.0;  // S as given (0: the Eq. NS30 minimum, which moves with M)
   bool have_params = false;
   cudaStream_t st;
   Arena ar;
@@ -510,6 +513,7 @@ struct Impl : ImplBase {
   void set_params(const pf_params& prm) override {
     p = derive(prm, g);
     sigma = prm.sigma;
+    prm_S = prm.S;
     q.idt = (T)(1.0 / p.dt);
     q.irho0 = (T)(1.0 / p.rho0);
     q.inum = (T)(1.0 / p.nu_m);
@@ -669,6 +673,168 @@ struct Impl : ImplBase {
   int get_tuning(int knob) const override {
     if (knob < 0 || knob >= PF_TUNE_COUNT) throw ApiError(PF_ERR_ARG, "unknown tuning knob");
     return tune[knob];
+  }
+
+
+  // ------------------------------------------------------------------ adjoint
+  std::unique_ptr<Arena> adj_ar;
+  int adj_K = 0, adj_nseg = 0;
+  std::vector<T*> ck_n, ck_o, st_buf;
+  T *a_phis = nullptr, *a_adv = nullptr, *a_delta = nullptr, *a_eps = nullptr, *a_ebar = nullptr,
+    *a_rbar = nullptr, *a_mubar = nullptr, *a_tmp = nullptr, *a_next = nullptr, *a_cur = nullptr,
+    *a_next2 = nullptr, *a_cur2 = nullptr, *a_fin_n = nullptr, *a_fin_o = nullptr;
+  double *a_thb = nullptr, *a_part = nullptr;
+
+  void adj_alloc(int K, int nseg) {
+    if (adj_ar && adj_K >= K && adj_nseg >= nseg) return;
+    adj_ar.reset(new Arena());
+    const size_t nf = (size_t)d.fnx * d.fny * d.fnz;
+    ck_n.assign(nseg, nullptr);
+    ck_o.assign(nseg, nullptr);
+    for (int s = 0; s < nseg; ++s) {
+      ck_n[s] = adj_ar->get<T>(nf);
+      ck_o[s] = adj_ar->get<T>(nf);
+    }
+    st_buf.assign(K + 2, nullptr);
+    for (int m = 0; m < K + 2; ++m) st_buf[m] = adj_ar->get<T>(nf);
+    T** ws[] = {&a_phis, &a_adv, &a_delta, &a_eps, &a_ebar, &a_rbar, &a_mubar, &a_tmp,
+                &a_next, &a_cur, &a_next2, &a_cur2, &a_fin_n, &a_fin_o};
+    for (T** w : ws) *w = adj_ar->get<T>(nf);
+    a_thb = adj_ar->get<double>((size_t)d.fnx * d.fny);
+    a_part = adj_ar->get<double>((size_t)nred_blocks * 5);
+    adj_K = K;
+    adj_nseg = nseg;
+  }
+
+  void dcopy(T* dst, const T* src) {
+    const size_t nf = (size_t)d.fnx * d.fny * d.fnz;
+    PF_CUDA_TRY(cudaMemcpyAsync(dst, src, nf * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  }
+
+  void fine_solve(const T* in, T* out, double shift) {
+    const int nlf = d.fny * d.fnz;
+    rfft_x(FineArrPro<T>{in, d.fnx}, spF, d.fnx, nlf, pF, plFx, twFx);
+    if (d.dim == 3) fft_y(spF, d.fny, pF, d.fnx / 2 + 1, d.fnz, plFy, twFy, -1);
+    zsolve(spF, d.fnz, d.fny, pF, d.fnx / 2 + 1, eFx, eFy, Z_NEUMANN, d.h * d.h, shift, shift, false,
+           1.0 / ((double)d.fnx * d.fny), false);
+    if (d.dim == 3) fft_y(spF, d.fny, pF, d.fnx / 2 + 1, d.fnz, plFy, twFy, +1);
+    irfft_x(spF, ArrEpi<T>{out, d.fnx}, d.fnx, nlf, pF, plFx, twFx, (T)1);
+  }
+
+  // d c/d M and d alpha/d M of Eq. NS29 (S at its minimum moves with M)
+  void dshift_dM(double& dc, double& da) const {
+    const double M = p.mob;
+    if (prm_S <= 0.0) {
+      dc = -p.c / (2.0 * M);
+      da = p.c / (2.0 * M);
+      return;
+    }
+    const double S = p.S, eta2 = p.eta * p.eta;
+    const double kap = 4.0 * p.gamma0 * eta2 * eta2 / (p.lam * p.dt * S * S);
+    const double disc = 1.0 - kap / M;
+    if (disc <= 1e-300) throw ApiError(PF_ERR_DISCRIMINANT, "d alpha/dM is unbounded at the Eq. NS30 limit with a fixed S");
+    da = -S / (2.0 * eta2) * (kap / (M * M)) / (2.0 * std::sqrt(disc));
+    dc = da;
+  }
+
+  void adjoint_step(const T* pn, const T* po, const T* pnew, double& thb, double& mb) {
+    const size_t nf = (size_t)d.fnx * d.fny * d.fnz;
+    const RowLaunch lf = rows(d.fny * d.fnz, d.fnx);
+    const FineView<T> fv{pn, po};
+    const int fo = fc ^ 1;
+    const CoarseVel<T> vel{u[fc], u[fo], v[fc], v[fo], w[fc], w[fo]};
+    const T a1 = (T)(1.0 / (p.Ml * p.dt)), a2 = (T)(1.0 / p.Ml);
+    const int nb = nred_blocks;
+    k_adj_prep<T><<<lf.grid, lf.block, 0, st>>>(fv, vel, a_phis, a_adv, d, q);
+    k_sub<T><<<nb, 256, 0, st>>>(pnew, a_phis, a_delta, nf);
+    k_lapN_axpy<T><<<lf.grid, lf.block, 0, st>>>(a_delta, a_delta, (T)p.alpha, a_eps, d, q);
+    fine_solve(a_next, a_ebar, -p.alpha);  // (L_N + alpha) eps_bar = phi_bar^{n+1}
+    fine_solve(a_ebar, a_rbar, p.c);       // (L_N - c) R_bar = eps_bar
+    k_lapN_axpy<T><<<lf.grid, lf.block, 0, st>>>(a_rbar, (const T*)nullptr, (T)0, a_mubar, d, q);
+    k_sub<T><<<nb, 256, 0, st>>>(po, pn, a_tmp, nf);
+    k_dots<T><<<nb, 256, 0, st>>>(a_ebar, a_delta, a_rbar, a_eps, a_rbar, a_tmp, a_rbar, a_adv, nf, a_part);
+    k_adj_phibar<T><<<lf.grid, lf.block, 0, st>>>(a_phis, a_rbar, a_mubar, a_next, a_cur, a_next2, a_cur2, a_thb, vel,
+                                                  d, p, q, a1, a2);
+    k_sum_d<<<nb, 256, 0, st>>>(a_thb, (size_t)d.fnx * d.fny, a_part + (size_t)4 * nb);
+    check_launch();
+    std::vector<double> h((size_t)5 * nb);
+    PF_CUDA_TRY(cudaMemcpyAsync(h.data(), a_part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PF_CUDA_TRY(cudaStreamSynchronize(st));
+    double dots[4] = {0, 0, 0, 0}, th = 0;
+    for (int b = 0; b < nb; ++b) {
+      for (int k = 0; k < 4; ++k) dots[k] += h[(size_t)b * 4 + k];
+      th += h[(size_t)4 * nb + b];
+    }
+    const double alpha_bar = -dots[0], c_bar = dots[1], s1 = dots[2], s2 = dots[3];
+    double dc = 0, da = 0;
+    dshift_dM(dc, da);
+    const double M = p.mob;
+    mb += -(double)a1 / M * s1 + (double)a2 / M * s2 + c_bar * dc + alpha_bar * da;
+    thb += th;
+    std::swap(a_next, a_next2);
+    std::swap(a_cur, a_cur2);
+  }
+
+  // Gradients of an objective of phi after nsteps CH steps (velocity fixed):
+  // out[0] = J, out[1] = dJ/d theta_bot (per degree), out[2] = dJ/d mobility;
+  // dphi0 (optional) receives dJ/d phi^0.  Checkpoints every K steps; each
+  // segment is recomputed forward before its reverse sweep.
+  void adjoint(int nsteps, int K, int which, double out[3], void* dphi0, int on_dev) override {
+    if (!have_params) throw ApiError(PF_ERR_ARG, "pf_set_params must precede pf_adjoint");
+    if (nsteps < 1 || K < 1) throw ApiError(PF_ERR_ARG, "nsteps and ckpt_every must be >= 1");
+    if (which != 0 && which != 1) throw ApiError(PF_ERR_ARG, "objective must be PF_OBJ_WETTED or PF_OBJ_CENTROID_Z");
+    const int nseg = (nsteps + K - 1) / K;
+    adj_alloc(K, nseg);
+    const size_t nf = (size_t)d.fnx * d.fny * d.fnz;
+    // forward sweep with checkpoints of the BDF2 state (phi^n, phi^{n-1})
+    for (int s = 0; s < nseg; ++s) {
+      dcopy(ck_n[s], phi[pc]);
+      dcopy(ck_o[s], phi[pc ^ 1]);
+      step(std::min(K, nsteps - s * K), PF_STEP_CH_ONLY);
+    }
+    double dg[6];
+    diagnostics(dg);
+    const double J = which == 0 ? dg[2] : dg[5];
+    dcopy(a_fin_n, phi[pc]);
+    dcopy(a_fin_o, phi[pc ^ 1]);
+    const RowLaunch lf = rows(d.fny * d.fnz, d.fnx);
+    const double D = 0.5 * ((double)nf + dg[0] / std::pow(d.h, d.dim));
+    k_obj_seed<T><<<lf.grid, lf.block, 0, st>>>(a_next, d, which, dg[5], D);
+    PF_CUDA_TRY(cudaMemsetAsync(a_cur, 0, nf * sizeof(T), st));
+    double thb = 0, mb = 0;
+    for (int s = nseg - 1; s >= 0; --s) {
+      const int len = std::min(K, nsteps - s * K);
+      // recompute the segment: st_buf[0] = phi^{sK-1}, st_buf[m+1] = phi^{sK+m}
+      dcopy(phi[pc], ck_n[s]);
+      dcopy(phi[pc ^ 1], ck_o[s]);
+      dcopy(st_buf[0], ck_o[s]);
+      dcopy(st_buf[1], ck_n[s]);
+      for (int m = 1; m <= len; ++m) {
+        step(1, PF_STEP_CH_ONLY);
+        dcopy(st_buf[m + 1], phi[pc]);
+      }
+      for (int m = len; m >= 1; --m) adjoint_step(st_buf[m], st_buf[m - 1], st_buf[m + 1], thb, mb);
+    }
+    // phi^{-1} = phi^0 at start-up: both adjoints land on phi^0
+    {
+      // a_tmp = a_next + a_cur
+      std::vector<T> hn(nf), hc(nf);
+      PF_CUDA_TRY(cudaMemcpyAsync(hn.data(), a_next, nf * sizeof(T), cudaMemcpyDeviceToHost, st));
+      PF_CUDA_TRY(cudaMemcpyAsync(hc.data(), a_cur, nf * sizeof(T), cudaMemcpyDeviceToHost, st));
+      PF_CUDA_TRY(cudaStreamSynchronize(st));
+      for (size_t i = 0; i < nf; ++i) hn[i] += hc[i];
+      if (dphi0) {
+        if (on_dev) PF_CUDA_TRY(cudaMemcpyAsync(dphi0, hn.data(), nf * sizeof(T), cudaMemcpyHostToDevice, st));
+        else std::memcpy(dphi0, hn.data(), nf * sizeof(T));
+      }
+    }
+    // leave the context at phi^N, as pf_step would
+    dcopy(phi[pc], a_fin_n);
+    dcopy(phi[pc ^ 1], a_fin_o);
+    PF_CUDA_TRY(cudaStreamSynchronize(st));
+    out[0] = J;
+    out[1] = thb * M_PI / 180.0;
+    out[2] = mb;
   }
 
   // per-kernel average device time over nsteps direct (non-graph) steps
@@ -1138,6 +1304,11 @@ int pf_set_tuning(pf_ctx* ctx, int knob, int value) {
 int pf_get_tuning(const pf_ctx* ctx, int knob, int* value) {
   if (!ctx || !value) return PF_ERR_ARG;
   return guarded(const_cast<pf_ctx*>(ctx), [&] { *value = ctx->impl->get_tuning(knob); });
+}
+
+int pf_adjoint(pf_ctx* ctx, int nsteps, int ckpt_every, int objective, double out[3], void* dphi0, int dphi0_on_device) {
+  if (!ctx || !out) return PF_ERR_ARG;
+  return guarded(ctx, [&] { ctx->impl->adjoint(nsteps, ckpt_every, objective, out, dphi0, dphi0_on_device); });
 }
 
 const char* pf_last_error(const pf_ctx* ctx) { return ctx ? ctx->err.c_str() : g_init_err.c_str(); }

@@ -67,3 +67,18 @@ def test_gradients_equal_finite_differences(which):
     assert abs(th.grad.item() - fd_t) <= 1e-6 * max(1e-8, abs(fd_t)) + 1e-10
     assert abs(mob.grad.item() - fd_m) <= 1e-5 * max(1e-8, abs(fd_m)) + 1e-10
     assert abs(ad_p - fd_p) <= 1e-6 * max(1e-8, abs(fd_p)) + 1e-10
+
+
+def test_split_mobility_parts_add_up():
+    """The three copies of M in the split form carry gradients that add up to dJ/dM."""
+    w = tiny()
+    vel = wl.random_velocity(w.grid, 3, 0.3)
+    phi0 = wl.initial_phi(w)
+    prm = w.params.as_dict()
+    J, _, _, mob, _ = ch_torch.run(w.grid, prm, vel, phi0, 4, "centroid")
+    J.backward()
+    J2, _, _, parts, _ = ch_torch.run(w.grid, prm, vel, phi0, 4, "centroid", split_mobility=True)
+    J2.backward()
+    assert abs(J2.item() - J.item()) < 1e-15
+    total = sum(p.grad.item() for p in parts)
+    assert abs(total - mob.grad.item()) < 1e-12 * sum(abs(p.grad.item()) for p in parts)
