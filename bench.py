@@ -39,6 +39,27 @@ METRIC = "fine-mesh cell-steps/s (dual-res 3D) vs FP64 GPU path at stated error;
 UNIT = "fine cell-steps/s"
 
 
+def rank_env(env=os.environ):
+    """(world, rank, local_rank) as torchrun exports them; 1 process by default."""
+    return int(env.get("WORLD_SIZE", "1")), int(env.get("RANK", "0")), int(env.get("LOCAL_RANK", "0"))
+
+
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest x over all ranks (the slowest replica sets the job's time)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(cells, steps, world, elapsed):
+    """Whole-job throughput of `world` independent replicas, each advancing `cells`
+    fine cells by `steps` steps, over the max-over-ranks elapsed time."""
+    return cells * steps * world / elapsed
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -278,9 +299,7 @@ def main():
         return
 
     import torch
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -314,14 +333,12 @@ def main():
     torch.cuda.synchronize()
     elapsed = time_steps(solver, stream, args.steps)
     torch.cuda.synchronize()
+    elapsed = max_over_ranks(elapsed, dist, "cuda")
     if dist:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
         dist.barrier()
     clocks = clocks_stop(clk, clk_path) if rank == 0 else None
     ms_per_step = elapsed / args.steps * 1e3
-    value = g.fine_cells() * args.steps * world / elapsed
+    value = replica_value(g.fine_cells(), args.steps, world, elapsed)
 
     # ---------------- per-kernel profile and roofline ----------------
     prof, per_step = solver.profile(3)
@@ -353,32 +370,42 @@ def main():
     solver.get("phi", out=pin_out)
     diag = solver.diagnostics()
     t_e2e = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([t_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    t_e2e = max_over_ranks(t_e2e, dist, "cuda")
     h2d = 2 * phi0_f.nbytes  # phi^n and its start-up twin phi^{n-1}
     d2h = phi0_f.nbytes + 6 * 8
-    e2e = {"value": g.fine_cells() * args.steps * world / t_e2e, "unit": UNIT,
+    e2e = {"value": replica_value(g.fine_cells(), args.steps, world, t_e2e), "unit": UNIT,
            "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
            "note": "pf_set_fields(phi from pinned host) + pf_step(K) + pf_get_fields(phi) + pf_diagnostics"}
     launches = per_step * args.steps + (args.steps // 50 + 1)
 
     extra = {}
     if rank == 0 and not args.no_compare:
-        # accuracy of the mixed path against the FP64 GPU path on the same input
+        # accuracy of the mixed paths against the FP64 GPU path on the same input, per field
         nst = 20
-        sm = binding.Solver(g, w.params, binding.PF_MIXED, stream=stream.cuda_stream)
-        sm.load_state(phi0_f)
-        sm.step(nst)
-        phim = sm.get("phi").astype(np.float64)
+        fields = ("phi", "u", "w", "p", "tau")
+
+        def run_fields(prec, x0):
+            sv = binding.Solver(g, w.params, prec, stream=stream.cuda_stream)
+            sv.load_state(x0)
+            sv.step(nst)
+            out = {f: sv.get(f).astype(np.float64) for f in fields}
+            return sv, out
+
+        def field_err(a, b):
+            e = {"phi_maxabs": float(np.max(np.abs(a["phi"] - b["phi"])))}
+            for f in fields[1:]:
+                e[f + "_rel"] = float(np.max(np.abs(a[f] - b[f])) / max(np.max(np.abs(b[f])), 1e-300))
+            return e
+
+        sm, fm = run_fields(binding.PF_MIXED, phi0_f)
         sm.close()
         del sm
-        sd = binding.Solver(g, w.params, binding.PF_FP64, stream=stream.cuda_stream)
-        sd.load_state(phi0)
-        sd.step(nst)
-        phid = sd.get("phi")
-        ud = sd.coarse("u")
+        sz, fz = run_fields(binding.PF_MIXED_Z64, phi0_f)
+        sz.step(2)
+        tz = time_steps(sz, stream, 5)
+        sz.close()
+        del sz
+        sd, fd = run_fields(binding.PF_FP64, phi0)
         sd.step(2)
         t64 = time_steps(sd, stream, 5)
         sd.close()
@@ -386,8 +413,11 @@ def main():
         torch.cuda.empty_cache()
         extra["fp64_path"] = {"value": g.fine_cells() * 5 / t64, "ms_per_step": t64 / 5 * 1e3,
                               "speedup_mixed_over_fp64": (value / world) / (g.fine_cells() * 5 / t64),
-                              "mixed_phi_maxabs_err_vs_fp64_after_steps": float(np.max(np.abs(phim - phid))),
+                              "mixed_err_vs_fp64_after_steps": field_err(fm, fd),
                               "steps_compared": nst}
+        extra["mixed_z64_path"] = {"what": "mixed with FP64 wall-normal eliminations",
+                                   "value": g.fine_cells() * 5 / tz, "ms_per_step": tz / 5 * 1e3,
+                                   "err_vs_fp64_after_steps": field_err(fz, fd)}
         # single resolution: CSR (phi on the coarse mesh) and RSR (all fields on the fine mesh)
         csr = wl.Grid(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, 0)
         rsr = wl.Grid(2 * g.nx, 2 * g.ny, 2 * g.nz, g.lx, g.ly, g.lz, 0)

@@ -33,9 +33,11 @@
  *    TAU, TAU_OLD) are component-major: 3 components (xx, xz, zz) in 2D,
  *    6 (xx, yy, zz, xy, xz, yz) in 3D, each a coarse centre array.
  *  - Element type: a context computes and stores in double (PF_FP64) or in
- *    float with FP64 kept in the named places (PF_MIXED).  pf_set_fields and
- *    pf_get_fields move elements of the context's storage type: double for
- *    PF_FP64, float for PF_MIXED (see pf_field_info).
+ *    float with FP64 kept in the named places (PF_MIXED: the contact-line
+ *    flux, the pressure zero mode and the global reductions; PF_MIXED_Z64
+ *    adds the wall-normal tridiagonal eliminations of every transform solve).
+ *    pf_set_fields and pf_get_fields move elements of the context's storage
+ *    type: double for PF_FP64, float otherwise (see pf_field_info).
  */
 #ifndef DUALPF_H
 #define DUALPF_H
@@ -57,7 +59,7 @@ enum {
   PF_ERR_NOMEM = -7         /* device allocation failed                       */
 };
 
-enum { PF_FP64 = 0, PF_MIXED = 1 };
+enum { PF_FP64 = 0, PF_MIXED = 1, PF_MIXED_Z64 = 2 };
 
 /* Field identifiers for pf_set_fields / pf_get_fields. */
 enum {
@@ -89,7 +91,7 @@ typedef struct pf_ctx pf_ctx;
 typedef struct {
   int nx, ny, nz;
   double lx, ly, lz;
-  int precision; /* PF_FP64 | PF_MIXED */
+  int precision; /* PF_FP64 | PF_MIXED | PF_MIXED_Z64 */
   int dual;
 } pf_grid_desc;
 
@@ -179,6 +181,7 @@ int pf_profile(pf_ctx* ctx, int nsteps, int flags, int max_entries, char* names,
  * makes pf_batch_step return PF_ERR_TIMEOUT (the status is sticky).
  * Field access and diagnostics take a problem index 0..nproblems-1 and
  * behave as pf_set_fields / pf_get_fields / pf_diagnostics on that problem.
+ * Precision PF_FP64 or PF_MIXED (PF_MIXED_Z64: PF_ERR_UNSUPPORTED).
  * ------------------------------------------------------------------------ */
 typedef struct pf_batch pf_batch;
 int pf_batch_create(pf_batch** out, int nproblems, const pf_grid_desc* grids, const pf_params* params,
@@ -238,8 +241,10 @@ int pf_adjoint(pf_ctx* ctx, int nsteps, int ckpt_every, int objective, double ou
  *   PF_TUNE_YFFT_COLS    kx columns per CTA of the y transforms (power of two <= 32)
  *   PF_TUNE_ZSOLVE_COLS  kx columns per CTA of the z solves (multiple of 16, <= 64)
  *   PF_TUNE_ROW_BLOCK    threads per CTA of the row kernels (multiple of 32)
+ *   PF_TUNE_CH_ZCHUNK    fine z planes one CTA of the 3D CH right side walks (>= 2)
  * Errors: PF_ERR_ARG for an unknown knob or a value that does not fit. */
-enum { PF_TUNE_XFFT_PAIRS = 0, PF_TUNE_YFFT_COLS = 1, PF_TUNE_ZSOLVE_COLS = 2, PF_TUNE_ROW_BLOCK = 3, PF_TUNE_COUNT = 4 };
+enum { PF_TUNE_XFFT_PAIRS = 0, PF_TUNE_YFFT_COLS = 1, PF_TUNE_ZSOLVE_COLS = 2, PF_TUNE_ROW_BLOCK = 3, PF_TUNE_CH_ZCHUNK = 4,
+       PF_TUNE_COUNT = 5 };
 int pf_set_tuning(pf_ctx* ctx, int knob, int value);
 int pf_get_tuning(const pf_ctx* ctx, int knob, int* value);
 

@@ -21,6 +21,7 @@ KNOBS = {
     1: ("yfft_cols", [4, 8, 16], ("fft_y_fine", "fft_y_coarse")),
     2: ("zsolve_cols", [16, 32], ("zsolve_pair", "zsolve")),
     3: ("row_block", [64, 128, 256], ("ns_rhs", "div", "correct", "polymer_stage1", "polymer_stage2")),
+    4: ("ch_zchunk", [16, 32, 64], ("ch_rhs",)),
 }
 
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "tuning.json")
@@ -60,7 +61,7 @@ def tune(grid: wl.Grid, params: wl.Params, precision: int, phi0=None, steps: int
         s.profile(1)  # warm: graph-free launches, allocations touched
         best = {}
         for knob, (name, cands, kernels) in KNOBS.items():
-            if grid.dim == 2 and name == "yfft_cols":
+            if grid.dim == 2 and name in ("yfft_cols", "ch_zchunk"):
                 continue
             timings = {}
             for v in cands:

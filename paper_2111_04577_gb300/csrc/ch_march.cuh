@@ -1,0 +1,269 @@
+// Cahn-Hilliard right side on the 3D fine mesh, marching along z.
+//
+// Computes the same R as k_ch_rhs (ch_tiled.cuh; Eqs. NS25-NS34 in increment
+// form, velocity prolonged by Eq. dual1, wall flux g of Eqs. NS15-NS16/NS34 in
+// FP64):
+//     phi* = 2 phi^n - phi^{n-1}
+//     mu*  = f(phi*) - (L_N phi* + B(g))
+//     R    = (phi^{n-1} - phi^n)/(M lambda dt) - div(u* phi*)/(M lambda) + L_N mu*
+// A CTA owns a TX x TY column of fine cells and walks a chunk of z planes.
+// Shared memory holds rings of planes: phi* with a 2-cell x/y halo (five
+// planes: the one being loaded and z-1..z+2), mu* with a 1-cell halo (three
+// planes), phi^{n-1} - phi^n of the owned cells (four planes), and the
+// extrapolated coarse velocities of the current coarse plane (two slots).
+// Every thread keeps the same x/y positions for the whole march, so index
+// arithmetic is done once; the next phi plane is prefetched into registers
+// while the current planes are computed.
+//
+// Per plane: store the prefetched plane; sync; prefetch the next one; mu* of
+// plane z+1; sync; R of plane z.  The ring depths make every slot that is
+// written after a barrier one that no thread can still be reading.
+#pragma once
+#include "ch.cuh"
+
+namespace pf {
+
+struct MarchTile {
+  static constexpr int TX = 64, TY = 8, NT = 256;
+  static constexpr int SX = TX + 4, SY = TY + 4, SP = SX * SY;  // phi* plane with 2-cell halo
+  static constexpr int MX = TX + 2, MY = TY + 2, MP = MX * MY;  // mu* plane with 1-cell halo
+  static constexpr int OP = TX * TY;                            // owned cells per plane
+  static constexpr int NPS = 5, NMS = 3, NDS = 4;               // ring depths
+  static constexpr int KS = (SP + NT - 1) / NT;                 // staged phi* elements per thread
+  static constexpr int KM = (MP + NT - 1) / NT;                 // mu* elements per thread
+  static constexpr int KO = OP / NT;                            // owned cells per thread
+  // coarse velocity box of one coarse plane: x, y from one cell before the tile
+  __host__ __device__ static constexpr int VX(int rs) { return (TX >> rs) + 2; }
+  __host__ __device__ static constexpr int VY(int rs) { return (TY >> rs) + 2; }
+  // elements of T in shared memory
+  __host__ __device__ static constexpr int smem_elems(int rs) {
+    return NPS * SP + NMS * MP + NDS * OP + 2 * 4 * VX(rs) * VY(rs);
+  }
+};
+
+__device__ __forceinline__ int pmod_m(int x, int n) {
+  x %= n;
+  return x < 0 ? x + n : x;
+}
+
+template <class T>
+__global__ void __launch_bounds__(MarchTile::NT, 3) k_ch_rhs_march(const FineView<T> f, const CoarseVel<T> vel,
+                                                                T* __restrict__ R, double* __restrict__ gwall,
+                                                                const Dims d, const Phys p, const PhysT<T> q,
+                                                                const T inv_mldt, const T inv_ml, const int nzc) {
+  using TL = MarchTile;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int VX = TL::VX(d.rs), VY = TL::VY(d.rs), NV = VX * VY;
+  T* ps = reinterpret_cast<T*>(smraw);  // [NPS][SY][SX]
+  T* ms = ps + TL::NPS * TL::SP;        // [NMS][MY][MX]
+  T* ds = ms + TL::NMS * TL::MP;        // [NDS][TY][TX]
+  T* vb = ds + TL::NDS * TL::OP;        // [2 slots][u, v, w_lo, w_hi][VY][VX]
+  const int t = threadIdx.x;
+  const int x0 = blockIdx.x * TL::TX, y0 = blockIdx.y * TL::TY;
+  const int fnx = d.fnx, fny = d.fny, fnz = d.fnz;
+  const size_t plane = (size_t)fnx * fny;
+  const int zb = blockIdx.z * nzc, ze = min(zb + nzc, fnz);
+
+  // ---- per-thread positions, fixed for the whole march ----
+  int sxy[TL::KS];  // global x/y offset of each staged phi* element (-1: none)
+  int sown[TL::KS]; // owned-cell index of a staged element, or -1
+#pragma unroll
+  for (int k = 0; k < TL::KS; ++k) {
+    const int e = t + k * TL::NT;
+    sxy[k] = -1;
+    sown[k] = -1;
+    if (e < TL::SP) {
+      const int yy = e / TL::SX, xx = e - yy * TL::SX;
+      sxy[k] = pmod_m(y0 - 2 + yy, fny) * fnx + pmod_m(x0 - 2 + xx, fnx);
+      if (xx >= 2 && xx < TL::TX + 2 && yy >= 2 && yy < TL::TY + 2) sown[k] = (yy - 2) * TL::TX + (xx - 2);
+    }
+  }
+  // mu* positions: offset in the phi* plane, owner flag for the wall flux
+  int mso[TL::KM];
+  int mcol[TL::KM];  // wall column (y * fnx + x) when owned, else -1
+#pragma unroll
+  for (int k = 0; k < TL::KM; ++k) {
+    const int e = t + k * TL::NT;
+    mso[k] = -1;
+    mcol[k] = -1;
+    if (e < TL::MP) {
+      const int my = e / TL::MX, mx = e - my * TL::MX;
+      mso[k] = (my + 1) * TL::SX + (mx + 1);
+      const int gx = x0 - 1 + mx, gy = y0 - 1 + my;
+      if (mx >= 1 && mx <= TL::TX && my >= 1 && my <= TL::TY && gx < fnx && gy < fny) mcol[k] = gy * fnx + gx;
+    }
+  }
+  // coarse velocity box origin and loader positions
+  const int cx0 = (x0 >> d.rs) - 1, cy0 = (y0 >> d.rs) - 1;
+  const int cplane = d.nx * d.ny;
+
+  auto star_load = [&](int gz, T (&reg)[TL::KS], T (&dreg)[TL::KS]) {
+    const size_t zo = (size_t)min(max(gz, 0), fnz - 1) * plane;
+#pragma unroll
+    for (int k = 0; k < TL::KS; ++k) {
+      if (sxy[k] >= 0) {
+        const size_t o = zo + sxy[k];
+        const T a = f.pn[o], b = f.po[o];
+        reg[k] = (T)2 * a - b;
+        dreg[k] = b - a;
+      }
+    }
+  };
+  auto star_store = [&](int slot, int dslot, const T (&reg)[TL::KS], const T (&dreg)[TL::KS]) {
+    T* pp = ps + slot * TL::SP;
+    T* dd = ds + dslot * TL::OP;
+#pragma unroll
+    for (int k = 0; k < TL::KS; ++k) {
+      const int e = t + k * TL::NT;
+      if (e < TL::SP) {
+        pp[e] = reg[k];
+        if (sown[k] >= 0) dd[sown[k]] = dreg[k];
+      }
+    }
+  };
+  auto vel_load = [&](int kc, int slot) {
+    T* vu = vb + slot * 4 * NV;
+    const int czw = kc + 1;  // w faces kc and kc + 1 (kc + 1 <= nz)
+    for (int e = t; e < NV; e += TL::NT) {
+      const int yy = e / VX, xx = e - yy * VX;
+      const int cx = pmod_m(cx0 + xx, d.nx), cy = pmod_m(cy0 + yy, d.ny);
+      const size_t oc = (size_t)kc * cplane + cy * d.nx + cx;
+      const size_t colw = (size_t)cy * d.nx + cx;
+      vu[e] = vel.us(oc);
+      vu[NV + e] = vel.vs(oc);
+      vu[2 * NV + e] = vel.ws((size_t)kc * cplane + colw);
+      vu[3 * NV + e] = vel.ws((size_t)czw * cplane + colw);
+    }
+  };
+  // mu* of plane gz into ring slot mslot, from phi* slots (gz-1, gz, gz+1)
+  auto mu_plane = [&](int gz, int sm1, int s0, int sp1, int mslot) {
+    T* mm = ms + mslot * TL::MP;
+    const T* pm = ps + sm1 * TL::SP;
+    const T* pc = ps + s0 * TL::SP;
+    const T* pq = ps + sp1 * TL::SP;
+#pragma unroll
+    for (int k = 0; k < TL::KM; ++k) {
+      const int e = t + k * TL::NT;
+      if (mso[k] < 0) continue;
+      if (gz < 0 || gz >= fnz) {
+        mm[e] = (T)0;
+        continue;
+      }
+      const int o = mso[k];
+      const T c0 = pc[o];
+      T lap = pc[o + 1] + pc[o - 1] - 2 * c0;
+      lap += pc[o + TL::SX] + pc[o - TL::SX] - 2 * c0;
+      const T czp = gz + 1 < fnz ? pq[o] : c0;
+      const T czm = gz > 0 ? pm[o] : c0;
+      lap = (lap + czp + czm - 2 * c0) * q.ih2;
+      T B = 0;
+      if (gz == 0) {
+        const double g = wall_g(p.cos_bot, (double)c0, (double)czp, p.eta);
+        if (mcol[k] >= 0) gwall[mcol[k]] = g;
+        B += (T)(g / d.h);
+      }
+      if (gz == fnz - 1) {
+        const double g = wall_g(p.cos_top, (double)c0, (double)czm, p.eta);
+        if (mcol[k] >= 0) gwall[plane + mcol[k]] = g;
+        B += (T)(g / d.h);
+      }
+      mm[e] = c0 * (c0 * c0 - 1) * q.ie2 - (lap + B);
+    }
+  };
+
+  // ---- owned cells: fixed offsets of the face velocities in the box ----
+  // thread t owns (tx, ty) and (tx, ty + TY/2)
+  const int tx = t % TL::TX, tyb = t / TL::TX;
+  const int gx = x0 + tx;
+  const bool xin = gx < fnx;
+  // x faces gx and gx + 1; y faces gy and gy + 1 (unwrapped: the box holds the periodic images)
+  const int iu0 = (gx >> d.rs) - cx0, iu1 = ((gx + 1) >> d.rs) - cx0;
+  const bool hu0 = (gx & (d.r - 1)) != 0, hu1 = ((gx + 1) & (d.r - 1)) != 0;
+  const int iwx = (gx >> d.rs) - cx0;
+
+  // ---- prologue: phi* planes zb-2 .. zb+1, mu* planes zb-1, zb ----
+  {
+    T reg[TL::KS], dreg[TL::KS];
+#pragma unroll
+    for (int k = 0; k < TL::KS; ++k) reg[k] = dreg[k] = (T)0;
+    for (int j = 0; j < 4; ++j) {
+      star_load(zb - 2 + j, reg, dreg);
+      star_store(j, j >= 2 ? j - 2 : 3, reg, dreg);  // d slots: plane zb + m at m & 3
+    }
+  }
+  __syncthreads();
+  mu_plane(zb - 1, 0, 1, 2, 0);
+  mu_plane(zb, 1, 2, 3, 1);
+  T reg[TL::KS], dreg[TL::KS];
+#pragma unroll
+  for (int k = 0; k < TL::KS; ++k) reg[k] = dreg[k] = (T)0;
+  star_load(zb + 2, reg, dreg);
+  int kc_loaded = -1;
+
+  for (int z = zb; z < ze; ++z) {
+    const int m = z - zb;
+    // ring slots: phi* plane zb + j at (j + 2) % 5; mu* plane zb + j at (j + 1) % 3; d plane zb + j at j & 3
+    const int sP = (m + 4) % 5;  // plane z + 2
+    star_store(sP, (m + 2) & 3, reg, dreg);
+    const int kc = z >> d.rs;
+    if (kc != kc_loaded) {
+      vel_load(kc, kc & 1);
+      kc_loaded = kc;
+    }
+    __syncthreads();
+    if (z + 1 < ze) star_load(z + 3, reg, dreg);
+    mu_plane(z + 1, (m + 2) % 5, (m + 3) % 5, (m + 4) % 5, (m + 2) % 3);
+    __syncthreads();
+    // ---- R of plane z ----
+    const T* pm = ps + ((m + 1) % 5) * TL::SP;
+    const T* pc = ps + ((m + 2) % 5) * TL::SP;
+    const T* pq = ps + ((m + 3) % 5) * TL::SP;
+    const T* mmm = ms + (m % 3) * TL::MP;
+    const T* mmc = ms + ((m + 1) % 3) * TL::MP;
+    const T* mmp = ms + ((m + 2) % 3) * TL::MP;
+    const T* dd = ds + (m & 3) * TL::OP;
+    const T* vu = vb + (kc & 1) * 4 * NV;
+    const T* vv = vu + NV;
+    const T* vw = vu + 2 * NV;
+    // fine z faces z (bottom) and z + 1 (top) of this plane, in layers of the box
+    const int kf0 = (z >> d.rs) - kc, kf1 = ((z + 1) >> d.rs) - kc;
+    const bool hw0 = (z & (d.r - 1)) != 0, hw1 = ((z + 1) & (d.r - 1)) != 0;
+#pragma unroll
+    for (int k = 0; k < TL::KO; ++k) {
+      const int ty = tyb + k * (TL::TY / TL::KO);
+      const int gy = y0 + ty;
+      if (!xin || gy >= fny) continue;
+      const int iv0 = (gy >> d.rs) - cy0, iv1 = ((gy + 1) >> d.rs) - cy0;
+      const bool hv0 = (gy & (d.r - 1)) != 0, hv1 = ((gy + 1) & (d.r - 1)) != 0;
+      const int jr = ((gy >> d.rs) - cy0) * VX;  // box row of this fine row
+      // prolonged face velocities (Eq. dual1)
+      const T ua = vu[jr + iu0], ub = vu[jr + iu1];
+      const T u0 = hu0 ? (T)0.5 * (ua + vu[jr + iu0 + 1]) : ua;
+      const T u1 = hu1 ? (T)0.5 * (ub + vu[jr + iu1 + 1]) : ub;
+      const T va = vv[iv0 * VX + iwx], vb1 = vv[iv1 * VX + iwx];
+      const T v0 = hv0 ? (T)0.5 * (va + vv[(iv0 + 1) * VX + iwx]) : va;
+      const T v1 = hv1 ? (T)0.5 * (vb1 + vv[(iv1 + 1) * VX + iwx]) : vb1;
+      const T wa = vw[kf0 * NV + jr + iwx], wb = vw[kf1 * NV + jr + iwx];
+      const T w0 = hw0 ? (T)0.5 * (wa + vw[(kf0 + 1) * NV + jr + iwx]) : wa;
+      const T w1 = hw1 ? (T)0.5 * (wb + vw[(kf1 + 1) * NV + jr + iwx]) : wb;
+      const int so = (ty + 2) * TL::SX + (tx + 2);
+      const T c0 = pc[so];
+      T adv = u1 * (c0 + pc[so + 1]) - u0 * (pc[so - 1] + c0);
+      adv += v1 * (c0 + pc[so + TL::SX]) - v0 * (pc[so - TL::SX] + c0);
+      if (z + 1 < fnz) adv += w1 * (c0 + pq[so]);
+      if (z > 0) adv -= w0 * (pm[so] + c0);
+      adv *= (T)0.5 * q.ih;
+      const int mo = (ty + 1) * TL::MX + (tx + 1);
+      const T m0 = mmc[mo];
+      T lap = mmc[mo + 1] + mmc[mo - 1] - 2 * m0;
+      lap += mmc[mo + TL::MX] + mmc[mo - TL::MX] - 2 * m0;
+      const T mzp = z + 1 < fnz ? mmp[mo] : m0;
+      const T mzm = z > 0 ? mmm[mo] : m0;
+      lap = (lap + mzp + mzm - 2 * m0) * q.ih2;
+      const size_t o = (size_t)z * plane + (size_t)gy * fnx + gx;
+      R[o] = dd[ty * TL::TX + tx] * inv_mldt - adv * inv_ml + lap;
+    }
+  }
+}
+
+}  // namespace pf

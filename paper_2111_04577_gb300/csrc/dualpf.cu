@@ -21,6 +21,7 @@
 #include "../../include/dualpf.h"
 #include "ch.cuh"
 #include "ch_tiled.cuh"
+#include "ch_march.cuh"
 #include "ns.cuh"
 #include "ns_rhs.cuh"
 #include "polymer.cuh"
@@ -326,6 +327,7 @@ struct Impl : ImplBase {
     PF_CUDA_TRY(cudaFuncSetAttribute(k_rfft_x<T, FineArrPro<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict<T, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict<T, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict<T, 3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
@@ -423,10 +425,11 @@ struct Impl : ImplBase {
       const size_t sm = (TL::NS + TL::NM + 3 * TL::NV(d.rs, d.rys)) * sizeof(T);
       k_ch_rhs<T, 2><<<grid, 256, sm, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml);
     } else {
-      using TL = RhsTile<3, sizeof(T)>;
-      dim3 grid((d.fnx + TL::TX - 1) / TL::TX, (d.fny + TL::TY - 1) / TL::TY, (d.fnz + TL::TZ - 1) / TL::TZ);
-      const size_t sm = (TL::NS + TL::NM + 3 * TL::NV(d.rs, d.rys)) * sizeof(T);
-      k_ch_rhs<T, 3><<<grid, 256, sm, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml);
+      using TL = MarchTile;
+      const int nzc = std::min(d.fnz, tune[PF_TUNE_CH_ZCHUNK] > 0 ? tune[PF_TUNE_CH_ZCHUNK] : 32);
+      dim3 grid((d.fnx + TL::TX - 1) / TL::TX, (d.fny + TL::TY - 1) / TL::TY, (d.fnz + nzc - 1) / nzc);
+      const size_t sm = (size_t)TL::smem_elems(d.rs) * sizeof(T);
+      k_ch_rhs_march<T><<<grid, TL::NT, sm, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml, nzc);
     }
     const int nlf = d.fny * d.fnz;
     rfft_x(FineArrPro<T>{mu, d.fnx}, spF, d.fnx, nlf, pF, plFx, twFx);
@@ -495,8 +498,8 @@ struct Impl : ImplBase {
       }
       mark("polymer_stage1");
       const RowLaunch lp = rows(d.ny * d.nz, d.nx, 128);
-      if (d.dim == 2) k_polymer<T, 2><<<lp.grid, lp.block, 0, st>>>(P, d, q, 1);
-      else k_polymer<T, 3><<<lp.grid, lp.block, 0, st>>>(P, d, q, 1);
+      if (d.dim == 2) k_polymer<T, 2, 1><<<lp.grid, lp.block, 0, st>>>(P, d, q);
+      else k_polymer<T, 3, 1><<<lp.grid, lp.block, 0, st>>>(P, d, q);
       for (int c = 0; c < ncomp; ++c) {
         P.th[c] = theta1[c];
         P.base[c] = theta[c];
@@ -504,8 +507,8 @@ struct Impl : ImplBase {
         P.tau[c] = tau[fo][c];
       }
       mark("polymer_stage2");
-      if (d.dim == 2) k_polymer<T, 2><<<lp.grid, lp.block, 0, st>>>(P, d, q, 2);
-      else k_polymer<T, 3><<<lp.grid, lp.block, 0, st>>>(P, d, q, 2);
+      if (d.dim == 2) k_polymer<T, 2, 2><<<lp.grid, lp.block, 0, st>>>(P, d, q);
+      else k_polymer<T, 3, 2><<<lp.grid, lp.block, 0, st>>>(P, d, q);
     }
   }
 
@@ -665,6 +668,7 @@ struct Impl : ImplBase {
       if (knob == PF_TUNE_ZSOLVE_COLS && (value % 16 || value > 64 || (size_t)std::max(d.fnz, d.nz) * value * (sizeof(cpx<T>) + 2 * sizeof(TC)) > (size_t)kMaxSmem))
         throw ApiError(PF_ERR_ARG, "z-solve columns must be a multiple of 16 that fits in shared memory");
       if (knob == PF_TUNE_ROW_BLOCK && (value % 32 || value > 1024)) throw ApiError(PF_ERR_ARG, "row block must be a multiple of 32");
+      if (knob == PF_TUNE_CH_ZCHUNK && value < 2) throw ApiError(PF_ERR_ARG, "z chunk must be at least 2 planes");
     }
     tune[knob] = value;
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
@@ -1220,7 +1224,8 @@ int pf_init_grid(pf_ctx** out, const pf_grid_desc* g, void* stream) {
     const double dx = g->lx / g->nx;
     if (std::fabs(g->lz / g->nz - dx) > 1e-9 * dx || (g->ny > 1 && std::fabs(g->ly / g->ny - dx) > 1e-9 * dx))
       throw pf::ApiError(PF_ERR_ARG, "cells must be cubes: lx/nx = ly/ny = lz/nz");
-    if (g->precision != PF_FP64 && g->precision != PF_MIXED) throw pf::ApiError(PF_ERR_ARG, "precision must be PF_FP64 or PF_MIXED");
+    if (g->precision != PF_FP64 && g->precision != PF_MIXED && g->precision != PF_MIXED_Z64)
+      throw pf::ApiError(PF_ERR_ARG, "precision must be PF_FP64, PF_MIXED or PF_MIXED_Z64");
     if (g->nx % 2 || (g->ny > 1 && g->ny % 2)) throw pf::ApiError(PF_ERR_UNSUPPORTED, "nx and ny (3D) must be even");
     for (int n : {g->nx, g->ny, g->nz})
       if (!pf::smooth(n)) throw pf::ApiError(PF_ERR_UNSUPPORTED, "sizes must be 2^a 3^b 5^c 7^d");
@@ -1231,6 +1236,7 @@ int pf_init_grid(pf_ctx** out, const pf_grid_desc* g, void* stream) {
       ctx->own_stream = true;
     }
     if (g->precision == PF_FP64) ctx->impl.reset(new pf::Impl<double, double>(*g, ctx->stream));
+    else if (g->precision == PF_MIXED_Z64) ctx->impl.reset(new pf::Impl<float, double>(*g, ctx->stream));
     else ctx->impl.reset(new pf::Impl<float, float>(*g, ctx->stream));
   });
   if (rc != PF_OK) {
@@ -1342,6 +1348,8 @@ int pf_batch_create(pf_batch** out, int nproblems, const pf_grid_desc* grids, co
   int rc = bguarded(b.get(), [&] {
     for (int i = 0; i < nproblems; ++i) {
       const pf_grid_desc& g = grids[i];
+      if (g.precision != PF_FP64 && g.precision != PF_MIXED)
+        throw pf::ApiError(PF_ERR_UNSUPPORTED, "batched problems run PF_FP64 or PF_MIXED");
       if (g.nx < 2 || g.nz < 2 || g.nx % 2) throw pf::ApiError(PF_ERR_ARG, "need even nx >= 2 and nz >= 2");
       const double dx = g.lx / g.nx;
       if (std::fabs(g.lz / g.nz - dx) > 1e-9 * dx) throw pf::ApiError(PF_ERR_ARG, "cells must be squares");

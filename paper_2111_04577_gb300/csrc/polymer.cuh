@@ -38,28 +38,36 @@ __device__ __forceinline__ T fexp(T x) { return exp(x); }
 template <>
 __device__ __forceinline__ float fexp<float>(float x) { return __expf(x); }
 
-// one Jacobi rotation zeroing A[p][q] (A symmetric, full storage), V <- V J
+// Symmetric N x N matrix held as its N diagonal and N(N-1)/2 off-diagonal
+// entries; off-diagonal slot of (p, q): 2D (0,1) -> 0; 3D (0,1) -> 0,
+// (0,2) -> 1, (1,2) -> 2.
+template <int N>
+__device__ __forceinline__ constexpr int off_slot(int p, int q) {
+  return N == 2 ? 0 : (p + q - 1);
+}
+
+// One Jacobi rotation P (P_pp = P_qq = c, P_pq = s, P_qp = -s) that zeroes
+// a_pq: A <- P^T A P on the unique entries only, V <- V P.
 template <class T, int N>
-__device__ __forceinline__ void jacobi_rot(T A[N][N], T V[N][N], int p, int q) {
-  const T apq = A[p][q];
+__device__ __forceinline__ void jacobi_rot_sym(T (&dg)[N], T (&of)[N == 2 ? 1 : 3], T (&V)[N][N], int p, int q) {
+  const int pq = off_slot<N>(p, q);
+  const T apq = of[pq];
   if (apq == (T)0) return;
-  const T th = (A[q][q] - A[p][p]) / (2 * apq);
+  const T th = (dg[q] - dg[p]) / (2 * apq);
   const T ath = fabs(th);
   // t = sgn(th)/(|th| + sqrt(th^2 + 1)), the smaller root; 1/(2 th) when th^2 would overflow
   T t = ath > (T)1e15 ? (T)0.5 / ath : (T)1 / (ath + sqrt(ath * ath + (T)1));
   if (th < 0) t = -t;
-  const T c = (T)1 / sqrt(t * t + (T)1), s = t * c;
-#pragma unroll
-  for (int r = 0; r < N; ++r) {
-    const T arp = A[r][p], arq = A[r][q];
-    A[r][p] = c * arp - s * arq;
-    A[r][q] = s * arp + c * arq;
-  }
-#pragma unroll
-  for (int r = 0; r < N; ++r) {
-    const T apr = A[p][r], aqr = A[q][r];
-    A[p][r] = c * apr - s * aqr;
-    A[q][r] = s * apr + c * aqr;
+  const T c = rsqrt(t * t + (T)1), s = t * c;
+  dg[p] -= t * apq;
+  dg[q] += t * apq;
+  of[pq] = 0;
+  if (N == 3) {
+    const int r = 3 - p - q;
+    const int rp = off_slot<N>(r < p ? r : p, r < p ? p : r), rq = off_slot<N>(r < q ? r : q, r < q ? q : r);
+    const T arp = of[rp], arq = of[rq];
+    of[rp] = c * arp - s * arq;
+    of[rq] = s * arp + c * arq;
   }
 #pragma unroll
   for (int r = 0; r < N; ++r) {
@@ -69,34 +77,31 @@ __device__ __forceinline__ void jacobi_rot(T A[N][N], T V[N][N], int p, int q) {
   }
 }
 
-// symmetric eigen-decomposition A = V diag(w) V^T by cyclic Jacobi rotations
+// symmetric eigen-decomposition A = V diag(w) V^T by cyclic Jacobi rotations;
+// on entry (dg, of) hold A, on exit dg holds the eigenvalues w
 template <class T, int N>
-__device__ __forceinline__ void eig_sym(T A[N][N], T w[N], T V[N][N]) {
+__device__ __forceinline__ void eig_sym(T (&dg)[N], T (&of)[N == 2 ? 1 : 3], T (&V)[N][N]) {
 #pragma unroll
   for (int a = 0; a < N; ++a)
 #pragma unroll
     for (int b = 0; b < N; ++b) V[a][b] = (a == b) ? (T)1 : (T)0;
+  if (N == 2) {  // one rotation diagonalises a 2 x 2 matrix
+    jacobi_rot_sym<T, N>(dg, of, V, 0, 1);
+    return;
+  }
   const T eps2 = sizeof(T) == 4 ? (T)1e-14 : (T)1e-30;
 #pragma unroll 1
   for (int sweep = 0; sweep < (sizeof(T) == 4 ? 6 : 10); ++sweep) {
     T off = 0, dia = 0;
 #pragma unroll
-    for (int a = 0; a < N; ++a) {
-      dia += A[a][a] * A[a][a];
+    for (int a = 0; a < N; ++a) dia += dg[a] * dg[a];
 #pragma unroll
-      for (int b = a + 1; b < N; ++b) off += A[a][b] * A[a][b];
-    }
+    for (int o = 0; o < (N == 2 ? 1 : 3); ++o) off += of[o] * of[o];
     if (off <= eps2 * dia || off == (T)0) break;
-    if (N == 2) {
-      jacobi_rot<T, N>(A, V, 0, 1);
-    } else {
-      jacobi_rot<T, N>(A, V, 0, 1);
-      jacobi_rot<T, N>(A, V, 0, N - 1);
-      jacobi_rot<T, N>(A, V, 1, N - 1);
-    }
+    jacobi_rot_sym<T, N>(dg, of, V, 0, 1);
+    jacobi_rot_sym<T, N>(dg, of, V, 0, 2);
+    jacobi_rot_sym<T, N>(dg, of, V, 1, 2);
   }
-#pragma unroll
-  for (int a = 0; a < N; ++a) w[a] = A[a][a];
 }
 
 template <class T>
@@ -118,161 +123,184 @@ __device__ __forceinline__ int comp_of(int a, int b) {
   return s == 1 ? 3 : (s == 2 ? 4 : 5);
 }
 
-template <class T, int N>
-__device__ __forceinline__ void k_polymer_b(PolyIn<T> P, Dims d, PhysT<T> q, int stage, const int3 bid, unsigned char* smraw) {
-  const int plane = d.nx * d.ny;
+// one RK2-TVD stage at one coarse cell; STAGE 2 also forms tau
+template <class T, int N, int STAGE>
+__device__ __forceinline__ void polymer_cell(const PolyIn<T>& P, const Dims& d, const PhysT<T>& q, const RowIdx& x) {
+  const int nx = d.nx, plane = d.nx * d.ny;
   const T iD = q.iD;
-  const T dt = q.dt, ilh = q.ilh;
   constexpr int NC = N == 2 ? 3 : 6;
-  RowIdx x;
-  if (!row_index_b(bid, d.nx, d.ny, x)) return;
+  const int i = x.i, j = x.j, k = x.k;
+  const int id = x.row * nx + i;
+  // wrapped neighbour offsets, computed once
+  const int ox = (i + 1 == nx) ? 1 - nx : 1, oxm = (i == 0) ? nx - 1 : -1;
+  const int oy = N == 3 ? ((j + 1 == d.ny) ? (1 - d.ny) * nx : nx) : 0;
+  const int oym = N == 3 ? ((j == 0) ? (d.ny - 1) * nx : -nx) : 0;
+  const bool top = k + 1 == d.nz, bot = k == 0;
+  const T* __restrict__ U = P.u;
+  const T* __restrict__ Vv = P.v;
+  const T* __restrict__ W = P.w;
+  auto uc = [&](int c) -> T { return (T)0.5 * (U[c] + U[c + ox]); };
+  auto wc = [&](int c) -> T { return (T)0.5 * (W[c] + W[c + plane]); };
+  // velocity gradient L[a][b] = du_a/dx_b; wall ghosts 2 u_w - u_0 (tangential), w = 0
+  T L[N][N];
+  const T uc0 = uc(id);
+  const T ucp = top ? q.uw2_top - uc0 : uc(id + plane);
+  const T ucm = bot ? q.uw2_bot - uc0 : uc(id - plane);
+  const T dudx = (U[id + ox] - U[id]) * iD;
+  const T dudz = (ucp - ucm) * (T)0.5 * iD;
+  const T dwdx = (wc(id + ox) - wc(id + oxm)) * (T)0.5 * iD;
+  const T dwdz = (W[id + plane] - W[id]) * iD;
+  if (N == 2) {
+    L[0][0] = dudx;
+    L[0][N - 1] = dudz;
+    L[N - 1][0] = dwdx;
+    L[N - 1][N - 1] = dwdz;
+  } else {
+    auto vc = [&](int c) -> T { return (T)0.5 * (Vv[c] + Vv[c + oy]); };
+    const T vc0 = vc(id);
+    const T vcp = top ? -vc0 : vc(id + plane);
+    const T vcm = bot ? -vc0 : vc(id - plane);
+    L[0][0] = dudx;
+    L[0][1] = (uc(id + oy) - uc(id + oym)) * (T)0.5 * iD;
+    L[0][N - 1] = dudz;
+    L[1][0] = (vc(id + ox) - vc(id + oxm)) * (T)0.5 * iD;
+    L[1][1] = (Vv[id + oy] - Vv[id]) * iD;
+    L[1][N - 1] = (vcp - vcm) * (T)0.5 * iD;
+    L[N - 1][0] = dwdx;
+    L[N - 1][1] = (wc(id + oy) - wc(id + oym)) * (T)0.5 * iD;
+    L[N - 1][N - 1] = dwdz;
+  }
+  // advection div(u Theta), central conservative fluxes, no wall flux
+  T adv[NC], th0[NC];
   {
-    const int i = x.i, j = x.j, k = x.k;
-    const int id = x.row * d.nx + i;
-    auto C = [&](int ii, int jj, int kk) { return (kk * d.ny + wrap(jj, d.ny)) * d.nx + wrap(ii, d.nx); };
-    // velocity gradient L[a][b] = du_a/dx_b (Eq. NS23 uses its transpose convention)
-    auto uc = [&](int ii, int jj, int kk) -> T {  // centre-averaged u, ghosts at walls
-      if (kk < 0) return q.uw2_bot - (T)0.5 * (P.u[C(ii, jj, 0)] + P.u[C(ii + 1, jj, 0)]);
-      if (kk >= d.nz) return q.uw2_top - (T)0.5 * (P.u[C(ii, jj, d.nz - 1)] + P.u[C(ii + 1, jj, d.nz - 1)]);
-      return (T)0.5 * (P.u[C(ii, jj, kk)] + P.u[C(ii + 1, jj, kk)]);
-    };
-    auto vc = [&](int ii, int jj, int kk) -> T {
-      if (kk < 0) return -(T)0.5 * (P.v[C(ii, jj, 0)] + P.v[C(ii, jj + 1, 0)]);
-      if (kk >= d.nz) return -(T)0.5 * (P.v[C(ii, jj, d.nz - 1)] + P.v[C(ii, jj + 1, d.nz - 1)]);
-      return (T)0.5 * (P.v[C(ii, jj, kk)] + P.v[C(ii, jj + 1, kk)]);
-    };
-    auto wc = [&](int ii, int jj, int kk) -> T { return (T)0.5 * (P.w[C(ii, jj, kk)] + P.w[C(ii, jj, kk + 1)]); };
-    T L[N][N];
-    const T dudx = (P.u[C(i + 1, j, k)] - P.u[id]) * iD;
-    const T dwdz = (P.w[id + plane] - P.w[id]) * iD;
-    const T dudz = (uc(i, j, k + 1) - uc(i, j, k - 1)) * (T)0.5 * iD;
-    const T dwdx = (wc(i + 1, j, k) - wc(i - 1, j, k)) * (T)0.5 * iD;
-    if (N == 2) {
-      L[0][0] = dudx; L[0][1] = dudz;
-      L[1][0] = dwdx; L[1][N - 1] = dwdz;
-    } else {
-      L[0][0] = dudx;
-      L[0][1] = (uc(i, j + 1, k) - uc(i, j - 1, k)) * (T)0.5 * iD;
-      L[0][N - 1] = dudz;
-      L[1][0] = (vc(i + 1, j, k) - vc(i - 1, j, k)) * (T)0.5 * iD;
-      L[1][1] = (P.v[C(i, j + 1, k)] - P.v[id]) * iD;
-      L[1][N - 1] = (vc(i, j, k + 1) - vc(i, j, k - 1)) * (T)0.5 * iD;
-      L[N - 1][0] = dwdx;
-      L[N - 1][1] = (wc(i, j + 1, k) - wc(i, j - 1, k)) * (T)0.5 * iD;
-      L[N - 1][N - 1] = dwdz;
+    const T ul = U[id], ur = U[id + ox];
+    const T wb = W[id], wt = W[id + plane];
+    const T vl = N == 3 ? Vv[id] : (T)0, vr = N == 3 ? Vv[id + oy] : (T)0;
+#pragma unroll
+    for (int cq = 0; cq < NC; ++cq) {
+      const T* __restrict__ th = P.th[cq];
+      const T t0 = th[id];
+      T a = ur * (t0 + th[id + ox]) - ul * (th[id + oxm] + t0);
+      if (!top) a += wt * (t0 + th[id + plane]);
+      if (!bot) a -= wb * (th[id - plane] + t0);
+      if (N == 3) a += vr * (t0 + th[id + oy]) - vl * (th[id + oym] + t0);
+      adv[cq] = (T)0.5 * iD * a;
+      th0[cq] = t0;
     }
-    // advection div(u Theta), central conservative fluxes, no wall flux
-    T adv[NC];
-    {
-      const T ul = P.u[id], ur = P.u[C(i + 1, j, k)];
-      const T wb = P.w[id], wt = P.w[id + plane];
-      const int xm = C(i - 1, j, k), xp = C(i + 1, j, k);
+  }
+  // eigen-decomposition of Theta at the cell
+  T dg[N], of[N == 2 ? 1 : 3], R[N][N];
 #pragma unroll
-      for (int cq = 0; cq < NC; ++cq) {
-        const T t0 = P.th[cq][id];
-        T a = (ur * (t0 + P.th[cq][xp]) - ul * (P.th[cq][xm] + t0));
-        if (k + 1 < d.nz) a += wt * (t0 + P.th[cq][id + plane]);
-        if (k > 0) a -= wb * (P.th[cq][id - plane] + t0);
-        if (N == 3) {
-          const T vl = P.v[id], vr = P.v[C(i, j + 1, k)];
-          a += vr * (t0 + P.th[cq][C(i, j + 1, k)]) - vl * (P.th[cq][C(i, j - 1, k)] + t0);
-        }
-        adv[cq] = (T)0.5 * iD * a;
-      }
+  for (int a = 0; a < N; ++a) dg[a] = th0[comp_of<N>(a, a)];
+  if (N == 2) of[0] = th0[comp_of<N>(0, 1)];
+  else {
+    of[0] = th0[comp_of<N>(0, 1)];
+    of[1] = th0[comp_of<N>(0, 2)];
+    of[2] = th0[comp_of<N>(1, 2)];
+  }
+  eig_sym<T, N>(dg, of, R);
+  // M~ = R^T L R
+  T LR[N][N], Mt[N][N];
+#pragma unroll
+  for (int a = 0; a < N; ++a)
+#pragma unroll
+    for (int b = 0; b < N; ++b) {
+      T s = 0;
+#pragma unroll
+      for (int c = 0; c < N; ++c) s += L[a][c] * R[c][b];
+      LR[a][b] = s;
     }
-    // eigen-decomposition of Theta at the cell
-    T A[N][N], th[N], R[N][N];
 #pragma unroll
-    for (int a = 0; a < N; ++a)
+  for (int a = 0; a < N; ++a)
 #pragma unroll
-      for (int b = 0; b < N; ++b) A[a][b] = P.th[comp_of<N>(a, b)][id];
-    eig_sym<T, N>(A, th, R);
-    // M~ = R^T L R
-    T LR[N][N], Mt[N][N];
+    for (int b = 0; b < N; ++b) {
+      T s = 0;
 #pragma unroll
-    for (int a = 0; a < N; ++a)
-#pragma unroll
-      for (int b = 0; b < N; ++b) {
-        T s = 0;
-#pragma unroll
-        for (int c = 0; c < N; ++c) s += L[a][c] * R[c][b];
-        LR[a][b] = s;
-      }
-#pragma unroll
-    for (int a = 0; a < N; ++a)
-#pragma unroll
-      for (int b = 0; b < N; ++b) {
-        T s = 0;
-#pragma unroll
-        for (int c = 0; c < N; ++c) s += R[c][a] * LR[c][b];
-        Mt[a][b] = s;
-      }
-    // RH in the eigenbasis
-    T H[N][N];
-#pragma unroll
-    for (int a = 0; a < N; ++a) {
-      H[a][a] = 2 * Mt[a][a] + (fexp<T>(-th[a]) - (T)1) * ilh;
-#pragma unroll
-      for (int b = a + 1; b < N; ++b) {
-        const T dd = th[b] - th[a];
-        T o;
-        if (dd > 0) o = (Mt[a][b] + fexp<T>(-dd) * Mt[b][a]) * dexpm1<T>(-dd);
-        else o = (fexp<T>(dd) * Mt[a][b] + Mt[b][a]) * dexpm1<T>(dd);
-        H[a][b] = o;
-        H[b][a] = o;
-      }
+      for (int c = 0; c < N; ++c) s += R[c][a] * LR[c][b];
+      Mt[a][b] = s;
     }
-    // back to the physical basis: R H R^T
-    T HR[N][N];
+  // RH in the eigenbasis
+  T H[N][N];
 #pragma unroll
-    for (int a = 0; a < N; ++a)
+  for (int a = 0; a < N; ++a) {
+    H[a][a] = 2 * Mt[a][a] + (fexp<T>(-dg[a]) - (T)1) * q.ilh;
 #pragma unroll
-      for (int b = 0; b < N; ++b) {
-        T s = 0;
+    for (int b = a + 1; b < N; ++b) {
+      const T dd = dg[b] - dg[a];
+      T o;
+      if (dd > 0) o = (Mt[a][b] + fexp<T>(-dd) * Mt[b][a]) * dexpm1<T>(-dd);
+      else o = (fexp<T>(dd) * Mt[a][b] + Mt[b][a]) * dexpm1<T>(dd);
+      H[a][b] = o;
+      H[b][a] = o;
+    }
+  }
+  // back to the physical basis: R H R^T
+  T HR[N][N];
 #pragma unroll
-        for (int c = 0; c < N; ++c) s += H[a][c] * R[b][c];
-        HR[a][b] = s;
-      }
-    T newth[NC];
+  for (int a = 0; a < N; ++a)
+#pragma unroll
+    for (int b = 0; b < N; ++b) {
+      T s = 0;
+#pragma unroll
+      for (int c = 0; c < N; ++c) s += H[a][c] * R[b][c];
+      HR[a][b] = s;
+    }
+  const T dt = q.dt;
+  T newth[NC];
+#pragma unroll
+  for (int a = 0; a < N; ++a)
+#pragma unroll
+    for (int b = a; b < N; ++b) {
+      T s = 0;
+#pragma unroll
+      for (int c = 0; c < N; ++c) s += R[a][c] * HR[c][b];
+      const int cq = comp_of<N>(a, b);
+      const T rh = s - adv[cq];
+      const T t0 = th0[cq];
+      newth[cq] = STAGE == 1 ? t0 + dt * rh : (T)0.5 * P.base[cq][id] + (T)0.5 * (t0 + dt * rh);
+    }
+#pragma unroll
+  for (int cq = 0; cq < NC; ++cq) P.out[cq][id] = newth[cq];
+  if (STAGE == 2) {
+    // tau = (1 + phi)/2 (mu_p/lambda_H) (R e^theta R^T - I)
+#pragma unroll
+    for (int a = 0; a < N; ++a) dg[a] = newth[comp_of<N>(a, a)];
+    if (N == 2) of[0] = newth[comp_of<N>(0, 1)];
+    else {
+      of[0] = newth[comp_of<N>(0, 1)];
+      of[1] = newth[comp_of<N>(0, 2)];
+      of[2] = newth[comp_of<N>(1, 2)];
+    }
+    eig_sym<T, N>(dg, of, R);
+    T ex[N];
+#pragma unroll
+    for (int c = 0; c < N; ++c) ex[c] = fexp<T>(dg[c]);
+    const T wgt = (T)0.5 * ((T)1 + P.phic[id]) * q.wtau;
 #pragma unroll
     for (int a = 0; a < N; ++a)
 #pragma unroll
       for (int b = a; b < N; ++b) {
         T s = 0;
 #pragma unroll
-        for (int c = 0; c < N; ++c) s += R[a][c] * HR[c][b];
-        const int cq = comp_of<N>(a, b);
-        const T rh = s - adv[cq];
-        const T t0 = P.th[cq][id];
-        newth[cq] = stage == 1 ? t0 + dt * rh : (T)0.5 * P.base[cq][id] + (T)0.5 * (t0 + dt * rh);
+        for (int c = 0; c < N; ++c) s += R[a][c] * ex[c] * R[b][c];
+        P.tau[comp_of<N>(a, b)][id] = wgt * (s - (a == b ? (T)1 : (T)0));
       }
-#pragma unroll
-    for (int cq = 0; cq < NC; ++cq) P.out[cq][id] = newth[cq];
-    if (stage == 2) {
-      // tau = (1 + phi)/2 (mu_p/lambda_H) (R e^theta R^T - I)
-#pragma unroll
-      for (int a = 0; a < N; ++a)
-#pragma unroll
-        for (int b = 0; b < N; ++b) A[a][b] = newth[comp_of<N>(a, b)];
-      eig_sym<T, N>(A, th, R);
-      const T wgt = (T)0.5 * ((T)1 + P.phic[id]) * q.wtau;
-#pragma unroll
-      for (int a = 0; a < N; ++a)
-#pragma unroll
-        for (int b = a; b < N; ++b) {
-          T s = 0;
-#pragma unroll
-          for (int c = 0; c < N; ++c) s += R[a][c] * fexp<T>(th[c]) * R[b][c];
-          P.tau[comp_of<N>(a, b)][id] = wgt * (s - (a == b ? (T)1 : (T)0));
-        }
-    }
   }
 }
 
 template <class T, int N>
-__global__ void k_polymer(PolyIn<T> P, Dims d, PhysT<T> q, int stage) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  k_polymer_b<T, N>(P, d, q, stage, make_int3(blockIdx.x, blockIdx.y, blockIdx.z), smraw);
+__device__ __forceinline__ void k_polymer_b(const PolyIn<T>& P, const Dims& d, const PhysT<T>& q, int stage, const int3 bid, unsigned char*) {
+  RowIdx x;
+  if (!row_index_b(bid, d.nx, d.ny, x)) return;
+  if (stage == 1) polymer_cell<T, N, 1>(P, d, q, x);
+  else polymer_cell<T, N, 2>(P, d, q, x);
+}
+
+template <class T, int N, int STAGE>
+__global__ void k_polymer(const __grid_constant__ PolyIn<T> P, const Dims d, const PhysT<T> q) {
+  RowIdx x;
+  if (!row_index(d.nx, d.ny, x)) return;
+  polymer_cell<T, N, STAGE>(P, d, q, x);
 }
 
 }  // namespace pf

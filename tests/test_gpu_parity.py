@@ -134,12 +134,13 @@ def test_config1_fp64_full_run():
     assert np.allclose(dg["centroid"], ob.centroid(ref.phi, g), rtol=1e-10, atol=1e-12)
 
 
-def test_config1_mixed_full_run():
-    """Mixed path on config 1: 2e-4 max-abs on phi, 1e-3 relative on u, w."""
+@pytest.mark.parametrize("prec", [binding.PF_MIXED, binding.PF_MIXED_Z64])
+def test_config1_mixed_full_run(prec):
+    """Mixed paths on config 1: 2e-4 max-abs on phi, 1e-3 relative on u, w."""
     w = wl.config("c1")
     g = w.grid
     phi0 = wl.initial_phi(w)
-    s = binding.Solver(g, w.params, binding.PF_MIXED)
+    s = binding.Solver(g, w.params, prec)
     s.load_state(phi0)
     s.step(w.steps)
     ref = ostep.run(g, w.params.as_dict(), phi0, w.steps)
@@ -152,7 +153,7 @@ def test_mass_conservation_gpu_fp64_and_mixed():
     w = wl.scaled(wl.config("c2"), 32, 16)
     g = w.grid
     phi0 = wl.initial_phi(w)
-    for prec, tol in ((binding.PF_FP64, 1e-13), (binding.PF_MIXED, 1e-5)):
+    for prec, tol in ((binding.PF_FP64, 1e-13), (binding.PF_MIXED, 1e-5), (binding.PF_MIXED_Z64, 1e-5)):
         s = binding.Solver(g, w.params, prec)
         s.load_state(phi0)
         m0 = s.diagnostics()["mass"]
