@@ -242,9 +242,12 @@ int pf_adjoint(pf_ctx* ctx, int nsteps, int ckpt_every, int objective, double ou
  *   PF_TUNE_ZSOLVE_COLS  kx columns per CTA of the z solves (multiple of 16, <= 64)
  *   PF_TUNE_ROW_BLOCK    threads per CTA of the row kernels (multiple of 32)
  *   PF_TUNE_CH_ZCHUNK    fine z planes one CTA of the 3D CH right side walks (>= 2)
+ *   PF_TUNE_CH_MINB      CTAs per SM the 3D CH right side's registers are sized for (2, 3)
+ *   PF_TUNE_NS_MINB      CTAs per SM the NS right side's registers are sized for (3, 4)
+ *   PF_TUNE_G_ZCHUNK     coarse layers one CTA of the 3D restriction walks (>= 1)
  * Errors: PF_ERR_ARG for an unknown knob or a value that does not fit. */
 enum { PF_TUNE_XFFT_PAIRS = 0, PF_TUNE_YFFT_COLS = 1, PF_TUNE_ZSOLVE_COLS = 2, PF_TUNE_ROW_BLOCK = 3, PF_TUNE_CH_ZCHUNK = 4,
-       PF_TUNE_COUNT = 5 };
+       PF_TUNE_CH_MINB = 5, PF_TUNE_NS_MINB = 6, PF_TUNE_G_ZCHUNK = 7, PF_TUNE_COUNT = 8 };
 int pf_set_tuning(pf_ctx* ctx, int knob, int value);
 int pf_get_tuning(const pf_ctx* ctx, int knob, int* value);
 

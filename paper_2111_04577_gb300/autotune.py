@@ -22,6 +22,9 @@ KNOBS = {
     2: ("zsolve_cols", [16, 32], ("zsolve_pair", "zsolve")),
     3: ("row_block", [64, 128, 256], ("ns_rhs", "div", "correct", "polymer_stage1", "polymer_stage2")),
     4: ("ch_zchunk", [16, 32, 64], ("ch_rhs",)),
+    5: ("ch_minb", [2, 3], ("ch_rhs",)),
+    6: ("ns_minb", [3, 4], ("ns_rhs",)),
+    7: ("g_zchunk", [4, 8, 16], ("ch_G_restrict",)),
 }
 
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "tuning.json")
@@ -61,7 +64,7 @@ def tune(grid: wl.Grid, params: wl.Params, precision: int, phi0=None, steps: int
         s.profile(1)  # warm: graph-free launches, allocations touched
         best = {}
         for knob, (name, cands, kernels) in KNOBS.items():
-            if grid.dim == 2 and name in ("yfft_cols", "ch_zchunk"):
+            if grid.dim == 2 and name in ("yfft_cols", "ch_zchunk", "ch_minb", "g_zchunk"):
                 continue
             timings = {}
             for v in cands:

@@ -46,8 +46,10 @@ __device__ __forceinline__ int pmod_m(int x, int n) {
   return x < 0 ? x + n : x;
 }
 
-template <class T>
-__global__ void __launch_bounds__(MarchTile::NT, 3) k_ch_rhs_march(const FineView<T> f, const CoarseVel<T> vel,
+// MINB: CTAs per SM the register budget is sized for (a launch variant; the
+// arithmetic is the same)
+template <class T, int MINB>
+__global__ void __launch_bounds__(MarchTile::NT, MINB) k_ch_rhs_march(const FineView<T> f, const CoarseVel<T> vel,
                                                                 T* __restrict__ R, double* __restrict__ gwall,
                                                                 const Dims d, const Phys p, const PhysT<T> q,
                                                                 const T inv_mldt, const T inv_ml, const int nzc) {
@@ -262,6 +264,212 @@ __global__ void __launch_bounds__(MarchTile::NT, 3) k_ch_rhs_march(const FineVie
       lap = (lap + mzp + mzm - 2 * m0) * q.ih2;
       const size_t o = (size_t)z * plane + (size_t)gy * fnx + gx;
       R[o] = dd[ty * TL::TX + tx] * inv_mldt - adv * inv_ml + lap;
+    }
+  }
+}
+
+}  // namespace pf
+
+namespace pf {
+
+// ---------------------------------------------------------------------------
+// Chemical potential and restriction on the 3D dual mesh (r = 2), marching
+// along z.  Same outputs as k_ch_G_restrict (ch_tiled.cuh; Eqs. NS5, dual2,
+// dual3): G = lambda(-(L_N phi + B(g)) + f(phi)) on the fine mesh, then the
+// 2 x 2 x 2 means of phi and G at coarse centres, faces and edges.
+// A CTA owns CX x CY coarse columns and walks coarse layers k; layer k needs
+// fine planes 2k-1, 2k, 2k+1 (z mirrored at the walls).  phi is staged with a
+// one-cell x/y halo in a ring of four planes, G of the two new planes is formed
+// in shared memory, and each thread turns the 3 x 3 fine neighbourhood of its
+// coarse cell into the seven means through 2 x 2 plane sums; the sums of plane
+// 2k+1 serve as plane 2k-1 of the next layer.
+// ---------------------------------------------------------------------------
+struct GrMarch {
+  static constexpr int CX = 32, CY = 8, NT = CX * CY;
+  static constexpr int FX = 2 * CX + 1, FY = 2 * CY + 1, FP = FX * FY;  // G region (fine)
+  static constexpr int PX = FX + 2, PY = FY + 2, PP = PX * PY;          // phi with halo
+  static constexpr int NPS = 4;
+  static constexpr int KP = (PP + NT - 1) / NT;
+  static constexpr int KG = (FP + NT - 1) / NT;
+  static constexpr int smem_elems() { return NPS * PP + 2 * FP; }
+};
+
+// 2 x 2 sums of a 3 x 3 neighbourhood: hh = offsets {0,1}x{0,1}, lh = {-1,0}x{0,1},
+// hl = {0,1}x{-1,0}, ll = {-1,0}x{-1,0} (x first)
+template <class T>
+struct Quad {
+  T hh, lh, hl, ll;
+};
+
+template <class T>
+__device__ __forceinline__ Quad<T> quad_sums(const T* p, int o, int sx) {
+  // p[o + b * sx + a], a, b in {-1, 0, 1}
+  T rlo[3], rhi[3];
+#pragma unroll
+  for (int b = -1; b <= 1; ++b) {
+    const T m = p[o + b * sx - 1], c = p[o + b * sx], q = p[o + b * sx + 1];
+    rlo[b + 1] = m + c;
+    rhi[b + 1] = c + q;
+  }
+  Quad<T> r;
+  r.hh = rhi[1] + rhi[2];
+  r.lh = rlo[1] + rlo[2];
+  r.hl = rhi[0] + rhi[1];
+  r.ll = rlo[0] + rlo[1];
+  return r;
+}
+
+template <class T>
+__global__ void __launch_bounds__(GrMarch::NT, 2) k_ch_G_restrict_march(const T* __restrict__ phi,
+                                                                        const double* __restrict__ gwall,
+                                                                        Restricted<T> out, const Dims d,
+                                                                        const PhysT<T> q, const int nkc) {
+  using TL = GrMarch;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* ps = reinterpret_cast<T*>(smraw);  // [NPS][PY][PX], fine plane zf at slot (zf + 1) & 3
+  T* gs = ps + TL::NPS * TL::PP;        // [2][FY][FX], fine plane zf at slot zf & 1
+  const int t = threadIdx.x;
+  const int cx0 = blockIdx.x * TL::CX, cy0 = blockIdx.y * TL::CY;
+  const int kb = blockIdx.z * nkc, ke = min(kb + nkc, d.nz + 1);  // coarse layers kb..ke-1 (nz: top face)
+  const int fnx = d.fnx, fny = d.fny, fnz = d.fnz;
+  const size_t plane = (size_t)fnx * fny;
+  const int fx0 = 2 * cx0 - 2, fy0 = 2 * cy0 - 2;  // fine origin of the phi tile
+  // per-thread staging offsets (x/y part), fixed for the march
+  int sxy[TL::KP];
+#pragma unroll
+  for (int kq = 0; kq < TL::KP; ++kq) {
+    const int e = t + kq * TL::NT;
+    sxy[kq] = -1;
+    if (e < TL::PP) {
+      const int yy = e / TL::PX, xx = e - yy * TL::PX;
+      sxy[kq] = pmod_m(fy0 + yy, fny) * fnx + pmod_m(fx0 + xx, fnx);
+    }
+  }
+  // per-thread G positions: offset in the phi tile, and the wall column
+  int go[TL::KG], gcol[TL::KG];
+#pragma unroll
+  for (int kq = 0; kq < TL::KG; ++kq) {
+    const int e = t + kq * TL::NT;
+    go[kq] = -1;
+    gcol[kq] = 0;
+    if (e < TL::FP) {
+      const int yy = e / TL::FX, xx = e - yy * TL::FX;
+      go[kq] = (yy + 1) * TL::PX + (xx + 1);
+      gcol[kq] = pmod_m(fy0 + 1 + yy, fny) * fnx + pmod_m(fx0 + 1 + xx, fnx);
+    }
+  }
+  auto load_plane = [&](int zf, T (&reg)[TL::KP]) {
+    const size_t zo = (size_t)min(max(zf, 0), fnz - 1) * plane;
+#pragma unroll
+    for (int kq = 0; kq < TL::KP; ++kq)
+      if (sxy[kq] >= 0) reg[kq] = phi[zo + sxy[kq]];
+  };
+  auto store_plane = [&](int zf, const T (&reg)[TL::KP]) {
+    T* p = ps + ((zf + 1) & 3) * TL::PP;
+#pragma unroll
+    for (int kq = 0; kq < TL::KP; ++kq) {
+      const int e = t + kq * TL::NT;
+      if (e < TL::PP) p[e] = reg[kq];
+    }
+  };
+  // G of fine plane zf (0 <= zf < fnz) into slot zf & 1, from phi planes zf-1..zf+1
+  auto g_plane = [&](int zf) {
+    const T* pm = ps + ((zf) & 3) * TL::PP;  // plane zf - 1
+    const T* pc = ps + ((zf + 1) & 3) * TL::PP;
+    const T* pq = ps + ((zf + 2) & 3) * TL::PP;
+    T* g = gs + (zf & 1) * TL::FP;
+#pragma unroll
+    for (int kq = 0; kq < TL::KG; ++kq) {
+      const int e = t + kq * TL::NT;
+      if (go[kq] < 0) continue;
+      const int o = go[kq];
+      const T c0 = pc[o];
+      T lap = pc[o + 1] + pc[o - 1] - 2 * c0;
+      lap += pc[o + TL::PX] + pc[o - TL::PX] - 2 * c0;
+      const T czp = zf + 1 < fnz ? pq[o] : c0;
+      const T czm = zf > 0 ? pm[o] : c0;
+      lap = (lap + czp + czm - 2 * c0) * q.ih2;
+      T B = 0;
+      if (zf == 0) B += (T)gwall[gcol[kq]] * q.ih;
+      if (zf == fnz - 1) B += (T)gwall[plane + gcol[kq]] * q.ih;
+      g[e] = q.lam * (-(lap + B) + c0 * (c0 * c0 - 1) * q.ie2);
+    }
+  };
+  // this thread's coarse cell and its fine centre (2i, 2j) in the tiles
+  const int lx = t % TL::CX, ly = t / TL::CX;
+  const int i = cx0 + lx, j = cy0 + ly;
+  const bool own = i < d.nx && j < d.ny;
+  const int po = (2 * ly + 2) * TL::PX + (2 * lx + 2);  // phi tile: fine (2i, 2j)
+  const int gq = (2 * ly + 1) * TL::FX + (2 * lx + 1);  // G region: fine (2i, 2j)
+  const T eighth = (T)0.125;
+  Quad<T> qpm{}, qgm{};  // sums of fine plane 2k-1
+  T reg[TL::KP];
+#pragma unroll
+  for (int kq = 0; kq < TL::KP; ++kq) reg[kq] = (T)0;
+  // ---- prologue: phi planes 2kb-2 .. 2kb (and G of 2kb-1 when kb > 0) ----
+  for (int zf = 2 * kb - 2; zf <= 2 * kb; ++zf) {
+    load_plane(zf, reg);
+    store_plane(zf, reg);
+  }
+  __syncthreads();
+  if (kb > 0) {
+    g_plane(2 * kb - 1);
+    __syncthreads();
+    qpm = quad_sums(ps + ((2 * kb) & 3) * TL::PP, po, TL::PX);
+    qgm = quad_sums(gs + ((2 * kb - 1) & 1) * TL::FP, gq, TL::FX);
+  }
+  // phi planes 2k+1, 2k+2 of the next layer are prefetched into registers
+  T ra[TL::KP], rb[TL::KP];
+#pragma unroll
+  for (int kq = 0; kq < TL::KP; ++kq) ra[kq] = rb[kq] = (T)0;
+  if (kb < d.nz) {
+    load_plane(2 * kb + 1, ra);
+    load_plane(2 * kb + 2, rb);
+  }
+  for (int k = kb; k < ke; ++k) {
+    if (k < d.nz) {
+      // into the slots of planes 2k-3, 2k-2: free after the previous layer's barrier
+      store_plane(2 * k + 1, ra);
+      store_plane(2 * k + 2, rb);
+      __syncthreads();
+      if (k + 1 < min(ke, d.nz)) {
+        load_plane(2 * k + 3, ra);
+        load_plane(2 * k + 4, rb);
+      }
+      g_plane(2 * k);
+      g_plane(2 * k + 1);
+      __syncthreads();
+      const Quad<T> p0 = quad_sums(ps + ((2 * k + 1) & 3) * TL::PP, po, TL::PX);
+      const Quad<T> p1 = quad_sums(ps + ((2 * k + 2) & 3) * TL::PP, po, TL::PX);
+      const Quad<T> g0 = quad_sums(gs + ((2 * k) & 1) * TL::FP, gq, TL::FX);
+      const Quad<T> g1 = quad_sums(gs + ((2 * k + 1) & 1) * TL::FP, gq, TL::FX);
+      if (k == 0) {  // fine plane -1 mirrors plane 0
+        qpm = p0;
+        qgm = g0;
+      }
+      if (own) {
+        const size_t id = ((size_t)k * d.ny + j) * d.nx + i;
+        out.phic[id] = (p0.hh + p1.hh) * eighth;
+        out.Gc[id] = (g0.hh + g1.hh) * eighth;
+        out.phifx[id] = (p0.lh + p1.lh) * eighth;
+        out.Gfx[id] = (g0.lh + g1.lh) * eighth;
+        out.phify[id] = (p0.hl + p1.hl) * eighth;
+        out.Gfy[id] = (g0.hl + g1.hl) * eighth;
+        out.phiexy[id] = (p0.ll + p1.ll) * eighth;
+        out.phifz[id] = (qpm.hh + p0.hh) * eighth;
+        out.Gfz[id] = (qgm.hh + g0.hh) * eighth;
+        out.phiexz[id] = (qpm.lh + p0.lh) * eighth;
+        out.phieyz[id] = (qpm.hl + p0.hl) * eighth;
+      }
+      qpm = p1;
+      qgm = g1;
+      __syncthreads();
+    } else if (own) {  // top wall face k = nz: fine plane 2nz mirrors 2nz-1
+      const size_t id = ((size_t)k * d.ny + j) * d.nx + i;
+      out.phifz[id] = (qpm.hh + qpm.hh) * eighth;
+      out.Gfz[id] = (qgm.hh + qgm.hh) * eighth;
+      out.phiexz[id] = (qpm.lh + qpm.lh) * eighth;
+      out.phieyz[id] = (qpm.hl + qpm.hl) * eighth;
     }
   }
 }

@@ -22,6 +22,7 @@
 #include "ch.cuh"
 #include "ch_tiled.cuh"
 #include "ch_march.cuh"
+#include "zsolve_seg.cuh"
 #include "ns.cuh"
 #include "ns_rhs.cuh"
 #include "polymer.cuh"
@@ -323,11 +324,14 @@ struct Impl : ImplBase {
   void set_smem_limits() {
     PF_CUDA_TRY(cudaFuncSetAttribute(k_fft_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_zsolve<T, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PF_CUDA_TRY(cudaFuncSetAttribute(k_zsolve_seg<T, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_rfft_x<T, ArrPro<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_rfft_x<T, FineArrPro<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
-    PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict_march<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict<T, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict<T, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict<T, 3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
@@ -390,11 +394,19 @@ struct Impl : ImplBase {
     zs.shift1 = s1;
     zs.shift2 = s2;
     zs.scale = scale;
-    const int tx = tune[PF_TUNE_ZSOLVE_COLS] > 0 ? tune[PF_TUNE_ZSOLVE_COLS] : (sizeof(T) == 4 ? 32 : 16);
-    const size_t sm = (size_t)rows * tx * (sizeof(cpx<T>) + sizeof(TC) * (zs.same ? 1 : 2));
-    dim3 grid((ncol + tx - 1) / tx, ny);
     mark(two ? "zsolve_pair" : "zsolve");
-    k_zsolve<T, TC><<<grid, 256, sm, st>>>(data, ex, ey, zs, tx);
+    const int txs = tune[PF_TUNE_ZSOLVE_COLS] > 0 ? tune[PF_TUNE_ZSOLVE_COLS] : 16;
+    const int nseg = (rows + ZSEG - 1) / ZSEG;
+    const size_t sms = zsolve_seg_smem<TC>(rows, txs, two && !zs.same);
+    if ((size_t)2 * txs * nseg <= 512 && sms <= (size_t)kMaxSmem) {
+      dim3 grid((ncol + txs - 1) / txs, ny);
+      k_zsolve_seg<T, TC><<<grid, 2 * txs * nseg, sms, st>>>(data, ex, ey, zs, txs);
+    } else {  // very long z lines: one sequential lane pair per column
+      const int tx = sizeof(T) == 4 ? 32 : 16;
+      const size_t sm = (size_t)rows * tx * (sizeof(cpx<T>) + sizeof(TC) * (zs.same ? 1 : 2));
+      dim3 grid((ncol + tx - 1) / tx, ny);
+      k_zsolve<T, TC><<<grid, 256, sm, st>>>(data, ex, ey, zs, tx);
+    }
     if (poisson) {
       mark("zero_mode");
       k_zero_mode<T><<<1, 32, 0, st>>>(data, rows, ny, pitch, h2, scale, zwork);
@@ -429,7 +441,8 @@ struct Impl : ImplBase {
       const int nzc = std::min(d.fnz, tune[PF_TUNE_CH_ZCHUNK] > 0 ? tune[PF_TUNE_CH_ZCHUNK] : 32);
       dim3 grid((d.fnx + TL::TX - 1) / TL::TX, (d.fny + TL::TY - 1) / TL::TY, (d.fnz + nzc - 1) / nzc);
       const size_t sm = (size_t)TL::smem_elems(d.rs) * sizeof(T);
-      k_ch_rhs_march<T><<<grid, TL::NT, sm, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml, nzc);
+      if (tune[PF_TUNE_CH_MINB] == 2) k_ch_rhs_march<T, 2><<<grid, TL::NT, sm, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml, nzc);
+      else k_ch_rhs_march<T, 3><<<grid, TL::NT, sm, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml, nzc);
     }
     const int nlf = d.fny * d.fnz;
     rfft_x(FineArrPro<T>{mu, d.fnx}, spF, d.fnx, nlf, pF, plFx, twFx);
@@ -451,8 +464,14 @@ struct Impl : ImplBase {
       using TL = GrTile<3>;
       const size_t sm = TL::smem_elems(d.r, d.ry) * sizeof(T);
       dim3 grid((d.nx + TL::CX - 1) / TL::CX, (d.ny + TL::CY - 1) / TL::CY, (d.nz + TL::CZ - 1) / TL::CZ);
-      if (d.r == 2) k_ch_G_restrict<T, 3, 2><<<grid, 256, sm, st>>>(phi[po], gwall, rs, d, q);
-      else k_ch_G_restrict<T, 3, 1><<<grid, 256, sm, st>>>(phi[po], gwall, rs, d, q);
+      if (d.r == 2) {
+        using TM = GrMarch;
+        const int nkc = tune[PF_TUNE_G_ZCHUNK] > 0 ? tune[PF_TUNE_G_ZCHUNK] : 16;
+        dim3 gm((d.nx + TM::CX - 1) / TM::CX, (d.ny + TM::CY - 1) / TM::CY, (d.nz + 1 + nkc - 1) / nkc);
+        k_ch_G_restrict_march<T><<<gm, TM::NT, TM::smem_elems() * sizeof(T), st>>>(phi[po], gwall, rs, d, q, nkc);
+      } else {
+        k_ch_G_restrict<T, 3, 1><<<grid, 256, sm, st>>>(phi[po], gwall, rs, d, q);
+      }
     }
     const RowLaunch lw = rows(d.ny * (d.nz + 1), d.nx);
     const RowLaunch lc = rows(d.ny * d.nz, d.nx);
@@ -472,8 +491,14 @@ struct Impl : ImplBase {
     }
     A.rs = rs;
     mark("ns_rhs");
-    if (d.dim == 2) k_ns_rhs_v2<T, 2><<<lc.grid, lc.block, 0, st>>>(A, d, q, ru, rv, rw, p.visco);
-    else k_ns_rhs_v2<T, 3><<<lc.grid, lc.block, 0, st>>>(A, d, q, ru, rv, rw, p.visco);
+    const bool ns3 = tune[PF_TUNE_NS_MINB] == 3;
+    if (d.dim == 2) {
+      if (ns3) k_ns_rhs_v2<T, 2, 3><<<lc.grid, lc.block, 0, st>>>(A, d, q, ru, rv, rw, p.visco);
+      else k_ns_rhs_v2<T, 2, 4><<<lc.grid, lc.block, 0, st>>>(A, d, q, ru, rv, rw, p.visco);
+    } else {
+      if (ns3) k_ns_rhs_v2<T, 3, 3><<<lc.grid, lc.block, 0, st>>>(A, d, q, ru, rv, rw, p.visco);
+      else k_ns_rhs_v2<T, 3, 4><<<lc.grid, lc.block, 0, st>>>(A, d, q, ru, rv, rw, p.visco);
+    }
     const double kk = p.gamma0 / (p.dt * p.nu_m);
     // u~, v~ land in the n-1 buffers (free once the right sides exist)
     coarse_solve(ru, u[fo], spU, d.nz, Z_DIRICH, kk, false);
@@ -669,6 +694,9 @@ struct Impl : ImplBase {
         throw ApiError(PF_ERR_ARG, "z-solve columns must be a multiple of 16 that fits in shared memory");
       if (knob == PF_TUNE_ROW_BLOCK && (value % 32 || value > 1024)) throw ApiError(PF_ERR_ARG, "row block must be a multiple of 32");
       if (knob == PF_TUNE_CH_ZCHUNK && value < 2) throw ApiError(PF_ERR_ARG, "z chunk must be at least 2 planes");
+      if (knob == PF_TUNE_G_ZCHUNK && value < 1) throw ApiError(PF_ERR_ARG, "z chunk must be at least 1 layer");
+      if (knob == PF_TUNE_CH_MINB && value != 2 && value != 3) throw ApiError(PF_ERR_ARG, "CH register budget: 2 or 3 CTAs per SM");
+      if (knob == PF_TUNE_NS_MINB && value != 3 && value != 4) throw ApiError(PF_ERR_ARG, "NS register budget: 3 or 4 CTAs per SM");
     }
     tune[knob] = value;
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);

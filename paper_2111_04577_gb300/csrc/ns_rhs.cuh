@@ -236,8 +236,9 @@ __device__ __forceinline__ void k_ns_rhs_v2_b(const NsIn<T>& a, const Dims d, co
   }
 }
 
-template <class T, int DIM>
-__global__ void __launch_bounds__(256) k_ns_rhs_v2(const __grid_constant__ NsIn<T> a, const Dims d, const PhysT<T> q, T* __restrict__ ru, T* __restrict__ rv, T* __restrict__ rw, const int have_tau) {
+// MINB: CTAs of 256 threads per SM the register budget is sized for
+template <class T, int DIM, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_ns_rhs_v2(const __grid_constant__ NsIn<T> a, const Dims d, const PhysT<T> q, T* __restrict__ ru, T* __restrict__ rv, T* __restrict__ rw, const int have_tau) {
   extern __shared__ __align__(16) unsigned char smraw[];
   k_ns_rhs_v2_b<T, DIM>(a, d, q, ru, rv, rw, have_tau, make_int3(blockIdx.x, blockIdx.y, blockIdx.z), smraw);
 }

@@ -299,39 +299,29 @@ __global__ void k_zsolve(cpx<T>* __restrict__ data, const double* __restrict__ e
 }
 
 // The (kx, ky) = (0, 0) column of a pure Neumann Poisson problem is singular
-// (constants).  Solved in FP64 with the last row replaced by x = 0, then the
-// mean is removed -- the zero mode set to zero, as in Eq. NS37's solver.
+// (constants).  Row k of it says f_{k+1/2} - f_{k-1/2} = h^2 r_k for the
+// face differences f_{k+1/2} = x_{k+1} - x_k, with f = 0 through both walls;
+// so f is the running sum of h^2 r and x the running sum of f (the last row
+// is the compatibility condition and is dropped).  The mean of x is then
+// removed: the zero mode set to zero, as in Eq. NS37's solver.  FP64, no
+// division; one thread per real/imaginary part.
 template <class T>
 __device__ __forceinline__ void k_zero_mode_b(cpx<T>* __restrict__ data, int rows, int ny, int pitch, double h2, double scale, double* __restrict__ work, const int3 bid, unsigned char* smraw) {
   if (threadIdx.x > 1 || bid.x != 0) return;
   const int part = threadIdx.x;
   const size_t zstride = (size_t)ny * pitch * 2;
   T* base = reinterpret_cast<T*>(data) + part;
-  double* cp = work + (size_t)part * 2 * rows;
-  double* dp = cp + rows;
-  double cprev = 0, dprev = 0;
+  double* xs = work + (size_t)part * rows;
+  const double hs = h2 * scale;
+  double f = 0.0, x = 0.0, sum = 0.0;
   for (int k = 0; k < rows; ++k) {
-    double r = (double)base[(size_t)k * zstride] * h2 * scale;
-    double bk = ((k == 0 || k == rows - 1) ? -1.0 : -2.0) - cprev;
-    if (k == rows - 1) {
-      bk = 1.0;
-      r = 0.0;
-      dprev = 0.0;
-    }
-    const double m = 1.0 / bk;
-    cp[k] = (k == rows - 1) ? 0.0 : m;
-    dp[k] = (r - dprev) * m;
-    cprev = m;
-    dprev = dp[k];
-  }
-  double x = 0, sum = 0;
-  for (int k = rows - 1; k >= 0; --k) {
-    x = dp[k] - (k < rows - 1 ? cp[k] * x : 0.0);
-    dp[k] = x;
+    xs[k] = x;
     sum += x;
+    f += (double)base[(size_t)k * zstride] * hs;
+    x += f;
   }
   const double mean = sum / rows;
-  for (int k = 0; k < rows; ++k) base[(size_t)k * zstride] = (T)(dp[k] - mean);
+  for (int k = 0; k < rows; ++k) base[(size_t)k * zstride] = (T)(xs[k] - mean);
 }
 
 template <class T>

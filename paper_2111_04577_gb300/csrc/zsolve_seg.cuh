@@ -1,0 +1,271 @@
+// Wall-normal tridiagonal solves of the transform solvers (Eqs. NS26-NS27,
+// NS36-NS37 after the DFT along x and y), parallel along z.
+//
+// Per (kx, ky) mode and real/imaginary part, the system along z (rows scaled
+// by h^2: off-diagonals 1, diagonal D_k = -2 - sigma inside, the boundary
+// value at the two end rows, sigma = (k^2 + shift) h^2) is solved by LU:
+//   factors   m_k = 1 / (D_k - m_{k-1}),             m_{-1} = 0
+//   forward   d_k = m_k (r_k - d_{k-1})              (r = scale h^2 rhs)
+//   backward  x_k = d_k - m_k x_{k+1}
+// and, for the pair (L - shift2) y = h^2 x of the CH step, solve 2 is
+// eliminated from the last row down while solve 1 substitutes, with the
+// factors g_k = m2_{R-1-k} of the mirrored recurrence (the end rows are the
+// same at both walls):
+//   q_k = g_k (h^2 x_k - q_{k+1}),   y_k = q_k - g_k y_{k-1}.
+// Every step above is a first-order linear recurrence z_k = a_k z_prev + b_k.
+// The rows are cut into segments of ZSEG = 16; thread (lane, segment) keeps its
+// 16 values in registers, runs each recurrence over its segment from a zero
+// start while multiplying up a_k, then adds the carried-in value times the
+// running product once the segment ends of all earlier segments are combined.
+// The factors have a closed form (LuClosed below), so every thread forms those
+// of its own rows.
+// A lane is one real component of one kx column; consecutive lanes are
+// consecutive reals of a row, so every row of a segment is one coalesced
+// access per warp.  The segment length is fixed, so the arithmetic of a
+// column does not depend on the columns per CTA.
+#pragma once
+#include "spectral.cuh"
+
+namespace pf {
+
+constexpr int ZSEG = 16;
+
+template <class TC>
+__device__ __forceinline__ TC zs_exp2(TC x) { return exp2(x); }
+template <>
+__device__ __forceinline__ float zs_exp2<float>(float x) { return exp2f(x); }
+template <class TC>
+__device__ __forceinline__ TC zs_log2(TC x) { return log2(x); }
+template <>
+__device__ __forceinline__ float zs_log2<float>(float x) { return log2f(x); }
+
+// LU factors of the z system in closed form.  With the interior diagonal
+// D = -2 - sigma, the pivots are ratios U_{k+1}/U_k of U_{k+1} = D U_k - U_{k-1},
+// U_0 = 1, U_1 = D_0 (the end-row diagonal), so with the roots l1 (|l1| > 1) and
+// l2 = 1/l1 of x^2 - D x + 1, rho = l2/l1 and beta = (l1 - D_0)/(D_0 - l2):
+//   m_k = U_k / U_{k+1} = (1/l1) (1 + beta rho^k) / (1 + beta rho^{k+1}),  k < R-1,
+// and the last row, whose diagonal is the other end row, m_{R-1} = 1/(D_0 - m_{R-2}).
+// D^2 - 4 is formed as sigma (sigma + 4) to avoid cancellation.  (sigma = 0, the
+// singular Poisson mode, gives NaN; that column is not stored.)
+template <class TC>
+struct LuClosed {
+  TC il1, beta, lr, d0;
+  int R;
+  __device__ __forceinline__ LuClosed(int rows, int bc, TC sg) : R(rows) {
+    const TC D = (TC)-2 - sg;
+    d0 = zdiag<TC>(0, rows, bc, sg);
+    const TC l1 = (D - sqrt(sg * (sg + (TC)4))) * (TC)0.5;
+    const TC l2 = (TC)1 / l1;
+    il1 = l2;
+    beta = (l1 - d0) / (d0 - l2);
+    lr = zs_log2<TC>(l2 / l1);
+  }
+  __device__ __forceinline__ TC interior(int k) const {
+    const TC pk = zs_exp2<TC>((TC)k * lr);
+    const TC pk1 = zs_exp2<TC>((TC)(k + 1) * lr);
+    return il1 * ((TC)1 + beta * pk) / ((TC)1 + beta * pk1);
+  }
+  __device__ __forceinline__ TC m(int k) const {
+    if (R == 1) return (TC)1 / d0;
+    if (k < R - 1) return interior(k);
+    return (TC)1 / (d0 - interior(R - 2));
+  }
+};
+
+// smem (TC): f1[R][tx], f2[R][tx] (pair with two shifts), car[4 phases][2][S][L]
+template <class T, class TC>
+__global__ void __launch_bounds__(512, 2) k_zsolve_seg(cpx<T>* __restrict__ data, const double* __restrict__ eigx,
+                                                     const double* __restrict__ eigy, const ZSolve zs, const int tx) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int R = zs.rows;
+  const int L = 2 * tx;
+  const int S = (R + ZSEG - 1) / ZSEG;
+  const int lane = threadIdx.x % L, s = threadIdx.x / L;
+  const int c = lane >> 1;
+  const int ky = blockIdx.y;
+  const int col0 = blockIdx.x * tx;
+  const int col = col0 + c;
+  const bool in = col < zs.ncol;
+  const bool dual = zs.two && !zs.same;
+  TC* f1 = reinterpret_cast<TC*>(smraw);
+  TC* f2 = dual ? f1 + (size_t)R * tx : f1;
+  TC* car = f1 + (size_t)R * tx * (dual ? 2 : 1);  // [4][2][S][L]
+  const int k0 = s * ZSEG;
+  const int nk = max(0, min(ZSEG, R - k0));
+  // ---- loads first: the rows of this lane, in flight during the factor phase ----
+  T* gcol = reinterpret_cast<T*>(data + (size_t)ky * zs.pitch + col0) + lane;
+  const size_t zstride = (size_t)zs.ny * zs.pitch * 2;  // reals between rows
+  TC v[ZSEG];
+  {
+    const T* gp = gcol + (size_t)k0 * zstride;
+#pragma unroll
+    for (int j = 0; j < ZSEG; ++j) {
+      v[j] = (in && j < nk) ? (TC)*gp : (TC)0;
+      gp += zstride;
+    }
+  }
+  const TC k2 = (TC)(-(eigx[in ? col : col0] + eigy[ky]));
+  const TC h2 = (TC)zs.h2;
+  const TC sg1 = (k2 + (TC)zs.shift1) * h2;
+  const TC sg2 = (k2 + (TC)zs.shift2) * h2;
+  // ---- factors in closed form: the two lanes of a column share the rows ----
+  const int part = lane & 1;
+  auto factors = [&](TC sg, TC* f) {
+    const LuClosed<TC> lu(R, zs.bc, sg);
+    for (int j = part; j < nk; j += 2) f[(size_t)(k0 + j) * tx + c] = lu.m(k0 + j);
+  };
+  factors(sg1, f1);
+  if (dual) factors(sg2, f2);
+  __syncthreads();
+  const TC rs = (TC)(zs.h2 * zs.scale);
+  // carried-in value of a linear recurrence, from the (product, last) pairs of the earlier segments
+  auto carry_fwd = [&](const TC* cp) -> TC {
+    const TC* cz = cp + (size_t)S * L;
+    TC g = 0;
+    for (int t = 0; t < s; ++t) g = cp[(size_t)t * L + lane] * g + cz[(size_t)t * L + lane];
+    return g;
+  };
+  auto carry_bwd = [&](const TC* cp) -> TC {
+    const TC* cz = cp + (size_t)S * L;
+    TC g = 0;
+    for (int t = S - 1; t > s; --t) g = cp[(size_t)t * L + lane] * g + cz[(size_t)t * L + lane];
+    return g;
+  };
+  TC* cA = car;
+  TC* cB = car + (size_t)2 * S * L;
+  TC* cC = car + (size_t)4 * S * L;
+  TC* cD = car + (size_t)6 * S * L;
+  // ---- solve 1, forward: d_k = -m_k d_{k-1} + m_k r_k ----
+  {
+    TC z = 0, P = 1;
+#pragma unroll
+    for (int j = 0; j < ZSEG; ++j)
+      if (j < nk) {
+        const TC m = f1[(size_t)(k0 + j) * tx + c];
+        z = m * (v[j] * rs - z);
+        v[j] = z;
+        P *= -m;
+      }
+    cA[(size_t)s * L + lane] = P;
+    cA[(size_t)(S + s) * L + lane] = z;
+  }
+  __syncthreads();
+  {
+    const TC g = carry_fwd(cA);
+    TC p = 1;
+#pragma unroll
+    for (int j = 0; j < ZSEG; ++j)
+      if (j < nk) {
+        p *= -f1[(size_t)(k0 + j) * tx + c];
+        v[j] += p * g;
+      }
+  }
+  // ---- solve 1, backward: x_k = -m_k x_{k+1} + d_k ----
+  {
+    TC z = 0, P = 1;
+#pragma unroll
+    for (int j = ZSEG - 1; j >= 0; --j)
+      if (j < nk) {
+        const TC m = f1[(size_t)(k0 + j) * tx + c];
+        z = v[j] - m * z;
+        v[j] = z;
+        P *= -m;
+      }
+    cB[(size_t)s * L + lane] = P;
+    cB[(size_t)(S + s) * L + lane] = z;
+  }
+  __syncthreads();
+  const bool keep = in && !(zs.skip_zero && col == 0 && ky == 0);
+  if (!zs.two) {
+    const TC g = carry_bwd(cB);
+    TC p = 1;
+#pragma unroll
+    for (int j = ZSEG - 1; j >= 0; --j)
+      if (j < nk) {
+        p *= -f1[(size_t)(k0 + j) * tx + c];
+        v[j] += p * g;
+      }
+    if (keep) {
+      T* gp = gcol + (size_t)k0 * zstride;
+#pragma unroll
+      for (int j = 0; j < ZSEG; ++j)
+        if (j < nk) {
+          gp[0] = (T)v[j];
+          gp += zstride;
+        }
+    }
+    return;
+  }
+  // ---- finish solve 1 and run solve 2's elimination in the same backward pass ----
+  {
+    const TC g = carry_bwd(cB);
+    TC p = 1, z = 0, P = 1;
+#pragma unroll
+    for (int j = ZSEG - 1; j >= 0; --j)
+      if (j < nk) {
+        const int k = k0 + j;
+        p *= -f1[(size_t)k * tx + c];
+        const TC x = v[j] + p * g;
+        const TC gk = f2[(size_t)(R - 1 - k) * tx + c];
+        z = gk * (h2 * x - z);
+        v[j] = z;
+        P *= -gk;
+      }
+    cC[(size_t)s * L + lane] = P;
+    cC[(size_t)(S + s) * L + lane] = z;
+  }
+  __syncthreads();
+  {
+    const TC g = carry_bwd(cC);
+    TC p = 1;
+#pragma unroll
+    for (int j = ZSEG - 1; j >= 0; --j)
+      if (j < nk) {
+        p *= -f2[(size_t)(R - 1 - (k0 + j)) * tx + c];
+        v[j] += p * g;
+      }
+  }
+  // ---- solve 2, forward substitution: y_k = -g_k y_{k-1} + q_k ----
+  {
+    TC z = 0, P = 1;
+#pragma unroll
+    for (int j = 0; j < ZSEG; ++j)
+      if (j < nk) {
+        const TC gk = f2[(size_t)(R - 1 - (k0 + j)) * tx + c];
+        z = v[j] - gk * z;
+        v[j] = z;
+        P *= -gk;
+      }
+    cD[(size_t)s * L + lane] = P;
+    cD[(size_t)(S + s) * L + lane] = z;
+  }
+  __syncthreads();
+  {
+    const TC g = carry_fwd(cD);
+    TC p = 1;
+#pragma unroll
+    for (int j = 0; j < ZSEG; ++j)
+      if (j < nk) {
+        p *= -f2[(size_t)(R - 1 - (k0 + j)) * tx + c];
+        v[j] += p * g;
+      }
+    if (keep) {
+      T* gp = gcol + (size_t)k0 * zstride;
+#pragma unroll
+      for (int j = 0; j < ZSEG; ++j)
+        if (j < nk) {
+          gp[0] = (T)v[j];
+          gp += zstride;
+        }
+    }
+  }
+}
+
+// shared memory of k_zsolve_seg in bytes
+template <class TC>
+inline size_t zsolve_seg_smem(int rows, int tx, bool dual) {
+  const int S = (rows + ZSEG - 1) / ZSEG;
+  return sizeof(TC) * ((size_t)rows * tx * (dual ? 2 : 1) + (size_t)8 * S * 2 * tx);
+}
+
+}  // namespace pf

@@ -42,6 +42,8 @@ def workload(g, **kw):
 CH_CASES = [
     (2, 16, 8, 1), (2, 24, 12, 1), (2, 20, 10, 0), (2, 28, 6, 1),
     (3, 16, 8, 1), (3, 12, 6, 1), (3, 10, 4, 0),
+    # deep z: several 32-row solve segments with a ragged last one
+    (2, 12, 40, 1), (2, 16, 48, 0), (3, 8, 20, 1),
 ]
 
 
@@ -85,6 +87,8 @@ FULL_CASES = [
     (2, 24, 12, 0, dict(ratio_rho=10.0, ratio_mu=5.0, theta_deg=60.0)),
     (3, 16, 8, 1, dict(ratio_rho=1000.0, ratio_mu=20.0, theta_deg=90.0, Wi=2.0, beta=0.3)),
     (3, 12, 6, 1, dict(ratio_rho=1000.0, ratio_mu=50.0, theta_deg=45.0)),
+    # deep z: coarse u/p 40 rows, w 39 faces, fine 80 rows
+    (2, 16, 40, 1, dict(ratio_rho=100.0, ratio_mu=10.0, theta_deg=70.0, Wi=0.5, beta=0.5)),
 ]
 
 
