@@ -293,6 +293,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="keep the built-in launch shapes")
     ap.add_argument("--nx", type=int, default=0,
                     help="run the workload's physics at another coarse nx (ny = nx, nz = nx/2); profiling only")
+    ap.add_argument("--nz", type=int, default=0, help="with --nx: coarse nz (default nx/2); profiling only")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -310,7 +311,7 @@ def main():
     build.build()
     w = workload(args.config)
     if args.nx:
-        w = wl.scaled(w, args.nx, args.nx // 2)
+        w = wl.scaled(w, args.nx, args.nz or args.nx // 2)
     g = w.grid
     stream = torch.cuda.Stream()
     prec = binding.PF_MIXED

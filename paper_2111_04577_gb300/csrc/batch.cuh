@@ -36,6 +36,7 @@ struct FinePro {
 template <class T>
 struct PlainEpi {
   static constexpr const char* name = "irfft_x";
+  static constexpr bool kPre = false;
   T* a;
   int n;
   __device__ __forceinline__ void operator()(int line, int x, T v) const { a[(size_t)line * n + x] = v; }

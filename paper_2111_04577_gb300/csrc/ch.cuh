@@ -71,9 +71,16 @@ struct CoarseVel {
 template <class T>
 struct ChFinish {
   static constexpr const char* name = "ch_ifftx_finish";
+  static constexpr bool kPre = true;  // phi^n, phi^{n-1} are staged before the transform
   const T* pn;
   T* po_new;  // holds phi^{n-1} on entry, phi^{n+1} on exit
   int fnx;
+  __device__ __forceinline__ const T* pre0() const { return pn; }
+  __device__ __forceinline__ const T* pre1() const { return po_new; }
+  __device__ __forceinline__ int pre_n() const { return fnx; }
+  __device__ __forceinline__ void apply(int line, int i, T delta, T vn, T vo) const {
+    po_new[(size_t)line * fnx + i] = (T)2 * vn - vo + delta;
+  }
   __device__ __forceinline__ void operator()(int line, int i, T delta) const {
     const size_t id = (size_t)line * fnx + i;
     po_new[id] = (T)2 * pn[id] - po_new[id] + delta;

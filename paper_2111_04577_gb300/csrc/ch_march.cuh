@@ -475,3 +475,276 @@ __global__ void __launch_bounds__(GrMarch::NT, 2) k_ch_G_restrict_march(const T*
 }
 
 }  // namespace pf
+
+namespace pf {
+
+// ---------------------------------------------------------------------------
+// k_ch_rhs_march4: the z-marching CH right side of k_ch_rhs_march (same R,
+// same arithmetic per cell), FP32, with each thread owning four consecutive x
+// cells of one row so that every shared-memory access moves a float4 and the
+// offsets are shared by four cells.  Needs fnx % 4 == 0 (float4 rows never
+// straddle the periodic seam).  RS = log2 of the refinement ratio (fine/coarse).
+// Planes carry 4 floats of padding on both ends: the halo chunks read one
+// float beyond their row, and only lanes that are never used depend on it.
+// ---------------------------------------------------------------------------
+struct March4 {
+  static constexpr int TX = 64, TY = 16, NT = 256, CH = TX / 4;  // 16 chunks per row
+  static constexpr int SXC = CH + 2, SXF = 4 * SXC;               // phi* chunks (x0-4 .. x0+68)
+  static constexpr int SY = TY + 4, SPF = SY * SXF + 8;            // phi* rows y0-2 .. y0+18, padded plane
+  static constexpr int MY = TY + 2, MPF = MY * SXF + 8;            // mu* rows y0-1 .. y0+17
+  static constexpr int OPF = TX * TY;                              // owned cells per plane
+  static constexpr int NPS = 5, NMS = 3, NDS = 4;
+  static constexpr int NSC = SY * SXC, NMC = MY * SXC;             // staged / mu chunks per plane
+  static constexpr int KS = (NSC + NT - 1) / NT, KM = (NMC + NT - 1) / NT;
+  __host__ __device__ static constexpr int VX(int rs) { return (TX >> rs) + 2; }
+  __host__ __device__ static constexpr int VY(int rs) { return (TY >> rs) + 2; }
+  __host__ __device__ static constexpr int smem_floats(int rs) {
+    return NPS * SPF + NMS * MPF + NDS * OPF + 8 * VX(rs) * VY(rs);
+  }
+};
+
+template <int RS, int MINB>
+__global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineView<float> f, const CoarseVel<float> vel,
+                                                                     float* __restrict__ R, double* __restrict__ gwall,
+                                                                     const Dims d, const Phys p, const PhysT<float> q,
+                                                                     const float inv_mldt, const float inv_ml,
+                                                                     const int nzc) {
+  using TL = March4;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* ps = reinterpret_cast<float*>(smraw);  // [NPS][4 + SY*SXF + 4]
+  float* ms = ps + TL::NPS * TL::SPF;           // [NMS][4 + MY*SXF + 4]
+  float* ds = ms + TL::NMS * TL::MPF;           // [NDS][TY][TX]
+  float* vb = ds + TL::NDS * TL::OPF;           // [2][u, v, w_lo, w_hi][VY][VX]
+  constexpr int VX = TL::VX(RS), VY = TL::VY(RS), NV = VX * VY;
+  const int t = threadIdx.x;
+  const int x0 = blockIdx.x * TL::TX, y0 = blockIdx.y * TL::TY;
+  const int fnx = d.fnx, fny = d.fny, fnz = d.fnz;
+  const size_t plane = (size_t)fnx * fny;
+  const int zb = blockIdx.z * nzc, ze = min(zb + nzc, fnz);
+  // ---- staging chunks: global x/y offset (multiple of 4) and owned slot ----
+  int sxy[TL::KS], sown[TL::KS];
+#pragma unroll
+  for (int k = 0; k < TL::KS; ++k) {
+    const int e = t + k * TL::NT;
+    sxy[k] = -1;
+    sown[k] = -1;
+    if (e < TL::NSC) {
+      const int yy = e / TL::SXC, xc = e - yy * TL::SXC;
+      sxy[k] = pmod_m(y0 - 2 + yy, fny) * fnx + pmod_m(x0 - 4 + 4 * xc, fnx);
+      if (yy >= 2 && yy < TL::TY + 2 && xc >= 1 && xc <= TL::CH) sown[k] = (yy - 2) * TL::TX + 4 * (xc - 1);
+    }
+  }
+  auto star_load = [&](int gz, float4 (&rg)[TL::KS], float4 (&dg)[TL::KS]) {
+    const size_t zo = (size_t)min(max(gz, 0), fnz - 1) * plane;
+#pragma unroll
+    for (int k = 0; k < TL::KS; ++k)
+      if (sxy[k] >= 0) {
+        const float4 a = *reinterpret_cast<const float4*>(f.pn + zo + sxy[k]);
+        const float4 b = *reinterpret_cast<const float4*>(f.po + zo + sxy[k]);
+        rg[k] = make_float4(2.f * a.x - b.x, 2.f * a.y - b.y, 2.f * a.z - b.z, 2.f * a.w - b.w);
+        dg[k] = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, b.w - a.w);
+      }
+  };
+  auto star_store = [&](int slot, int dslot, const float4 (&rg)[TL::KS], const float4 (&dg)[TL::KS]) {
+    float* pp = ps + slot * TL::SPF + 4;
+    float* dd = ds + dslot * TL::OPF;
+#pragma unroll
+    for (int k = 0; k < TL::KS; ++k) {
+      const int e = t + k * TL::NT;
+      if (e < TL::NSC) {
+        reinterpret_cast<float4*>(pp)[e] = rg[k];
+        if (sown[k] >= 0) *reinterpret_cast<float4*>(dd + sown[k]) = dg[k];
+      }
+    }
+  };
+  const int cx0 = (x0 >> RS) - 1, cy0 = (y0 >> RS) - 1;
+  const int cplane = d.nx * d.ny;
+  auto vel_load = [&](int kc, int slot) {
+    float* vu = vb + slot * 4 * NV;
+    for (int e = t; e < NV; e += TL::NT) {
+      const int yy = e / VX, xx = e - yy * VX;
+      const int cx = pmod_m(cx0 + xx, d.nx), cy = pmod_m(cy0 + yy, d.ny);
+      const size_t colw = (size_t)cy * d.nx + cx;
+      const size_t oc = (size_t)kc * cplane + colw;
+      vu[e] = vel.us(oc);
+      vu[NV + e] = vel.vs(oc);
+      vu[2 * NV + e] = vel.ws(oc);
+      vu[3 * NV + e] = vel.ws((size_t)(kc + 1) * cplane + colw);
+    }
+  };
+  // ---- mu* of one plane, four x cells per chunk ----
+  auto mu_plane = [&](int gz, int sm1, int s0, int sp1, int mslot) {
+    float* mm = ms + mslot * TL::MPF + 4;
+    const float* pm = ps + sm1 * TL::SPF + 4;
+    const float* pc = ps + s0 * TL::SPF + 4;
+    const float* pq = ps + sp1 * TL::SPF + 4;
+#pragma unroll
+    for (int k = 0; k < TL::KM; ++k) {
+      const int e = t + k * TL::NT;
+      if (e >= TL::NMC) continue;
+      float4* mo = reinterpret_cast<float4*>(mm) + e;
+      if (gz < 0 || gz >= fnz) {
+        *mo = make_float4(0.f, 0.f, 0.f, 0.f);
+        continue;
+      }
+      const int my = e / TL::SXC, mc = e - my * TL::SXC;
+      const int o = (my + 1) * TL::SXF + 4 * mc;  // phi* row my+1
+      const float4 c = *reinterpret_cast<const float4*>(pc + o);
+      const float l = pc[o - 1], r = pc[o + 4];
+      const float4 up = *reinterpret_cast<const float4*>(pc + o + TL::SXF);
+      const float4 dn = *reinterpret_cast<const float4*>(pc + o - TL::SXF);
+      const float4 zp = gz + 1 < fnz ? *reinterpret_cast<const float4*>(pq + o) : c;
+      const float4 zm = gz > 0 ? *reinterpret_cast<const float4*>(pm + o) : c;
+      const float cv[6] = {l, c.x, c.y, c.z, c.w, r};
+      const float uv[4] = {up.x, up.y, up.z, up.w}, dv[4] = {dn.x, dn.y, dn.z, dn.w};
+      const float zpv[4] = {zp.x, zp.y, zp.z, zp.w}, zmv[4] = {zm.x, zm.y, zm.z, zm.w};
+      float outv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float c0 = cv[i + 1];
+        float lap = cv[i + 2] + cv[i] - 2 * c0;
+        lap += uv[i] + dv[i] - 2 * c0;
+        lap = (lap + zpv[i] + zmv[i] - 2 * c0) * q.ih2;
+        outv[i] = c0 * (c0 * c0 - 1) * q.ie2 - lap;
+      }
+      if (gz == 0 || gz == fnz - 1) {
+        const int gy = y0 - 1 + my;
+        const bool rown = my >= 1 && my <= TL::TY && gy < fny;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int gx = x0 - 4 + 4 * mc + i;
+          const bool own = rown && gx >= x0 && gx < x0 + TL::TX && gx < fnx;
+          const size_t col = (size_t)gy * fnx + gx;
+          if (gz == 0) {
+            const double g = wall_g(p.cos_bot, (double)cv[i + 1], (double)zpv[i], p.eta);
+            if (own) gwall[col] = g;
+            outv[i] -= (float)(g / d.h);
+          }
+          if (gz == fnz - 1) {
+            const double g = wall_g(p.cos_top, (double)cv[i + 1], (double)zmv[i], p.eta);
+            if (own) gwall[plane + col] = g;
+            outv[i] -= (float)(g / d.h);
+          }
+        }
+      }
+      *mo = make_float4(outv[0], outv[1], outv[2], outv[3]);
+    }
+  };
+  // ---- owned chunk of this thread ----
+  const int cx = t % TL::CH, ty = t / TL::CH;
+  const int gx = x0 + 4 * cx, gy = y0 + ty;
+  const bool act = gx < fnx && gy < fny;
+  const int so = (ty + 2) * TL::SXF + 4 * (cx + 1);  // phi* center chunk
+  const int mo = (ty + 1) * TL::SXF + 4 * (cx + 1);  // mu* center chunk
+  const int dof = ty * TL::TX + 4 * cx;
+  // velocity box rows/columns (Eq. dual1)
+  const int urow = ((ty >> RS) + 1) * VX;
+  const int cb = ((4 * cx) >> RS) + 1;  // box column of the chunk's first coarse cell
+  const bool yodd = RS == 1 && (gy & 1);
+  const int vr0 = ((ty >> RS) + 1) * VX, vr1 = (((ty + 1) >> RS) + 1) * VX;
+
+  // ---- prologue ----
+  {
+    float4 rg[TL::KS], dg[TL::KS];
+#pragma unroll
+    for (int k = 0; k < TL::KS; ++k) rg[k] = dg[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int j = 0; j < 4; ++j) {
+      star_load(zb - 2 + j, rg, dg);
+      star_store(j, j >= 2 ? j - 2 : 3, rg, dg);
+    }
+  }
+  __syncthreads();
+  mu_plane(zb - 1, 0, 1, 2, 0);
+  mu_plane(zb, 1, 2, 3, 1);
+  float4 rg[TL::KS], dg[TL::KS];
+#pragma unroll
+  for (int k = 0; k < TL::KS; ++k) rg[k] = dg[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  star_load(zb + 2, rg, dg);
+  int kc_loaded = -1;
+  for (int z = zb; z < ze; ++z) {
+    const int m = z - zb;
+    star_store((m + 4) % 5, (m + 2) & 3, rg, dg);
+    const int kc = z >> RS;
+    if (kc != kc_loaded) {  // slot kc & 1: its last readers (layer kc - 2) are done
+      vel_load(kc, kc & 1);
+      kc_loaded = kc;
+    }
+    __syncthreads();
+    if (z + 1 < ze) star_load(z + 3, rg, dg);
+    mu_plane(z + 1, (m + 2) % 5, (m + 3) % 5, (m + 4) % 5, (m + 2) % 3);
+    __syncthreads();
+    if (!act) continue;
+    const float* pm = ps + ((m + 1) % 5) * TL::SPF + 4;
+    const float* pc = ps + ((m + 2) % 5) * TL::SPF + 4;
+    const float* pq = ps + ((m + 3) % 5) * TL::SPF + 4;
+    const float* mmm = ms + (m % 3) * TL::MPF + 4;
+    const float* mmc = ms + ((m + 1) % 3) * TL::MPF + 4;
+    const float* mmp = ms + ((m + 2) % 3) * TL::MPF + 4;
+    const float* vu = vb + (kc & 1) * 4 * NV;
+    const float* vv = vu + NV;
+    const float* vw = vu + 2 * NV;
+    // face velocities of the four cells
+    float uf[5];
+#pragma unroll
+    for (int fq = 0; fq < 5; ++fq) {
+      const int cc = cb + ((4 * cx + fq) >> RS) - ((4 * cx) >> RS);
+      const float a = vu[urow + cc];
+      uf[fq] = (RS == 1 && (fq & 1)) ? 0.5f * (a + vu[urow + cc + 1]) : a;
+    }
+    float vlo[4], vhi[4], wlo[4], whi[4];
+    const int kf0 = (z >> RS) - kc, kf1 = ((z + 1) >> RS) - kc;
+    const bool hw0 = RS == 1 && (z & 1), hw1 = RS == 1 && ((z + 1) & 1);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int cc = cb + ((4 * cx + i) >> RS) - ((4 * cx) >> RS);
+      // y faces gy (lo) and gy + 1 (hi)
+      const float a0 = vv[vr0 + cc];
+      vlo[i] = yodd ? 0.5f * (a0 + vv[vr0 + VX + cc]) : a0;
+      const float a1 = vv[vr1 + cc];
+      vhi[i] = (RS == 1 && !yodd) ? 0.5f * (a1 + vv[vr1 + VX + cc]) : a1;
+      // z faces z (lo) and z + 1 (hi)
+      const float w0 = vw[kf0 * NV + urow + cc];
+      wlo[i] = hw0 ? 0.5f * (w0 + vw[(kf0 + 1) * NV + urow + cc]) : w0;
+      const float w1 = vw[kf1 * NV + urow + cc];
+      whi[i] = hw1 ? 0.5f * (w1 + vw[(kf1 + 1) * NV + urow + cc]) : w1;
+    }
+    const float4 c4 = *reinterpret_cast<const float4*>(pc + so);
+    const float pv[6] = {pc[so - 1], c4.x, c4.y, c4.z, c4.w, pc[so + 4]};
+    const float4 up = *reinterpret_cast<const float4*>(pc + so + TL::SXF);
+    const float4 dn = *reinterpret_cast<const float4*>(pc + so - TL::SXF);
+    const float4 zp = *reinterpret_cast<const float4*>(pq + so);
+    const float4 zm = *reinterpret_cast<const float4*>(pm + so);
+    const float uvp[4] = {up.x, up.y, up.z, up.w}, dvp[4] = {dn.x, dn.y, dn.z, dn.w};
+    const float zpp[4] = {zp.x, zp.y, zp.z, zp.w}, zmp[4] = {zm.x, zm.y, zm.z, zm.w};
+    const float4 m4 = *reinterpret_cast<const float4*>(mmc + mo);
+    const float mv[6] = {mmc[mo - 1], m4.x, m4.y, m4.z, m4.w, mmc[mo + 4]};
+    const float4 mu4 = *reinterpret_cast<const float4*>(mmc + mo + TL::SXF);
+    const float4 md4 = *reinterpret_cast<const float4*>(mmc + mo - TL::SXF);
+    const float4 mzp4 = *reinterpret_cast<const float4*>(mmp + mo);
+    const float4 mzm4 = *reinterpret_cast<const float4*>(mmm + mo);
+    const float muv[4] = {mu4.x, mu4.y, mu4.z, mu4.w}, mdv[4] = {md4.x, md4.y, md4.z, md4.w};
+    const float mzpv[4] = {mzp4.x, mzp4.y, mzp4.z, mzp4.w}, mzmv[4] = {mzm4.x, mzm4.y, mzm4.z, mzm4.w};
+    const float4 d4 = *reinterpret_cast<const float4*>(ds + (m & 3) * TL::OPF + dof);
+    const float dv[4] = {d4.x, d4.y, d4.z, d4.w};
+    float out[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float c0 = pv[i + 1];
+      float adv = uf[i + 1] * (c0 + pv[i + 2]) - uf[i] * (pv[i] + c0);
+      adv += vhi[i] * (c0 + uvp[i]) - vlo[i] * (dvp[i] + c0);
+      if (z + 1 < fnz) adv += whi[i] * (c0 + zpp[i]);
+      if (z > 0) adv -= wlo[i] * (zmp[i] + c0);
+      adv *= 0.5f * q.ih;
+      const float m0 = mv[i + 1];
+      float lap = mv[i + 2] + mv[i] - 2 * m0;
+      lap += muv[i] + mdv[i] - 2 * m0;
+      const float mzp = z + 1 < fnz ? mzpv[i] : m0;
+      const float mzm = z > 0 ? mzmv[i] : m0;
+      lap = (lap + mzp + mzm - 2 * m0) * q.ih2;
+      out[i] = dv[i] * inv_mldt - adv * inv_ml + lap;
+    }
+    *reinterpret_cast<float4*>(R + (size_t)z * plane + (size_t)gy * fnx + gx) = make_float4(out[0], out[1], out[2], out[3]);
+  }
+}
+
+}  // namespace pf

@@ -16,6 +16,7 @@
 #include <stdexcept>
 #include <string>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/dualpf.h"
@@ -104,6 +105,7 @@ struct FineArrPro {
 template <class T>
 struct ArrEpi {
   static constexpr const char* name = "irfft_x_coarse";
+  static constexpr bool kPre = false;
   T* a;
   int n;
   __device__ __forceinline__ void operator()(int line, int x, T v) const { a[(size_t)line * n + x] = v; }
@@ -331,6 +333,11 @@ struct Impl : ImplBase {
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    if constexpr (std::is_same<T, float>::value) {
+      PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march4<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+      PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march4<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+      PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march4<0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    }
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict_march<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict<T, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict<T, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
@@ -368,7 +375,7 @@ struct Impl : ImplBase {
     const int npair = tune[PF_TUNE_XFFT_PAIRS] > 0 ? tune[PF_TUNE_XFFT_PAIRS] : std::max(1, 1024 / n);
     const int pairs = (nlines + 1) / 2;
     const int grid = (pairs + npair - 1) / npair;
-    const size_t sm = 2 * (size_t)npair * n * sizeof(cpx<T>);
+    const size_t sm = irfft_x_smem<T, Epi>(n, npair);
     mark(Epi::name);
     k_irfft_x<T, Epi><<<grid, 256, sm, st>>>(in, epi, n, nlines, pitch, pl, tw, npair, scale);
   }
@@ -439,10 +446,28 @@ struct Impl : ImplBase {
     } else {
       using TL = MarchTile;
       const int nzc = std::min(d.fnz, tune[PF_TUNE_CH_ZCHUNK] > 0 ? tune[PF_TUNE_CH_ZCHUNK] : 32);
+      bool done = false;
+      if constexpr (std::is_same<T, float>::value) {
+        if (d.fnx % 4 == 0) {  // four x cells per thread, float4 rows
+          using T4 = March4;
+          dim3 g4((d.fnx + T4::TX - 1) / T4::TX, (d.fny + T4::TY - 1) / T4::TY, (d.fnz + nzc - 1) / nzc);
+          const size_t s4 = (size_t)T4::smem_floats(d.rs) * sizeof(float);
+          const bool b2 = tune[PF_TUNE_CH_MINB] == 2;
+          if (d.rs == 1) {
+            if (b2) k_ch_rhs_march4<1, 2><<<g4, T4::NT, s4, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml, nzc);
+            else k_ch_rhs_march4<1, 3><<<g4, T4::NT, s4, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml, nzc);
+          } else {
+            k_ch_rhs_march4<0, 2><<<g4, T4::NT, s4, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml, nzc);
+          }
+          done = true;
+        }
+      }
+      if (!done) {
       dim3 grid((d.fnx + TL::TX - 1) / TL::TX, (d.fny + TL::TY - 1) / TL::TY, (d.fnz + nzc - 1) / nzc);
       const size_t sm = (size_t)TL::smem_elems(d.rs) * sizeof(T);
       if (tune[PF_TUNE_CH_MINB] == 2) k_ch_rhs_march<T, 2><<<grid, TL::NT, sm, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml, nzc);
       else k_ch_rhs_march<T, 3><<<grid, TL::NT, sm, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml, nzc);
+      }
     }
     const int nlf = d.fny * d.fnz;
     rfft_x(FineArrPro<T>{mu, d.fnx}, spF, d.fnx, nlf, pF, plFx, twFx);
@@ -685,7 +710,7 @@ struct Impl : ImplBase {
     if (value < 0) throw ApiError(PF_ERR_ARG, "tuning value must be >= 0");
     auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
     if (value > 0) {
-      if (knob == PF_TUNE_XFFT_PAIRS && (value > 16 || 2 * (size_t)value * std::max(d.fnx, d.nx) * sizeof(cpx<T>) > (size_t)kMaxSmem))
+      if (knob == PF_TUNE_XFFT_PAIRS && (value > 16 || irfft_x_smem<T, ChFinish<T>>(std::max(d.fnx, d.nx), value) > (size_t)kMaxSmem))
         throw ApiError(PF_ERR_ARG, "x-transform line pairs do not fit in shared memory");
       if (knob == PF_TUNE_YFFT_COLS && (!pow2(value) || value > 32 || 2 * (size_t)value * std::max(d.fny, d.ny) * sizeof(cpx<T>) > (size_t)kMaxSmem))
         throw ApiError(PF_ERR_ARG, "y-transform columns must be a power of two that fits in shared memory");
@@ -1139,7 +1164,7 @@ struct Batch : BatchBase {
       // shared memory of the largest pass
       auto zsm = [&](const ZSolve& z) { return (size_t)z.rows * tx * (sizeof(cpx<T>) + sizeof(T) * (z.same ? 1 : 2)); };
       maxsm = std::max(maxsm, (size_t)(TR::NS + TR::NM + 3 * TR::NV(d.rs, 0)) * sizeof(T));
-      maxsm = std::max(maxsm, 2 * (size_t)B.npairF * d.fnx * sizeof(cpx<T>));
+      maxsm = std::max(maxsm, irfft_x_smem<T, ChFinish<T>>(d.fnx, B.npairF));
       maxsm = std::max(maxsm, 2 * (size_t)B.npairC * d.nx * sizeof(cpx<T>));
       maxsm = std::max(maxsm, (size_t)TG::smem_elems(d.r, 1) * sizeof(T));
       maxsm = std::max({maxsm, zsm(B.zpair), zsm(B.zu), zsm(B.zw), zsm(B.zp)});

@@ -16,6 +16,8 @@
 // (R e^Lambda R^T - I) (Eq. NS46); the momentum equation receives
 // tau = (1 + phi)/2 tau_p (Eq. NS12, droplet phase viscoelastic).
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace pf {
@@ -77,6 +79,38 @@ __device__ __forceinline__ void jacobi_rot_sym(T (&dg)[N], T (&of)[N == 2 ? 1 : 
   }
 }
 
+// FP32: the same rotation with tan(phi) written as g / (|h| + sqrt(h^2 + g^2)) sgn(h),
+// h = a_qq - a_pp, g = 2 a_pq (equal to the smaller root above), one fast divide
+// and reciprocal square roots; the rotation stays orthogonal to rounding.
+template <int N>
+__device__ __forceinline__ void jacobi_rot_sym_f(float (&dg)[N], float (&of)[N == 2 ? 1 : 3], float (&V)[N][N], int p,
+                                                 int q) {
+  const int pq = off_slot<N>(p, q);
+  const float apq = of[pq];
+  if (apq == 0.f) return;
+  const float h = dg[q] - dg[p], g = 2.f * apq;
+  const float r = sqrtf(fmaf(h, h, g * g));
+  float t = __fdividef(g, fabsf(h) + r);
+  if (h < 0.f) t = -t;
+  const float c = rsqrtf(fmaf(t, t, 1.f)), s = t * c;
+  dg[p] -= t * apq;
+  dg[q] += t * apq;
+  of[pq] = 0.f;
+  if (N == 3) {
+    const int r3 = 3 - p - q;
+    const int rp = off_slot<N>(r3 < p ? r3 : p, r3 < p ? p : r3), rq = off_slot<N>(r3 < q ? r3 : q, r3 < q ? q : r3);
+    const float arp = of[rp], arq = of[rq];
+    of[rp] = c * arp - s * arq;
+    of[rq] = s * arp + c * arq;
+  }
+#pragma unroll
+  for (int rr = 0; rr < N; ++rr) {
+    const float vrp = V[rr][p], vrq = V[rr][q];
+    V[rr][p] = c * vrp - s * vrq;
+    V[rr][q] = s * vrp + c * vrq;
+  }
+}
+
 // symmetric eigen-decomposition A = V diag(w) V^T by cyclic Jacobi rotations;
 // on entry (dg, of) hold A, on exit dg holds the eigenvalues w
 template <class T, int N>
@@ -85,8 +119,12 @@ __device__ __forceinline__ void eig_sym(T (&dg)[N], T (&of)[N == 2 ? 1 : 3], T (
   for (int a = 0; a < N; ++a)
 #pragma unroll
     for (int b = 0; b < N; ++b) V[a][b] = (a == b) ? (T)1 : (T)0;
+  auto rot = [&](int p, int q) {
+    if constexpr (std::is_same<T, float>::value) jacobi_rot_sym_f<N>(dg, of, V, p, q);
+    else jacobi_rot_sym<T, N>(dg, of, V, p, q);
+  };
   if (N == 2) {  // one rotation diagonalises a 2 x 2 matrix
-    jacobi_rot_sym<T, N>(dg, of, V, 0, 1);
+    rot(0, 1);
     return;
   }
   const T eps2 = sizeof(T) == 4 ? (T)1e-14 : (T)1e-30;
@@ -98,9 +136,9 @@ __device__ __forceinline__ void eig_sym(T (&dg)[N], T (&of)[N == 2 ? 1 : 3], T (
 #pragma unroll
     for (int o = 0; o < (N == 2 ? 1 : 3); ++o) off += of[o] * of[o];
     if (off <= eps2 * dia || off == (T)0) break;
-    jacobi_rot_sym<T, N>(dg, of, V, 0, 1);
-    jacobi_rot_sym<T, N>(dg, of, V, 0, 2);
-    jacobi_rot_sym<T, N>(dg, of, V, 1, 2);
+    rot(0, 1);
+    rot(0, 2);
+    rot(1, 2);
   }
 }
 

@@ -171,11 +171,13 @@ def config(name: str, **kw) -> Workload:
 
 
 def scaled(w: Workload, nx: int, nz: int, ny: int | None = None) -> Workload:
-    """Same physics and domain, another coarse resolution (tests use small copies)."""
+    """Same physics and x/y domain, another coarse resolution (tests use small
+    copies); lz follows nz so that cells stay cubic."""
     g = w.grid
     ny = (1 if g.dim == 2 else nx) if ny is None else ny
     ly = g.ly if g.dim == 3 else g.lx / nx
-    return Workload(w.name + f"@{nx}x{ny}x{nz}", Grid(nx, ny, nz, g.lx, ly, g.lz, g.dual),
+    lz = nz * g.lx / nx
+    return Workload(w.name + f"@{nx}x{ny}x{nz}", Grid(nx, ny, nz, g.lx, ly, lz, g.dual),
                     Params(**w.params.as_dict()), w.steps, w.R0, w.seed, w.amp, dict(w.extra))
 
 

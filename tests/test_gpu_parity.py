@@ -153,6 +153,30 @@ def test_config1_mixed_full_run(prec):
     assert rel(s.coarse("w"), ref.vel[2]) < 1e-3
 
 
+@pytest.mark.parametrize("cfg,nx,nz,steps", [("c2", 32, 16, 40), ("c4", 16, 8, 20)])
+def test_viscoelastic_mixed_vs_oracle(cfg, nx, nz, steps):
+    """Mixed path with the Oldroyd-B polymer: 2e-4 max-abs on phi, 1e-3 relative
+    on velocity and on every Theta component."""
+    w = wl.scaled(wl.config(cfg), nx, nz)
+    g = w.grid
+    phi0 = wl.initial_phi(w)
+    vel = wl.random_velocity(g, 11, 0.2)
+    s = binding.Solver(g, w.params, binding.PF_MIXED)
+    s.load_state(phi0, vel)
+    s.step(steps)
+    ref = ostep.State(g, w.params.as_dict(), phi0, vel0=vel)
+    for _ in range(steps):
+        ref.step()
+    assert np.max(np.abs(s.fine("phi") - ref.phi)) < 2e-4
+    assert rel(s.coarse("u"), ref.vel[0]) < 1e-3
+    assert rel(s.coarse("w"), ref.vel[2]) < 1e-3
+    th = s.coarse("theta")
+    idx = [(0, 0), (0, 1), (1, 1)] if g.dim == 2 else [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    scale = max(np.max(np.abs(ref.theta)), 1e-300)
+    for q, (a, b) in enumerate(idx):
+        assert np.max(np.abs(th[q] - ref.theta[..., a, b])) < 1e-3 * scale, q
+
+
 def test_mass_conservation_gpu_fp64_and_mixed():
     w = wl.scaled(wl.config("c2"), 32, 16)
     g = w.grid
