@@ -60,6 +60,53 @@ def replica_value(cells, steps, world, elapsed):
     return cells * steps * world / elapsed
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of each kernel in
+# one step, in bytes per fine cell, from one ncu capture of the 512x512x64 fine
+# case of this workload's physics; every pass moves data in proportion to the
+# cells, so a full launch scales by its fine cells.  Each entry keeps the
+# sha256 of the source files that define the kernel when the counters were
+# taken: once a kernel changes its traffic reads null until it is measured again.
+TRAFFIC = {
+    "ch_rhs": (14.46, ["paper_2111_04577_gb300/csrc/ch_march.cuh", "paper_2111_04577_gb300/csrc/ch.cuh"], "4a4bc68b8c628481"),
+    "ns_rhs": (16.664, ["paper_2111_04577_gb300/csrc/ns_rhs.cuh", "paper_2111_04577_gb300/csrc/ns.cuh"], "6eea63dfff4645fc"),
+    "polymer_stage2": (13.718, ["paper_2111_04577_gb300/csrc/polymer.cuh"], "e47ead9d9a095597"),
+    "fft_y_fine": (9.235, ["paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "cf9ebcc27278b7f6"),
+    "fft_y_coarse": (4.063, ["paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "cf9ebcc27278b7f6"),
+    "ch_G_restrict": (6.845, ["paper_2111_04577_gb300/csrc/ch_march.cuh", "paper_2111_04577_gb300/csrc/ch.cuh"], "4a4bc68b8c628481"),
+    "polymer_stage1": (7.077, ["paper_2111_04577_gb300/csrc/polymer.cuh"], "e47ead9d9a095597"),
+    "ch_ifftx_finish": (14.164, ["paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "cf9ebcc27278b7f6"),
+    "rfft_x_fine": (5.217, ["paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "cf9ebcc27278b7f6"),
+    "zsolve_pair": (4.705, ["paper_2111_04577_gb300/csrc/zsolve_seg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh"], "141a00fbc127012a"),
+    "rfft_x_coarse": (1.998, ["paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "cf9ebcc27278b7f6"),
+    "irfft_x_coarse": (2.029, ["paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "cf9ebcc27278b7f6"),
+    "zsolve": (2.027, ["paper_2111_04577_gb300/csrc/zsolve_seg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh"], "141a00fbc127012a"),
+    "correct": (2.485, ["paper_2111_04577_gb300/csrc/ns.cuh"], "d1c3da3fba12bb38"),
+    "div": (1.485, ["paper_2111_04577_gb300/csrc/ns.cuh"], "d1c3da3fba12bb38"),
+}
+
+
+def _sha(paths):
+    import hashlib
+    h = hashlib.sha256()
+    for q in paths:
+        with open(os.path.join(ROOT, q), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel, fine_cells):
+    ent = TRAFFIC.get(kernel)
+    if not ent:
+        return None
+    per_cell, srcs, sha = ent
+    try:
+        if _sha(srcs) != sha:
+            return None
+    except OSError:
+        return None
+    return per_cell * fine_cells
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -349,12 +396,16 @@ def main():
     rows = []
     for name, ms, cnt in prof:
         byt = ab.get(name, 0)
+        trk = traffic_for(name, g.fine_cells())
         rows.append({"kernel": name, "launches": cnt, "ms": ms, "alg_bytes": byt,
-                     "gbs": byt / (ms * 1e-3) / 1e9 if ms > 0 else 0.0})
+                     "gbs": byt / (ms * 1e-3) / 1e9 if ms > 0 else 0.0,
+                     "dram_bytes": trk})
     dom = max(rows, key=lambda r: r["ms"])
     total_ms = sum(r["ms"] for r in rows)
+    tr = traffic_for(dom["kernel"], g.fine_cells())
     roofline = {"bound": "hbm", "kernel": dom["kernel"], "achieved": dom["gbs"], "peak": peak, "unit": "GB/s",
-                "frac": dom["gbs"] / peak, "traffic": None, "peak_kind": peak_kind,
+                "frac": dom["gbs"] / peak,
+                "traffic": None if tr is None else tr / max(1, dom["launches"]), "peak_kind": peak_kind,
                 "alg_bytes_per_launch": dom["alg_bytes"] / max(1, dom["launches"]),
                 "launch_ms": dom["ms"] / max(1, dom["launches"])}
     step_bytes = sum(ab.values())

@@ -948,10 +948,17 @@ struct Impl : ImplBase {
     return nlaunch;
   }
 
+  // sum of phi after a run of steps: finite unless a NaN or Inf appeared
   double mass_check() {
-    double out[6];
-    diagnostics(out);
-    return out[0];
+    const size_t n = (size_t)d.fnx * d.fny * d.fnz;
+    k_sum_phi<T><<<nred_blocks, 256, 0, st>>>(phi[pc], n, partial);
+    check_launch();
+    std::vector<double> h((size_t)nred_blocks);
+    PF_CUDA_TRY(cudaMemcpyAsync(h.data(), partial, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PF_CUDA_TRY(cudaStreamSynchronize(st));
+    double s = 0.0;
+    for (double v : h) s += v;
+    return s;
   }
 
   void step(int nsteps, int flags) override {
