@@ -191,6 +191,11 @@ int pf_batch_set_fields(pf_batch* b, int problem, int field_id, const void* src,
 int pf_batch_get_fields(pf_batch* b, int problem, int field_id, void* dst, size_t bytes, int dst_on_device);
 int pf_batch_step(pf_batch* b, int nsteps);
 int pf_batch_diagnostics(pf_batch* b, int problem, double out[6]);
+/* pf_adjoint on one problem of the batch (its own buffers and parameters):
+ * the same CH adjoint, run with the single-problem kernels; afterwards the
+ * problem holds phi^N.  Errors as pf_adjoint, PF_ERR_ARG for a bad index. */
+int pf_batch_adjoint(pf_batch* b, int problem, int nsteps, int ckpt_every, int objective, double out[3], void* dphi0,
+                     int dphi0_on_device);
 const char* pf_batch_last_error(const pf_batch* b);
 void pf_batch_destroy(pf_batch* b);
 
@@ -245,9 +250,11 @@ int pf_adjoint(pf_ctx* ctx, int nsteps, int ckpt_every, int objective, double ou
  *   PF_TUNE_CH_MINB      CTAs per SM the 3D CH right side's registers are sized for (2, 3)
  *   PF_TUNE_NS_MINB      CTAs per SM the NS right side's registers are sized for (3, 4)
  *   PF_TUNE_G_ZCHUNK     coarse layers one CTA of the 3D restriction walks (>= 1)
+ *   PF_TUNE_NS_KZ        z rows one CTA of the NS right side walks (1..64)
  * Errors: PF_ERR_ARG for an unknown knob or a value that does not fit. */
 enum { PF_TUNE_XFFT_PAIRS = 0, PF_TUNE_YFFT_COLS = 1, PF_TUNE_ZSOLVE_COLS = 2, PF_TUNE_ROW_BLOCK = 3, PF_TUNE_CH_ZCHUNK = 4,
-       PF_TUNE_CH_MINB = 5, PF_TUNE_NS_MINB = 6, PF_TUNE_G_ZCHUNK = 7, PF_TUNE_COUNT = 8 };
+       PF_TUNE_CH_MINB = 5, PF_TUNE_NS_MINB = 6, PF_TUNE_G_ZCHUNK = 7,
+       PF_TUNE_NS_KZ = 8, PF_TUNE_COUNT = 9 };
 int pf_set_tuning(pf_ctx* ctx, int knob, int value);
 int pf_get_tuning(const pf_ctx* ctx, int knob, int* value);
 

@@ -27,7 +27,7 @@ EXPORTS = ["pf_init_grid", "pf_set_params", "pf_field_info", "pf_set_fields", "p
            "pf_get_fields", "pf_diagnostics", "pf_profile", "pf_diagnostics_noalloc", "pf_last_error",
            "pf_destroy", "pf_batch_create", "pf_batch_field_info", "pf_batch_set_fields", "pf_batch_get_fields",
            "pf_batch_step", "pf_batch_diagnostics", "pf_batch_last_error", "pf_batch_destroy", "pf_set_tuning",
-           "pf_get_tuning", "pf_adjoint"]
+           "pf_get_tuning", "pf_adjoint", "pf_batch_adjoint"]
 PF_OBJ_WETTED, PF_OBJ_CENTROID_Z = 0, 1
 PROFILE_NAME = 48
 
@@ -87,6 +87,8 @@ def load(path: str = LIB_PATH):
             getattr(lib, f).restype = C.c_int
         lib.pf_adjoint.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), vp, C.c_int]
         lib.pf_adjoint.restype = C.c_int
+        lib.pf_batch_adjoint.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), vp, C.c_int]
+        lib.pf_batch_adjoint.restype = C.c_int
         lib.pf_set_tuning.argtypes = [vp, C.c_int, C.c_int]
         lib.pf_get_tuning.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
         lib.pf_set_tuning.restype = C.c_int
@@ -300,6 +302,20 @@ class Batch:
 
     def step(self, n=1):
         self._chk(self.lib.pf_batch_step(self.h, int(n)))
+
+    def adjoint(self, b, nsteps, ckpt_every=50, objective=PF_OBJ_WETTED, want_phi=True):
+        """Solver.adjoint for problem b of the batch; leaves that problem at phi^N."""
+        out = (C.c_double * 3)()
+        g = None
+        ptr = None
+        if want_phi:
+            cnt, _ = self.info(b, "phi")
+            g = np.empty(cnt, dtype=self.dtype)
+            ptr = g.ctypes.data_as(C.c_void_p)
+        self._chk(self.lib.pf_batch_adjoint(self.h, int(b), int(nsteps), int(ckpt_every), int(objective), out, ptr, 0))
+        if g is not None:
+            g = g.reshape(self.grids[b].fine_shape)
+        return out[0], out[1], out[2], g
 
     def diagnostics(self, b):
         out = (C.c_double * 6)()

@@ -24,6 +24,7 @@
 #include "ch_tiled.cuh"
 #include "ch_march.cuh"
 #include "zsolve_seg.cuh"
+#include "fft_reg.cuh"
 #include "ns.cuh"
 #include "ns_rhs.cuh"
 #include "polymer.cuh"
@@ -339,6 +340,15 @@ struct Impl : ImplBase {
       PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march4<0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     }
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict_march<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    for (int n : {64, 128, 256, 512, 1024})
+      reg_fft_dispatch(n, [&](auto NN) {
+        constexpr int N = decltype(NN)::value;
+        PF_CUDA_TRY(cudaFuncSetAttribute(k_rfft_x_reg<T, N, FineArrPro<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+        PF_CUDA_TRY(cudaFuncSetAttribute(k_rfft_x_reg<T, N, ArrPro<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+        PF_CUDA_TRY(cudaFuncSetAttribute(k_irfft_x_reg<T, N, ChFinish<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+        PF_CUDA_TRY(cudaFuncSetAttribute(k_irfft_x_reg<T, N, ArrEpi<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+        PF_CUDA_TRY(cudaFuncSetAttribute(k_fft_y_reg<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+      });
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict<T, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict<T, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict<T, 3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
@@ -361,8 +371,24 @@ struct Impl : ImplBase {
     r.grid = dim3(nrows, (nxrow + bs - 1) / bs);
     return r;
   }
+  // line pairs per CTA of the register-resident x transforms (NT = n/8 threads a line)
+  int reg_lpc(int n) const {
+    const int nt = n / 8;
+    const int want = tune[PF_TUNE_XFFT_PAIRS] > 0 ? tune[PF_TUNE_XFFT_PAIRS] : std::max(1, 256 / nt);
+    return std::max(1, std::min(want, 1024 / nt));
+  }
   template <class Pro>
   void rfft_x(Pro pro, cpx<T>* out, int n, int nlines, int pitch, const FftPlan& pl, const cpx<T>* tw) {
+    if (reg_fft_size(n)) {
+      const int lpc = reg_lpc(n), pairs = (nlines + 1) / 2;
+      const size_t sm = (size_t)lpc * n * sizeof(cpx<T>);
+      mark(Pro::name);
+      reg_fft_dispatch(n, [&](auto NN) {
+        constexpr int N = decltype(NN)::value;
+        k_rfft_x_reg<T, N, Pro><<<(pairs + lpc - 1) / lpc, lpc * (N / 8), sm, st>>>(pro, out, nlines, pitch, tw);
+      });
+      return;
+    }
     const int npair = tune[PF_TUNE_XFFT_PAIRS] > 0 ? tune[PF_TUNE_XFFT_PAIRS] : std::max(1, 1024 / n);
     const int pairs = (nlines + 1) / 2;
     const int grid = (pairs + npair - 1) / npair;
@@ -372,6 +398,16 @@ struct Impl : ImplBase {
   }
   template <class Epi>
   void irfft_x(const cpx<T>* in, Epi epi, int n, int nlines, int pitch, const FftPlan& pl, const cpx<T>* tw, T scale) {
+    if (reg_fft_size(n)) {
+      const int lpc = reg_lpc(n), pairs = (nlines + 1) / 2;
+      const size_t sm = (size_t)lpc * n * (sizeof(cpx<T>) + (Epi::kPre ? 4 * sizeof(T) : 0));
+      mark(Epi::name);
+      reg_fft_dispatch(n, [&](auto NN) {
+        constexpr int N = decltype(NN)::value;
+        k_irfft_x_reg<T, N, Epi><<<(pairs + lpc - 1) / lpc, lpc * (N / 8), sm, st>>>(in, epi, nlines, pitch, tw, scale);
+      });
+      return;
+    }
     const int npair = tune[PF_TUNE_XFFT_PAIRS] > 0 ? tune[PF_TUNE_XFFT_PAIRS] : std::max(1, 1024 / n);
     const int pairs = (nlines + 1) / 2;
     const int grid = (pairs + npair - 1) / npair;
@@ -380,6 +416,18 @@ struct Impl : ImplBase {
     k_irfft_x<T, Epi><<<grid, 256, sm, st>>>(in, epi, n, nlines, pitch, pl, tw, npair, scale);
   }
   void fft_y(cpx<T>* data, int ny, int pitch, int ncol, int levels, const FftPlan& pl, const cpx<T>* tw, int sign) {
+    if (reg_fft_size(ny)) {
+      const int nt = ny / 8;
+      const int want = tune[PF_TUNE_YFFT_COLS] > 0 ? tune[PF_TUNE_YFFT_COLS] : 8;
+      const int txc = std::max(1, std::min(want, 1024 / nt));
+      const size_t sm = (size_t)txc * ny * sizeof(cpx<T>);
+      mark(ny == d.fny && levels == d.fnz && d.r > 1 ? "fft_y_fine" : "fft_y_coarse");
+      reg_fft_dispatch(ny, [&](auto NN) {
+        constexpr int N = decltype(NN)::value;
+        k_fft_y_reg<T, N><<<dim3((ncol + txc - 1) / txc, levels), txc * (N / 8), sm, st>>>(data, pitch, ncol, tw, sign);
+      });
+      return;
+    }
     const int tx = tune[PF_TUNE_YFFT_COLS] > 0 ? tune[PF_TUNE_YFFT_COLS] : (sizeof(T) == 4 ? 8 : 4);
     dim3 grid((ncol + tx - 1) / tx, levels);
     const size_t sm = 2 * (size_t)ny * tx * sizeof(cpx<T>);
@@ -517,7 +565,17 @@ struct Impl : ImplBase {
     A.rs = rs;
     mark("ns_rhs");
     const bool ns3 = tune[PF_TUNE_NS_MINB] == 3;
-    if (d.dim == 2) {
+    const int kz = tune[PF_TUNE_NS_KZ] > 1 ? tune[PF_TUNE_NS_KZ] : 1;
+    if (kz > 1) {
+      const dim3 gz(d.ny * ((d.nz + kz - 1) / kz), lc.grid.y);
+      if (d.dim == 2) {
+        if (ns3) k_ns_rhs_v2z<T, 2, 3><<<gz, lc.block, 0, st>>>(A, d, q, ru, rv, rw, p.visco, kz);
+        else k_ns_rhs_v2z<T, 2, 4><<<gz, lc.block, 0, st>>>(A, d, q, ru, rv, rw, p.visco, kz);
+      } else {
+        if (ns3) k_ns_rhs_v2z<T, 3, 3><<<gz, lc.block, 0, st>>>(A, d, q, ru, rv, rw, p.visco, kz);
+        else k_ns_rhs_v2z<T, 3, 4><<<gz, lc.block, 0, st>>>(A, d, q, ru, rv, rw, p.visco, kz);
+      }
+    } else if (d.dim == 2) {
       if (ns3) k_ns_rhs_v2<T, 2, 3><<<lc.grid, lc.block, 0, st>>>(A, d, q, ru, rv, rw, p.visco);
       else k_ns_rhs_v2<T, 2, 4><<<lc.grid, lc.block, 0, st>>>(A, d, q, ru, rv, rw, p.visco);
     } else {
@@ -720,6 +778,7 @@ struct Impl : ImplBase {
       if (knob == PF_TUNE_ROW_BLOCK && (value % 32 || value > 1024)) throw ApiError(PF_ERR_ARG, "row block must be a multiple of 32");
       if (knob == PF_TUNE_CH_ZCHUNK && value < 2) throw ApiError(PF_ERR_ARG, "z chunk must be at least 2 planes");
       if (knob == PF_TUNE_G_ZCHUNK && value < 1) throw ApiError(PF_ERR_ARG, "z chunk must be at least 1 layer");
+      if (knob == PF_TUNE_NS_KZ && value > 64) throw ApiError(PF_ERR_ARG, "NS z rows per CTA must be <= 64");
       if (knob == PF_TUNE_CH_MINB && value != 2 && value != 3) throw ApiError(PF_ERR_ARG, "CH register budget: 2 or 3 CTAs per SM");
       if (knob == PF_TUNE_NS_MINB && value != 3 && value != 4) throw ApiError(PF_ERR_ARG, "NS register budget: 3 or 4 CTAs per SM");
     }
@@ -1457,6 +1516,12 @@ int pf_batch_step(pf_batch* b, int nsteps) {
 int pf_batch_diagnostics(pf_batch* b, int problem, double out[6]) {
   if (!b || !out) return PF_ERR_ARG;
   return bguarded(b, [&] { b->impl->problem(problem)->diagnostics(out); });
+}
+
+int pf_batch_adjoint(pf_batch* b, int problem, int nsteps, int ckpt_every, int objective, double out[3], void* dphi0,
+                     int dphi0_on_device) {
+  if (!b || !out) return PF_ERR_ARG;
+  return bguarded(b, [&] { b->impl->problem(problem)->adjoint(nsteps, ckpt_every, objective, out, dphi0, dphi0_on_device); });
 }
 
 const char* pf_batch_last_error(const pf_batch* b) { return b ? b->err.c_str() : g_init_err.c_str(); }

@@ -1,0 +1,249 @@
+// Register-resident FFT of power-of-two lines (64 <= N <= 4096) for the
+// periodic directions of the transform solves (Sections 3.2.1-3.2.2).
+//
+// The same self-sorting (Stockham) factorisation as fft.cuh: stage s combines
+// sub-transforms of length L into length L*P; with M = N/(L*P), butterfly
+// bf = (j, k), j = bf / M, k = bf % M, gathers z_c = w_N^{c j M} Y[j M P + k + c M]
+// and writes the length-P DFT of z to Y'[(j + L q) M + k].  Here a line is
+// owned by NT = N/8 threads, each holding 8 elements in registers, and the
+// small radix (2 or 4, when log2 N is not a multiple of 3) goes first, the
+// radix-8 stages after it:
+//  - on entry thread t holds x[t + NT c], c = 0..7, which is exactly the input
+//    of the first stage's butterflies (bf = t + NT i, j = 0), so the first
+//    stage reads registers loaded straight from global memory;
+//  - stages exchange through one shared buffer of N complex per line, in place
+//    (every thread reads its inputs, barrier, then writes);
+//  - the last (radix-8) stage has M = 1 and j = t, so its outputs
+//    Y'[t + NT q] stay in registers in natural order for the epilogue.
+// Two shared-memory round trips for N = 512 instead of four, and one buffer
+// instead of two.  Every thread of the CTA must call reg_fft together (the
+// stages use __syncthreads()).
+#pragma once
+#include <type_traits>
+
+#include "spectral.cuh"
+
+namespace pf {
+
+template <int N>
+struct RegFftShape {
+  static constexpr int log2n() {
+    int l = 0;
+    for (int n = N; n > 1; n >>= 1) ++l;
+    return l;
+  }
+  static constexpr int NT = N / 8;
+  static constexpr int P0 = log2n() % 3 == 0 ? 8 : (log2n() % 3 == 1 ? 2 : 4);  // first radix
+  static_assert(N >= 64 && N <= 4096 && (N & (N - 1)) == 0, "power of two in [64, 4096]");
+};
+
+template <class T, int P>
+__device__ __forceinline__ void reg_dft(cpx<T>* z, int sign) {
+  if constexpr (P == 8) dft8<T>(z, sign);
+  else dft_small<T, P>(z, sign);
+}
+
+// one stage; FIRST: inputs already in registers; LAST: outputs stay in registers
+template <class T, int N, int L, int P, bool FIRST>
+__device__ __forceinline__ void reg_stage(cpx<T> (&v)[8], cpx<T>* __restrict__ sm, const cpx<T>* __restrict__ tw,
+                                          int sign, int t) {
+  constexpr int NT = N / 8, M = N / (L * P), NB = 8 / P;
+  constexpr bool LAST = L * P == N;
+  if constexpr (!FIRST) {
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      const int bf = t + NT * i, j = bf / M, k = bf % M;
+#pragma unroll
+      for (int c = 0; c < P; ++c) v[i + NB * c] = sm[j * M * P + k + c * M];
+    }
+    if constexpr (!LAST) __syncthreads();  // every read of this stage before the in-place writes
+  }
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int bf = t + NT * i, j = bf / M, k = bf % M;
+    cpx<T> z[P];
+#pragma unroll
+    for (int c = 0; c < P; ++c) {
+      cpx<T> a = v[i + NB * c];
+      if (!FIRST && c > 0) {
+        cpx<T> w = tw[c * j * M];
+        if (sign > 0) w.im = -w.im;
+        a = a * w;
+      }
+      z[c] = a;
+    }
+    reg_dft<T, P>(z, sign);
+    if constexpr (LAST) {
+      // dst = j + L q = t + NT q (M = 1, NB = 1)
+#pragma unroll
+      for (int q = 0; q < P; ++q) v[q] = z[q];
+    } else {
+#pragma unroll
+      for (int q = 0; q < P; ++q) sm[(j + L * q) * M + k] = z[q];
+    }
+  }
+  if constexpr (!LAST) __syncthreads();
+}
+
+template <class T, int N, int L>
+__device__ __forceinline__ void reg_rest(cpx<T> (&v)[8], cpx<T>* sm, const cpx<T>* tw, int sign, int t) {
+  if constexpr (L < N) {
+    reg_stage<T, N, L, 8, false>(v, sm, tw, sign, t);
+    reg_rest<T, N, L * 8>(v, sm, tw, sign, t);
+  }
+}
+
+// Whole transform of one line: thread t (0 <= t < N/8) holds x[t + NT c] in
+// v[c] on entry and X[t + NT q] in v[q] on exit; sm is the line's N-element
+// shared buffer (its contents are undefined afterwards); tw[m] = exp(-2 pi i m/N).
+template <class T, int N>
+__device__ __forceinline__ void reg_fft(cpx<T> (&v)[8], cpx<T>* sm, const cpx<T>* tw, int sign, int t) {
+  using S = RegFftShape<N>;
+  reg_stage<T, N, 1, S::P0, true>(v, sm, tw, sign, t);
+  reg_rest<T, N, S::P0>(v, sm, tw, sign, t);
+}
+
+// ---------------------------------------------------------------------------
+// Forward real FFT along x, two real lines per complex transform (as
+// k_rfft_x in spectral.cuh): a CTA of NT * LPC threads owns LPC line pairs.
+// smem: LPC * N complex.
+// ---------------------------------------------------------------------------
+template <class T, int N, class Pro>
+__global__ void __launch_bounds__(1024) k_rfft_x_reg(Pro pro, cpx<T>* __restrict__ out, int nlines, int pitch,
+                                                     const cpx<T>* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int NT = N / 8;
+  const int m = threadIdx.x / NT, t = threadIdx.x % NT;
+  const int lpc = blockDim.x / NT;
+  const int l0 = 2 * (blockIdx.x * lpc + m), l1 = l0 + 1;
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw) + (size_t)m * N;
+  cpx<T> v[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int x = t + NT * c;
+    v[c] = mk<T>(l0 < nlines ? pro(l0, x) : (T)0, l1 < nlines ? pro(l1, x) : (T)0);
+  }
+  reg_fft<T, N>(v, sm, tw, -1, t);
+  __syncthreads();  // the last stage's reads of sm are done
+#pragma unroll
+  for (int q = 0; q < 8; ++q) sm[t + NT * q] = v[q];
+  __syncthreads();
+  if (l0 >= nlines) return;
+  for (int k = t; k <= N / 2; k += NT) {
+    const cpx<T> zk = sm[k];
+    const cpx<T> zn = conjg(sm[k == 0 ? 0 : N - k]);
+    out[(size_t)l0 * pitch + k] = scal(zk + zn, (T)0.5);
+    const cpx<T> dd = zk - zn;  // B = -i/2 dd
+    if (l1 < nlines) out[(size_t)l1 * pitch + k] = mk(dd.im * (T)0.5, -dd.re * (T)0.5);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Inverse real FFT along x (as k_irfft_x): the input A + iB of each line pair
+// is built in registers from the two half spectra, the output goes from
+// registers to the epilogue.  An epilogue with kPre has its two arrays copied
+// into shared memory by cp.async before the transform (smem after the line
+// buffers: LPC * 4 * N elements of T).
+// ---------------------------------------------------------------------------
+template <class T, int N, class Epi>
+__global__ void __launch_bounds__(1024) k_irfft_x_reg(const cpx<T>* __restrict__ in, Epi epi, int nlines, int pitch,
+                                                      const cpx<T>* __restrict__ tw, T scale) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int NT = N / 8;
+  const int m = threadIdx.x / NT, t = threadIdx.x % NT;
+  const int lpc = blockDim.x / NT;
+  const int l0 = 2 * (blockIdx.x * lpc + m), l1 = l0 + 1;
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw) + (size_t)m * N;
+  T* pre = reinterpret_cast<T*>(reinterpret_cast<cpx<T>*>(smraw) + (size_t)lpc * N) + (size_t)m * 4 * N;
+  if constexpr (Epi::kPre) {
+#pragma unroll
+    for (int li = 0; li < 2; ++li) {
+      const int l = l0 + li;
+      if (l >= nlines) continue;
+      const T* s0 = epi.pre0() + (size_t)l * epi.pre_n();
+      const T* s1 = epi.pre1() + (size_t)l * epi.pre_n();
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int x = t + NT * q;
+        cp_async_elem(pre + (size_t)(2 * li) * N + x, s0 + x);
+        cp_async_elem(pre + (size_t)(2 * li + 1) * N + x, s1 + x);
+      }
+    }
+    cp_async_commit();
+  }
+  cpx<T> v[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int x = t + NT * c;
+    const int k = x <= N / 2 ? x : N - x;
+    cpx<T> A = mk<T>(0, 0), B = mk<T>(0, 0);
+    if (l0 < nlines) A = in[(size_t)l0 * pitch + k];
+    if (l1 < nlines) B = in[(size_t)l1 * pitch + k];
+    if (x > N / 2) {
+      A = conjg(A);
+      B = conjg(B);
+    }
+    v[c] = mk(A.re - B.im, A.im + B.re);  // A + i B
+  }
+  reg_fft<T, N>(v, sm, tw, +1, t);
+  if constexpr (Epi::kPre) cp_async_wait_all();  // this thread's own copies
+  if (l0 >= nlines) return;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int x = t + NT * q;
+    if constexpr (Epi::kPre) {
+      epi.apply(l0, x, v[q].re * scale, pre[x], pre[N + x]);
+      if (l1 < nlines) epi.apply(l1, x, v[q].im * scale, pre[2 * N + x], pre[3 * N + x]);
+    } else {
+      epi(l0, x, v[q].re * scale);
+      if (l1 < nlines) epi(l1, x, v[q].im * scale);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Complex FFT along y, in place (as k_fft_y): a CTA of NT * TXC threads owns
+// TXC consecutive kx columns of one z level; thread (t, col) = threadIdx
+// (t * TXC + col), so each warp reads rows of TXC contiguous values.
+// smem: TXC * N complex.
+// ---------------------------------------------------------------------------
+template <class T, int N>
+__global__ void __launch_bounds__(1024) k_fft_y_reg(cpx<T>* __restrict__ data, int pitch, int ncol,
+                                                    const cpx<T>* __restrict__ tw, int sign) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int NT = N / 8;
+  const int txc = blockDim.x / NT;
+  const int col = threadIdx.x % txc, t = threadIdx.x / txc;
+  const int c = blockIdx.x * txc + col;
+  const bool in = c < ncol;
+  cpx<T>* base = data + (size_t)blockIdx.y * N * pitch + c;
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw) + (size_t)col * N;
+  cpx<T> v[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = in ? base[(size_t)(t + NT * q) * pitch] : mk<T>(0, 0);
+  reg_fft<T, N>(v, sm, tw, sign, t);
+  if (!in) return;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) base[(size_t)(t + NT * q) * pitch] = v[q];
+}
+
+}  // namespace pf
+
+namespace pf {
+
+// sizes with a register-resident kernel
+__host__ __device__ inline bool reg_fft_size(int n) { return n >= 64 && n <= 1024 && (n & (n - 1)) == 0; }
+
+// call f(std::integral_constant<int, N>{}) for the runtime size n (one of reg_fft_size)
+template <class F>
+inline void reg_fft_dispatch(int n, F&& f) {
+  switch (n) {
+    case 64: f(std::integral_constant<int, 64>{}); break;
+    case 128: f(std::integral_constant<int, 128>{}); break;
+    case 256: f(std::integral_constant<int, 256>{}); break;
+    case 512: f(std::integral_constant<int, 512>{}); break;
+    default: f(std::integral_constant<int, 1024>{}); break;
+  }
+}
+
+}  // namespace pf

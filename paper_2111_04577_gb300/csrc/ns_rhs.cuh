@@ -244,3 +244,21 @@ __global__ void __launch_bounds__(256, MINB) k_ns_rhs_v2(const __grid_constant__
 }
 
 }  // namespace pf
+
+namespace pf {
+
+// The same rows, but each CTA walks kz consecutive z rows at one (j): the rows
+// it has just read are the z neighbours of the next, so they come from L1.
+template <class T, int DIM, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_ns_rhs_v2z(const __grid_constant__ NsIn<T> a, const Dims d,
+                                                          const PhysT<T> q, T* __restrict__ ru, T* __restrict__ rv,
+                                                          T* __restrict__ rw, const int have_tau, const int kz) {
+  const int j = blockIdx.x % d.ny, kc = blockIdx.x / d.ny;
+  for (int kk = 0; kk < kz; ++kk) {
+    const int k = kc * kz + kk;
+    if (k >= d.nz) break;
+    k_ns_rhs_v2_b<T, DIM>(a, d, q, ru, rv, rw, have_tau, make_int3(k * d.ny + j, blockIdx.y, 0), nullptr);
+  }
+}
+
+}  // namespace pf

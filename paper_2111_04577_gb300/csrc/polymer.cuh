@@ -300,16 +300,58 @@ __device__ __forceinline__ void polymer_cell(const PolyIn<T>& P, const Dims& d, 
 #pragma unroll
   for (int cq = 0; cq < NC; ++cq) P.out[cq][id] = newth[cq];
   if (STAGE == 2) {
-    // tau = (1 + phi)/2 (mu_p/lambda_H) (R e^theta R^T - I)
+    // tau = (1 + phi)/2 (mu_p/lambda_H) (W e^theta W^T - I), W the eigenvectors of
+    // Theta^{n+1}.  Theta^{n+1} differs from the stage's Theta by O(dt), so in 3D
+    // it is first rotated into that Theta's eigenbasis R (R^T Theta^{n+1} R is
+    // nearly diagonal and Jacobi converges in about a sweep); W = R V.
+    if constexpr (N == 3) {
+      T A[N][N], B[N][N];
 #pragma unroll
-    for (int a = 0; a < N; ++a) dg[a] = newth[comp_of<N>(a, a)];
-    if (N == 2) of[0] = newth[comp_of<N>(0, 1)];
-    else {
+      for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int b = 0; b < N; ++b) A[a][b] = newth[comp_of<N>(a, b)];
+#pragma unroll
+      for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int b = 0; b < N; ++b) {
+          T sab = 0;
+#pragma unroll
+          for (int c = 0; c < N; ++c) sab += A[a][c] * R[c][b];
+          B[a][b] = sab;  // Theta^{n+1} R
+        }
+      auto rot = [&](int a, int b) {  // (R^T Theta^{n+1} R)_ab
+        T sab = 0;
+#pragma unroll
+        for (int c = 0; c < N; ++c) sab += R[c][a] * B[c][b];
+        return sab;
+      };
+      dg[0] = rot(0, 0);
+      dg[1] = rot(1, 1);
+      dg[2] = rot(2, 2);
+      of[0] = rot(0, 1);
+      of[1] = rot(0, 2);
+      of[2] = rot(1, 2);
+      T V[N][N];
+      eig_sym<T, N>(dg, of, V);
+#pragma unroll
+      for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int b = 0; b < N; ++b) {
+          T sab = 0;
+#pragma unroll
+          for (int c = 0; c < N; ++c) sab += R[a][c] * V[c][b];
+          B[a][b] = sab;
+        }
+#pragma unroll
+      for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int b = 0; b < N; ++b) R[a][b] = B[a][b];
+    } else {
+#pragma unroll
+      for (int a = 0; a < N; ++a) dg[a] = newth[comp_of<N>(a, a)];
       of[0] = newth[comp_of<N>(0, 1)];
-      of[1] = newth[comp_of<N>(0, 2)];
-      of[2] = newth[comp_of<N>(1, 2)];
+      eig_sym<T, N>(dg, of, R);
     }
-    eig_sym<T, N>(dg, of, R);
     T ex[N];
 #pragma unroll
     for (int c = 0; c < N; ++c) ex[c] = fexp<T>(dg[c]);

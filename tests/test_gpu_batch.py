@@ -85,3 +85,26 @@ def test_batch_fp64_matches_oracle():
         assert rel(bt.get(b, "u").reshape(nz, ny, nx), r.vel[0]) < 1e-10, b
         assert rel(bt.get(b, "w").reshape(nz + 1, ny, nx), r.vel[2]) < 1e-10, b
     bt.close()
+
+
+def test_batch_adjoint_matches_single_problem_adjoint():
+    """pf_batch_adjoint on each problem equals pf_adjoint on a standalone
+    context holding the same state (the same kernels: bitwise in FP64)."""
+    ws = problems()[:3]
+    bt = binding.Batch([w.grid for w in ws], [w.params for w in ws], binding.PF_FP64)
+    for b, w in enumerate(ws):
+        vel = wl.random_velocity(w.grid, 20 + b, 0.2)
+        phi0 = wl.initial_phi(w)
+        bt.set(b, "phi", phi0)
+        bt.set(b, "phi_old", phi0)
+        for name, a in zip(("u", "w"), (vel[0], vel[2])):
+            bt.set(b, name, a)
+            bt.set(b, name + "_old", a)
+        s = binding.Solver(w.grid, w.params, binding.PF_FP64)
+        s.load_state(phi0, vel)
+        ref = s.adjoint(6, 2, binding.PF_OBJ_WETTED)
+        got = bt.adjoint(b, 6, 2, binding.PF_OBJ_WETTED)
+        assert got[0] == ref[0] and got[1] == ref[1] and got[2] == ref[2]
+        assert np.array_equal(got[3], ref[3])
+        s.close()
+    bt.close()

@@ -44,6 +44,8 @@ CH_CASES = [
     (3, 16, 8, 1), (3, 12, 6, 1), (3, 10, 4, 0),
     # deep z: several 32-row solve segments with a ragged last one
     (2, 12, 40, 1), (2, 16, 48, 0), (3, 8, 20, 1),
+    # power-of-two lines >= 64: the register-resident transforms
+    (3, 32, 8, 1), (2, 64, 8, 1),
 ]
 
 
@@ -89,6 +91,8 @@ FULL_CASES = [
     (3, 12, 6, 1, dict(ratio_rho=1000.0, ratio_mu=50.0, theta_deg=45.0)),
     # deep z: coarse u/p 40 rows, w 39 faces, fine 80 rows
     (2, 16, 40, 1, dict(ratio_rho=100.0, ratio_mu=10.0, theta_deg=70.0, Wi=0.5, beta=0.5)),
+    # coarse and fine lines of 64 and 128 points (register-resident transforms)
+    (3, 64, 4, 1, dict(ratio_rho=1000.0, ratio_mu=20.0, theta_deg=80.0, Wi=1.0, beta=0.3)),
 ]
 
 
