@@ -70,18 +70,11 @@ TRAFFIC = {
     "ch_rhs": (14.46, ["paper_2111_04577_gb300/csrc/ch_march.cuh", "paper_2111_04577_gb300/csrc/ch.cuh"], "4a4bc68b8c628481"),
     "ns_rhs": (16.664, ["paper_2111_04577_gb300/csrc/ns_rhs.cuh", "paper_2111_04577_gb300/csrc/ns.cuh"], "6eea63dfff4645fc"),
     "polymer_stage2": (13.718, ["paper_2111_04577_gb300/csrc/polymer.cuh"], "e47ead9d9a095597"),
-    "fft_y_fine": (9.235, ["paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "cf9ebcc27278b7f6"),
-    "fft_y_coarse": (4.063, ["paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "cf9ebcc27278b7f6"),
     "ch_G_restrict": (6.845, ["paper_2111_04577_gb300/csrc/ch_march.cuh", "paper_2111_04577_gb300/csrc/ch.cuh"], "4a4bc68b8c628481"),
     "polymer_stage1": (7.077, ["paper_2111_04577_gb300/csrc/polymer.cuh"], "e47ead9d9a095597"),
-    "ch_ifftx_finish": (14.164, ["paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "cf9ebcc27278b7f6"),
-    "rfft_x_fine": (5.217, ["paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "cf9ebcc27278b7f6"),
     "zsolve_pair": (4.705, ["paper_2111_04577_gb300/csrc/zsolve_seg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh"], "141a00fbc127012a"),
-    "rfft_x_coarse": (1.998, ["paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "cf9ebcc27278b7f6"),
-    "irfft_x_coarse": (2.029, ["paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "cf9ebcc27278b7f6"),
     "zsolve": (2.027, ["paper_2111_04577_gb300/csrc/zsolve_seg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh"], "141a00fbc127012a"),
     "correct": (2.485, ["paper_2111_04577_gb300/csrc/ns.cuh"], "d1c3da3fba12bb38"),
-    "div": (1.485, ["paper_2111_04577_gb300/csrc/ns.cuh"], "d1c3da3fba12bb38"),
 }
 
 
@@ -141,12 +134,12 @@ def alg_bytes(grid, esize, visco=True):
         "ch_ifftx_finish": 2 * E * sf + 3 * E * nf,
         "ch_G_restrict": E * nf + (11 if d3 else 7) * E * nc,
         "ns_rhs": (2 * (nvel + 1) + (2 * ncomp if visco else 0) + (11 if d3 else 7) + nvel) * E * nc,
-        "rfft_x_coarse": nsolve * (E * nc + 2 * E * sc),
+        "rfft_x_coarse": nvel * (E * nc + 2 * E * sc),
+        "div_rfft_x_coarse": nvel * E * nc + 2 * E * sc,  # reads u~, v~, w~: the Poisson right side formed in place
         "fft_y_coarse": (2 * nsolve * 2 * (2 * E * sc)) if d3 else 0,
         "zsolve": nsolve * 2 * (2 * E * sc),
         "zero_mode": 0,
         "irfft_x_coarse": nsolve * (2 * E * sc + E * nc),
-        "div": (nvel + 1) * E * nc,
         "correct": (2 * nvel + 3) * E * nc,
         "polymer_stage1": (2 * ncomp + nvel) * E * nc,
         "polymer_stage2": (4 * ncomp + nvel + 1) * E * nc,

@@ -18,7 +18,7 @@ from . import workloads as wl
 
 KNOBS = {
     0: ("xfft_pairs", [1, 2, 4, 8], ("rfft_x_fine", "ch_ifftx_finish", "rfft_x_coarse", "irfft_x_coarse")),
-    1: ("yfft_cols", [4, 8, 16], ("fft_y_fine", "fft_y_coarse")),
+    1: ("yfft_cols", [8, 16, 32], ("fft_y_fine", "fft_y_coarse")),
     2: ("zsolve_cols", [16, 32], ("zsolve_pair", "zsolve")),
     3: ("row_block", [64, 128, 256], ("ns_rhs", "div", "correct", "polymer_stage1", "polymer_stage2")),
     4: ("ch_zchunk", [16, 32, 64], ("ch_rhs",)),

@@ -320,7 +320,7 @@ __device__ __forceinline__ Quad<T> quad_sums(const T* p, int o, int sx) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(GrMarch::NT, 2) k_ch_G_restrict_march(const T* __restrict__ phi,
+__global__ void __launch_bounds__(GrMarch::NT, 3) k_ch_G_restrict_march(const T* __restrict__ phi,
                                                                         const double* __restrict__ gwall,
                                                                         Restricted<T> out, const Dims d,
                                                                         const PhysT<T> q, const int nkc) {

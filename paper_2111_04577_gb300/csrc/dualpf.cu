@@ -96,6 +96,28 @@ struct ArrPro {
   int n;
   __device__ __forceinline__ T operator()(int line, int x) const { return a[(size_t)line * n + x]; }
 };
+// The Poisson right side coef * div(u~) of Eq. NS37 produced on the fly for the
+// pressure solve's x transform (same arithmetic as k_div, no stored array).
+template <class T>
+struct DivPro {
+  static constexpr const char* name = "div_rfft_x_coarse";
+  const T *ut, *vt, *wt;
+  Dims d;
+  T coef, iD;
+  __device__ __forceinline__ T operator()(int line, int i) const {
+    const int k = line / d.ny, j = line - k * d.ny;
+    const size_t plane = (size_t)d.nx * d.ny;
+    const size_t id = (size_t)line * d.nx + i;
+    const size_t rowb = id - i;
+    T dv = (ut[rowb + (i + 1 == d.nx ? 0 : i + 1)] - ut[id]) * iD;
+    if (d.dim == 3) dv += (vt[((size_t)k * d.ny + (j + 1 == d.ny ? 0 : j + 1)) * d.nx + i] - vt[id]) * iD;
+    const T wtop = (k < d.nz - 1) ? wt[id] : (T)0;   // face k+1 -> row k
+    const T wbot = (k > 0) ? wt[id - plane] : (T)0;  // face k   -> row k-1
+    dv += (wtop - wbot) * iD;
+    return coef * dv;
+  }
+};
+
 template <class T>
 struct FineArrPro {
   static constexpr const char* name = "rfft_x_fine";
@@ -300,6 +322,55 @@ struct Impl : ImplBase {
   ~Impl() override {
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
     for (auto e : mark_ev) cudaEventDestroy(e);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (st2) cudaStreamDestroy(st2);
+  }
+
+  // The polymer update of step n needs u^{n+1}, Theta and the restricted phi
+  // only, so pf_step runs it during step n+1's CH transform chain on a second
+  // stream (joined before the restriction overwrites the restricted phi); the
+  // last one of a call is run at the end of the call.  Every update sees the
+  // same inputs as in the sequential order.
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool poly_pending = false;  // the update for the velocity in parity fc is owed
+  void ensure_side_stream() {
+    if (st2) return;
+    PF_CUDA_TRY(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
+    PF_CUDA_TRY(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+    PF_CUDA_TRY(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+  }
+  // both LCR stages for the velocity in parity fv (tau written to parity fv)
+  void launch_polymer(int fv, cudaStream_t s) {
+    PolyIn<T> P{};
+    P.u = u[fv];
+    P.v = v[fv];
+    P.w = w[fv];
+    P.phic = rs.phic;
+    for (int c = 0; c < ncomp; ++c) {
+      P.th[c] = theta[c];
+      P.out[c] = theta1[c];
+    }
+    mark("polymer_stage1");
+    const RowLaunch lp = rows(d.ny * d.nz, d.nx, 128);
+    if (d.dim == 2) k_polymer<T, 2, 1><<<lp.grid, lp.block, 0, s>>>(P, d, q);
+    else k_polymer<T, 3, 1><<<lp.grid, lp.block, 0, s>>>(P, d, q);
+    for (int c = 0; c < ncomp; ++c) {
+      P.th[c] = theta1[c];
+      P.base[c] = theta[c];
+      P.out[c] = theta[c];
+      P.tau[c] = tau[fv][c];
+    }
+    mark("polymer_stage2");
+    if (d.dim == 2) k_polymer<T, 2, 2><<<lp.grid, lp.block, 0, s>>>(P, d, q);
+    else k_polymer<T, 3, 2><<<lp.grid, lp.block, 0, s>>>(P, d, q);
+  }
+  void flush_polymer() {
+    if (!poly_pending) return;
+    poly_pending = false;
+    launch_polymer(fc, st);
+    check_launch();
   }
 
   cpx<T>* twiddles(int n) {
@@ -329,6 +400,7 @@ struct Impl : ImplBase {
     PF_CUDA_TRY(cudaFuncSetAttribute(k_zsolve<T, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_zsolve_seg<T, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_rfft_x<T, ArrPro<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PF_CUDA_TRY(cudaFuncSetAttribute(k_rfft_x<T, DivPro<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_rfft_x<T, FineArrPro<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
@@ -340,14 +412,16 @@ struct Impl : ImplBase {
       PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march4<0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     }
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict_march<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PF_CUDA_TRY(cudaFuncSetAttribute(k_zero_mode_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     for (int n : {64, 128, 256, 512, 1024})
       reg_fft_dispatch(n, [&](auto NN) {
         constexpr int N = decltype(NN)::value;
         PF_CUDA_TRY(cudaFuncSetAttribute(k_rfft_x_reg<T, N, FineArrPro<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
         PF_CUDA_TRY(cudaFuncSetAttribute(k_rfft_x_reg<T, N, ArrPro<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+        PF_CUDA_TRY(cudaFuncSetAttribute(k_rfft_x_reg<T, N, DivPro<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
         PF_CUDA_TRY(cudaFuncSetAttribute(k_irfft_x_reg<T, N, ChFinish<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
         PF_CUDA_TRY(cudaFuncSetAttribute(k_irfft_x_reg<T, N, ArrEpi<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
-        PF_CUDA_TRY(cudaFuncSetAttribute(k_fft_y_reg<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+        PF_CUDA_TRY(cudaFuncSetAttribute(k_fft_y_reg<T, N, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
       });
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict<T, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict<T, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
@@ -381,7 +455,7 @@ struct Impl : ImplBase {
   void rfft_x(Pro pro, cpx<T>* out, int n, int nlines, int pitch, const FftPlan& pl, const cpx<T>* tw) {
     if (reg_fft_size(n)) {
       const int lpc = reg_lpc(n), pairs = (nlines + 1) / 2;
-      const size_t sm = (size_t)lpc * n * sizeof(cpx<T>);
+      const size_t sm = (size_t)lpc * fft_pad_len(n) * sizeof(cpx<T>);
       mark(Pro::name);
       reg_fft_dispatch(n, [&](auto NN) {
         constexpr int N = decltype(NN)::value;
@@ -417,14 +491,15 @@ struct Impl : ImplBase {
   }
   void fft_y(cpx<T>* data, int ny, int pitch, int ncol, int levels, const FftPlan& pl, const cpx<T>* tw, int sign) {
     if (reg_fft_size(ny)) {
-      const int nt = ny / 8;
-      const int want = tune[PF_TUNE_YFFT_COLS] > 0 ? tune[PF_TUNE_YFFT_COLS] : 8;
-      const int txc = std::max(1, std::min(want, 1024 / nt));
-      const size_t sm = (size_t)txc * ny * sizeof(cpx<T>);
+      constexpr int E = 16;  // elements a thread: 16-column tiles read 128-byte rows
+      const int nt = ny / E;
+      const int want = tune[PF_TUNE_YFFT_COLS] > 0 ? tune[PF_TUNE_YFFT_COLS] : 16;
+      const int txc = std::max(1, std::min(want, 512 / nt));
+      const size_t sm = (size_t)txc * fft_pad_len(ny) * sizeof(cpx<T>);
       mark(ny == d.fny && levels == d.fnz && d.r > 1 ? "fft_y_fine" : "fft_y_coarse");
       reg_fft_dispatch(ny, [&](auto NN) {
         constexpr int N = decltype(NN)::value;
-        k_fft_y_reg<T, N><<<dim3((ncol + txc - 1) / txc, levels), txc * (N / 8), sm, st>>>(data, pitch, ncol, tw, sign);
+        k_fft_y_reg<T, N, E><<<dim3((ncol + txc - 1) / txc, levels), txc * (N / E), sm, st>>>(data, pitch, ncol, tw, sign);
       });
       return;
     }
@@ -464,14 +539,21 @@ struct Impl : ImplBase {
     }
     if (poisson) {
       mark("zero_mode");
-      k_zero_mode<T><<<1, 32, 0, st>>>(data, rows, ny, pitch, h2, scale, zwork);
+      if ((size_t)2 * rows * sizeof(double) <= (size_t)kMaxSmem)
+        k_zero_mode_smem<T><<<1, 256, 2 * rows * sizeof(double), st>>>(data, rows, ny, pitch, h2, scale);
+      else
+        k_zero_mode<T><<<1, 32, 0, st>>>(data, rows, ny, pitch, h2, scale, zwork);
     }
   }
 
   // one transform solve on the coarse mesh: rhs (real, lines of nx) -> out
   void coarse_solve(const T* rhs, T* out, cpx<T>* sp, int rows, int bc, double shift, bool poisson) {
+    coarse_solve_pro(ArrPro<T>{rhs, d.nx}, out, sp, rows, bc, shift, poisson);
+  }
+  template <class Pro>
+  void coarse_solve_pro(Pro pro, T* out, cpx<T>* sp, int rows, int bc, double shift, bool poisson) {
     const int nlines = d.ny * rows;
-    rfft_x(ArrPro<T>{rhs, d.nx}, sp, d.nx, nlines, pC, plCx, twCx);
+    rfft_x(pro, sp, d.nx, nlines, pC, plCx, twCx);
     if (d.dim == 3) fft_y(sp, d.ny, pC, d.nx / 2 + 1, rows, plCy, twCy, -1);
     zsolve(sp, rows, d.ny, pC, d.nx / 2 + 1, eCx, eCy, bc, d.dx * d.dx, shift, shift, false,
            1.0 / ((double)d.nx * d.ny), poisson);
@@ -479,8 +561,16 @@ struct Impl : ImplBase {
     irfft_x(sp, ArrEpi<T>{out, d.nx}, d.nx, nlines, pC, plCx, twCx, (T)1);
   }
 
-  void launch_step(int flags) {
+  // pend_in: first run the owed polymer update (parity fc) on the side stream,
+  // joined before the restriction; defer: leave this step's update owed.
+  void launch_step(int flags, bool pend_in = false, bool defer = false) {
     const int po = pc ^ 1, fo = fc ^ 1;
+    if (pend_in) {
+      PF_CUDA_TRY(cudaEventRecord(ev_fork, st));
+      PF_CUDA_TRY(cudaStreamWaitEvent(st2, ev_fork, 0));
+      launch_polymer(fc, st2);
+      PF_CUDA_TRY(cudaEventRecord(ev_join, st2));
+    }
     // ---- Cahn-Hilliard on the fine mesh ----
     FineView<T> fv{phi[pc], phi[po]};
     const CoarseVel<T> vel{u[fc], u[fo], v[fc], v[fo], w[fc], w[fo]};
@@ -525,6 +615,7 @@ struct Impl : ImplBase {
     if (d.dim == 3) fft_y(spF, d.fny, pF, d.fnx / 2 + 1, d.fnz, plFy, twFy, +1);
     irfft_x(spF, ChFinish<T>{phi[pc], phi[po], d.fnx}, d.fnx, nlf, pF, plFx, twFx, (T)1);
     if (flags & PF_STEP_CH_ONLY) return;
+    if (pend_in) PF_CUDA_TRY(cudaStreamWaitEvent(st, ev_join, 0));  // the update read the restricted phi
     // ---- chemical potential and restriction to the coarse mesh ----
     mark("ch_G_restrict");
     if (d.dim == 2) {
@@ -587,37 +678,14 @@ struct Impl : ImplBase {
     coarse_solve(ru, u[fo], spU, d.nz, Z_DIRICH, kk, false);
     if (d.dim == 3) coarse_solve(rv, v[fo], spV, d.nz, Z_DIRICH, kk, false);
     coarse_solve(rw, wt, spW, d.nz - 1, Z_FACES, kk, false);
-    mark("div");
-    k_div<T><<<lc.grid, lc.block, 0, st>>>(u[fo], v[fo], wt, dv, d, (T)(p.gamma0 * p.rho0 / p.dt));
-    coarse_solve(dv, pp, spP, d.nz, Z_NEUMANN, 0.0, true);
+    // pressure Poisson (Eq. NS37), its right side formed inside the first transform
+    coarse_solve_pro(DivPro<T>{u[fo], v[fo], wt, d, (T)(p.gamma0 * p.rho0 / p.dt), (T)(1.0 / d.dx)}, pp, spP, d.nz,
+                     Z_NEUMANN, 0.0, true);
     mark("correct");
     k_correct<T><<<lw.grid, lw.block, 0, st>>>(u[fo], v[fo], wt, w[fo], pp, pr[fc], pr[fo], d,
                                                   (T)(p.dt / (p.gamma0 * p.rho0)));
     // ---- polymer ----
-    if (p.visco) {
-      PolyIn<T> P{};
-      P.u = u[fo];
-      P.v = v[fo];
-      P.w = w[fo];
-      P.phic = rs.phic;
-      for (int c = 0; c < ncomp; ++c) {
-        P.th[c] = theta[c];
-        P.out[c] = theta1[c];
-      }
-      mark("polymer_stage1");
-      const RowLaunch lp = rows(d.ny * d.nz, d.nx, 128);
-      if (d.dim == 2) k_polymer<T, 2, 1><<<lp.grid, lp.block, 0, st>>>(P, d, q);
-      else k_polymer<T, 3, 1><<<lp.grid, lp.block, 0, st>>>(P, d, q);
-      for (int c = 0; c < ncomp; ++c) {
-        P.th[c] = theta1[c];
-        P.base[c] = theta[c];
-        P.out[c] = theta[c];
-        P.tau[c] = tau[fo][c];
-      }
-      mark("polymer_stage2");
-      if (d.dim == 2) k_polymer<T, 2, 2><<<lp.grid, lp.block, 0, st>>>(P, d, q);
-      else k_polymer<T, 3, 2><<<lp.grid, lp.block, 0, st>>>(P, d, q);
-    }
+    if (p.visco && !defer) launch_polymer(fo, st);
   }
 
   // ------------------------------------------------------------------ API
@@ -704,6 +772,7 @@ struct Impl : ImplBase {
   }
 
   void set_field(int f, const void* src, size_t bytes, int on_dev) override {
+    flush_polymer();
     if (f == PF_G) throw ApiError(PF_ERR_ARG, "PF_G is read-only");
     copy_field(f, src, bytes, on_dev);
     int twin = -1;
@@ -718,6 +787,7 @@ struct Impl : ImplBase {
   }
 
   void get_field(int f, void* dst, size_t bytes, int on_dev) override {
+    flush_polymer();
     size_t cnt, eb;
     field_info(f, &cnt, &eb);
     if (f == PF_G) {  // chemical potential of phi^n, formed on request
@@ -739,18 +809,18 @@ struct Impl : ImplBase {
     if (e != cudaSuccess) throw CudaError(e, "kernel launch", __FILE__, __LINE__);
   }
 
-  void run_one(int flags) {
+  void run_one(int flags, bool pend_in, bool defer) {
     if (flags & PF_STEP_NO_GRAPH) {
-      launch_step(flags);
+      launch_step(flags, pend_in, defer);
       check_launch();
       return;
     }
-    auto key = std::make_tuple(pc, fc, flags & PF_STEP_CH_ONLY);
+    auto key = std::make_tuple(pc, fc, (flags & PF_STEP_CH_ONLY) | (pend_in ? 2 : 0) | (defer ? 4 : 0));
     auto it = graphs.find(key);
     if (it == graphs.end()) {
       cudaGraph_t gr;
       PF_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-      launch_step(flags);
+      launch_step(flags, pend_in, defer);
       cudaError_t le = cudaGetLastError();
       cudaError_t ce = cudaStreamEndCapture(st, &gr);
       if (le != cudaSuccess) throw CudaError(le, "kernel launch during capture", __FILE__, __LINE__);
@@ -896,6 +966,7 @@ struct Impl : ImplBase {
   // dphi0 (optional) receives dJ/d phi^0.  Checkpoints every K steps; each
   // segment is recomputed forward before its reverse sweep.
   void adjoint(int nsteps, int K, int which, double out[3], void* dphi0, int on_dev) override {
+    flush_polymer();
     if (!have_params) throw ApiError(PF_ERR_ARG, "pf_set_params must precede pf_adjoint");
     if (nsteps < 1 || K < 1) throw ApiError(PF_ERR_ARG, "nsteps and ckpt_every must be >= 1");
     if (which != 0 && which != 1) throw ApiError(PF_ERR_ARG, "objective must be PF_OBJ_WETTED or PF_OBJ_CENTROID_Z");
@@ -957,6 +1028,7 @@ struct Impl : ImplBase {
   void profile(int nsteps, int flags, std::vector<std::string>& names, std::vector<double>& ms,
                std::vector<int>& counts, int& per_step) override {
     if (!have_params) throw ApiError(PF_ERR_ARG, "pf_set_params must precede pf_profile");
+    flush_polymer();
     std::map<std::string, double> acc;
     std::map<std::string, int> cnt;
     std::vector<std::string> order;
@@ -1023,11 +1095,17 @@ struct Impl : ImplBase {
   void step(int nsteps, int flags) override {
     if (!have_params) throw ApiError(PF_ERR_ARG, "pf_set_params must precede pf_step");
     if (nsteps < 0) throw ApiError(PF_ERR_ARG, "nsteps < 0");
+    flush_polymer();  // owed by a call that stopped early
+    const bool visco_steps = p.visco && !(flags & PF_STEP_CH_ONLY);
+    if (visco_steps) ensure_side_stream();
     for (int s = 0; s < nsteps; ++s) {
-      run_one(flags);
+      const bool pend_in = visco_steps && poly_pending;
+      run_one(flags, pend_in, visco_steps);
+      poly_pending = visco_steps;
       pc ^= 1;
       if (!(flags & PF_STEP_CH_ONLY)) fc ^= 1;
       ++steps_done;
+      if (s == nsteps - 1) flush_polymer();
       if (steps_done % 50 == 0 || s == nsteps - 1) {
         const double m = mass_check();
         if (!std::isfinite(m)) throw ApiError(PF_ERR_NONFINITE, "phi mass is not finite after step " + std::to_string(steps_done));

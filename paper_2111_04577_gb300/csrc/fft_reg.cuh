@@ -5,16 +5,16 @@
 // sub-transforms of length L into length L*P; with M = N/(L*P), butterfly
 // bf = (j, k), j = bf / M, k = bf % M, gathers z_c = w_N^{c j M} Y[j M P + k + c M]
 // and writes the length-P DFT of z to Y'[(j + L q) M + k].  Here a line is
-// owned by NT = N/8 threads, each holding 8 elements in registers, and the
+// owned by NT = N/E threads, each holding E (8 or 16) elements in registers, and the
 // small radix (2 or 4, when log2 N is not a multiple of 3) goes first, the
 // radix-8 stages after it:
-//  - on entry thread t holds x[t + NT c], c = 0..7, which is exactly the input
+//  - on entry thread t holds x[t + NT c], c = 0..E-1, which is exactly the input
 //    of the first stage's butterflies (bf = t + NT i, j = 0), so the first
 //    stage reads registers loaded straight from global memory;
 //  - stages exchange through one shared buffer of N complex per line, in place
 //    (every thread reads its inputs, barrier, then writes);
-//  - the last (radix-8) stage has M = 1 and j = t, so its outputs
-//    Y'[t + NT q] stay in registers in natural order for the epilogue.
+//  - the last (radix-8) stage has M = 1, so its outputs Y'[t + NT c] stay in
+//    registers in natural order for the epilogue.
 // Two shared-memory round trips for N = 512 instead of four, and one buffer
 // instead of two.  Every thread of the CTA must call reg_fft together (the
 // stages use __syncthreads()).
@@ -37,24 +37,36 @@ struct RegFftShape {
   static_assert(N >= 64 && N <= 4096 && (N & (N - 1)) == 0, "power of two in [64, 4096]");
 };
 
+// Shared-memory slot of element i of a line: one pad element after every 8, so
+// that the strided accesses of the radix-8 stages (8t + c, 64j + k + 8c) fall
+// in distinct banks.  A line buffer holds fft_pad_len(N) elements.
+// (PAD = false: element i at slot i.)
+template <bool PAD = true>
+__host__ __device__ constexpr int fft_pad(int i) { return PAD ? i + (i >> 3) : i; }
+__host__ __device__ constexpr int fft_pad_len(int n) { return n + n / 8; }
+
 template <class T, int P>
 __device__ __forceinline__ void reg_dft(cpx<T>* z, int sign) {
   if constexpr (P == 8) dft8<T>(z, sign);
   else dft_small<T, P>(z, sign);
 }
 
-// one stage; FIRST: inputs already in registers; LAST: outputs stay in registers
-template <class T, int N, int L, int P, bool FIRST>
-__device__ __forceinline__ void reg_stage(cpx<T> (&v)[8], cpx<T>* __restrict__ sm, const cpx<T>* __restrict__ tw,
-                                          int sign, int t) {
-  constexpr int NT = N / 8, M = N / (L * P), NB = 8 / P;
+// one stage; FIRST: inputs already in registers; LAST: outputs stay in registers.
+// E elements a thread (8 or 16): NT = N/E threads a line, E/P butterflies a stage.
+// sm element i sits at sm[fft_pad(i) * ss] (ss = 1 for a line buffer of its own; the
+// y transform interleaves its columns, ss = columns per CTA, so that the
+// threads of a warp, which are consecutive columns, hit consecutive banks).
+template <class T, int N, int E, int L, int P, bool FIRST, bool PAD>
+__device__ __forceinline__ void reg_stage(cpx<T> (&v)[E], cpx<T>* __restrict__ sm, const cpx<T>* __restrict__ tw,
+                                          int sign, int t, int ss) {
+  constexpr int NT = N / E, M = N / (L * P), NB = E / P;
   constexpr bool LAST = L * P == N;
   if constexpr (!FIRST) {
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
       const int bf = t + NT * i, j = bf / M, k = bf % M;
 #pragma unroll
-      for (int c = 0; c < P; ++c) v[i + NB * c] = sm[j * M * P + k + c * M];
+      for (int c = 0; c < P; ++c) v[i + NB * c] = sm[fft_pad<PAD>(j * M * P + k + c * M) * ss];
     }
     if constexpr (!LAST) __syncthreads();  // every read of this stage before the in-place writes
   }
@@ -74,39 +86,40 @@ __device__ __forceinline__ void reg_stage(cpx<T> (&v)[8], cpx<T>* __restrict__ s
     }
     reg_dft<T, P>(z, sign);
     if constexpr (LAST) {
-      // dst = j + L q = t + NT q (M = 1, NB = 1)
+      // M = 1: dst = j + L q = t + NT (i + NB q)
 #pragma unroll
-      for (int q = 0; q < P; ++q) v[q] = z[q];
+      for (int q = 0; q < P; ++q) v[i + NB * q] = z[q];
     } else {
 #pragma unroll
-      for (int q = 0; q < P; ++q) sm[(j + L * q) * M + k] = z[q];
+      for (int q = 0; q < P; ++q) sm[fft_pad<PAD>((j + L * q) * M + k) * ss] = z[q];
     }
   }
   if constexpr (!LAST) __syncthreads();
 }
 
-template <class T, int N, int L>
-__device__ __forceinline__ void reg_rest(cpx<T> (&v)[8], cpx<T>* sm, const cpx<T>* tw, int sign, int t) {
+template <class T, int N, int E, int L, bool PAD>
+__device__ __forceinline__ void reg_rest(cpx<T> (&v)[E], cpx<T>* sm, const cpx<T>* tw, int sign, int t, int ss) {
   if constexpr (L < N) {
-    reg_stage<T, N, L, 8, false>(v, sm, tw, sign, t);
-    reg_rest<T, N, L * 8>(v, sm, tw, sign, t);
+    reg_stage<T, N, E, L, 8, false, PAD>(v, sm, tw, sign, t, ss);
+    reg_rest<T, N, E, L * 8, PAD>(v, sm, tw, sign, t, ss);
   }
 }
 
-// Whole transform of one line: thread t (0 <= t < N/8) holds x[t + NT c] in
+// Whole transform of one line: thread t (0 <= t < N/E) holds x[t + NT c] in
 // v[c] on entry and X[t + NT q] in v[q] on exit; sm is the line's N-element
-// shared buffer (its contents are undefined afterwards); tw[m] = exp(-2 pi i m/N).
-template <class T, int N>
-__device__ __forceinline__ void reg_fft(cpx<T> (&v)[8], cpx<T>* sm, const cpx<T>* tw, int sign, int t) {
+// shared buffer, element i at sm[fft_pad(i) * ss] (its contents are undefined
+// afterwards); tw[m] = exp(-2 pi i m/N).
+template <class T, int N, int E = 8, bool PAD = true>
+__device__ __forceinline__ void reg_fft(cpx<T> (&v)[E], cpx<T>* sm, const cpx<T>* tw, int sign, int t, int ss = 1) {
   using S = RegFftShape<N>;
-  reg_stage<T, N, 1, S::P0, true>(v, sm, tw, sign, t);
-  reg_rest<T, N, S::P0>(v, sm, tw, sign, t);
+  reg_stage<T, N, E, 1, S::P0, true, PAD>(v, sm, tw, sign, t, ss);
+  reg_rest<T, N, E, S::P0, PAD>(v, sm, tw, sign, t, ss);
 }
 
 // ---------------------------------------------------------------------------
 // Forward real FFT along x, two real lines per complex transform (as
 // k_rfft_x in spectral.cuh): a CTA of NT * LPC threads owns LPC line pairs.
-// smem: LPC * N complex.
+// smem: LPC * fft_pad_len(N) complex.
 // ---------------------------------------------------------------------------
 template <class T, int N, class Pro>
 __global__ void __launch_bounds__(1024) k_rfft_x_reg(Pro pro, cpx<T>* __restrict__ out, int nlines, int pitch,
@@ -116,7 +129,7 @@ __global__ void __launch_bounds__(1024) k_rfft_x_reg(Pro pro, cpx<T>* __restrict
   const int m = threadIdx.x / NT, t = threadIdx.x % NT;
   const int lpc = blockDim.x / NT;
   const int l0 = 2 * (blockIdx.x * lpc + m), l1 = l0 + 1;
-  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw) + (size_t)m * N;
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw) + (size_t)m * fft_pad_len(N);
   cpx<T> v[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
@@ -126,12 +139,12 @@ __global__ void __launch_bounds__(1024) k_rfft_x_reg(Pro pro, cpx<T>* __restrict
   reg_fft<T, N>(v, sm, tw, -1, t);
   __syncthreads();  // the last stage's reads of sm are done
 #pragma unroll
-  for (int q = 0; q < 8; ++q) sm[t + NT * q] = v[q];
+  for (int q = 0; q < 8; ++q) sm[fft_pad(t + NT * q)] = v[q];
   __syncthreads();
   if (l0 >= nlines) return;
   for (int k = t; k <= N / 2; k += NT) {
-    const cpx<T> zk = sm[k];
-    const cpx<T> zn = conjg(sm[k == 0 ? 0 : N - k]);
+    const cpx<T> zk = sm[fft_pad(k)];
+    const cpx<T> zn = conjg(sm[fft_pad(k == 0 ? 0 : N - k)]);
     out[(size_t)l0 * pitch + k] = scal(zk + zn, (T)0.5);
     const cpx<T> dd = zk - zn;  // B = -i/2 dd
     if (l1 < nlines) out[(size_t)l1 * pitch + k] = mk(dd.im * (T)0.5, -dd.re * (T)0.5);
@@ -143,7 +156,7 @@ __global__ void __launch_bounds__(1024) k_rfft_x_reg(Pro pro, cpx<T>* __restrict
 // is built in registers from the two half spectra, the output goes from
 // registers to the epilogue.  An epilogue with kPre has its two arrays copied
 // into shared memory by cp.async before the transform (smem after the line
-// buffers: LPC * 4 * N elements of T).
+// buffers: LPC * 4 * N elements of T).  Line buffers: LPC * N complex.
 // ---------------------------------------------------------------------------
 template <class T, int N, class Epi>
 __global__ void __launch_bounds__(1024) k_irfft_x_reg(const cpx<T>* __restrict__ in, Epi epi, int nlines, int pitch,
@@ -153,7 +166,7 @@ __global__ void __launch_bounds__(1024) k_irfft_x_reg(const cpx<T>* __restrict__
   const int m = threadIdx.x / NT, t = threadIdx.x % NT;
   const int lpc = blockDim.x / NT;
   const int l0 = 2 * (blockIdx.x * lpc + m), l1 = l0 + 1;
-  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw) + (size_t)m * N;
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw) + (size_t)m * N;  // unpadded line buffers
   T* pre = reinterpret_cast<T*>(reinterpret_cast<cpx<T>*>(smraw) + (size_t)lpc * N) + (size_t)m * 4 * N;
   if constexpr (Epi::kPre) {
 #pragma unroll
@@ -185,7 +198,7 @@ __global__ void __launch_bounds__(1024) k_irfft_x_reg(const cpx<T>* __restrict__
     }
     v[c] = mk(A.re - B.im, A.im + B.re);  // A + i B
   }
-  reg_fft<T, N>(v, sm, tw, +1, t);
+  reg_fft<T, N, 8, false>(v, sm, tw, +1, t);  // unpadded here: fewer registers measured faster
   if constexpr (Epi::kPre) cp_async_wait_all();  // this thread's own copies
   if (l0 >= nlines) return;
 #pragma unroll
@@ -202,29 +215,29 @@ __global__ void __launch_bounds__(1024) k_irfft_x_reg(const cpx<T>* __restrict__
 }
 
 // ---------------------------------------------------------------------------
-// Complex FFT along y, in place (as k_fft_y): a CTA of NT * TXC threads owns
-// TXC consecutive kx columns of one z level; thread (t, col) = threadIdx
-// (t * TXC + col), so each warp reads rows of TXC contiguous values.
-// smem: TXC * N complex.
+// Complex FFT along y, in place (as k_fft_y): a CTA of NT * TXC threads
+// (NT = N/E) owns TXC consecutive kx columns of one z level; thread (t, col) =
+// threadIdx (t * TXC + col), so each warp reads rows of TXC contiguous values.
+// smem: TXC * fft_pad_len(N) complex.
 // ---------------------------------------------------------------------------
-template <class T, int N>
-__global__ void __launch_bounds__(1024) k_fft_y_reg(cpx<T>* __restrict__ data, int pitch, int ncol,
-                                                    const cpx<T>* __restrict__ tw, int sign) {
+template <class T, int N, int E>
+__global__ void __launch_bounds__(512) k_fft_y_reg(cpx<T>* __restrict__ data, int pitch, int ncol,
+                                                   const cpx<T>* __restrict__ tw, int sign) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  constexpr int NT = N / 8;
+  constexpr int NT = N / E;
   const int txc = blockDim.x / NT;
   const int col = threadIdx.x % txc, t = threadIdx.x / txc;
   const int c = blockIdx.x * txc + col;
   const bool in = c < ncol;
   cpx<T>* base = data + (size_t)blockIdx.y * N * pitch + c;
-  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw) + (size_t)col * N;
-  cpx<T> v[8];
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw) + col;  // columns interleaved: element i at sm[i * txc]
+  cpx<T> v[E];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = in ? base[(size_t)(t + NT * q) * pitch] : mk<T>(0, 0);
-  reg_fft<T, N>(v, sm, tw, sign, t);
+  for (int q = 0; q < E; ++q) v[q] = in ? base[(size_t)(t + NT * q) * pitch] : mk<T>(0, 0);
+  reg_fft<T, N, E>(v, sm, tw, sign, t, txc);
   if (!in) return;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) base[(size_t)(t + NT * q) * pitch] = v[q];
+  for (int q = 0; q < E; ++q) base[(size_t)(t + NT * q) * pitch] = v[q];
 }
 
 }  // namespace pf

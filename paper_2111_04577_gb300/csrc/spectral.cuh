@@ -371,6 +371,42 @@ __device__ __forceinline__ void k_zero_mode_b(cpx<T>* __restrict__ data, int row
   for (int k = 0; k < rows; ++k) base[(size_t)k * zstride] = (T)(xs[k] - mean);
 }
 
+// The same solve with the column staged in shared memory: every thread loads
+// rows in parallel, one thread per real/imaginary part runs the two running
+// sums there, and the mean-free result is written back in parallel.
+// smem: 2 * rows doubles.
+template <class T>
+__global__ void k_zero_mode_smem(cpx<T>* __restrict__ data, int rows, int ny, int pitch, double h2, double scale) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* col = reinterpret_cast<double*>(smraw);  // [2][rows]
+  __shared__ double mean[2];
+  const size_t zstride = (size_t)ny * pitch * 2;
+  T* base = reinterpret_cast<T*>(data);
+  for (int e = threadIdx.x; e < 2 * rows; e += blockDim.x) {
+    const int part = e / rows, k = e - part * rows;
+    col[e] = (double)base[(size_t)k * zstride + part];
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double* c = col + (size_t)threadIdx.x * rows;
+    const double hs = h2 * scale;
+    double f = 0.0, x = 0.0, sum = 0.0;
+    for (int k = 0; k < rows; ++k) {
+      const double r = c[k];
+      c[k] = x;
+      sum += x;
+      f += r * hs;
+      x += f;
+    }
+    mean[threadIdx.x] = sum / rows;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 2 * rows; e += blockDim.x) {
+    const int part = e / rows, k = e - part * rows;
+    base[(size_t)k * zstride + part] = (T)(col[e] - mean[part]);
+  }
+}
+
 template <class T>
 __global__ void k_zero_mode(cpx<T>* __restrict__ data, int rows, int ny, int pitch, double h2, double scale, double* __restrict__ work) {
   extern __shared__ __align__(16) unsigned char smraw[];
