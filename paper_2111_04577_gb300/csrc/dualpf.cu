@@ -322,9 +322,10 @@ struct Impl : ImplBase {
   ~Impl() override {
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
     for (auto e : mark_ev) cudaEventDestroy(e);
-    if (ev_fork) cudaEventDestroy(ev_fork);
-    if (ev_join) cudaEventDestroy(ev_join);
+    for (cudaEvent_t e : {ev_fork, ev_join, ev_ns, ev_v, ev_w})
+      if (e) cudaEventDestroy(e);
     if (st2) cudaStreamDestroy(st2);
+    if (st3) cudaStreamDestroy(st3);
   }
 
   // The polymer update of step n needs u^{n+1}, Theta and the restricted phi
@@ -335,12 +336,24 @@ struct Impl : ImplBase {
   cudaStream_t st2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool poly_pending = false;  // the update for the velocity in parity fc is owed
+  // the coarse velocity solves (u, v, w: independent chains) also run on three
+  // streams; st3 and the events below serve that fork/join
+  cudaStream_t st3 = nullptr;
+  cudaEvent_t ev_ns = nullptr, ev_v = nullptr, ev_w = nullptr;
   void ensure_side_stream() {
     if (st2) return;
     PF_CUDA_TRY(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
-    PF_CUDA_TRY(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
-    PF_CUDA_TRY(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+    PF_CUDA_TRY(cudaStreamCreateWithFlags(&st3, cudaStreamNonBlocking));
+    for (cudaEvent_t* e : {&ev_fork, &ev_join, &ev_ns, &ev_v, &ev_w})
+      PF_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   }
+  // launches issued while alive go to stream s (the launchers use the member st)
+  struct OnStream {
+    cudaStream_t& ref;
+    cudaStream_t saved;
+    OnStream(cudaStream_t& r, cudaStream_t s) : ref(r), saved(r) { ref = s; }
+    ~OnStream() { ref = saved; }
+  };
   // both LCR stages for the velocity in parity fv (tau written to parity fv)
   void launch_polymer(int fv, cudaStream_t s) {
     PolyIn<T> P{};
@@ -674,10 +687,32 @@ struct Impl : ImplBase {
       else k_ns_rhs_v2<T, 3, 4><<<lc.grid, lc.block, 0, st>>>(A, d, q, ru, rv, rw, p.visco);
     }
     const double kk = p.gamma0 / (p.dt * p.nu_m);
-    // u~, v~ land in the n-1 buffers (free once the right sides exist)
-    coarse_solve(ru, u[fo], spU, d.nz, Z_DIRICH, kk, false);
-    if (d.dim == 3) coarse_solve(rv, v[fo], spV, d.nz, Z_DIRICH, kk, false);
-    coarse_solve(rw, wt, spW, d.nz - 1, Z_FACES, kk, false);
+    // u~, v~ land in the n-1 buffers (free once the right sides exist).  The
+    // three solves share nothing but their inputs, so outside pf_profile (which
+    // times kernels one after another) they run on three streams.
+    if (!prof) {
+      ensure_side_stream();
+      PF_CUDA_TRY(cudaEventRecord(ev_ns, st));
+      PF_CUDA_TRY(cudaStreamWaitEvent(st2, ev_ns, 0));
+      {
+        OnStream on(st, st2);
+        coarse_solve(rw, wt, spW, d.nz - 1, Z_FACES, kk, false);
+        PF_CUDA_TRY(cudaEventRecord(ev_w, st));
+      }
+      if (d.dim == 3) {
+        PF_CUDA_TRY(cudaStreamWaitEvent(st3, ev_ns, 0));
+        OnStream on(st, st3);
+        coarse_solve(rv, v[fo], spV, d.nz, Z_DIRICH, kk, false);
+        PF_CUDA_TRY(cudaEventRecord(ev_v, st));
+      }
+      coarse_solve(ru, u[fo], spU, d.nz, Z_DIRICH, kk, false);
+      PF_CUDA_TRY(cudaStreamWaitEvent(st, ev_w, 0));
+      if (d.dim == 3) PF_CUDA_TRY(cudaStreamWaitEvent(st, ev_v, 0));
+    } else {
+      coarse_solve(ru, u[fo], spU, d.nz, Z_DIRICH, kk, false);
+      if (d.dim == 3) coarse_solve(rv, v[fo], spV, d.nz, Z_DIRICH, kk, false);
+      coarse_solve(rw, wt, spW, d.nz - 1, Z_FACES, kk, false);
+    }
     // pressure Poisson (Eq. NS37), its right side formed inside the first transform
     coarse_solve_pro(DivPro<T>{u[fo], v[fo], wt, d, (T)(p.gamma0 * p.rho0 / p.dt), (T)(1.0 / d.dx)}, pp, spP, d.nz,
                      Z_NEUMANN, 0.0, true);
@@ -1097,7 +1132,7 @@ struct Impl : ImplBase {
     if (nsteps < 0) throw ApiError(PF_ERR_ARG, "nsteps < 0");
     flush_polymer();  // owed by a call that stopped early
     const bool visco_steps = p.visco && !(flags & PF_STEP_CH_ONLY);
-    if (visco_steps) ensure_side_stream();
+    if (!(flags & PF_STEP_CH_ONLY)) ensure_side_stream();  // before any capture
     for (int s = 0; s < nsteps; ++s) {
       const bool pend_in = visco_steps && poly_pending;
       run_one(flags, pend_in, visco_steps);
