@@ -212,3 +212,24 @@ def test_overlapped_polymer_update_matches_sequential_order(prec):
         b.step(1)
     for name in ("phi", "u", "v", "w", "p", "theta", "tau"):
         assert np.array_equal(a.get(name), b.get(name)), name
+
+
+@pytest.mark.parametrize("dim,nx,nz,theta", [(2, 16, 8, 0.0), (2, 16, 8, 180.0), (3, 12, 6, 0.0), (2, 20, 2, 30.0)])
+def test_degenerate_cases_fp64(dim, nx, nz, theta):
+    """Contact angles at the ends of the range (cos = +-1, full wetting and
+    non-wetting), and the thinnest wall-to-wall mesh (two coarse rows, four
+    fine ones, so every fine row touches a wall or its neighbour)."""
+    g = grid(dim, nx, nz, 1)
+    w = workload(g, theta_deg=theta, ratio_rho=10.0, ratio_mu=5.0, Wi=0.5, beta=0.5)
+    w.params.theta_top_deg = 180.0 - theta
+    phi0 = wl.initial_phi(w)
+    vel = wl.random_velocity(g, 8, 0.1)
+    s = binding.Solver(g, w.params, binding.PF_FP64)
+    s.load_state(phi0, vel)
+    ref = ostep.State(g, w.params.as_dict(), phi0, vel0=vel)
+    for _ in range(3):
+        s.step(1)
+        ref.step()
+    assert rel(s.fine("phi"), ref.phi) < FP64_TOL
+    assert rel(s.coarse("u"), ref.vel[0]) < FP64_TOL
+    assert rel(s.coarse("w"), ref.vel[2]) < FP64_TOL
