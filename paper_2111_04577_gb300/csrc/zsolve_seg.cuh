@@ -24,6 +24,9 @@
 // access per warp.  The segment length is fixed, so the arithmetic of a
 // column does not depend on the columns per CTA.
 #pragma once
+#include <cstddef>
+#include <type_traits>
+
 #include "spectral.cuh"
 
 namespace pf {
@@ -74,7 +77,7 @@ struct LuClosed {
 
 // smem (TC): f1[R][tx], f2[R][tx] (pair with two shifts), car[4 phases][2][S][L]
 template <class T, class TC>
-__global__ void __launch_bounds__(512, 2) k_zsolve_seg(cpx<T>* __restrict__ data, const double* __restrict__ eigx,
+__global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 2 : 1) k_zsolve_seg(cpx<T>* __restrict__ data, const double* __restrict__ eigx,
                                                      const double* __restrict__ eigy, const ZSolve zs, const int tx) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int R = zs.rows;
@@ -109,10 +112,22 @@ __global__ void __launch_bounds__(512, 2) k_zsolve_seg(cpx<T>* __restrict__ data
   const TC sg1 = (k2 + (TC)zs.shift1) * h2;
   const TC sg2 = (k2 + (TC)zs.shift2) * h2;
   // ---- factors in closed form: the two lanes of a column share the rows ----
+  // Each lane forms rows k0 + part, k0 + part + 2, ...; rho^k is advanced by
+  // rho^2 from row to row instead of being raised afresh.
   const int part = lane & 1;
   auto factors = [&](TC sg, TC* f) {
     const LuClosed<TC> lu(R, zs.bc, sg);
-    for (int j = part; j < nk; j += 2) f[(size_t)(k0 + j) * tx + c] = lu.m(k0 + j);
+    const TC rho = zs_exp2<TC>(lu.lr), rho2 = rho * rho;
+    TC pk = zs_exp2<TC>((TC)(k0 + part) * lu.lr);  // rho^k
+    for (int j = part; j < nk; j += 2) {
+      const int k = k0 + j;
+      TC m;
+      if (R == 1) m = (TC)1 / lu.d0;
+      else if (k < R - 1) m = lu.il1 * ((TC)1 + lu.beta * pk) / ((TC)1 + lu.beta * pk * rho);
+      else m = (TC)1 / (lu.d0 - lu.interior(R - 2));
+      f[(size_t)k * tx + c] = m;
+      pk *= rho2;
+    }
   };
   factors(sg1, f1);
   if (dual) factors(sg2, f2);
@@ -135,130 +150,138 @@ __global__ void __launch_bounds__(512, 2) k_zsolve_seg(cpx<T>* __restrict__ data
   TC* cB = car + (size_t)2 * S * L;
   TC* cC = car + (size_t)4 * S * L;
   TC* cD = car + (size_t)6 * S * L;
+  // Every pass below runs between barriers; a full segment (all but possibly
+  // the last) takes a copy of the loop without the row-count predicate.
+  const bool full = nk == ZSEG;
+  auto pass = [&](auto&& body) {
+    if (full) body(std::true_type{});
+    else body(std::false_type{});
+  };
+  const TC* m1 = f1 + c;                         // m_k at m1[k * tx]
+  const TC* g2 = f2 + (size_t)(R - 1) * tx + c;  // g_k = m2_{R-1-k} at g2[-k * tx]
   // ---- solve 1, forward: d_k = -m_k d_{k-1} + m_k r_k ----
-  {
+  pass([&](auto F) {
+    constexpr bool FULL = decltype(F)::value;
     TC z = 0, P = 1;
 #pragma unroll
     for (int j = 0; j < ZSEG; ++j)
-      if (j < nk) {
-        const TC m = f1[(size_t)(k0 + j) * tx + c];
+      if (FULL || j < nk) {
+        const TC m = m1[(size_t)(k0 + j) * tx];
         z = m * (v[j] * rs - z);
         v[j] = z;
         P *= -m;
       }
     cA[(size_t)s * L + lane] = P;
     cA[(size_t)(S + s) * L + lane] = z;
-  }
+  });
   __syncthreads();
-  {
+  // ---- fix-up of solve 1 forward, then solve 1 backward: x_k = -m_k x_{k+1} + d_k ----
+  pass([&](auto F) {
+    constexpr bool FULL = decltype(F)::value;
     const TC g = carry_fwd(cA);
     TC p = 1;
 #pragma unroll
     for (int j = 0; j < ZSEG; ++j)
-      if (j < nk) {
-        p *= -f1[(size_t)(k0 + j) * tx + c];
+      if (FULL || j < nk) {
+        p *= -m1[(size_t)(k0 + j) * tx];
         v[j] += p * g;
       }
-  }
-  // ---- solve 1, backward: x_k = -m_k x_{k+1} + d_k ----
-  {
     TC z = 0, P = 1;
 #pragma unroll
     for (int j = ZSEG - 1; j >= 0; --j)
-      if (j < nk) {
-        const TC m = f1[(size_t)(k0 + j) * tx + c];
+      if (FULL || j < nk) {
+        const TC m = m1[(size_t)(k0 + j) * tx];
         z = v[j] - m * z;
         v[j] = z;
         P *= -m;
       }
     cB[(size_t)s * L + lane] = P;
     cB[(size_t)(S + s) * L + lane] = z;
-  }
+  });
   __syncthreads();
   const bool keep = in && !(zs.skip_zero && col == 0 && ky == 0);
-  if (!zs.two) {
-    const TC g = carry_bwd(cB);
-    TC p = 1;
+  auto store = [&](auto F) {
+    constexpr bool FULL = decltype(F)::value;
+    if (!keep) return;
+    T* gp = gcol + (size_t)k0 * zstride;
 #pragma unroll
-    for (int j = ZSEG - 1; j >= 0; --j)
-      if (j < nk) {
-        p *= -f1[(size_t)(k0 + j) * tx + c];
-        v[j] += p * g;
+    for (int j = 0; j < ZSEG; ++j)
+      if (FULL || j < nk) {
+        gp[0] = (T)v[j];
+        gp += zstride;
       }
-    if (keep) {
-      T* gp = gcol + (size_t)k0 * zstride;
+  };
+  if (!zs.two) {
+    pass([&](auto F) {
+      constexpr bool FULL = decltype(F)::value;
+      const TC g = carry_bwd(cB);
+      TC p = 1;
 #pragma unroll
-      for (int j = 0; j < ZSEG; ++j)
-        if (j < nk) {
-          gp[0] = (T)v[j];
-          gp += zstride;
+      for (int j = ZSEG - 1; j >= 0; --j)
+        if (FULL || j < nk) {
+          p *= -m1[(size_t)(k0 + j) * tx];
+          v[j] += p * g;
         }
-    }
+      store(F);
+    });
     return;
   }
   // ---- finish solve 1 and run solve 2's elimination in the same backward pass ----
-  {
+  pass([&](auto F) {
+    constexpr bool FULL = decltype(F)::value;
     const TC g = carry_bwd(cB);
     TC p = 1, z = 0, P = 1;
 #pragma unroll
     for (int j = ZSEG - 1; j >= 0; --j)
-      if (j < nk) {
+      if (FULL || j < nk) {
         const int k = k0 + j;
-        p *= -f1[(size_t)k * tx + c];
+        p *= -m1[(size_t)k * tx];
         const TC x = v[j] + p * g;
-        const TC gk = f2[(size_t)(R - 1 - k) * tx + c];
+        const TC gk = g2[-(ptrdiff_t)k * tx];
         z = gk * (h2 * x - z);
         v[j] = z;
         P *= -gk;
       }
     cC[(size_t)s * L + lane] = P;
     cC[(size_t)(S + s) * L + lane] = z;
-  }
+  });
   __syncthreads();
-  {
+  // ---- fix-up of solve 2's elimination, then its forward substitution: y_k = -g_k y_{k-1} + q_k ----
+  pass([&](auto F) {
+    constexpr bool FULL = decltype(F)::value;
     const TC g = carry_bwd(cC);
     TC p = 1;
 #pragma unroll
     for (int j = ZSEG - 1; j >= 0; --j)
-      if (j < nk) {
-        p *= -f2[(size_t)(R - 1 - (k0 + j)) * tx + c];
+      if (FULL || j < nk) {
+        p *= -g2[-(ptrdiff_t)(k0 + j) * tx];
         v[j] += p * g;
       }
-  }
-  // ---- solve 2, forward substitution: y_k = -g_k y_{k-1} + q_k ----
-  {
     TC z = 0, P = 1;
 #pragma unroll
     for (int j = 0; j < ZSEG; ++j)
-      if (j < nk) {
-        const TC gk = f2[(size_t)(R - 1 - (k0 + j)) * tx + c];
+      if (FULL || j < nk) {
+        const TC gk = g2[-(ptrdiff_t)(k0 + j) * tx];
         z = v[j] - gk * z;
         v[j] = z;
         P *= -gk;
       }
     cD[(size_t)s * L + lane] = P;
     cD[(size_t)(S + s) * L + lane] = z;
-  }
+  });
   __syncthreads();
-  {
+  pass([&](auto F) {
+    constexpr bool FULL = decltype(F)::value;
     const TC g = carry_fwd(cD);
     TC p = 1;
 #pragma unroll
     for (int j = 0; j < ZSEG; ++j)
-      if (j < nk) {
-        p *= -f2[(size_t)(R - 1 - (k0 + j)) * tx + c];
+      if (FULL || j < nk) {
+        p *= -g2[-(ptrdiff_t)(k0 + j) * tx];
         v[j] += p * g;
       }
-    if (keep) {
-      T* gp = gcol + (size_t)k0 * zstride;
-#pragma unroll
-      for (int j = 0; j < ZSEG; ++j)
-        if (j < nk) {
-          gp[0] = (T)v[j];
-          gp += zstride;
-        }
-    }
-  }
+    store(F);
+  });
 }
 
 // shared memory of k_zsolve_seg in bytes
