@@ -22,7 +22,7 @@ KNOBS = {
     2: ("zsolve_cols", [16, 32], ("zsolve_pair", "zsolve")),
     3: ("row_block", [64, 128, 256], ("ns_rhs", "div", "correct", "polymer_stage1", "polymer_stage2")),
     4: ("ch_zchunk", [16, 32, 64], ("ch_rhs",)),
-    5: ("ch_minb", [2, 3], ("ch_rhs",)),
+    5: ("ch_minb", [2, 3, 4], ("ch_rhs",)),
     6: ("ns_minb", [3, 4], ("ns_rhs",)),
     7: ("g_zchunk", [4, 8, 16], ("ch_G_restrict",)),
     8: ("ns_kz", [1, 2, 4], ("ns_rhs",)),

@@ -97,7 +97,7 @@ __device__ __forceinline__ void batch_run_item(const BatchProb<T>& B, int pass, 
       if (d.r == 2) k_ch_G_restrict_b<T, 2, 2>(B.phi[po], B.gwall, B.rs, d, B.q, bid, sm);
       else k_ch_G_restrict_b<T, 2, 1>(B.phi[po], B.gwall, B.rs, d, B.q, bid, sm);
       break;
-    case BP_NSRHS: k_ns_rhs_v2_b<T, 2>(B.ns[fc], d, B.q, B.ru, B.ru, B.rw, B.visco, bid, sm); break;
+    case BP_NSRHS: k_ns_rhs_v2_b<T, 2>(B.ns[fc], d, B.q, B.ru, B.ru, B.rw, B.visco, bid); break;
     case BP_U_RFFT:
       k_rfft_x_b<T, FinePro<T>>(FinePro<T>{B.ru, d.nx}, B.spU, d.nx, d.nz, B.pC, B.plCx, B.twCx, B.npairC, bid, sm);
       break;

@@ -492,14 +492,13 @@ struct March4 {
   static constexpr int SXC = CH + 2, SXF = 4 * SXC;               // phi* chunks (x0-4 .. x0+68)
   static constexpr int SY = TY + 4, SPF = SY * SXF + 8;            // phi* rows y0-2 .. y0+18, padded plane
   static constexpr int MY = TY + 2, MPF = MY * SXF + 8;            // mu* rows y0-1 .. y0+17
-  static constexpr int OPF = TX * TY;                              // owned cells per plane
-  static constexpr int NPS = 5, NMS = 3, NDS = 4;
+  static constexpr int NPS = 5, NMS = 3;
   static constexpr int NSC = SY * SXC, NMC = MY * SXC;             // staged / mu chunks per plane
   static constexpr int KS = (NSC + NT - 1) / NT, KM = (NMC + NT - 1) / NT;
   __host__ __device__ static constexpr int VX(int rs) { return (TX >> rs) + 2; }
   __host__ __device__ static constexpr int VY(int rs) { return (TY >> rs) + 2; }
   __host__ __device__ static constexpr int smem_floats(int rs) {
-    return NPS * SPF + NMS * MPF + NDS * OPF + 8 * VX(rs) * VY(rs);
+    return NPS * SPF + NMS * MPF + 4 * VX(rs) * VY(rs);
   }
 };
 
@@ -513,28 +512,25 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
   extern __shared__ __align__(16) unsigned char smraw[];
   float* ps = reinterpret_cast<float*>(smraw);  // [NPS][4 + SY*SXF + 4]
   float* ms = ps + TL::NPS * TL::SPF;           // [NMS][4 + MY*SXF + 4]
-  float* ds = ms + TL::NMS * TL::MPF;           // [NDS][TY][TX]
-  float* vb = ds + TL::NDS * TL::OPF;           // [2][u, v, w_lo, w_hi][VY][VX]
+  float* vb = ms + TL::NMS * TL::MPF;           // [u, v, w_lo, w_hi][VY][VX]
   constexpr int VX = TL::VX(RS), VY = TL::VY(RS), NV = VX * VY;
   const int t = threadIdx.x;
   const int x0 = blockIdx.x * TL::TX, y0 = blockIdx.y * TL::TY;
   const int fnx = d.fnx, fny = d.fny, fnz = d.fnz;
   const size_t plane = (size_t)fnx * fny;
   const int zb = blockIdx.z * nzc, ze = min(zb + nzc, fnz);
-  // ---- staging chunks: global x/y offset (multiple of 4) and owned slot ----
-  int sxy[TL::KS], sown[TL::KS];
+  // ---- staging chunks: global x/y offset (multiple of 4) ----
+  int sxy[TL::KS];
 #pragma unroll
   for (int k = 0; k < TL::KS; ++k) {
     const int e = t + k * TL::NT;
     sxy[k] = -1;
-    sown[k] = -1;
     if (e < TL::NSC) {
       const int yy = e / TL::SXC, xc = e - yy * TL::SXC;
       sxy[k] = pmod_m(y0 - 2 + yy, fny) * fnx + pmod_m(x0 - 4 + 4 * xc, fnx);
-      if (yy >= 2 && yy < TL::TY + 2 && xc >= 1 && xc <= TL::CH) sown[k] = (yy - 2) * TL::TX + 4 * (xc - 1);
     }
   }
-  auto star_load = [&](int gz, float4 (&rg)[TL::KS], float4 (&dg)[TL::KS]) {
+  auto star_load = [&](int gz, float4 (&rg)[TL::KS]) {
     const size_t zo = (size_t)min(max(gz, 0), fnz - 1) * plane;
 #pragma unroll
     for (int k = 0; k < TL::KS; ++k)
@@ -542,25 +538,20 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
         const float4 a = *reinterpret_cast<const float4*>(f.pn + zo + sxy[k]);
         const float4 b = *reinterpret_cast<const float4*>(f.po + zo + sxy[k]);
         rg[k] = make_float4(2.f * a.x - b.x, 2.f * a.y - b.y, 2.f * a.z - b.z, 2.f * a.w - b.w);
-        dg[k] = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, b.w - a.w);
       }
   };
-  auto star_store = [&](int slot, int dslot, const float4 (&rg)[TL::KS], const float4 (&dg)[TL::KS]) {
+  auto star_store = [&](int slot, const float4 (&rg)[TL::KS]) {
     float* pp = ps + slot * TL::SPF + 4;
-    float* dd = ds + dslot * TL::OPF;
 #pragma unroll
     for (int k = 0; k < TL::KS; ++k) {
       const int e = t + k * TL::NT;
-      if (e < TL::NSC) {
-        reinterpret_cast<float4*>(pp)[e] = rg[k];
-        if (sown[k] >= 0) *reinterpret_cast<float4*>(dd + sown[k]) = dg[k];
-      }
+      if (e < TL::NSC) reinterpret_cast<float4*>(pp)[e] = rg[k];
     }
   };
   const int cx0 = (x0 >> RS) - 1, cy0 = (y0 >> RS) - 1;
   const int cplane = d.nx * d.ny;
-  auto vel_load = [&](int kc, int slot) {
-    float* vu = vb + slot * 4 * NV;
+  auto vel_load = [&](int kc) {
+    float* vu = vb;
     for (int e = t; e < NV; e += TL::NT) {
       const int yy = e / VX, xx = e - yy * VX;
       const int cx = pmod_m(cx0 + xx, d.nx), cy = pmod_m(cy0 + yy, d.ny);
@@ -636,7 +627,7 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
   const bool act = gx < fnx && gy < fny;
   const int so = (ty + 2) * TL::SXF + 4 * (cx + 1);  // phi* center chunk
   const int mo = (ty + 1) * TL::SXF + 4 * (cx + 1);  // mu* center chunk
-  const int dof = ty * TL::TX + 4 * cx;
+  const size_t gof = (size_t)gy * fnx + gx;  // owned chunk within a plane
   // velocity box rows/columns (Eq. dual1)
   const int urow = ((ty >> RS) + 1) * VX;
   const int cb = ((4 * cx) >> RS) + 1;  // box column of the chunk's first coarse cell
@@ -645,42 +636,49 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
 
   // ---- prologue ----
   {
-    float4 rg[TL::KS], dg[TL::KS];
+    float4 rg[TL::KS];
 #pragma unroll
-    for (int k = 0; k < TL::KS; ++k) rg[k] = dg[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = 0; k < TL::KS; ++k) rg[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int j = 0; j < 4; ++j) {
-      star_load(zb - 2 + j, rg, dg);
-      star_store(j, j >= 2 ? j - 2 : 3, rg, dg);
+      star_load(zb - 2 + j, rg);
+      star_store(j, rg);
     }
   }
   __syncthreads();
   mu_plane(zb - 1, 0, 1, 2, 0);
   mu_plane(zb, 1, 2, 3, 1);
-  float4 rg[TL::KS], dg[TL::KS];
+  float4 rg[TL::KS];
 #pragma unroll
-  for (int k = 0; k < TL::KS; ++k) rg[k] = dg[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-  star_load(zb + 2, rg, dg);
+  for (int k = 0; k < TL::KS; ++k) rg[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  star_load(zb + 2, rg);
   int kc_loaded = -1;
-  for (int z = zb; z < ze; ++z) {
-    const int m = z - zb;
-    star_store((m + 4) % 5, (m + 2) & 3, rg, dg);
+  // ring positions m % 5 and m % 3, advanced per plane (no integer division in the loop)
+  int m5 = 0, m3 = 0;
+  auto r5 = [](int a) { return a >= 5 ? a - 5 : a; };
+  auto r3 = [](int a) { return a >= 3 ? a - 3 : a; };
+  for (int z = zb; z < ze; ++z, m5 = r5(m5 + 1), m3 = r3(m3 + 1)) {
+    star_store(r5(m5 + 4), rg);
     const int kc = z >> RS;
-    if (kc != kc_loaded) {  // slot kc & 1: its last readers (layer kc - 2) are done
-      vel_load(kc, kc & 1);
+    __syncthreads();
+    // one velocity box: every reader of the previous layer has passed the barrier above
+    if (kc != kc_loaded) {
+      vel_load(kc);
       kc_loaded = kc;
     }
-    __syncthreads();
-    if (z + 1 < ze) star_load(z + 3, rg, dg);
-    mu_plane(z + 1, (m + 2) % 5, (m + 3) % 5, (m + 4) % 5, (m + 2) % 3);
+    if (z + 1 < ze) star_load(z + 3, rg);
+    mu_plane(z + 1, r5(m5 + 2), r5(m5 + 3), r5(m5 + 4), r3(m3 + 2));
     __syncthreads();
     if (!act) continue;
-    const float* pm = ps + ((m + 1) % 5) * TL::SPF + 4;
-    const float* pc = ps + ((m + 2) % 5) * TL::SPF + 4;
-    const float* pq = ps + ((m + 3) % 5) * TL::SPF + 4;
-    const float* mmm = ms + (m % 3) * TL::MPF + 4;
-    const float* mmc = ms + ((m + 1) % 3) * TL::MPF + 4;
-    const float* mmp = ms + ((m + 2) % 3) * TL::MPF + 4;
-    const float* vu = vb + (kc & 1) * 4 * NV;
+    // owned phi^n and phi^{n-1} of this plane (read from L2: the plane was staged three planes ago)
+    const float4 an = *reinterpret_cast<const float4*>(f.pn + (size_t)z * plane + gof);
+    const float4 bo = *reinterpret_cast<const float4*>(f.po + (size_t)z * plane + gof);
+    const float* pm = ps + r5(m5 + 1) * TL::SPF + 4;
+    const float* pc = ps + r5(m5 + 2) * TL::SPF + 4;
+    const float* pq = ps + r5(m5 + 3) * TL::SPF + 4;
+    const float* mmm = ms + m3 * TL::MPF + 4;
+    const float* mmc = ms + r3(m3 + 1) * TL::MPF + 4;
+    const float* mmp = ms + r3(m3 + 2) * TL::MPF + 4;
+    const float* vu = vb;
     const float* vv = vu + NV;
     const float* vw = vu + 2 * NV;
     // face velocities of the four cells
@@ -724,8 +722,7 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
     const float4 mzm4 = *reinterpret_cast<const float4*>(mmm + mo);
     const float muv[4] = {mu4.x, mu4.y, mu4.z, mu4.w}, mdv[4] = {md4.x, md4.y, md4.z, md4.w};
     const float mzpv[4] = {mzp4.x, mzp4.y, mzp4.z, mzp4.w}, mzmv[4] = {mzm4.x, mzm4.y, mzm4.z, mzm4.w};
-    const float4 d4 = *reinterpret_cast<const float4*>(ds + (m & 3) * TL::OPF + dof);
-    const float dv[4] = {d4.x, d4.y, d4.z, d4.w};
+    const float dv[4] = {bo.x - an.x, bo.y - an.y, bo.z - an.z, bo.w - an.w};
     float out[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -743,7 +740,7 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
       lap = (lap + mzp + mzm - 2 * m0) * q.ih2;
       out[i] = dv[i] * inv_mldt - adv * inv_ml + lap;
     }
-    *reinterpret_cast<float4*>(R + (size_t)z * plane + (size_t)gy * fnx + gx) = make_float4(out[0], out[1], out[2], out[3]);
+    *reinterpret_cast<float4*>(R + (size_t)z * plane + gof) = make_float4(out[0], out[1], out[2], out[3]);
   }
 }
 

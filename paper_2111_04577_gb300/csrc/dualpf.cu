@@ -422,6 +422,7 @@ struct Impl : ImplBase {
     if constexpr (std::is_same<T, float>::value) {
       PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march4<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
       PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march4<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+      PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march4<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
       PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march4<0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     }
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict_march<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
@@ -603,9 +604,10 @@ struct Impl : ImplBase {
           using T4 = March4;
           dim3 g4((d.fnx + T4::TX - 1) / T4::TX, (d.fny + T4::TY - 1) / T4::TY, (d.fnz + nzc - 1) / nzc);
           const size_t s4 = (size_t)T4::smem_floats(d.rs) * sizeof(float);
-          const bool b2 = tune[PF_TUNE_CH_MINB] == 2;
+          const int mb = tune[PF_TUNE_CH_MINB];
           if (d.rs == 1) {
-            if (b2) k_ch_rhs_march4<1, 2><<<g4, T4::NT, s4, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml, nzc);
+            if (mb == 2) k_ch_rhs_march4<1, 2><<<g4, T4::NT, s4, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml, nzc);
+            else if (mb == 4) k_ch_rhs_march4<1, 4><<<g4, T4::NT, s4, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml, nzc);
             else k_ch_rhs_march4<1, 3><<<g4, T4::NT, s4, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml, nzc);
           } else {
             k_ch_rhs_march4<0, 2><<<g4, T4::NT, s4, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml, nzc);
@@ -670,7 +672,7 @@ struct Impl : ImplBase {
     mark("ns_rhs");
     const bool ns3 = tune[PF_TUNE_NS_MINB] == 3;
     const int kz = tune[PF_TUNE_NS_KZ] > 1 ? tune[PF_TUNE_NS_KZ] : 1;
-    if (kz > 1) {
+    {
       const dim3 gz(d.ny * ((d.nz + kz - 1) / kz), lc.grid.y);
       if (d.dim == 2) {
         if (ns3) k_ns_rhs_v2z<T, 2, 3><<<gz, lc.block, 0, st>>>(A, d, q, ru, rv, rw, p.visco, kz);
@@ -679,12 +681,6 @@ struct Impl : ImplBase {
         if (ns3) k_ns_rhs_v2z<T, 3, 3><<<gz, lc.block, 0, st>>>(A, d, q, ru, rv, rw, p.visco, kz);
         else k_ns_rhs_v2z<T, 3, 4><<<gz, lc.block, 0, st>>>(A, d, q, ru, rv, rw, p.visco, kz);
       }
-    } else if (d.dim == 2) {
-      if (ns3) k_ns_rhs_v2<T, 2, 3><<<lc.grid, lc.block, 0, st>>>(A, d, q, ru, rv, rw, p.visco);
-      else k_ns_rhs_v2<T, 2, 4><<<lc.grid, lc.block, 0, st>>>(A, d, q, ru, rv, rw, p.visco);
-    } else {
-      if (ns3) k_ns_rhs_v2<T, 3, 3><<<lc.grid, lc.block, 0, st>>>(A, d, q, ru, rv, rw, p.visco);
-      else k_ns_rhs_v2<T, 3, 4><<<lc.grid, lc.block, 0, st>>>(A, d, q, ru, rv, rw, p.visco);
     }
     const double kk = p.gamma0 / (p.dt * p.nu_m);
     // u~, v~ land in the n-1 buffers (free once the right sides exist).  The
@@ -884,7 +880,7 @@ struct Impl : ImplBase {
       if (knob == PF_TUNE_CH_ZCHUNK && value < 2) throw ApiError(PF_ERR_ARG, "z chunk must be at least 2 planes");
       if (knob == PF_TUNE_G_ZCHUNK && value < 1) throw ApiError(PF_ERR_ARG, "z chunk must be at least 1 layer");
       if (knob == PF_TUNE_NS_KZ && value > 64) throw ApiError(PF_ERR_ARG, "NS z rows per CTA must be <= 64");
-      if (knob == PF_TUNE_CH_MINB && value != 2 && value != 3) throw ApiError(PF_ERR_ARG, "CH register budget: 2 or 3 CTAs per SM");
+      if (knob == PF_TUNE_CH_MINB && (value < 2 || value > 4)) throw ApiError(PF_ERR_ARG, "CH register budget: 2, 3 or 4 CTAs per SM");
       if (knob == PF_TUNE_NS_MINB && value != 3 && value != 4) throw ApiError(PF_ERR_ARG, "NS register budget: 3 or 4 CTAs per SM");
     }
     tune[knob] = value;

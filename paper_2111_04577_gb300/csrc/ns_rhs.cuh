@@ -13,7 +13,7 @@
 namespace pf {
 
 template <class T, int DIM>
-__device__ __forceinline__ void k_ns_rhs_v2_b(const NsIn<T>& a, const Dims d, const PhysT<T> q, T* __restrict__ ru, T* __restrict__ rv, T* __restrict__ rw, const int have_tau, const int3 bid, unsigned char* smraw) {
+__device__ __forceinline__ void k_ns_rhs_v2_b(const NsIn<T>& a, const Dims d, const PhysT<T> q, T* __restrict__ ru, T* __restrict__ rv, T* __restrict__ rw, const int have_tau, const int3 bid) {
   constexpr bool D3 = DIM == 3;
   RowIdx ix;
   if (!row_index_b(bid, d.nx, d.ny, ix)) return;
@@ -236,19 +236,11 @@ __device__ __forceinline__ void k_ns_rhs_v2_b(const NsIn<T>& a, const Dims d, co
   }
 }
 
-// MINB: CTAs of 256 threads per SM the register budget is sized for
-template <class T, int DIM, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_ns_rhs_v2(const __grid_constant__ NsIn<T> a, const Dims d, const PhysT<T> q, T* __restrict__ ru, T* __restrict__ rv, T* __restrict__ rw, const int have_tau) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  k_ns_rhs_v2_b<T, DIM>(a, d, q, ru, rv, rw, have_tau, make_int3(blockIdx.x, blockIdx.y, blockIdx.z), smraw);
-}
 
-}  // namespace pf
-
-namespace pf {
-
-// The same rows, but each CTA walks kz consecutive z rows at one (j): the rows
-// it has just read are the z neighbours of the next, so they come from L1.
+// Each CTA walks kz consecutive z rows at one (j) (kz = 1: one row per CTA):
+// the rows it has just read are the z neighbours of the next, so they come
+// from L1.  Every kz runs the same compiled loop body, so the result does not
+// depend on kz.  MINB: CTAs of 256 threads per SM the register budget is sized for.
 template <class T, int DIM, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_ns_rhs_v2z(const __grid_constant__ NsIn<T> a, const Dims d,
                                                           const PhysT<T> q, T* __restrict__ ru, T* __restrict__ rv,
@@ -257,7 +249,7 @@ __global__ void __launch_bounds__(256, MINB) k_ns_rhs_v2z(const __grid_constant_
   for (int kk = 0; kk < kz; ++kk) {
     const int k = kc * kz + kk;
     if (k >= d.nz) break;
-    k_ns_rhs_v2_b<T, DIM>(a, d, q, ru, rv, rw, have_tau, make_int3(k * d.ny + j, blockIdx.y, 0), nullptr);
+    k_ns_rhs_v2_b<T, DIM>(a, d, q, ru, rv, rw, have_tau, make_int3(k * d.ny + j, blockIdx.y, 0));
   }
 }
 

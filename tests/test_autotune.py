@@ -38,3 +38,25 @@ def test_tuned_context_matches_default():
         s.step(3)
     assert np.array_equal(a.get("phi"), b.get("phi"))
     assert np.array_equal(a.get("u"), b.get("u"))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("knob", sorted(autotune.KNOBS))
+def test_every_candidate_matches_default(knob):
+    """Each launch shape a knob offers computes the same bits as the built-in
+    one: the knobs change how work is split, never the arithmetic of a cell."""
+    build.build()
+    w = wl.scaled(wl.config("c4"), 32, 16)
+    g = w.grid
+    name, cands, _ = autotune.KNOBS[knob]
+    phi0 = wl.initial_phi(w)
+    ref = binding.Solver(g, w.params, binding.PF_MIXED)
+    ref.load_state(phi0)
+    ref.step(3)
+    for v in cands:
+        s = binding.Solver(g, w.params, binding.PF_MIXED)
+        s.set_tuning(knob, int(v))
+        s.load_state(phi0)
+        s.step(3)
+        for f in ("phi", "u", "w", "p"):
+            assert np.array_equal(ref.get(f), s.get(f)), (name, v, f)
