@@ -20,6 +20,7 @@
 // written after a barrier one that no thread can still be reading.
 #pragma once
 #include "ch.cuh"
+#include "spectral.cuh"
 
 namespace pf {
 
@@ -498,7 +499,7 @@ struct March4 {
   __host__ __device__ static constexpr int VX(int rs) { return (TX >> rs) + 2; }
   __host__ __device__ static constexpr int VY(int rs) { return (TY >> rs) + 2; }
   __host__ __device__ static constexpr int smem_floats(int rs) {
-    return NPS * SPF + NMS * MPF + 4 * VX(rs) * VY(rs);
+    return NPS * SPF + NMS * MPF + 4 * VX(rs) * VY(rs) + 8 * NSC;
   }
 };
 
@@ -513,6 +514,7 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
   float* ps = reinterpret_cast<float*>(smraw);  // [NPS][4 + SY*SXF + 4]
   float* ms = ps + TL::NPS * TL::SPF;           // [NMS][4 + MY*SXF + 4]
   float* vb = ms + TL::NMS * TL::MPF;           // [u, v, w_lo, w_hi][VY][VX]
+  float4* raw = reinterpret_cast<float4*>(vb + 4 * TL::VX(RS) * TL::VY(RS));  // [phi^n, phi^{n-1}][NSC] in flight
   constexpr int VX = TL::VX(RS), VY = TL::VY(RS), NV = VX * VY;
   const int t = threadIdx.x;
   const int x0 = blockIdx.x * TL::TX, y0 = blockIdx.y * TL::TY;
@@ -530,22 +532,30 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
       sxy[k] = pmod_m(y0 - 2 + yy, fny) * fnx + pmod_m(x0 - 4 + 4 * xc, fnx);
     }
   }
-  auto star_load = [&](int gz, float4 (&rg)[TL::KS]) {
+  // the next plane's phi^n and phi^{n-1} chunks go straight to shared memory
+  // (cp.async, no register staging); each thread later combines the chunks it
+  // copied itself into phi* = 2 phi^n - phi^{n-1}
+  auto star_load = [&](int gz) {
     const size_t zo = (size_t)min(max(gz, 0), fnz - 1) * plane;
 #pragma unroll
     for (int k = 0; k < TL::KS; ++k)
       if (sxy[k] >= 0) {
-        const float4 a = *reinterpret_cast<const float4*>(f.pn + zo + sxy[k]);
-        const float4 b = *reinterpret_cast<const float4*>(f.po + zo + sxy[k]);
-        rg[k] = make_float4(2.f * a.x - b.x, 2.f * a.y - b.y, 2.f * a.z - b.z, 2.f * a.w - b.w);
+        const int e = t + k * TL::NT;
+        cp_async16(raw + e, f.pn + zo + sxy[k]);
+        cp_async16(raw + TL::NSC + e, f.po + zo + sxy[k]);
       }
+    cp_async_commit();
   };
-  auto star_store = [&](int slot, const float4 (&rg)[TL::KS]) {
+  auto star_store = [&](int slot) {
+    cp_async_wait_all();  // this thread's own copies
     float* pp = ps + slot * TL::SPF + 4;
 #pragma unroll
     for (int k = 0; k < TL::KS; ++k) {
       const int e = t + k * TL::NT;
-      if (e < TL::NSC) reinterpret_cast<float4*>(pp)[e] = rg[k];
+      if (e < TL::NSC) {
+        const float4 a = raw[e], b = raw[TL::NSC + e];
+        reinterpret_cast<float4*>(pp)[e] = make_float4(2.f * a.x - b.x, 2.f * a.y - b.y, 2.f * a.z - b.z, 2.f * a.w - b.w);
+      }
     }
   };
   const int cx0 = (x0 >> RS) - 1, cy0 = (y0 >> RS) - 1;
@@ -635,29 +645,28 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
   const int vr0 = ((ty >> RS) + 1) * VX, vr1 = (((ty + 1) >> RS) + 1) * VX;
 
   // ---- prologue ----
-  {
-    float4 rg[TL::KS];
-#pragma unroll
-    for (int k = 0; k < TL::KS; ++k) rg[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int j = 0; j < 4; ++j) {
-      star_load(zb - 2 + j, rg);
-      star_store(j, rg);
-    }
+  for (int j = 0; j < 4; ++j) {
+    star_load(zb - 2 + j);
+    star_store(j);
   }
   __syncthreads();
   mu_plane(zb - 1, 0, 1, 2, 0);
   mu_plane(zb, 1, 2, 3, 1);
-  float4 rg[TL::KS];
-#pragma unroll
-  for (int k = 0; k < TL::KS; ++k) rg[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-  star_load(zb + 2, rg);
+  star_load(zb + 2);
+  // owned phi^n and phi^{n-1} of the plane being formed, read one plane ahead
+  // (an L2 hit: the plane was staged three planes earlier)
+  float4 an = make_float4(0.f, 0.f, 0.f, 0.f), bo = an;
+  if (act) {
+    an = *reinterpret_cast<const float4*>(f.pn + (size_t)zb * plane + gof);
+    bo = *reinterpret_cast<const float4*>(f.po + (size_t)zb * plane + gof);
+  }
   int kc_loaded = -1;
   // ring positions m % 5 and m % 3, advanced per plane (no integer division in the loop)
   int m5 = 0, m3 = 0;
   auto r5 = [](int a) { return a >= 5 ? a - 5 : a; };
   auto r3 = [](int a) { return a >= 3 ? a - 3 : a; };
   for (int z = zb; z < ze; ++z, m5 = r5(m5 + 1), m3 = r3(m3 + 1)) {
-    star_store(r5(m5 + 4), rg);
+    star_store(r5(m5 + 4));
     const int kc = z >> RS;
     __syncthreads();
     // one velocity box: every reader of the previous layer has passed the barrier above
@@ -665,13 +674,10 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
       vel_load(kc);
       kc_loaded = kc;
     }
-    if (z + 1 < ze) star_load(z + 3, rg);
+    if (z + 1 < ze) star_load(z + 3);
     mu_plane(z + 1, r5(m5 + 2), r5(m5 + 3), r5(m5 + 4), r3(m3 + 2));
     __syncthreads();
     if (!act) continue;
-    // owned phi^n and phi^{n-1} of this plane (read from L2: the plane was staged three planes ago)
-    const float4 an = *reinterpret_cast<const float4*>(f.pn + (size_t)z * plane + gof);
-    const float4 bo = *reinterpret_cast<const float4*>(f.po + (size_t)z * plane + gof);
     const float* pm = ps + r5(m5 + 1) * TL::SPF + 4;
     const float* pc = ps + r5(m5 + 2) * TL::SPF + 4;
     const float* pq = ps + r5(m5 + 3) * TL::SPF + 4;
@@ -741,6 +747,10 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
       out[i] = dv[i] * inv_mldt - adv * inv_ml + lap;
     }
     *reinterpret_cast<float4*>(R + (size_t)z * plane + gof) = make_float4(out[0], out[1], out[2], out[3]);
+    if (z + 1 < ze) {
+      an = *reinterpret_cast<const float4*>(f.pn + (size_t)(z + 1) * plane + gof);
+      bo = *reinterpret_cast<const float4*>(f.po + (size_t)(z + 1) * plane + gof);
+    }
   }
 }
 
