@@ -581,17 +581,25 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
     const float* pq = ps + sp1 * TL::SPF + 4;
 #pragma unroll
     for (int k = 0; k < TL::KM; ++k) {
-      const int e = t + k * TL::NT;
-      if (e >= TL::NMC) continue;
+      // whole warps take part (the x neighbours come by shuffle); lanes past
+      // the end repeat the last chunk and store nothing
+      const int e0 = t + k * TL::NT;
+      if (e0 - (t & 31) >= TL::NMC) continue;  // warp-uniform
+      const bool valid = e0 < TL::NMC;
+      const int e = valid ? e0 : TL::NMC - 1;
       float4* mo = reinterpret_cast<float4*>(mm) + e;
       if (gz < 0 || gz >= fnz) {
-        *mo = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (valid) *mo = make_float4(0.f, 0.f, 0.f, 0.f);
         continue;
       }
       const int my = e / TL::SXC, mc = e - my * TL::SXC;
       const int o = (my + 1) * TL::SXF + 4 * mc;  // phi* row my+1
       const float4 c = *reinterpret_cast<const float4*>(pc + o);
-      const float l = pc[o - 1], r = pc[o + 4];
+      // x neighbours from the adjacent lanes (consecutive chunks of a row);
+      // shared memory only at a row end or a warp edge
+      float l = __shfl_up_sync(0xffffffffu, c.w, 1), r = __shfl_down_sync(0xffffffffu, c.x, 1);
+      if (mc == 0 || (t & 31) == 0) l = pc[o - 1];
+      if (mc == TL::SXC - 1 || (t & 31) == 31) r = pc[o + 4];
       const float4 up = *reinterpret_cast<const float4*>(pc + o + TL::SXF);
       const float4 dn = *reinterpret_cast<const float4*>(pc + o - TL::SXF);
       const float4 zp = gz + 1 < fnz ? *reinterpret_cast<const float4*>(pq + o) : c;
@@ -614,7 +622,7 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int gx = x0 - 4 + 4 * mc + i;
-          const bool own = rown && gx >= x0 && gx < x0 + TL::TX && gx < fnx;
+          const bool own = valid && rown && gx >= x0 && gx < x0 + TL::TX && gx < fnx;
           const size_t col = (size_t)gy * fnx + gx;
           if (gz == 0) {
             const double g = wall_g(p.cos_bot, (double)cv[i + 1], (double)zpv[i], p.eta);
@@ -628,7 +636,7 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
           }
         }
       }
-      *mo = make_float4(outv[0], outv[1], outv[2], outv[3]);
+      if (valid) *mo = make_float4(outv[0], outv[1], outv[2], outv[3]);
     }
   };
   // ---- owned chunk of this thread ----
@@ -677,7 +685,8 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
     if (z + 1 < ze) star_load(z + 3);
     mu_plane(z + 1, r5(m5 + 2), r5(m5 + 3), r5(m5 + 4), r3(m3 + 2));
     __syncthreads();
-    if (!act) continue;
+    // every lane forms its chunk (the shuffles below need whole warps); lanes
+    // outside the mesh read only inside the tiles and store nothing
     const float* pm = ps + r5(m5 + 1) * TL::SPF + 4;
     const float* pc = ps + r5(m5 + 2) * TL::SPF + 4;
     const float* pq = ps + r5(m5 + 3) * TL::SPF + 4;
@@ -713,7 +722,10 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
       whi[i] = hw1 ? 0.5f * (w1 + vw[(kf1 + 1) * NV + urow + cc]) : w1;
     }
     const float4 c4 = *reinterpret_cast<const float4*>(pc + so);
-    const float pv[6] = {pc[so - 1], c4.x, c4.y, c4.z, c4.w, pc[so + 4]};
+    float pl = __shfl_up_sync(0xffffffffu, c4.w, 1), pr = __shfl_down_sync(0xffffffffu, c4.x, 1);
+    if (cx == 0) pl = pc[so - 1];
+    if (cx == TL::CH - 1) pr = pc[so + 4];
+    const float pv[6] = {pl, c4.x, c4.y, c4.z, c4.w, pr};
     const float4 up = *reinterpret_cast<const float4*>(pc + so + TL::SXF);
     const float4 dn = *reinterpret_cast<const float4*>(pc + so - TL::SXF);
     const float4 zp = *reinterpret_cast<const float4*>(pq + so);
@@ -721,7 +733,10 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
     const float uvp[4] = {up.x, up.y, up.z, up.w}, dvp[4] = {dn.x, dn.y, dn.z, dn.w};
     const float zpp[4] = {zp.x, zp.y, zp.z, zp.w}, zmp[4] = {zm.x, zm.y, zm.z, zm.w};
     const float4 m4 = *reinterpret_cast<const float4*>(mmc + mo);
-    const float mv[6] = {mmc[mo - 1], m4.x, m4.y, m4.z, m4.w, mmc[mo + 4]};
+    float ml = __shfl_up_sync(0xffffffffu, m4.w, 1), mr = __shfl_down_sync(0xffffffffu, m4.x, 1);
+    if (cx == 0) ml = mmc[mo - 1];
+    if (cx == TL::CH - 1) mr = mmc[mo + 4];
+    const float mv[6] = {ml, m4.x, m4.y, m4.z, m4.w, mr};
     const float4 mu4 = *reinterpret_cast<const float4*>(mmc + mo + TL::SXF);
     const float4 md4 = *reinterpret_cast<const float4*>(mmc + mo - TL::SXF);
     const float4 mzp4 = *reinterpret_cast<const float4*>(mmp + mo);
@@ -746,6 +761,7 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
       lap = (lap + mzp + mzm - 2 * m0) * q.ih2;
       out[i] = dv[i] * inv_mldt - adv * inv_ml + lap;
     }
+    if (!act) continue;
     *reinterpret_cast<float4*>(R + (size_t)z * plane + gof) = make_float4(out[0], out[1], out[2], out[3]);
     if (z + 1 < ze) {
       an = *reinterpret_cast<const float4*>(f.pn + (size_t)(z + 1) * plane + gof);
