@@ -287,11 +287,17 @@ namespace pf {
 // ---------------------------------------------------------------------------
 struct GrMarch {
   static constexpr int CX = 32, CY = 8, NT = CX * CY;
-  static constexpr int FX = 2 * CX + 1, FY = 2 * CY + 1, FP = FX * FY;  // G region (fine)
-  static constexpr int PX = FX + 2, PY = FY + 2, PP = PX * PY;          // phi with halo
+  static constexpr int FX = 2 * CX + 1, FY = 2 * CY + 1, FN = FX * FY;  // G region (fine)
+  static constexpr int PX = FX + 2, PY = FY + 2, PN = PX * PY;          // phi with halo
+  // row strides even (G rows one wider: they are stored one column to the
+  // right) so that every pair starting at an even index is one aligned
+  // two-element load; slot sizes even for the same reason
+  static constexpr int SGX = FX + 1, FP = SGX * FY;
+  static constexpr int SPX = PX + 1, PP = SPX * PY;
+  static_assert(SPX == FX + 3 && SGX % 2 == 0 && SPX % 2 == 0 && FP % 2 == 0 && PP % 2 == 0, "G tile layout");
   static constexpr int NPS = 4;
-  static constexpr int KP = (PP + NT - 1) / NT;
-  static constexpr int KG = (FP + NT - 1) / NT;
+  static constexpr int KP = (PN + NT - 1) / NT;
+  static constexpr int KG = (FN + NT - 1) / NT;
   static constexpr int smem_elems() { return NPS * PP + 2 * FP; }
 };
 
@@ -303,12 +309,27 @@ struct Quad {
 };
 
 template <class T>
+struct Pair;
+template <>
+struct Pair<float> {
+  using type = float2;
+};
+template <>
+struct Pair<double> {
+  using type = double2;
+};
+
+template <class T>
 __device__ __forceinline__ Quad<T> quad_sums(const T* p, int o, int sx) {
-  // p[o + b * sx + a], a, b in {-1, 0, 1}
+  // p[o + b * sx + a], a, b in {-1, 0, 1}; o and sx even, p two-element aligned:
+  // each row is read as the pairs (-2, -1) and (0, 1)
+  using P2 = typename Pair<T>::type;
   T rlo[3], rhi[3];
 #pragma unroll
   for (int b = -1; b <= 1; ++b) {
-    const T m = p[o + b * sx - 1], c = p[o + b * sx], q = p[o + b * sx + 1];
+    const P2 lo = *reinterpret_cast<const P2*>(p + o + b * sx - 2);
+    const P2 hi = *reinterpret_cast<const P2*>(p + o + b * sx);
+    const T m = lo.y, c = hi.x, q = hi.y;
     rlo[b + 1] = m + c;
     rhi[b + 1] = c + q;
   }
@@ -328,7 +349,7 @@ __global__ void __launch_bounds__(GrMarch::NT, 3) k_ch_G_restrict_march(const T*
   using TL = GrMarch;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* ps = reinterpret_cast<T*>(smraw);  // [NPS][PY][PX], fine plane zf at slot (zf + 1) & 3
-  T* gs = ps + TL::NPS * TL::PP;        // [2][FY][FX], fine plane zf at slot zf & 1
+  T* gs = ps + TL::NPS * TL::PP;        // [2][FY][SGX], fine plane zf at slot zf & 1
   const int t = threadIdx.x;
   const int cx0 = blockIdx.x * TL::CX, cy0 = blockIdx.y * TL::CY;
   const int kb = blockIdx.z * nkc, ke = min(kb + nkc, d.nz + 1);  // coarse layers kb..ke-1 (nz: top face)
@@ -336,28 +357,29 @@ __global__ void __launch_bounds__(GrMarch::NT, 3) k_ch_G_restrict_march(const T*
   const size_t plane = (size_t)fnx * fny;
   const int fx0 = 2 * cx0 - 2, fy0 = 2 * cy0 - 2;  // fine origin of the phi tile
   // per-thread staging offsets (x/y part), fixed for the march
-  int sxy[TL::KP];
+  // staged element e = yy * PX + xx sits at yy * SPX + xx = e + yy in a slot
+  int sxy[TL::KP], sso[TL::KP];
 #pragma unroll
   for (int kq = 0; kq < TL::KP; ++kq) {
     const int e = t + kq * TL::NT;
     sxy[kq] = -1;
-    if (e < TL::PP) {
+    sso[kq] = 0;
+    if (e < TL::PN) {
       const int yy = e / TL::PX, xx = e - yy * TL::PX;
       sxy[kq] = pmod_m(fy0 + yy, fny) * fnx + pmod_m(fx0 + xx, fnx);
+      sso[kq] = e + yy;
     }
   }
   // per-thread G positions: offset in the phi tile, and the wall column
-  int go[TL::KG], gcol[TL::KG];
+  // G element e = yy * FX + xx: its row yy (-1: none); it reads phi at
+  // (yy + 1) * SPX + xx + 1 = e + 3 yy + FX + 4 (SPX = FX + 3) and is stored at
+  // yy * SGX + xx + 1 = e + yy + 1 (SGX = FX + 1; one column to the right, so
+  // that fine x even lands on an even index)
+  int gy[TL::KG];
 #pragma unroll
   for (int kq = 0; kq < TL::KG; ++kq) {
     const int e = t + kq * TL::NT;
-    go[kq] = -1;
-    gcol[kq] = 0;
-    if (e < TL::FP) {
-      const int yy = e / TL::FX, xx = e - yy * TL::FX;
-      go[kq] = (yy + 1) * TL::PX + (xx + 1);
-      gcol[kq] = pmod_m(fy0 + 1 + yy, fny) * fnx + pmod_m(fx0 + 1 + xx, fnx);
-    }
+    gy[kq] = e < TL::FN ? e / TL::FX : -1;
   }
   auto load_plane = [&](int zf, T (&reg)[TL::KP]) {
     const size_t zo = (size_t)min(max(zf, 0), fnz - 1) * plane;
@@ -368,10 +390,8 @@ __global__ void __launch_bounds__(GrMarch::NT, 3) k_ch_G_restrict_march(const T*
   auto store_plane = [&](int zf, const T (&reg)[TL::KP]) {
     T* p = ps + ((zf + 1) & 3) * TL::PP;
 #pragma unroll
-    for (int kq = 0; kq < TL::KP; ++kq) {
-      const int e = t + kq * TL::NT;
-      if (e < TL::PP) p[e] = reg[kq];
-    }
+    for (int kq = 0; kq < TL::KP; ++kq)
+      if (sxy[kq] >= 0) p[sso[kq]] = reg[kq];
   };
   // G of fine plane zf (0 <= zf < fnz) into slot zf & 1, from phi planes zf-1..zf+1
   auto g_plane = [&](int zf) {
@@ -381,27 +401,31 @@ __global__ void __launch_bounds__(GrMarch::NT, 3) k_ch_G_restrict_march(const T*
     T* g = gs + (zf & 1) * TL::FP;
 #pragma unroll
     for (int kq = 0; kq < TL::KG; ++kq) {
+      if (gy[kq] < 0) continue;
       const int e = t + kq * TL::NT;
-      if (go[kq] < 0) continue;
-      const int o = go[kq];
+      const int o = e + 3 * gy[kq] + TL::FX + 4;
       const T c0 = pc[o];
       T lap = pc[o + 1] + pc[o - 1] - 2 * c0;
-      lap += pc[o + TL::PX] + pc[o - TL::PX] - 2 * c0;
+      lap += pc[o + TL::SPX] + pc[o - TL::SPX] - 2 * c0;
       const T czp = zf + 1 < fnz ? pq[o] : c0;
       const T czm = zf > 0 ? pm[o] : c0;
       lap = (lap + czp + czm - 2 * c0) * q.ih2;
       T B = 0;
-      if (zf == 0) B += (T)gwall[gcol[kq]] * q.ih;
-      if (zf == fnz - 1) B += (T)gwall[plane + gcol[kq]] * q.ih;
-      g[e] = q.lam * (-(lap + B) + c0 * (c0 * c0 - 1) * q.ie2);
+      if (zf == 0 || zf == fnz - 1) {
+        const int yy = gy[kq], xx = e - yy * TL::FX;
+        const size_t gcol = (size_t)pmod_m(fy0 + 1 + yy, fny) * fnx + pmod_m(fx0 + 1 + xx, fnx);
+        if (zf == 0) B += (T)gwall[gcol] * q.ih;
+        if (zf == fnz - 1) B += (T)gwall[plane + gcol] * q.ih;
+      }
+      g[e + gy[kq] + 1] = q.lam * (-(lap + B) + c0 * (c0 * c0 - 1) * q.ie2);
     }
   };
   // this thread's coarse cell and its fine centre (2i, 2j) in the tiles
   const int lx = t % TL::CX, ly = t / TL::CX;
   const int i = cx0 + lx, j = cy0 + ly;
   const bool own = i < d.nx && j < d.ny;
-  const int po = (2 * ly + 2) * TL::PX + (2 * lx + 2);  // phi tile: fine (2i, 2j)
-  const int gq = (2 * ly + 1) * TL::FX + (2 * lx + 1);  // G region: fine (2i, 2j)
+  const int po = (2 * ly + 2) * TL::SPX + (2 * lx + 2);  // phi tile: fine (2i, 2j), even
+  const int gq = (2 * ly + 1) * TL::SGX + (2 * lx + 2);  // G region: fine (2i, 2j), even
   const T eighth = (T)0.125;
   Quad<T> qpm{}, qgm{};  // sums of fine plane 2k-1
   T reg[TL::KP];
@@ -416,8 +440,8 @@ __global__ void __launch_bounds__(GrMarch::NT, 3) k_ch_G_restrict_march(const T*
   if (kb > 0) {
     g_plane(2 * kb - 1);
     __syncthreads();
-    qpm = quad_sums(ps + ((2 * kb) & 3) * TL::PP, po, TL::PX);
-    qgm = quad_sums(gs + ((2 * kb - 1) & 1) * TL::FP, gq, TL::FX);
+    qpm = quad_sums(ps + ((2 * kb) & 3) * TL::PP, po, TL::SPX);
+    qgm = quad_sums(gs + ((2 * kb - 1) & 1) * TL::FP, gq, TL::SGX);
   }
   // phi planes 2k+1, 2k+2 of the next layer are prefetched into registers
   T ra[TL::KP], rb[TL::KP];
@@ -440,10 +464,10 @@ __global__ void __launch_bounds__(GrMarch::NT, 3) k_ch_G_restrict_march(const T*
       g_plane(2 * k);
       g_plane(2 * k + 1);
       __syncthreads();
-      const Quad<T> p0 = quad_sums(ps + ((2 * k + 1) & 3) * TL::PP, po, TL::PX);
-      const Quad<T> p1 = quad_sums(ps + ((2 * k + 2) & 3) * TL::PP, po, TL::PX);
-      const Quad<T> g0 = quad_sums(gs + ((2 * k) & 1) * TL::FP, gq, TL::FX);
-      const Quad<T> g1 = quad_sums(gs + ((2 * k + 1) & 1) * TL::FP, gq, TL::FX);
+      const Quad<T> p0 = quad_sums(ps + ((2 * k + 1) & 3) * TL::PP, po, TL::SPX);
+      const Quad<T> p1 = quad_sums(ps + ((2 * k + 2) & 3) * TL::PP, po, TL::SPX);
+      const Quad<T> g0 = quad_sums(gs + ((2 * k) & 1) * TL::FP, gq, TL::SGX);
+      const Quad<T> g1 = quad_sums(gs + ((2 * k + 1) & 1) * TL::FP, gq, TL::SGX);
       if (k == 0) {  // fine plane -1 mirrors plane 0
         qpm = p0;
         qgm = g0;
