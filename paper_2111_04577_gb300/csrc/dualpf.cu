@@ -322,7 +322,7 @@ struct Impl : ImplBase {
   ~Impl() override {
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
     for (auto e : mark_ev) cudaEventDestroy(e);
-    for (cudaEvent_t e : {ev_fork, ev_join, ev_ns, ev_v, ev_w})
+    for (cudaEvent_t e : {ev_fork, ev_join, ev_ns, ev_v, ev_w, ev_z0, ev_z1})
       if (e) cudaEventDestroy(e);
     if (st2) cudaStreamDestroy(st2);
     if (st3) cudaStreamDestroy(st3);
@@ -340,11 +340,13 @@ struct Impl : ImplBase {
   // streams; st3 and the events below serve that fork/join
   cudaStream_t st3 = nullptr;
   cudaEvent_t ev_ns = nullptr, ev_v = nullptr, ev_w = nullptr;
+  // the pressure's mean mode is solved on st3 beside the other columns
+  cudaEvent_t ev_z0 = nullptr, ev_z1 = nullptr;
   void ensure_side_stream() {
     if (st2) return;
     PF_CUDA_TRY(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
     PF_CUDA_TRY(cudaStreamCreateWithFlags(&st3, cudaStreamNonBlocking));
-    for (cudaEvent_t* e : {&ev_fork, &ev_join, &ev_ns, &ev_v, &ev_w})
+    for (cudaEvent_t* e : {&ev_fork, &ev_join, &ev_ns, &ev_v, &ev_w, &ev_z0, &ev_z1})
       PF_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   }
   // launches issued while alive go to stream s (the launchers use the member st)
@@ -538,6 +540,25 @@ struct Impl : ImplBase {
     zs.shift1 = s1;
     zs.shift2 = s2;
     zs.scale = scale;
+    // the mean mode (kx = ky = 0) of the pressure has its own solve, which the
+    // column solve skips; outside pf_profile it runs on st3 at the same time
+    auto zero_mode = [&]() {
+      mark("zero_mode");
+      if ((size_t)2 * rows * sizeof(double) <= (size_t)kMaxSmem)
+        k_zero_mode_smem<T><<<1, 256, 2 * rows * sizeof(double), st>>>(data, rows, ny, pitch, h2, scale);
+      else
+        k_zero_mode<T><<<1, 32, 0, st>>>(data, rows, ny, pitch, h2, scale, zwork);
+    };
+    const bool zside = poisson && !prof && st3 != nullptr;
+    if (zside) {
+      PF_CUDA_TRY(cudaEventRecord(ev_z0, st));
+      PF_CUDA_TRY(cudaStreamWaitEvent(st3, ev_z0, 0));
+      {
+        OnStream on(st, st3);
+        zero_mode();
+      }
+      PF_CUDA_TRY(cudaEventRecord(ev_z1, st3));
+    }
     mark(two ? "zsolve_pair" : "zsolve");
     const int txs = tune[PF_TUNE_ZSOLVE_COLS] > 0 ? tune[PF_TUNE_ZSOLVE_COLS] : 16;
     const int nseg = (rows + ZSEG - 1) / ZSEG;
@@ -551,13 +572,8 @@ struct Impl : ImplBase {
       dim3 grid((ncol + tx - 1) / tx, ny);
       k_zsolve<T, TC><<<grid, 256, sm, st>>>(data, ex, ey, zs, tx);
     }
-    if (poisson) {
-      mark("zero_mode");
-      if ((size_t)2 * rows * sizeof(double) <= (size_t)kMaxSmem)
-        k_zero_mode_smem<T><<<1, 256, 2 * rows * sizeof(double), st>>>(data, rows, ny, pitch, h2, scale);
-      else
-        k_zero_mode<T><<<1, 32, 0, st>>>(data, rows, ny, pitch, h2, scale, zwork);
-    }
+    if (zside) PF_CUDA_TRY(cudaStreamWaitEvent(st, ev_z1, 0));
+    else if (poisson) zero_mode();
   }
 
   // one transform solve on the coarse mesh: rhs (real, lines of nx) -> out

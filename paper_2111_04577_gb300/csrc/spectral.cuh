@@ -263,7 +263,8 @@ __device__ __forceinline__ void k_zsolve_b(cpx<T>* __restrict__ data, const doub
       R * tx,
       [&](int e) {
         const int k = qdiv(e, tx, itx), c = e - k * tx;
-        return c < ncol ? gbase[(size_t)k * zstride + c] : mk<T>(0, 0);
+        const bool mean_mode = zs.skip_zero && col0 + c == 0 && ky == 0;  // k_zero_mode's column
+        return c < ncol && !mean_mode ? gbase[(size_t)k * zstride + c] : mk<T>(0, 0);
       },
       [&](int e, cpx<T> v) { tile[e] = v; });
   __syncthreads();

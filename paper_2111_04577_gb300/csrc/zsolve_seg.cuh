@@ -98,12 +98,15 @@ __global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 2 : 1) k_zsolve_seg(cpx
   // ---- loads first: the rows of this lane, in flight during the factor phase ----
   T* gcol = reinterpret_cast<T*>(data + (size_t)ky * zs.pitch + col0) + lane;
   const size_t zstride = (size_t)zs.ny * zs.pitch * 2;  // reals between rows
+  // the (0,0) column of a Poisson solve belongs to k_zero_mode (which may run
+  // at the same time): neither read nor written here
+  const bool keep = in && !(zs.skip_zero && col == 0 && ky == 0);
   TC v[ZSEG];
   {
     const T* gp = gcol + (size_t)k0 * zstride;
 #pragma unroll
     for (int j = 0; j < ZSEG; ++j) {
-      v[j] = (in && j < nk) ? (TC)*gp : (TC)0;
+      v[j] = (keep && j < nk) ? (TC)*gp : (TC)0;
       gp += zstride;
     }
   }
@@ -199,7 +202,6 @@ __global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 2 : 1) k_zsolve_seg(cpx
     cB[(size_t)(S + s) * L + lane] = z;
   });
   __syncthreads();
-  const bool keep = in && !(zs.skip_zero && col == 0 && ky == 0);
   auto store = [&](auto F) {
     constexpr bool FULL = decltype(F)::value;
     if (!keep) return;
