@@ -218,10 +218,13 @@ __global__ void __launch_bounds__(1024) k_irfft_x_reg(const cpx<T>* __restrict__
 // Complex FFT along y, in place (as k_fft_y): a CTA of NT * TXC threads
 // (NT = N/E) owns TXC consecutive kx columns of one z level; thread (t, col) =
 // threadIdx (t * TXC + col), so each warp reads rows of TXC contiguous values.
-// smem: TXC * fft_pad_len(N) complex.
+// smem: TXC * fft_pad_len(N) complex.  FP32 lines of 512 and more are
+// compiled for two 512-thread CTAs per SM (64 registers, a few spilled): the
+// transform waits on DRAM, and twice the resident warps measured faster; the
+// shorter lines measured faster without the cap.
 // ---------------------------------------------------------------------------
 template <class T, int N, int E>
-__global__ void __launch_bounds__(512) k_fft_y_reg(cpx<T>* __restrict__ data, int pitch, int ncol,
+__global__ void __launch_bounds__(512, (sizeof(T) == 4 && N >= 512) ? 2 : 1) k_fft_y_reg(cpx<T>* __restrict__ data, int pitch, int ncol,
                                                    const cpx<T>* __restrict__ tw, int sign) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int NT = N / E;
