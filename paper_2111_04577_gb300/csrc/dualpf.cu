@@ -729,8 +729,12 @@ struct Impl : ImplBase {
     coarse_solve_pro(DivPro<T>{u[fo], v[fo], wt, d, (T)(p.gamma0 * p.rho0 / p.dt), (T)(1.0 / d.dx)}, pp, spP, d.nz,
                      Z_NEUMANN, 0.0, true);
     mark("correct");
-    k_correct<T><<<lw.grid, lw.block, 0, st>>>(u[fo], v[fo], wt, w[fo], pp, pr[fc], pr[fo], d,
-                                                  (T)(p.dt / (p.gamma0 * p.rho0)));
+    {
+      constexpr int kzc = 8;
+      const dim3 gc(d.ny * ((d.nz + 1 + kzc - 1) / kzc), lw.grid.y);
+      k_correct_z<T><<<gc, lw.block, 0, st>>>(u[fo], v[fo], wt, w[fo], pp, pr[fc], pr[fo], d,
+                                               (T)(p.dt / (p.gamma0 * p.rho0)), kzc);
+    }
     // ---- polymer ----
     if (p.visco && !defer) launch_polymer(fo, st);
   }

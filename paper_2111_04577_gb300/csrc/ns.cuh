@@ -82,4 +82,35 @@ __global__ void k_correct(T* __restrict__ u, T* __restrict__ v, const T* __restr
   k_correct_b(u, v, wt, w, pp, pn, pnew, d, cf, make_int3(blockIdx.x, blockIdx.y, blockIdx.z), smraw);
 }
 
+// The same update, each thread walking kz layers of its (i, j) column: p' of
+// the layer below stays in a register for the w correction.  blockIdx.x =
+// (z chunk, j), blockIdx.y = x block.  Same arithmetic per face as k_correct_b.
+template <class T>
+__global__ void k_correct_z(T* __restrict__ u, T* __restrict__ v, const T* __restrict__ wt, T* __restrict__ w,
+                            const T* __restrict__ pp, const T* __restrict__ pn, T* __restrict__ pnew, Dims d, T cf,
+                            int kz) {
+  const int i = blockIdx.y * blockDim.x + threadIdx.x;
+  if (i >= d.nx) return;
+  const int j = blockIdx.x % d.ny, k0 = (blockIdx.x / d.ny) * kz;
+  const size_t plane = (size_t)d.nx * d.ny;
+  const T iD = (T)(1.0 / d.dx);
+  const int im = wrap(i - 1, d.nx);
+  const size_t col = (size_t)j * d.nx, colm = (size_t)wrap(j - 1, d.ny) * d.nx;
+  T pbelow = k0 > 0 ? pp[(size_t)(k0 - 1) * plane + col + i] : (T)0;
+  const int k1 = min(k0 + kz, d.nz + 1);
+  for (int k = k0; k < k1; ++k) {
+    const size_t id = (size_t)k * plane + col + i;
+    if (k == d.nz) {
+      w[id] = (T)0;
+      break;
+    }
+    const T pc = pp[id];
+    w[id] = k == 0 ? (T)0 : wt[id - plane] - cf * (pc - pbelow) * iD;
+    u[id] = u[id] - cf * (pc - pp[(size_t)k * plane + col + im]) * iD;
+    if (d.dim == 3) v[id] = v[id] - cf * (pc - pp[(size_t)k * plane + colm + i]) * iD;
+    pnew[id] = pn[id] + pc;
+    pbelow = pc;
+  }
+}
+
 }  // namespace pf
