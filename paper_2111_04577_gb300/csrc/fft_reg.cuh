@@ -119,10 +119,11 @@ __device__ __forceinline__ void reg_fft(cpx<T> (&v)[E], cpx<T>* sm, const cpx<T>
 // ---------------------------------------------------------------------------
 // Forward real FFT along x, two real lines per complex transform (as
 // k_rfft_x in spectral.cuh): a CTA of NT * LPC threads owns LPC line pairs.
-// smem: LPC * fft_pad_len(N) complex.
+// smem: LPC * fft_pad_len(N) complex.  FP32 is held to 48 registers (five
+// 256-thread CTAs per SM instead of four), which measured faster.
 // ---------------------------------------------------------------------------
 template <class T, int N, class Pro>
-__global__ void __launch_bounds__(1024) k_rfft_x_reg(Pro pro, cpx<T>* __restrict__ out, int nlines, int pitch,
+__global__ void __launch_bounds__(1024) __maxnreg__(sizeof(T) == 4 ? 48 : 64) k_rfft_x_reg(Pro pro, cpx<T>* __restrict__ out, int nlines, int pitch,
                                                      const cpx<T>* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int NT = N / 8;
