@@ -67,21 +67,21 @@ def replica_value(cells, steps, world, elapsed):
 # sha256 of the source files that define the kernel when the counters were
 # taken: once a kernel changes its traffic reads null until it is measured again.
 TRAFFIC = {
-    "ch_rhs": (14.291, ["paper_2111_04577_gb300/csrc/ch_march.cuh", "paper_2111_04577_gb300/csrc/ch.cuh"], "39d4db9abb361687"),
-    "ns_rhs": (16.661, ["paper_2111_04577_gb300/csrc/ns_rhs.cuh", "paper_2111_04577_gb300/csrc/ns.cuh"], "89cb6e255be9360f"),
-    "polymer_stage2": (13.692, ["paper_2111_04577_gb300/csrc/polymer.cuh"], "a9d3a7007542cba4"),
-    "polymer_stage1": (7.087, ["paper_2111_04577_gb300/csrc/polymer.cuh"], "a9d3a7007542cba4"),
-    "ch_G_restrict": (6.829, ["paper_2111_04577_gb300/csrc/ch_march.cuh", "paper_2111_04577_gb300/csrc/ch.cuh"], "39d4db9abb361687"),
-    "fft_y_fine": (9.197, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "d9ba12d8726567ba"),
-    "fft_y_coarse": (4.041, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "d9ba12d8726567ba"),
-    "zsolve_pair": (4.792, ["paper_2111_04577_gb300/csrc/zsolve_seg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh"], "0cbe4d8535a29f68"),
-    "ch_ifftx_finish": (14.027, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "d9ba12d8726567ba"),
-    "zsolve": (2.028, ["paper_2111_04577_gb300/csrc/zsolve_seg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh"], "0cbe4d8535a29f68"),
-    "rfft_x_fine": (5.074, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "d9ba12d8726567ba"),
-    "irfft_x_coarse": (2.018, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "d9ba12d8726567ba"),
-    "correct": (2.487, ["paper_2111_04577_gb300/csrc/ns.cuh"], "d1c3da3fba12bb38"),
-    "rfft_x_coarse": (1.487, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "d9ba12d8726567ba"),
-    "div_rfft_x_coarse": (1.486, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "d9ba12d8726567ba"),
+    "ch_rhs": (14.343, ["paper_2111_04577_gb300/csrc/ch_march.cuh", "paper_2111_04577_gb300/csrc/ch.cuh"], "a92867c086d9aff2"),
+    "ns_rhs": (16.801, ["paper_2111_04577_gb300/csrc/ns_rhs.cuh", "paper_2111_04577_gb300/csrc/ns.cuh"], "66032cbf66bfe48a"),
+    "polymer_stage2": (13.691, ["paper_2111_04577_gb300/csrc/polymer.cuh"], "a9d3a7007542cba4"),
+    "polymer_stage1": (7.1, ["paper_2111_04577_gb300/csrc/polymer.cuh"], "a9d3a7007542cba4"),
+    "fft_y_fine": (10.604, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "5c8076e30bc3f4c9"),
+    "fft_y_coarse": (4.041, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "5c8076e30bc3f4c9"),
+    "ch_G_restrict": (6.76, ["paper_2111_04577_gb300/csrc/ch_march.cuh", "paper_2111_04577_gb300/csrc/ch.cuh"], "a92867c086d9aff2"),
+    "ch_ifftx_finish": (14.028, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "5c8076e30bc3f4c9"),
+    "zsolve_pair": (4.659, ["paper_2111_04577_gb300/csrc/zsolve_seg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh"], "e06825567d465ee1"),
+    "zsolve": (2.031, ["paper_2111_04577_gb300/csrc/zsolve_seg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh"], "e06825567d465ee1"),
+    "rfft_x_fine": (4.995, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "5c8076e30bc3f4c9"),
+    "irfft_x_coarse": (2.018, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "5c8076e30bc3f4c9"),
+    "rfft_x_coarse": (1.487, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "5c8076e30bc3f4c9"),
+    "correct": (2.486, ["paper_2111_04577_gb300/csrc/ns.cuh"], "23a9f2ee44332b71"),
+    "div_rfft_x_coarse": (1.486, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "5c8076e30bc3f4c9"),
 }
 
 
