@@ -239,6 +239,27 @@ enum { PF_OBJ_WETTED = 0, PF_OBJ_CENTROID_Z = 1 };
 int pf_adjoint(pf_ctx* ctx, int nsteps, int ckpt_every, int objective, double out[3], void* dphi0,
                int dphi0_on_device);
 
+/* Sensitivity of an objective to one scalar parameter through the whole
+ * coupled step of Section 3.2 (forward mode): the Cahn-Hilliard step with its
+ * wetting condition (Eqs. NS25-NS34), the restriction (Eq. dual2), the
+ * projection (Eqs. NS35-NS39) and the log-conformation update (Eqs.
+ * NS40-NS46), velocity and polymer stress included.  From the context's
+ * current state, a derivative-carrying FP64 copy of the state (each value
+ * paired with its derivative with respect to `param`) is advanced nsteps full
+ * steps; the context itself is not advanced.  The derivative follows by the
+ * chain rule through every kernel, so it is exact up to FP64 rounding: the
+ * value a reverse sweep gives for this one parameter.
+ *   param PF_PARAM_WI:        the Weissenberg number Wi = lambda_H (needs a
+ *                             viscoelastic context, wi > 0 and beta < 1)
+ *   param PF_PARAM_THETA_BOT: the bottom contact angle, per degree
+ *   objective: PF_OBJ_WETTED or PF_OBJ_CENTROID_Z, as pf_adjoint
+ * out[0] = J after nsteps steps, out[1] = dJ/d param.  The copy holds every
+ * field in 16 bytes per value (value and derivative) besides the context's
+ * own; its kernels are those of PF_FP64 run on that pair.
+ * Errors: PF_ERR_ARG, PF_ERR_NONFINITE, PF_ERR_CUDA, PF_ERR_NOMEM. */
+enum { PF_PARAM_WI = 0, PF_PARAM_THETA_BOT = 1 };
+int pf_tangent(pf_ctx* ctx, int nsteps, int param, int objective, double out[2]);
+
 /* Launch-shape knobs picked by the autotuner (paper_2111_04577_gb300/autotune.py);
  * 0 restores the built-in default.  They change only how the work is tiled,
  * never the arithmetic of a cell.

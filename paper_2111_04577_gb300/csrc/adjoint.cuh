@@ -145,7 +145,7 @@ __global__ void k_adj_phibar(const T* __restrict__ phis, const T* __restrict__ r
 }
 
 // FP64 partial sums of a double array
-__global__ void k_sum_d(const double* __restrict__ a, size_t n, double* __restrict__ partial) {
+static __global__ void k_sum_d(const double* __restrict__ a, size_t n, double* __restrict__ partial) {
   __shared__ double sh[256];
   double s = 0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) s += a[i];

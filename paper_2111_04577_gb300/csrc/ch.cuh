@@ -28,9 +28,11 @@ struct FineView {
   __device__ __forceinline__ T star(size_t i) const { return (T)2 * pn[i] - po[i]; }
 };
 
-// Contact-angle flux (Eqs. NS15-NS16, NS34 with D_w = 0), FP64.
-__device__ __forceinline__ double wall_g(double cth, double p0, double p1, double eta) {
-  const double w = 1.5 * p0 - 0.5 * p1;
+// Contact-angle flux (Eqs. NS15-NS16, NS34 with D_w = 0), in W = Wide<T>
+// (FP64, or Dual when derivatives are carried).
+template <class W>
+__device__ __forceinline__ W wall_g(W cth, W p0, W p1, double eta) {
+  const W w = 1.5 * p0 - 0.5 * p1;
   return cth * (1.0 - w * w) / (1.4142135623730951 * eta);
 }
 
@@ -89,7 +91,7 @@ struct ChFinish {
 
 // G = lambda (-(L_N phi + B(g)) + f(phi))  (Eq. NS5 with the wetting ghost)
 template <class T>
-__global__ void k_ch_G(const T* __restrict__ phi, const double* __restrict__ gwall, T* __restrict__ G, Dims d,
+__global__ void k_ch_G(const T* __restrict__ phi, const Wide<T>* __restrict__ gwall, T* __restrict__ G, Dims d,
                        PhysT<T> q) {
   RowIdx x;
   if (!row_index(d.fnx, d.fny, x)) return;

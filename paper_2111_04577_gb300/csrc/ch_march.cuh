@@ -51,7 +51,7 @@ __device__ __forceinline__ int pmod_m(int x, int n) {
 // arithmetic is the same)
 template <class T, int MINB>
 __global__ void __launch_bounds__(MarchTile::NT, MINB) k_ch_rhs_march(const FineView<T> f, const CoarseVel<T> vel,
-                                                                T* __restrict__ R, double* __restrict__ gwall,
+                                                                T* __restrict__ R, Wide<T>* __restrict__ gwall,
                                                                 const Dims d, const Phys p, const PhysT<T> q,
                                                                 const T inv_mldt, const T inv_ml, const int nzc) {
   using TL = MarchTile;
@@ -161,12 +161,12 @@ __global__ void __launch_bounds__(MarchTile::NT, MINB) k_ch_rhs_march(const Fine
       lap = (lap + czp + czm - 2 * c0) * q.ih2;
       T B = 0;
       if (gz == 0) {
-        const double g = wall_g(p.cos_bot, (double)c0, (double)czp, p.eta);
+        const Wide<T> g = wall_g(q.cbot, (Wide<T>)c0, (Wide<T>)czp, p.eta);
         if (mcol[k] >= 0) gwall[mcol[k]] = g;
         B += (T)(g / d.h);
       }
       if (gz == fnz - 1) {
-        const double g = wall_g(p.cos_top, (double)c0, (double)czm, p.eta);
+        const Wide<T> g = wall_g(q.ctop, (Wide<T>)c0, (Wide<T>)czm, p.eta);
         if (mcol[k] >= 0) gwall[plane + mcol[k]] = g;
         B += (T)(g / d.h);
       }
@@ -318,6 +318,13 @@ template <>
 struct Pair<double> {
   using type = double2;
 };
+struct DualPair {
+  Dual x, y;
+};
+template <>
+struct Pair<Dual> {
+  using type = DualPair;
+};
 
 template <class T>
 __device__ __forceinline__ Quad<T> quad_sums(const T* p, int o, int sx) {
@@ -343,7 +350,7 @@ __device__ __forceinline__ Quad<T> quad_sums(const T* p, int o, int sx) {
 
 template <class T>
 __global__ void __launch_bounds__(GrMarch::NT, 3) k_ch_G_restrict_march(const T* __restrict__ phi,
-                                                                        const double* __restrict__ gwall,
+                                                                        const Wide<T>* __restrict__ gwall,
                                                                         Restricted<T> out, const Dims d,
                                                                         const PhysT<T> q, const int nkc) {
   using TL = GrMarch;
@@ -649,12 +656,12 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
           const bool own = valid && rown && gx >= x0 && gx < x0 + TL::TX && gx < fnx;
           const size_t col = (size_t)gy * fnx + gx;
           if (gz == 0) {
-            const double g = wall_g(p.cos_bot, (double)cv[i + 1], (double)zpv[i], p.eta);
+            const double g = wall_g(q.cbot, (double)cv[i + 1], (double)zpv[i], p.eta);
             if (own) gwall[col] = g;
             outv[i] -= (float)(g / d.h);
           }
           if (gz == fnz - 1) {
-            const double g = wall_g(p.cos_top, (double)cv[i + 1], (double)zmv[i], p.eta);
+            const double g = wall_g(q.ctop, (double)cv[i + 1], (double)zmv[i], p.eta);
             if (own) gwall[plane + col] = g;
             outv[i] -= (float)(g / d.h);
           }

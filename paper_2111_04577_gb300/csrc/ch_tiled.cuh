@@ -45,7 +45,7 @@ struct RhsTile {
 };
 
 template <class T, int DIM>
-__device__ __forceinline__ void k_ch_rhs_b(const FineView<T> f, const CoarseVel<T> vel, T* __restrict__ R, double* __restrict__ gwall, const Dims d, const Phys p, const PhysT<T> q, const T inv_mldt, const T inv_ml, const int3 bid, unsigned char* smraw) {
+__device__ __forceinline__ void k_ch_rhs_b(const FineView<T> f, const CoarseVel<T> vel, T* __restrict__ R, Wide<T>* __restrict__ gwall, const Dims d, const Phys p, const PhysT<T> q, const T inv_mldt, const T inv_ml, const int3 bid, unsigned char* smraw) {
   using TL = RhsTile<DIM, sizeof(T)>;
   T* ps = reinterpret_cast<T*>(smraw);  // phi*, [SZ][SY][SX]
   T* ms = ps + TL::NS;                  // mu*,  [MZ][MY][MX]
@@ -133,12 +133,12 @@ __device__ __forceinline__ void k_ch_rhs_b(const FineView<T> f, const CoarseVel<
       const bool own = mx >= 1 && mx <= TL::TX && (DIM == 2 || (my >= 1 && my <= TL::TY));
       const int gx = x0 - 1 + mx, gy = DIM == 3 ? y0 - 1 + my : 0;
       if (gz == 0) {
-        const double g = wall_g(p.cos_bot, (double)c0, (double)czp, p.eta);
+        const Wide<T> g = wall_g(q.cbot, (Wide<T>)c0, (Wide<T>)czp, p.eta);
         if (own && gx < fnx && gy < fny) gwall[(size_t)gy * fnx + gx] = g;
         B += (T)(g / d.h);
       }
       if (gz == fnz - 1) {
-        const double g = wall_g(p.cos_top, (double)c0, (double)czm, p.eta);
+        const Wide<T> g = wall_g(q.ctop, (Wide<T>)c0, (Wide<T>)czm, p.eta);
         if (own && gx < fnx && gy < fny) gwall[plane + (size_t)gy * fnx + gx] = g;
         B += (T)(g / d.h);
       }
@@ -176,7 +176,7 @@ __device__ __forceinline__ void k_ch_rhs_b(const FineView<T> f, const CoarseVel<
 }
 
 template <class T, int DIM>
-__global__ void __launch_bounds__(256) k_ch_rhs(const FineView<T> f, const CoarseVel<T> vel, T* __restrict__ R, double* __restrict__ gwall, const Dims d, const Phys p, const PhysT<T> q, const T inv_mldt, const T inv_ml) {
+__global__ void __launch_bounds__(256) k_ch_rhs(const FineView<T> f, const CoarseVel<T> vel, T* __restrict__ R, Wide<T>* __restrict__ gwall, const Dims d, const Phys p, const PhysT<T> q, const T inv_mldt, const T inv_ml) {
   extern __shared__ __align__(16) unsigned char smraw[];
   k_ch_rhs_b<T, DIM>(f, vel, R, gwall, d, p, q, inv_mldt, inv_ml, make_int3(blockIdx.x, blockIdx.y, blockIdx.z), smraw);
 }
@@ -201,7 +201,7 @@ struct GrTile {
 };
 
 template <class T, int DIM, int R>
-__device__ __forceinline__ void k_ch_G_restrict_b(const T* __restrict__ phi, const double* __restrict__ gwall, Restricted<T> out, const Dims d, const PhysT<T> q, const int3 bid, unsigned char* smraw) {
+__device__ __forceinline__ void k_ch_G_restrict_b(const T* __restrict__ phi, const Wide<T>* __restrict__ gwall, Restricted<T> out, const Dims d, const PhysT<T> q, const int3 bid, unsigned char* smraw) {
   using TL = GrTile<DIM>;
   constexpr int RY = DIM == 3 ? R : 1;
   constexpr int GX = TL::GX(R), GY = TL::GY(RY), GZ = TL::GZ(R);
@@ -302,7 +302,7 @@ __device__ __forceinline__ void k_ch_G_restrict_b(const T* __restrict__ phi, con
 }
 
 template <class T, int DIM, int R>
-__global__ void __launch_bounds__(256) k_ch_G_restrict(const T* __restrict__ phi, const double* __restrict__ gwall, Restricted<T> out, const Dims d, const PhysT<T> q) {
+__global__ void __launch_bounds__(256) k_ch_G_restrict(const T* __restrict__ phi, const Wide<T>* __restrict__ gwall, Restricted<T> out, const Dims d, const PhysT<T> q) {
   extern __shared__ __align__(16) unsigned char smraw[];
   k_ch_G_restrict_b<T, DIM, R>(phi, gwall, out, d, q, make_int3(blockIdx.x, blockIdx.y, blockIdx.z), smraw);
 }

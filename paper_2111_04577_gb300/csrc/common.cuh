@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cstdio>
 
+#include "dual.cuh"
+
 namespace pf {
 
 // ---------------------------------------------------------------------------
@@ -74,6 +76,7 @@ struct PhysT {
   T ih, ih2, iD, iD2;                 // fine and coarse inverse spacings
   T ie2, lam;                         // 1/eta^2, lambda
   T dt, ilh, wtau;                    // dt, 1/lambda_H, mu_p/lambda_H
+  Wide<T> cbot, ctop;                 // cos(theta_s) of the two walls (FP64, or carrying a derivative)
 };
 
 // Kernels over rows of a mesh use a 2D grid: blockIdx.x = row (y, z pair),

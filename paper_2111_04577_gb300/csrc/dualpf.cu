@@ -135,7 +135,10 @@ struct ArrEpi {
 };
 
 struct ImplBase {
+  pf_params raw_prm{};  // the parameters as last given to pf_set_params
   virtual ~ImplBase() {}
+  virtual const pf_grid_desc& grid_desc() const = 0;
+  virtual bool params_ready() const = 0;
   virtual void set_params(const pf_params& prm) = 0;
   virtual void field_info(int f, size_t* count, size_t* eb) const = 0;
   virtual void set_field(int f, const void* src, size_t bytes, int on_dev) = 0;
@@ -210,7 +213,7 @@ struct Impl : ImplBase {
   T *phi[2], *u[2], *v[2], *w[2], *pr[2];
   T *theta[6], *theta1[6], *tau[2][6];
   T *mu, *G;
-  double* gwall;
+  Wide<T>* gwall;  // contact-line flux g of both walls (FP64; Dual when derivatives are carried)
   Restricted<T> rs{};
   T *ru, *rv, *rw, *wt, *pp, *dv;
   cpx<T> *spF, *spU, *spV, *spW, *spP;
@@ -218,8 +221,9 @@ struct Impl : ImplBase {
   FftPlan plFx, plFy, plCx, plCy;
   cpx<T> *twFx, *twFy, *twCx, *twCy;
   double *eFx, *eFy, *eCx, *eCy;
-  double* zwork;
+  Wide<T>* zwork;
   double* partial;
+  Wide<T>* wpartial;  // diagnostics partial sums
   int nred_blocks = 0;
   int pc = 0, fc = 0;  // parities: phi^n = phi[pc]; u^n = u[fc], ...
   std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;
@@ -276,7 +280,7 @@ struct Impl : ImplBase {
     }
     mu = ar.get<T>(nf);
     G = ar.get<T>(nf);
-    gwall = ar.get<double>(2 * (size_t)d.fnx * d.fny);
+    gwall = ar.get<Wide<T>>(2 * (size_t)d.fnx * d.fny);
     rs.phic = ar.get<T>(nc);
     rs.Gc = ar.get<T>(nc);
     rs.phifx = ar.get<T>(nc);
@@ -313,9 +317,11 @@ struct Impl : ImplBase {
     eFy = d.dim == 3 ? eigs(d.fny, d.h, d.fny) : eigs(1, d.h, 1);
     eCx = eigs(d.nx, d.dx, d.nx / 2 + 1);
     eCy = d.dim == 3 ? eigs(d.ny, d.dx, d.ny) : eigs(1, d.dx, 1);
-    zwork = ar.get<double>(4 * (size_t)(d.nz + 2));
+    zwork = ar.get<Wide<T>>(4 * (size_t)(d.nz + 2));
     nred_blocks = 2 * 152;
     partial = ar.get<double>((size_t)nred_blocks * RED_N);
+    wpartial = std::is_same<Wide<T>, double>::value ? reinterpret_cast<Wide<T>*>(partial)
+                                                    : ar.get<Wide<T>>((size_t)nred_blocks * RED_N);
     set_smem_limits();
   }
 
@@ -544,8 +550,8 @@ struct Impl : ImplBase {
     // column solve skips; outside pf_profile it runs on st3 at the same time
     auto zero_mode = [&]() {
       mark("zero_mode");
-      if ((size_t)2 * rows * sizeof(double) <= (size_t)kMaxSmem)
-        k_zero_mode_smem<T><<<1, 256, 2 * rows * sizeof(double), st>>>(data, rows, ny, pitch, h2, scale);
+      if ((size_t)2 * rows * sizeof(Wide<T>) <= (size_t)kMaxSmem)
+        k_zero_mode_smem<T><<<1, 256, 2 * rows * sizeof(Wide<T>), st>>>(data, rows, ny, pitch, h2, scale);
       else
         k_zero_mode<T><<<1, 32, 0, st>>>(data, rows, ny, pitch, h2, scale, zwork);
     };
@@ -740,8 +746,11 @@ struct Impl : ImplBase {
   }
 
   // ------------------------------------------------------------------ API
+  const pf_grid_desc& grid_desc() const override { return g; }
+  bool params_ready() const override { return have_params; }
   void set_params(const pf_params& prm) override {
     p = derive(prm, g);
+    raw_prm = prm;
     sigma = prm.sigma;
     prm_S = prm.S;
     q.idt = (T)(1.0 / p.dt);
@@ -767,6 +776,8 @@ struct Impl : ImplBase {
     q.dt = (T)p.dt;
     q.ilh = p.visco ? (T)(1.0 / p.lam_h) : (T)0;
     q.wtau = p.visco ? (T)(p.mu_p1 / p.lam_h) : (T)0;
+    q.cbot = p.cos_bot;
+    q.ctop = p.cos_top;
     have_params = true;
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
     graphs.clear();
@@ -1017,62 +1028,67 @@ struct Impl : ImplBase {
   // dphi0 (optional) receives dJ/d phi^0.  Checkpoints every K steps; each
   // segment is recomputed forward before its reverse sweep.
   void adjoint(int nsteps, int K, int which, double out[3], void* dphi0, int on_dev) override {
-    flush_polymer();
-    if (!have_params) throw ApiError(PF_ERR_ARG, "pf_set_params must precede pf_adjoint");
-    if (nsteps < 1 || K < 1) throw ApiError(PF_ERR_ARG, "nsteps and ckpt_every must be >= 1");
-    if (which != 0 && which != 1) throw ApiError(PF_ERR_ARG, "objective must be PF_OBJ_WETTED or PF_OBJ_CENTROID_Z");
-    const int nseg = (nsteps + K - 1) / K;
-    adj_alloc(K, nseg);
-    const size_t nf = (size_t)d.fnx * d.fny * d.fnz;
-    // forward sweep with checkpoints of the BDF2 state (phi^n, phi^{n-1})
-    for (int s = 0; s < nseg; ++s) {
-      dcopy(ck_n[s], phi[pc]);
-      dcopy(ck_o[s], phi[pc ^ 1]);
-      step(std::min(K, nsteps - s * K), PF_STEP_CH_ONLY);
-    }
-    double dg[6];
-    diagnostics(dg);
-    const double J = which == 0 ? dg[2] : dg[5];
-    dcopy(a_fin_n, phi[pc]);
-    dcopy(a_fin_o, phi[pc ^ 1]);
-    const RowLaunch lf = rows(d.fny * d.fnz, d.fnx);
-    const double D = 0.5 * ((double)nf + dg[0] / std::pow(d.h, d.dim));
-    k_obj_seed<T><<<lf.grid, lf.block, 0, st>>>(a_next, d, which, dg[5], D);
-    PF_CUDA_TRY(cudaMemsetAsync(a_cur, 0, nf * sizeof(T), st));
-    double thb = 0, mb = 0;
-    for (int s = nseg - 1; s >= 0; --s) {
-      const int len = std::min(K, nsteps - s * K);
-      // recompute the segment: st_buf[0] = phi^{sK-1}, st_buf[m+1] = phi^{sK+m}
-      dcopy(phi[pc], ck_n[s]);
-      dcopy(phi[pc ^ 1], ck_o[s]);
-      dcopy(st_buf[0], ck_o[s]);
-      dcopy(st_buf[1], ck_n[s]);
-      for (int m = 1; m <= len; ++m) {
-        step(1, PF_STEP_CH_ONLY);
-        dcopy(st_buf[m + 1], phi[pc]);
+    if constexpr (IsDual<T>::value) {  // derivative-carrying steps have no reverse sweep
+      (void)nsteps, (void)K, (void)which, (void)out, (void)dphi0, (void)on_dev;
+      throw ApiError(PF_ERR_UNSUPPORTED, "the adjoint runs on PF_FP64, PF_MIXED and PF_MIXED_Z64 contexts");
+    } else {
+      flush_polymer();
+      if (!have_params) throw ApiError(PF_ERR_ARG, "pf_set_params must precede pf_adjoint");
+      if (nsteps < 1 || K < 1) throw ApiError(PF_ERR_ARG, "nsteps and ckpt_every must be >= 1");
+      if (which != 0 && which != 1) throw ApiError(PF_ERR_ARG, "objective must be PF_OBJ_WETTED or PF_OBJ_CENTROID_Z");
+      const int nseg = (nsteps + K - 1) / K;
+      adj_alloc(K, nseg);
+      const size_t nf = (size_t)d.fnx * d.fny * d.fnz;
+      // forward sweep with checkpoints of the BDF2 state (phi^n, phi^{n-1})
+      for (int s = 0; s < nseg; ++s) {
+        dcopy(ck_n[s], phi[pc]);
+        dcopy(ck_o[s], phi[pc ^ 1]);
+        step(std::min(K, nsteps - s * K), PF_STEP_CH_ONLY);
       }
-      for (int m = len; m >= 1; --m) adjoint_step(st_buf[m], st_buf[m - 1], st_buf[m + 1], thb, mb);
-    }
-    // phi^{-1} = phi^0 at start-up: both adjoints land on phi^0
-    {
-      // a_tmp = a_next + a_cur
-      std::vector<T> hn(nf), hc(nf);
-      PF_CUDA_TRY(cudaMemcpyAsync(hn.data(), a_next, nf * sizeof(T), cudaMemcpyDeviceToHost, st));
-      PF_CUDA_TRY(cudaMemcpyAsync(hc.data(), a_cur, nf * sizeof(T), cudaMemcpyDeviceToHost, st));
+      double dg[6];
+      diagnostics(dg);
+      const double J = which == 0 ? dg[2] : dg[5];
+      dcopy(a_fin_n, phi[pc]);
+      dcopy(a_fin_o, phi[pc ^ 1]);
+      const RowLaunch lf = rows(d.fny * d.fnz, d.fnx);
+      const double D = 0.5 * ((double)nf + dg[0] / std::pow(d.h, d.dim));
+      k_obj_seed<T><<<lf.grid, lf.block, 0, st>>>(a_next, d, which, dg[5], D);
+      PF_CUDA_TRY(cudaMemsetAsync(a_cur, 0, nf * sizeof(T), st));
+      double thb = 0, mb = 0;
+      for (int s = nseg - 1; s >= 0; --s) {
+        const int len = std::min(K, nsteps - s * K);
+        // recompute the segment: st_buf[0] = phi^{sK-1}, st_buf[m+1] = phi^{sK+m}
+        dcopy(phi[pc], ck_n[s]);
+        dcopy(phi[pc ^ 1], ck_o[s]);
+        dcopy(st_buf[0], ck_o[s]);
+        dcopy(st_buf[1], ck_n[s]);
+        for (int m = 1; m <= len; ++m) {
+          step(1, PF_STEP_CH_ONLY);
+          dcopy(st_buf[m + 1], phi[pc]);
+        }
+        for (int m = len; m >= 1; --m) adjoint_step(st_buf[m], st_buf[m - 1], st_buf[m + 1], thb, mb);
+      }
+      // phi^{-1} = phi^0 at start-up: both adjoints land on phi^0
+      {
+        // a_tmp = a_next + a_cur
+        std::vector<T> hn(nf), hc(nf);
+        PF_CUDA_TRY(cudaMemcpyAsync(hn.data(), a_next, nf * sizeof(T), cudaMemcpyDeviceToHost, st));
+        PF_CUDA_TRY(cudaMemcpyAsync(hc.data(), a_cur, nf * sizeof(T), cudaMemcpyDeviceToHost, st));
+        PF_CUDA_TRY(cudaStreamSynchronize(st));
+        for (size_t i = 0; i < nf; ++i) hn[i] += hc[i];
+        if (dphi0) {
+          if (on_dev) PF_CUDA_TRY(cudaMemcpyAsync(dphi0, hn.data(), nf * sizeof(T), cudaMemcpyHostToDevice, st));
+          else std::memcpy(dphi0, hn.data(), nf * sizeof(T));
+        }
+      }
+      // leave the context at phi^N, as pf_step would
+      dcopy(phi[pc], a_fin_n);
+      dcopy(phi[pc ^ 1], a_fin_o);
       PF_CUDA_TRY(cudaStreamSynchronize(st));
-      for (size_t i = 0; i < nf; ++i) hn[i] += hc[i];
-      if (dphi0) {
-        if (on_dev) PF_CUDA_TRY(cudaMemcpyAsync(dphi0, hn.data(), nf * sizeof(T), cudaMemcpyHostToDevice, st));
-        else std::memcpy(dphi0, hn.data(), nf * sizeof(T));
-      }
+      out[0] = J;
+      out[1] = thb * M_PI / 180.0;
+      out[2] = mb;
     }
-    // leave the context at phi^N, as pf_step would
-    dcopy(phi[pc], a_fin_n);
-    dcopy(phi[pc ^ 1], a_fin_o);
-    PF_CUDA_TRY(cudaStreamSynchronize(st));
-    out[0] = J;
-    out[1] = thb * M_PI / 180.0;
-    out[2] = mb;
   }
 
   // per-kernel average device time over nsteps direct (non-graph) steps
@@ -1165,12 +1181,20 @@ struct Impl : ImplBase {
   }
 
   void diagnostics(double out[6]) override {
-    k_reduce<T><<<nred_blocks, 256, 0, st>>>(phi[pc], d, p, sigma, d.dim == 3 ? d.h : g.ly, partial);
+    Wide<T> w[6];
+    diagnostics_wide(w);
+    for (int q = 0; q < 6; ++q) out[q] = (double)w[q];
+  }
+  // the six diagnostics in Wide<T> (their derivatives too when T carries them)
+  void diagnostics_wide(Wide<T> out[6]) {
+    using W = Wide<T>;
+    k_reduce<T><<<nred_blocks, 256, 0, st>>>(phi[pc], d, p, sigma, d.dim == 3 ? d.h : g.ly, wpartial);
     check_launch();
-    std::vector<double> h((size_t)nred_blocks * RED_N);
-    PF_CUDA_TRY(cudaMemcpyAsync(h.data(), partial, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    std::vector<W> h((size_t)nred_blocks * RED_N);
+    PF_CUDA_TRY(cudaMemcpyAsync(h.data(), wpartial, h.size() * sizeof(W), cudaMemcpyDeviceToHost, st));
     PF_CUDA_TRY(cudaStreamSynchronize(st));
-    double s[RED_N] = {0};
+    W s[RED_N];
+    for (int q = 0; q < RED_N; ++q) s[q] = 0.0;
     for (int b = 0; b < nred_blocks; ++b)
       for (int q = 0; q < RED_N; ++q) s[q] += h[(size_t)b * RED_N + q];
     const double hd = std::pow(d.h, d.dim), hw = std::pow(d.h, d.dim - 1);
@@ -1457,6 +1481,10 @@ static int guarded(pf_ctx* ctx, F&& f) {
   }
 }
 
+// A translation unit that instantiates Impl for another element type
+// (tangent.cu) defines PF_IMPL_ONLY and includes this file without its
+// exported functions.
+#ifndef PF_IMPL_ONLY
 extern "C" {
 
 int pf_init_grid(pf_ctx** out, const pf_grid_desc* g, void* stream) {
@@ -1568,6 +1596,7 @@ int pf_adjoint(pf_ctx* ctx, int nsteps, int ckpt_every, int objective, double ou
 const char* pf_last_error(const pf_ctx* ctx) { return ctx ? ctx->err.c_str() : g_init_err.c_str(); }
 
 }  // extern "C"
+#endif
 
 struct pf_batch {
   std::unique_ptr<pf::BatchBase> impl;
@@ -1584,6 +1613,7 @@ static int bguarded(pf_batch* b, F&& f) {
   return rc;
 }
 
+#ifndef PF_IMPL_ONLY
 extern "C" {
 
 int pf_batch_create(pf_batch** out, int nproblems, const pf_grid_desc* grids, const pf_params* params, void* stream) {
@@ -1672,3 +1702,4 @@ void pf_destroy(pf_ctx* ctx) {
 }
 
 }  // extern "C"
+#endif

@@ -35,6 +35,12 @@ __device__ __forceinline__ double dexpm1<double>(double d) {
   return d / expm1(d);
 }
 
+template <>
+__device__ __forceinline__ Dual dexpm1<Dual>(Dual d) {
+  if (fabs(d.v) < 1e-6) return 1.0 - 0.5 * d + d * d * (1.0 / 12.0);
+  return d / expm1(d);
+}
+
 template <class T>
 __device__ __forceinline__ T fexp(T x) { return exp(x); }
 template <>

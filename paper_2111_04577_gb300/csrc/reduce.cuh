@@ -15,11 +15,13 @@ constexpr int RED_N = 8;  // sum phi, bulk energy density, wall energy, wetted, 
 // FP32 partials (FP64 fields are accumulated in FP64 throughout).
 constexpr int RGROUP = 8;
 
+// The accumulators are Wide<T>: FP64, or Dual when derivatives are carried.
 template <class T>
 __global__ void __launch_bounds__(256) k_reduce(const T* __restrict__ phi, Dims d, Phys p, double sigma, double dy,
-                                                double* __restrict__ partial) {
-  __shared__ double sh[RED_N][256];
-  double acc[RED_N];
+                                                Wide<T>* __restrict__ partial) {
+  using W = Wide<T>;
+  __shared__ W sh[RED_N][256];
+  W acc[RED_N];
 #pragma unroll
   for (int q = 0; q < RED_N; ++q) acc[q] = 0.0;
   const int rows = d.fny * d.fnz, fnx = d.fnx;
@@ -67,7 +69,7 @@ __global__ void __launch_bounds__(256) k_reduce(const T* __restrict__ phi, Dims 
       }
     }
 #pragma unroll
-    for (int q = 0; q < RED_N; ++q) acc[q] += (double)ga[q];
+    for (int q = 0; q < RED_N; ++q) acc[q] += (W)ga[q];
   }
 #pragma unroll
   for (int q = 0; q < RED_N; ++q) sh[q][threadIdx.x] = acc[q];

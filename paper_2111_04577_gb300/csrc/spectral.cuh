@@ -92,7 +92,7 @@ __global__ void k_rfft_x(Pro pro, cpx<T>* __restrict__ out, int n, int nlines, i
 // staging); completed by cp_async_wait_all.
 template <class T>
 __device__ __forceinline__ void cp_async_elem(T* sdst, const T* gsrc) {
-  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8 || sizeof(T) == 16, "4-, 8- or 16-byte elements");
   const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gsrc), "n"((int)sizeof(T)) : "memory");
 }
@@ -359,52 +359,54 @@ __global__ void k_zsolve(cpx<T>* __restrict__ data, const double* __restrict__ e
 // removed: the zero mode set to zero, as in Eq. NS37's solver.  FP64, no
 // division; one thread per real/imaginary part.
 template <class T>
-__device__ __forceinline__ void k_zero_mode_b(cpx<T>* __restrict__ data, int rows, int ny, int pitch, double h2, double scale, double* __restrict__ work, const int3 bid, unsigned char* smraw) {
+__device__ __forceinline__ void k_zero_mode_b(cpx<T>* __restrict__ data, int rows, int ny, int pitch, double h2, double scale, Wide<T>* __restrict__ work, const int3 bid, unsigned char* smraw) {
+  using W = Wide<T>;
   if (threadIdx.x > 1 || bid.x != 0) return;
   const int part = threadIdx.x;
   const size_t zstride = (size_t)ny * pitch * 2;
   T* base = reinterpret_cast<T*>(data) + part;
-  double* xs = work + (size_t)part * rows;
+  W* xs = work + (size_t)part * rows;
   const double hs = h2 * scale;
-  double f = 0.0, x = 0.0, sum = 0.0;
+  W f = 0.0, x = 0.0, sum = 0.0;
   for (int k = 0; k < rows; ++k) {
     xs[k] = x;
     sum += x;
-    f += (double)base[(size_t)k * zstride] * hs;
+    f += (W)base[(size_t)k * zstride] * hs;
     x += f;
   }
-  const double mean = sum / rows;
+  const W mean = sum / (double)rows;
   for (int k = 0; k < rows; ++k) base[(size_t)k * zstride] = (T)(xs[k] - mean);
 }
 
 // The same solve with the column staged in shared memory: every thread loads
 // rows in parallel, one thread per real/imaginary part runs the two running
 // sums there, and the mean-free result is written back in parallel.
-// smem: 2 * rows doubles.
+// smem: 2 * rows elements of Wide<T>.
 template <class T>
 __global__ void k_zero_mode_smem(cpx<T>* __restrict__ data, int rows, int ny, int pitch, double h2, double scale) {
+  using W = Wide<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
-  double* col = reinterpret_cast<double*>(smraw);  // [2][rows]
-  __shared__ double mean[2];
+  W* col = reinterpret_cast<W*>(smraw);  // [2][rows]
+  __shared__ W mean[2];
   const size_t zstride = (size_t)ny * pitch * 2;
   T* base = reinterpret_cast<T*>(data);
   for (int e = threadIdx.x; e < 2 * rows; e += blockDim.x) {
     const int part = e / rows, k = e - part * rows;
-    col[e] = (double)base[(size_t)k * zstride + part];
+    col[e] = (W)base[(size_t)k * zstride + part];
   }
   __syncthreads();
   if (threadIdx.x < 2) {
-    double* c = col + (size_t)threadIdx.x * rows;
+    W* c = col + (size_t)threadIdx.x * rows;
     const double hs = h2 * scale;
-    double f = 0.0, x = 0.0, sum = 0.0;
+    W f = 0.0, x = 0.0, sum = 0.0;
     for (int k = 0; k < rows; ++k) {
-      const double r = c[k];
+      const W r = c[k];
       c[k] = x;
       sum += x;
       f += r * hs;
       x += f;
     }
-    mean[threadIdx.x] = sum / rows;
+    mean[threadIdx.x] = sum / (double)rows;
   }
   __syncthreads();
   for (int e = threadIdx.x; e < 2 * rows; e += blockDim.x) {
@@ -414,7 +416,7 @@ __global__ void k_zero_mode_smem(cpx<T>* __restrict__ data, int rows, int ny, in
 }
 
 template <class T>
-__global__ void k_zero_mode(cpx<T>* __restrict__ data, int rows, int ny, int pitch, double h2, double scale, double* __restrict__ work) {
+__global__ void k_zero_mode(cpx<T>* __restrict__ data, int rows, int ny, int pitch, double h2, double scale, Wide<T>* __restrict__ work) {
   extern __shared__ __align__(16) unsigned char smraw[];
   k_zero_mode_b(data, rows, ny, pitch, h2, scale, work, make_int3(blockIdx.x, blockIdx.y, blockIdx.z), smraw);
 }
