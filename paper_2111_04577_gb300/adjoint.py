@@ -1,11 +1,14 @@
-"""torch.autograd.Function around the library's hand-written CH adjoint.
+"""torch.autograd.Functions around the library's gradients.
 
     J = CHObjective.apply(phi0, theta_bot_deg, mobility, solver, nsteps, ckpt_every, objective)
+    J = CoupledObjective.apply(wi, theta_bot_deg, solver, params, nsteps, objective)
 
-forward: loads phi0 (phi^{-1} = phi^0) into the solver and runs nsteps CH
-steps on the GPU (velocity fixed) to evaluate the objective; backward: reloads
-phi0 and calls pf_adjoint, which re-runs the forward with checkpoints and
-returns dJ/dphi0, dJ/dtheta_bot (per degree) and dJ/dmobility.
+CHObjective.forward loads phi0 (phi^{-1} = phi^0) into the solver and runs
+nsteps CH steps on the GPU (velocity fixed) to evaluate the objective; its
+backward reloads phi0 and calls pf_adjoint, which re-runs the forward with
+checkpoints and returns dJ/dphi0, dJ/dtheta_bot (per degree) and
+dJ/dmobility.  CoupledObjective takes the whole coupled step through
+pf_tangent (forward-mode derivatives in Wi and theta_bot).
 """
 from __future__ import annotations
 
@@ -41,3 +44,34 @@ class CHObjective(torch.autograd.Function):
         dphi_t = torch.from_numpy(np.asarray(dphi, dtype=np.float64) * g).to(dtype=dt, device=dev)
         return (dphi_t, torch.tensor(dth * g, dtype=torch.float64), torch.tensor(dm * g, dtype=torch.float64),
                 None, None, None, None, None)
+
+
+class CoupledObjective(torch.autograd.Function):
+    """J after nsteps full coupled steps (CH, NS, LCR) from the solver's
+    current state, as a function of Wi and theta_bot (degrees).  forward runs
+    pf_tangent for each parameter that requires a gradient (one
+    derivative-carrying run each, which also yields J), backward scales those
+    derivatives.  The solver is not advanced."""
+
+    @staticmethod
+    def forward(ctx, wi, theta_bot_deg, solver, params, nsteps, objective):
+        p = params.__class__(**params.as_dict())
+        p.wi = float(wi)
+        p.theta_bot_deg = float(theta_bot_deg)
+        solver.set_params(p)
+        need = (ctx.needs_input_grad[0], ctx.needs_input_grad[1])
+        grads = [0.0, 0.0]
+        J = None
+        for k, param in enumerate((binding.PF_PARAM_WI, binding.PF_PARAM_THETA_BOT)):
+            if need[k]:
+                J, grads[k] = solver.tangent(int(nsteps), param, int(objective))
+        if J is None:  # no gradient wanted: the value alone, from a run on a copy of the state
+            J, _ = solver.tangent(int(nsteps), binding.PF_PARAM_THETA_BOT, int(objective))
+        ctx.grads = grads
+        return torch.tensor(J, dtype=torch.float64)
+
+    @staticmethod
+    def backward(ctx, gJ):
+        g = float(gJ)
+        return (torch.tensor(ctx.grads[0] * g, dtype=torch.float64),
+                torch.tensor(ctx.grads[1] * g, dtype=torch.float64), None, None, None, None)

@@ -119,3 +119,20 @@ def test_tangent_errors():
     s2.load_state(wl.initial_phi(newt))
     with pytest.raises(binding.PFError):
         s2.tangent(2, binding.PF_PARAM_WI, binding.PF_OBJ_WETTED)
+
+
+def test_coupled_objective_autograd():
+    """torch.autograd through the coupled step: the gradients pf_tangent gives."""
+    import torch
+    from paper_2111_04577_gb300 import adjoint as padj
+    w, vel, n = case(2)
+    s = binding.Solver(w.grid, w.params, binding.PF_FP64)
+    s.load_state(wl.initial_phi(w), vel)
+    wi = torch.tensor(w.params.wi, dtype=torch.float64, requires_grad=True)
+    th = torch.tensor(w.params.theta_bot_deg, dtype=torch.float64, requires_grad=True)
+    J = padj.CoupledObjective.apply(wi, th, s, w.params, n, binding.PF_OBJ_WETTED)
+    (2.0 * J).backward()
+    Jt, dwi = s.tangent(n, binding.PF_PARAM_WI, binding.PF_OBJ_WETTED)
+    _, dth = s.tangent(n, binding.PF_PARAM_THETA_BOT, binding.PF_OBJ_WETTED)
+    assert float(J.detach()) == Jt
+    assert float(wi.grad) == 2.0 * dwi and float(th.grad) == 2.0 * dth
