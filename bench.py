@@ -282,6 +282,58 @@ def side_path(w, grid, precision, steps, warm, stream):
     return grid.fine_cells() * steps / t, t / steps * 1e3
 
 
+def gradients_leg(w, stream, nx=128, steps=10):
+    """Cost of the two gradient paths on the workload's physics at coarse
+    nx x nx x nx/2: pf_tangent (dJ/dWi through the whole coupled step, FP64
+    values and derivatives) and pf_adjoint (reverse sweep of the CH step,
+    velocity fixed, mixed), against the plain FP64 and mixed steps.  Wall
+    clock around each call (synchronising): the tangent's time includes the
+    copy of the state into its derivative-carrying buffers."""
+    import gc
+    import time
+    import torch
+    from paper_2111_04577_gb300 import binding, workloads as wl
+    ww = wl.scaled(w, nx, nx // 2)
+    g = ww.grid
+    out = {"grid": f"coarse {g.nx}x{g.ny}x{g.nz} / fine {2 * g.nx}x{2 * g.ny}x{2 * g.nz}", "steps": steps}
+    s = binding.Solver(g, ww.params, binding.PF_FP64, stream=stream.cuda_stream)
+    s.load_state(wl.initial_phi(ww))
+    s.step(2)
+    s.tangent(2, binding.PF_PARAM_WI, binding.PF_OBJ_WETTED)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J, dJ = s.tangent(steps, binding.PF_PARAM_WI, binding.PF_OBJ_WETTED)
+    t_tan = time.perf_counter() - t0
+    t64 = time_steps(s, stream, steps)
+    out["tangent_wi"] = {"ms_per_step": t_tan / steps * 1e3, "fp64_ms_per_step": t64 / steps * 1e3,
+                         "ratio": t_tan / t64, "J": J, "dJ_dWi": dJ}
+    s.close()
+    del s
+    s = binding.Solver(g, ww.params, binding.PF_MIXED, stream=stream.cuda_stream)
+    s.load_state(wl.initial_phi(ww).astype(s.dtype))
+    s.adjoint(2, 2, binding.PF_OBJ_WETTED, want_phi=False)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.adjoint(steps, 5, binding.PF_OBJ_WETTED, want_phi=True)
+    t_adj = time.perf_counter() - t0
+    s.load_state(wl.initial_phi(ww).astype(s.dtype))
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    s.step(2, binding.PF_STEP_CH_ONLY)
+    a.record(stream)
+    s.step(steps, binding.PF_STEP_CH_ONLY)
+    b.record(stream)
+    b.synchronize()
+    t_ch = a.elapsed_time(b) / 1e3
+    out["ch_adjoint"] = {"ms_per_step": t_adj / steps * 1e3, "ch_step_ms": t_ch / steps * 1e3,
+                         "ratio": t_adj / t_ch, "ckpt_every": 5}
+    s.close()
+    del s
+    gc.collect()
+    torch.cuda.synchronize()
+    return out
+
+
 def batch_leg(stream, nprob=64, steps=20):
     """64 uneven 2D droplets (coarse 64x32 .. 256x128, fine 2x, theta ~ U(30,150),
     Wi ~ U(0,2), beta = 0.5, mixed precision): one persistent launch per step
@@ -495,6 +547,8 @@ def main():
         }
     if rank == 0 and not args.no_compare:
         extra["batch_sweep"] = batch_leg(stream)
+        if w.params.wi > 0:
+            extra["gradients"] = gradients_leg(w, stream)
     cpu = cpu_sample(workload(args.config), 2, 64) if (rank == 0 and not args.no_cpu) else None
 
     if rank == 0:
