@@ -58,6 +58,13 @@ __global__ void k_lapN_axpy(const T* __restrict__ a, const T* __restrict__ b, T 
   out[id] = lap * q.ih2 + (b ? s * b[id] : (T)0);
 }
 
+// out = x + y
+template <class T>
+__global__ void k_add(const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = a[i] + b[i];
+}
+
 // out = x - y
 template <class T>
 __global__ void k_sub(const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ out, size_t n) {

@@ -949,7 +949,7 @@ struct Impl : ImplBase {
                 &a_next, &a_cur, &a_next2, &a_cur2, &a_fin_n, &a_fin_o};
     for (T** w : ws) *w = adj_ar->get<T>(nf);
     a_thb = adj_ar->get<double>((size_t)d.fnx * d.fny);
-    a_part = adj_ar->get<double>((size_t)nred_blocks * 5);
+    a_part = adj_ar->get<double>((size_t)nred_blocks * 5 * K);  // one slot per step of a segment
     adj_K = K;
     adj_nseg = nseg;
   }
@@ -959,6 +959,16 @@ struct Impl : ImplBase {
     PF_CUDA_TRY(cudaMemcpyAsync(dst, src, nf * sizeof(T), cudaMemcpyDeviceToDevice, st));
   }
 
+  // out = (L_N - c)^-1 (L_N + alpha)^-1 in: the forward step's paired transform solve
+  void fine_solve_pair(const T* in, T* out) {
+    const int nlf = d.fny * d.fnz;
+    rfft_x(FineArrPro<T>{in, d.fnx}, spF, d.fnx, nlf, pF, plFx, twFx);
+    if (d.dim == 3) fft_y(spF, d.fny, pF, d.fnx / 2 + 1, d.fnz, plFy, twFy, -1);
+    zsolve(spF, d.fnz, d.fny, pF, d.fnx / 2 + 1, eFx, eFy, Z_NEUMANN, d.h * d.h, p.c, -p.alpha, true,
+           1.0 / ((double)d.fnx * d.fny), false);
+    if (d.dim == 3) fft_y(spF, d.fny, pF, d.fnx / 2 + 1, d.fnz, plFy, twFy, +1);
+    irfft_x(spF, ArrEpi<T>{out, d.fnx}, d.fnx, nlf, pF, plFx, twFx, (T)1);
+  }
   void fine_solve(const T* in, T* out, double shift) {
     const int nlf = d.fny * d.fnz;
     rfft_x(FineArrPro<T>{in, d.fnx}, spF, d.fnx, nlf, pF, plFx, twFx);
@@ -985,7 +995,8 @@ struct Impl : ImplBase {
     dc = da;
   }
 
-  void adjoint_step(const T* pn, const T* po, const T* pnew, double& thb, double& mb) {
+  // one reverse step; its FP64 partial sums go to part[0 .. 5 nb) (read by adjoint_accumulate)
+  void adjoint_step(const T* pn, const T* po, const T* pnew, double* part) {
     const size_t nf = (size_t)d.fnx * d.fny * d.fnz;
     const RowLaunch lf = rows(d.fny * d.fnz, d.fnx);
     const FineView<T> fv{pn, po};
@@ -996,18 +1007,25 @@ struct Impl : ImplBase {
     k_adj_prep<T><<<lf.grid, lf.block, 0, st>>>(fv, vel, a_phis, a_adv, d, q);
     k_sub<T><<<nb, 256, 0, st>>>(pnew, a_phis, a_delta, nf);
     k_lapN_axpy<T><<<lf.grid, lf.block, 0, st>>>(a_delta, a_delta, (T)p.alpha, a_eps, d, q);
-    fine_solve(a_next, a_ebar, -p.alpha);  // (L_N + alpha) eps_bar = phi_bar^{n+1}
-    fine_solve(a_ebar, a_rbar, p.c);       // (L_N - c) R_bar = eps_bar
+    // (L_N + alpha) eps_bar = phi_bar^{n+1}, (L_N - c) R_bar = eps_bar: the two operators
+    // commute, so R_bar is the forward step's paired solve of phi_bar^{n+1}, and
+    // eps_bar = (L_N - c) R_bar is one stencil pass instead of a second solve
+    fine_solve_pair(a_next, a_rbar);
+    k_lapN_axpy<T><<<lf.grid, lf.block, 0, st>>>(a_rbar, a_rbar, (T)(-p.c), a_ebar, d, q);
     k_lapN_axpy<T><<<lf.grid, lf.block, 0, st>>>(a_rbar, (const T*)nullptr, (T)0, a_mubar, d, q);
     k_sub<T><<<nb, 256, 0, st>>>(po, pn, a_tmp, nf);
-    k_dots<T><<<nb, 256, 0, st>>>(a_ebar, a_delta, a_rbar, a_eps, a_rbar, a_tmp, a_rbar, a_adv, nf, a_part);
+    k_dots<T><<<nb, 256, 0, st>>>(a_ebar, a_delta, a_rbar, a_eps, a_rbar, a_tmp, a_rbar, a_adv, nf, part);
     k_adj_phibar<T><<<lf.grid, lf.block, 0, st>>>(a_phis, a_rbar, a_mubar, a_next, a_cur, a_next2, a_cur2, a_thb, vel,
                                                   d, p, q, a1, a2);
-    k_sum_d<<<nb, 256, 0, st>>>(a_thb, (size_t)d.fnx * d.fny, a_part + (size_t)4 * nb);
+    k_sum_d<<<nb, 256, 0, st>>>(a_thb, (size_t)d.fnx * d.fny, part + (size_t)4 * nb);
     check_launch();
-    std::vector<double> h((size_t)5 * nb);
-    PF_CUDA_TRY(cudaMemcpyAsync(h.data(), a_part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-    PF_CUDA_TRY(cudaStreamSynchronize(st));
+    std::swap(a_next, a_next2);
+    std::swap(a_cur, a_cur2);
+  }
+  // the parameter adjoints of one reverse step from its partial sums h[0 .. 5 nb)
+  void adjoint_accumulate(const double* h, double& thb, double& mb) {
+    const int nb = nred_blocks;
+    const T a1 = (T)(1.0 / (p.Ml * p.dt)), a2 = (T)(1.0 / p.Ml);
     double dots[4] = {0, 0, 0, 0}, th = 0;
     for (int b = 0; b < nb; ++b) {
       for (int k = 0; k < 4; ++k) dots[k] += h[(size_t)b * 4 + k];
@@ -1019,8 +1037,6 @@ struct Impl : ImplBase {
     const double M = p.mob;
     mb += -(double)a1 / M * s1 + (double)a2 / M * s2 + c_bar * dc + alpha_bar * da;
     thb += th;
-    std::swap(a_next, a_next2);
-    std::swap(a_cur, a_cur2);
   }
 
   // Gradients of an objective of phi after nsteps CH steps (velocity fixed):
@@ -1063,23 +1079,23 @@ struct Impl : ImplBase {
         dcopy(st_buf[0], ck_o[s]);
         dcopy(st_buf[1], ck_n[s]);
         for (int m = 1; m <= len; ++m) {
-          step(1, PF_STEP_CH_ONLY);
+          run_one(PF_STEP_CH_ONLY, false, false);
+          pc ^= 1;
+          ++steps_done;
           dcopy(st_buf[m + 1], phi[pc]);
         }
-        for (int m = len; m >= 1; --m) adjoint_step(st_buf[m], st_buf[m - 1], st_buf[m + 1], thb, mb);
+        const size_t slot = (size_t)5 * nred_blocks;
+        for (int m = len; m >= 1; --m) adjoint_step(st_buf[m], st_buf[m - 1], st_buf[m + 1], a_part + (len - m) * slot);
+        std::vector<double> h(len * slot);
+        PF_CUDA_TRY(cudaMemcpyAsync(h.data(), a_part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        PF_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int m = len; m >= 1; --m) adjoint_accumulate(h.data() + (len - m) * slot, thb, mb);
       }
       // phi^{-1} = phi^0 at start-up: both adjoints land on phi^0
-      {
-        // a_tmp = a_next + a_cur
-        std::vector<T> hn(nf), hc(nf);
-        PF_CUDA_TRY(cudaMemcpyAsync(hn.data(), a_next, nf * sizeof(T), cudaMemcpyDeviceToHost, st));
-        PF_CUDA_TRY(cudaMemcpyAsync(hc.data(), a_cur, nf * sizeof(T), cudaMemcpyDeviceToHost, st));
-        PF_CUDA_TRY(cudaStreamSynchronize(st));
-        for (size_t i = 0; i < nf; ++i) hn[i] += hc[i];
-        if (dphi0) {
-          if (on_dev) PF_CUDA_TRY(cudaMemcpyAsync(dphi0, hn.data(), nf * sizeof(T), cudaMemcpyHostToDevice, st));
-          else std::memcpy(dphi0, hn.data(), nf * sizeof(T));
-        }
+      if (dphi0) {  // a_tmp = a_next + a_cur, summed on the device
+        k_add<T><<<nred_blocks, 256, 0, st>>>(a_next, a_cur, a_tmp, nf);
+        check_launch();
+        PF_CUDA_TRY(cudaMemcpyAsync(dphi0, a_tmp, nf * sizeof(T), on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
       }
       // leave the context at phi^N, as pf_step would
       dcopy(phi[pc], a_fin_n);
