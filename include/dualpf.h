@@ -257,8 +257,18 @@ int pf_adjoint(pf_ctx* ctx, int nsteps, int ckpt_every, int objective, double ou
  * field in 16 bytes per value (value and derivative) besides the context's
  * own; its kernels are those of PF_FP64 run on that pair.
  * Errors: PF_ERR_ARG, PF_ERR_NONFINITE, PF_ERR_CUDA, PF_ERR_NOMEM. */
-enum { PF_PARAM_WI = 0, PF_PARAM_THETA_BOT = 1 };
+enum { PF_PARAM_WI = 0, PF_PARAM_THETA_BOT = 1, PF_PARAM_PHI0 = 2 };
 int pf_tangent(pf_ctx* ctx, int nsteps, int param, int objective, double out[2]);
+/* pf_tangent with two more choices.
+ *   flags PF_STEP_CH_ONLY: Cahn-Hilliard steps only, the velocity held fixed (the
+ *     model pf_adjoint differentiates); PF_PARAM_WI is then an error.
+ *   param PF_PARAM_PHI0: the directional derivative <dJ/dphi^0, dir> along the
+ *     fine-mesh array dir (FP64, layout of PF_PHI, host or device memory as
+ *     dir_on_device says, read only), with phi^{-1} = phi^0 as at start-up:
+ *     the derivative parts of PF_PHI and PF_PHI_OLD are both set to dir.
+ * dir is ignored for the other parameters. */
+int pf_tangent_ex(pf_ctx* ctx, int nsteps, int param, int objective, int flags, const void* dir, int dir_on_device,
+                  double out[2]);
 
 /* Launch-shape knobs picked by the autotuner (paper_2111_04577_gb300/autotune.py);
  * 0 restores the built-in default.  They change only how the work is tiled,

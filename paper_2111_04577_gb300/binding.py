@@ -27,9 +27,9 @@ EXPORTS = ["pf_init_grid", "pf_set_params", "pf_field_info", "pf_set_fields", "p
            "pf_get_fields", "pf_diagnostics", "pf_profile", "pf_diagnostics_noalloc", "pf_last_error",
            "pf_destroy", "pf_batch_create", "pf_batch_field_info", "pf_batch_set_fields", "pf_batch_get_fields",
            "pf_batch_step", "pf_batch_diagnostics", "pf_batch_last_error", "pf_batch_destroy", "pf_set_tuning",
-           "pf_get_tuning", "pf_adjoint", "pf_batch_adjoint", "pf_tangent"]
+           "pf_get_tuning", "pf_adjoint", "pf_batch_adjoint", "pf_tangent", "pf_tangent_ex"]
 PF_OBJ_WETTED, PF_OBJ_CENTROID_Z = 0, 1
-PF_PARAM_WI, PF_PARAM_THETA_BOT = 0, 1
+PF_PARAM_WI, PF_PARAM_THETA_BOT, PF_PARAM_PHI0 = 0, 1, 2
 PROFILE_NAME = 48
 
 
@@ -92,6 +92,8 @@ def load(path: str = LIB_PATH):
         lib.pf_batch_adjoint.restype = C.c_int
         lib.pf_tangent.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]
         lib.pf_tangent.restype = C.c_int
+        lib.pf_tangent_ex.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int, C.POINTER(C.c_double)]
+        lib.pf_tangent_ex.restype = C.c_int
         lib.pf_set_tuning.argtypes = [vp, C.c_int, C.c_int]
         lib.pf_get_tuning.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
         lib.pf_set_tuning.restype = C.c_int
@@ -211,12 +213,17 @@ class Solver:
             g = g.reshape(self.grid.fine_shape)
         return out[0], out[1], out[2], g
 
-    def tangent(self, nsteps, param=PF_PARAM_WI, objective=PF_OBJ_WETTED):
-        """(J, dJ/dparam) after nsteps full coupled steps from the current state,
-        by forward-mode derivatives (pf_tangent); the solver is not advanced.
-        dJ/dtheta_bot is per degree."""
+    def tangent(self, nsteps, param=PF_PARAM_WI, objective=PF_OBJ_WETTED, flags=0, direction=None):
+        """(J, dJ/dparam) after nsteps steps from the current state, by forward-mode
+        derivatives (pf_tangent_ex); the solver is not advanced.  dJ/dtheta_bot is
+        per degree; with param=PF_PARAM_PHI0, dJ/dparam is <dJ/dphi^0, direction>
+        (direction: a fine-mesh array).  flags=PF_STEP_CH_ONLY holds the velocity."""
         out = (C.c_double * 2)()
-        self._chk(self.lib.pf_tangent(self.h, int(nsteps), int(param), int(objective), out))
+        ptr = None
+        if direction is not None:
+            direction = np.ascontiguousarray(direction, dtype=np.float64).ravel()
+            ptr = direction.ctypes.data_as(C.c_void_p)
+        self._chk(self.lib.pf_tangent_ex(self.h, int(nsteps), int(param), int(objective), int(flags), ptr, 0, out))
         return out[0], out[1]
 
     def set_tuning(self, knob, value):

@@ -9,7 +9,9 @@
 //                    (Eqs. NS41, NS46), derivatives -1/lambda_H^2 and
 //                    -mu_p/lambda_H^2;
 //   theta_s (bottom): cos(theta_s) of the wall flux (Eq. NS34), derivative
-//                    -sin(theta_s) per radian.
+//                    -sin(theta_s) per radian;
+//   phi^0 along v:   the derivative parts of phi^n and phi^{n-1} set to v
+//                    (start-up phi^{-1} = phi^0), giving <dJ/dphi^0, v>.
 // The objective's derivative then follows by the chain rule through every
 // kernel, exactly up to FP64 rounding of the value and derivative parts: the
 // same result a reverse sweep gives for one parameter.
@@ -53,8 +55,23 @@ struct TangentRun {
     }
   }
 
-  void seed(int param) {
+  void seed(int param, const void* dir, int dir_on_device) {
     Impl<Dual, Dual>& I = *impl;
+    if (param == PF_PARAM_PHI0) {
+      if (!dir) throw ApiError(PF_ERR_ARG, "PF_PARAM_PHI0 needs a direction");
+      size_t cnt = 0, eb = 0;
+      I.field_info(PF_PHI, &cnt, &eb);
+      std::vector<double> v(cnt);
+      if (dir_on_device) PF_CUDA_TRY(cudaMemcpy(v.data(), dir, cnt * sizeof(double), cudaMemcpyDeviceToHost));
+      else std::memcpy(v.data(), dir, cnt * sizeof(double));
+      std::vector<Dual> hn(cnt), ho(cnt);
+      I.get_field(PF_PHI, hn.data(), cnt * sizeof(Dual), 0);
+      I.get_field(PF_PHI_OLD, ho.data(), cnt * sizeof(Dual), 0);
+      for (size_t i = 0; i < cnt; ++i) hn[i].d = ho[i].d = v[i];
+      I.set_field(PF_PHI, hn.data(), cnt * sizeof(Dual), 0);  // (sets PF_PHI_OLD too)
+      I.set_field(PF_PHI_OLD, ho.data(), cnt * sizeof(Dual), 0);
+      return;
+    }
     if (param == PF_PARAM_WI) {
       if (!I.p.visco) throw ApiError(PF_ERR_ARG, "Wi has no effect: the context is not viscoelastic");
       const double lh = I.p.lam_h;
@@ -64,7 +81,7 @@ struct TangentRun {
       const double th = I.raw_prm.theta_bot_deg * M_PI / 180.0;
       I.q.cbot = Dual(std::cos(th), -std::sin(th));
     } else {
-      throw ApiError(PF_ERR_ARG, "param must be PF_PARAM_WI or PF_PARAM_THETA_BOT");
+      throw ApiError(PF_ERR_ARG, "param must be PF_PARAM_WI, PF_PARAM_THETA_BOT or PF_PARAM_PHI0");
     }
   }
 };
@@ -73,21 +90,29 @@ struct TangentRun {
 
 extern "C" {
 
-int pf_tangent(pf_ctx* ctx, int nsteps, int param, int objective, double out[2]) {
+int pf_tangent_ex(pf_ctx* ctx, int nsteps, int param, int objective, int flags, const void* dir, int dir_on_device,
+                  double out[2]) {
   if (!ctx || !out) return PF_ERR_ARG;
   return guarded(ctx, [&] {
     if (nsteps < 1) throw pf::ApiError(PF_ERR_ARG, "nsteps must be >= 1");
     if (objective != PF_OBJ_WETTED && objective != PF_OBJ_CENTROID_Z)
       throw pf::ApiError(PF_ERR_ARG, "objective must be PF_OBJ_WETTED or PF_OBJ_CENTROID_Z");
+    if (flags & ~PF_STEP_CH_ONLY) throw pf::ApiError(PF_ERR_ARG, "flags: 0 or PF_STEP_CH_ONLY");
+    if (param == PF_PARAM_WI && (flags & PF_STEP_CH_ONLY))
+      throw pf::ApiError(PF_ERR_ARG, "Wi has no effect on CH steps with the velocity fixed");
     pf::TangentRun run(*ctx->impl, ctx->stream);
-    run.seed(param);
-    run.impl->step(nsteps, 0);
+    run.seed(param, dir, dir_on_device);
+    run.impl->step(nsteps, flags);
     pf::Dual w[6];
     run.impl->diagnostics_wide(w);
     const pf::Dual J = objective == PF_OBJ_WETTED ? w[2] : w[5];
     out[0] = J.v;
     out[1] = param == PF_PARAM_THETA_BOT ? J.d * M_PI / 180.0 : J.d;  // theta per degree, as pf_adjoint
   });
+}
+
+int pf_tangent(pf_ctx* ctx, int nsteps, int param, int objective, double out[2]) {
+  return pf_tangent_ex(ctx, nsteps, param, objective, 0, nullptr, 0, out);
 }
 
 }  // extern "C"

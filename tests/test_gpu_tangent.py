@@ -136,3 +136,25 @@ def test_coupled_objective_autograd():
     _, dth = s.tangent(n, binding.PF_PARAM_THETA_BOT, binding.PF_OBJ_WETTED)
     assert float(J.detach()) == Jt
     assert float(wi.grad) == 2.0 * dwi and float(th.grad) == 2.0 * dth
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_adjoint_dot_product_with_tangent(dim):
+    """The classical adjoint check, between two independent codes: the
+    hand-written reverse sweep of the CH step (velocity fixed) and forward-mode
+    derivatives of the forward kernels.  <dJ/dphi^0, v> and dJ/dtheta agree to
+    FP64 rounding (the benchmark spec: 1e-10 for adjoint against adjoint)."""
+    w, vel, _ = case(dim)
+    n = 8
+    rng = np.random.default_rng(5)
+    for obj in (binding.PF_OBJ_WETTED, binding.PF_OBJ_CENTROID_Z):
+        s = binding.Solver(w.grid, w.params, binding.PF_FP64)
+        s.load_state(wl.initial_phi(w), vel)
+        v = rng.standard_normal(w.grid.fine_shape)
+        J_t, dv = s.tangent(n, binding.PF_PARAM_PHI0, obj, binding.PF_STEP_CH_ONLY, v)
+        _, dth_t = s.tangent(n, binding.PF_PARAM_THETA_BOT, obj, binding.PF_STEP_CH_ONLY)
+        J_a, dth_a, _, dphi = s.adjoint(n, 3, obj)
+        assert abs(J_t - J_a) <= 1e-12 * abs(J_a)
+        dot = float(np.sum(dphi.astype(np.float64) * v))
+        assert abs(dv - dot) <= 1e-10 * max(abs(dot), 1e-300), (dv, dot)
+        assert abs(dth_t - dth_a) <= 1e-10 * abs(dth_a), (dth_t, dth_a)
