@@ -43,6 +43,27 @@ __device__ __forceinline__ Dual dexpm1<Dual>(Dual d) {
 
 template <class T>
 __device__ __forceinline__ T fexp(T x) { return exp(x); }
+
+// x / (e^x - 1) for x <= 0 given ex = e^x (which the caller already has).
+// FP32: for x > -1/4 the Bernoulli series 1 - x/2 + x^2/12 - x^4/720 +
+// x^6/30240 - x^8/1209600 (next term below 3e-14 there); below, x/(ex - 1),
+// where ex - 1 <= -0.22 carries no cancellation.  FP64 and Dual: dexpm1.
+template <class T>
+__device__ __forceinline__ T dexpm1_e(T x, T ex) {
+  (void)ex;
+  return dexpm1<T>(x);
+}
+template <>
+__device__ __forceinline__ float dexpm1_e<float>(float x, float ex) {
+  if (x > -0.25f) {
+    const float x2 = x * x;
+    float p = fmaf(x2, -1.f / 1209600.f, 1.f / 30240.f);
+    p = fmaf(x2, p, -1.f / 720.f);
+    p = fmaf(x2, p, 1.f / 12.f);
+    return fmaf(x2, p, fmaf(x, -0.5f, 1.f));
+  }
+  return __fdividef(x, ex - 1.f);
+}
 template <>
 __device__ __forceinline__ float fexp<float>(float x) { return __expf(x); }
 
@@ -95,7 +116,8 @@ __device__ __forceinline__ void jacobi_rot_sym_f(float (&dg)[N], float (&of)[N =
   const float apq = of[pq];
   if (apq == 0.f) return;
   const float h = dg[q] - dg[p], g = 2.f * apq;
-  const float r = sqrtf(fmaf(h, h, g * g));
+  const float a = fmaf(h, h, g * g);  // > 0 (apq != 0)
+  const float r = a * rsqrtf(a);      // sqrt(a) to a few ulp: t is the rotation's own, c and s follow it
   float t = __fdividef(g, fabsf(h) + r);
   if (h < 0.f) t = -t;
   const float c = rsqrtf(fmaf(t, t, 1.f)), s = t * c;
@@ -272,8 +294,11 @@ __device__ __forceinline__ void polymer_cell(const PolyIn<T>& P, const Dims& d, 
     for (int b = a + 1; b < N; ++b) {
       const T dd = dg[b] - dg[a];
       T o;
-      if (dd > 0) o = (Mt[a][b] + fexp<T>(-dd) * Mt[b][a]) * dexpm1<T>(-dd);
-      else o = (fexp<T>(dd) * Mt[a][b] + Mt[b][a]) * dexpm1<T>(dd);
+      const T x = dd > 0 ? -dd : dd;  // -|dd|
+      const T ex = fexp<T>(x);
+      const T wgt = dexpm1_e<T>(x, ex);
+      if (dd > 0) o = (Mt[a][b] + ex * Mt[b][a]) * wgt;
+      else o = (ex * Mt[a][b] + Mt[b][a]) * wgt;
       H[a][b] = o;
       H[b][a] = o;
     }
