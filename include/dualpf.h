@@ -252,12 +252,14 @@ int pf_adjoint(pf_ctx* ctx, int nsteps, int ckpt_every, int objective, double ou
  *   param PF_PARAM_WI:        the Weissenberg number Wi = lambda_H (needs a
  *                             viscoelastic context, wi > 0 and beta < 1)
  *   param PF_PARAM_THETA_BOT: the bottom contact angle, per degree
+ *   param PF_PARAM_MOBILITY:  the mobility M (with S following M when S = 0
+ *                             selects the bound of Eq. NS30, as pf_adjoint)
  *   objective: PF_OBJ_WETTED or PF_OBJ_CENTROID_Z, as pf_adjoint
  * out[0] = J after nsteps steps, out[1] = dJ/d param.  The copy holds every
  * field in 16 bytes per value (value and derivative) besides the context's
  * own; its kernels are those of PF_FP64 run on that pair.
  * Errors: PF_ERR_ARG, PF_ERR_NONFINITE, PF_ERR_CUDA, PF_ERR_NOMEM. */
-enum { PF_PARAM_WI = 0, PF_PARAM_THETA_BOT = 1, PF_PARAM_PHI0 = 2 };
+enum { PF_PARAM_WI = 0, PF_PARAM_THETA_BOT = 1, PF_PARAM_PHI0 = 2, PF_PARAM_MOBILITY = 3 };
 int pf_tangent(pf_ctx* ctx, int nsteps, int param, int objective, double out[2]);
 /* pf_tangent with two more choices.
  *   flags PF_STEP_CH_ONLY: Cahn-Hilliard steps only, the velocity held fixed (the

@@ -29,7 +29,7 @@ EXPORTS = ["pf_init_grid", "pf_set_params", "pf_field_info", "pf_set_fields", "p
            "pf_batch_step", "pf_batch_diagnostics", "pf_batch_last_error", "pf_batch_destroy", "pf_set_tuning",
            "pf_get_tuning", "pf_adjoint", "pf_batch_adjoint", "pf_tangent", "pf_tangent_ex"]
 PF_OBJ_WETTED, PF_OBJ_CENTROID_Z = 0, 1
-PF_PARAM_WI, PF_PARAM_THETA_BOT, PF_PARAM_PHI0 = 0, 1, 2
+PF_PARAM_WI, PF_PARAM_THETA_BOT, PF_PARAM_PHI0, PF_PARAM_MOBILITY = 0, 1, 2, 3
 PROFILE_NAME = 48
 
 

@@ -203,6 +203,11 @@ struct Impl : ImplBase {
   Dims d{};
   Phys p{};
   PhysT<T> q{};
+  // derivatives, with respect to one parameter, of constants the step forms on
+  // the host (nonzero only in a derivative-carrying step seeded with it)
+  struct {
+    double inv_mldt = 0, inv_ml = 0, c = 0, alpha = 0;
+  } dseed;
   double sigma = 1.0;
   double prm_S = 0.0;  // S as given (0: the Eq. NS30 minimum, which moves with M)
   bool have_params = false;
@@ -532,7 +537,8 @@ struct Impl : ImplBase {
     k_fft_y<T><<<grid, 256, sm, st>>>(data, ny, pitch, ncol, pl, tw, sign, tx);
   }
   void zsolve(cpx<T>* data, int rows, int ny, int pitch, int ncol, const double* ex, const double* ey, int bc,
-              double h2, double s1, double s2, bool two, double scale, bool poisson) {
+              double h2, double s1, double s2, bool two, double scale, bool poisson, double ds1 = 0.0,
+              double ds2 = 0.0) {
     ZSolve zs{};
     zs.rows = rows;
     zs.ny = ny;
@@ -540,11 +546,13 @@ struct Impl : ImplBase {
     zs.ncol = ncol;
     zs.bc = bc;
     zs.two = two ? 1 : 0;
-    zs.same = (!two || std::fabs(s1 - s2) <= 1e-14 * std::fabs(s1)) ? 1 : 0;
+    zs.same = (!two || (std::fabs(s1 - s2) <= 1e-14 * std::fabs(s1) && ds1 == ds2)) ? 1 : 0;
     zs.skip_zero = poisson ? 1 : 0;
     zs.h2 = h2;
     zs.shift1 = s1;
     zs.shift2 = s2;
+    zs.dshift1 = ds1;
+    zs.dshift2 = ds2;
     zs.scale = scale;
     // the mean mode (kx = ky = 0) of the pressure has its own solve, which the
     // column solve skips; outside pf_profile it runs on st3 at the same time
@@ -610,7 +618,11 @@ struct Impl : ImplBase {
     // ---- Cahn-Hilliard on the fine mesh ----
     FineView<T> fv{phi[pc], phi[po]};
     const CoarseVel<T> vel{u[fc], u[fo], v[fc], v[fo], w[fc], w[fo]};
-    const T inv_mldt = (T)(1.0 / (p.Ml * p.dt)), inv_ml = (T)(1.0 / p.Ml);
+    T inv_mldt = (T)(1.0 / (p.Ml * p.dt)), inv_ml = (T)(1.0 / p.Ml);
+    if constexpr (IsDual<T>::value) {
+      inv_mldt.d = dseed.inv_mldt;
+      inv_ml.d = dseed.inv_ml;
+    }
     mark("ch_rhs");
     if (d.dim == 2) {
       using TL = RhsTile<2, sizeof(T)>;
@@ -648,7 +660,7 @@ struct Impl : ImplBase {
     rfft_x(FineArrPro<T>{mu, d.fnx}, spF, d.fnx, nlf, pF, plFx, twFx);
     if (d.dim == 3) fft_y(spF, d.fny, pF, d.fnx / 2 + 1, d.fnz, plFy, twFy, -1);
     zsolve(spF, d.fnz, d.fny, pF, d.fnx / 2 + 1, eFx, eFy, Z_NEUMANN, d.h * d.h, p.c, -p.alpha, true,
-           1.0 / ((double)d.fnx * d.fny), false);
+           1.0 / ((double)d.fnx * d.fny), false, dseed.c, -dseed.alpha);
     if (d.dim == 3) fft_y(spF, d.fny, pF, d.fnx / 2 + 1, d.fnz, plFy, twFy, +1);
     irfft_x(spF, ChFinish<T>{phi[pc], phi[po], d.fnx}, d.fnx, nlf, pF, plFx, twFx, (T)1);
     if (flags & PF_STEP_CH_ONLY) return;

@@ -232,7 +232,19 @@ struct ZSolve {
   int same;        // shift2 == shift1
   int skip_zero;   // the (0,0) column is handled by k_zero_mode
   double h2, shift1, shift2, scale;
+  double dshift1, dshift2;  // derivatives of the shifts (used when TC carries derivatives)
 };
+
+// a shift in the elimination type: with Dual, its derivative as well
+template <class TC>
+__device__ __forceinline__ TC zshift(double s, double ds) {
+  (void)ds;
+  return (TC)s;
+}
+template <>
+__device__ __forceinline__ Dual zshift<Dual>(double s, double ds) {
+  return Dual(s, ds);
+}
 
 template <class TC>
 __device__ __forceinline__ TC recip(TC x) { return (TC)1 / x; }
@@ -277,7 +289,7 @@ __device__ __forceinline__ void k_zsolve_b(cpx<T>* __restrict__ data, const doub
     const int vs = 2 * tx;
     const TC k2 = (TC)(-(eigx[active ? col : 0] + eigy[ky]));
     const TC h2 = (TC)zs.h2;
-    const TC sg1 = (k2 + (TC)zs.shift1) * h2;
+    const TC sg1 = (k2 + zshift<TC>(zs.shift1, zs.dshift1)) * h2;
     const TC rs = (TC)(zs.h2 * zs.scale);
     // phase A: elimination of solve 1 (top row k = 0 first), modified rhs in place.
     // The factor recurrence m_k = 1/(b - m_{k-1}) is stationary once two
@@ -301,7 +313,7 @@ __device__ __forceinline__ void k_zsolve_b(cpx<T>* __restrict__ data, const doub
     }
     TC* c2 = cp;
     if (zs.two && !zs.same) {
-      const TC sg2 = (k2 + (TC)zs.shift2) * h2;
+      const TC sg2 = (k2 + zshift<TC>(zs.shift2, zs.dshift2)) * h2;
       TC cc = 0;
       for (int k = 0; k < R; ++k) {
         const TC m = recip<TC>(zdiag<TC>(k, R, zs.bc, sg2) - cc);

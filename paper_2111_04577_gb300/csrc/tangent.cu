@@ -11,7 +11,11 @@
 //   theta_s (bottom): cos(theta_s) of the wall flux (Eq. NS34), derivative
 //                    -sin(theta_s) per radian;
 //   phi^0 along v:   the derivative parts of phi^n and phi^{n-1} set to v
-//                    (start-up phi^{-1} = phi^0), giving <dJ/dphi^0, v>.
+//                    (start-up phi^{-1} = phi^0), giving <dJ/dphi^0, v>;
+//   M (mobility):    1/(M lambda dt) and 1/(M lambda) of the CH right side,
+//                    the two shifts c(M), -alpha(M) of the paired solve
+//                    (Eqs. NS26-NS30, through S when S follows Eq. NS30) and
+//                    the flux J = -(rho1 - rho2)/2 M grad G of Eq. NS36.
 // The objective's derivative then follows by the chain rule through every
 // kernel, exactly up to FP64 rounding of the value and derivative parts: the
 // same result a reverse sweep gives for one parameter.
@@ -77,11 +81,20 @@ struct TangentRun {
       const double lh = I.p.lam_h;
       I.q.ilh = Dual(1.0 / lh, -1.0 / (lh * lh));
       I.q.wtau = Dual(I.p.mu_p1 / lh, -I.p.mu_p1 / (lh * lh));
+    } else if (param == PF_PARAM_MOBILITY) {
+      const double M = I.p.mob;
+      double dc = 0, da = 0;
+      I.dshift_dM(dc, da);
+      I.dseed.inv_mldt = -(1.0 / (I.p.Ml * I.p.dt)) / M;
+      I.dseed.inv_ml = -(1.0 / I.p.Ml) / M;
+      I.dseed.c = dc;
+      I.dseed.alpha = da;
+      I.q.cj_dx.d = I.q.cj_dx.v / M;
     } else if (param == PF_PARAM_THETA_BOT) {
       const double th = I.raw_prm.theta_bot_deg * M_PI / 180.0;
       I.q.cbot = Dual(std::cos(th), -std::sin(th));
     } else {
-      throw ApiError(PF_ERR_ARG, "param must be PF_PARAM_WI, PF_PARAM_THETA_BOT or PF_PARAM_PHI0");
+      throw ApiError(PF_ERR_ARG, "param must be PF_PARAM_WI, PF_PARAM_THETA_BOT, PF_PARAM_PHI0 or PF_PARAM_MOBILITY");
     }
   }
 };

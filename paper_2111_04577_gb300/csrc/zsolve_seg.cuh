@@ -112,8 +112,8 @@ __global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 2 : 1) k_zsolve_seg(cpx
   }
   const TC k2 = (TC)(-(eigx[in ? col : col0] + eigy[ky]));
   const TC h2 = (TC)zs.h2;
-  const TC sg1 = (k2 + (TC)zs.shift1) * h2;
-  const TC sg2 = (k2 + (TC)zs.shift2) * h2;
+  const TC sg1 = (k2 + zshift<TC>(zs.shift1, zs.dshift1)) * h2;
+  const TC sg2 = (k2 + zshift<TC>(zs.shift2, zs.dshift2)) * h2;
   // ---- factors in closed form: the two lanes of a column share the rows ----
   // Each lane forms rows k0 + part, k0 + part + 2, ...; rho^k is advanced by
   // rho^2 from row to row instead of being raised afresh.

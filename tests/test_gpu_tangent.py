@@ -158,3 +158,31 @@ def test_adjoint_dot_product_with_tangent(dim):
         dot = float(np.sum(dphi.astype(np.float64) * v))
         assert abs(dv - dot) <= 1e-10 * max(abs(dot), 1e-300), (dv, dot)
         assert abs(dth_t - dth_a) <= 1e-10 * abs(dth_a), (dth_t, dth_a)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_mobility_sensitivity_equals_oracle_central_difference(dim):
+    """dJ/dM through the whole coupled step: M enters the CH right side, both
+    shifts of the paired solve (through S, which follows M at the Eq. NS30
+    bound) and the flux J of the momentum equation."""
+    w, vel, n = case(dim)
+    J, dJ = tangents(w, vel, n, binding.PF_PARAM_MOBILITY)
+    M = w.params.mobility
+    h = 1e-3 * M
+    fd = (oracle_J(w, vel, n, mobility=M + h) - oracle_J(w, vel, n, mobility=M - h)) / (2 * h)
+    assert close(dJ, fd, 1e-3), (dJ, fd)
+
+
+def test_mobility_tangent_equals_adjoint_velocity_fixed():
+    """With the velocity fixed, dJ/dM by forward mode equals the reverse
+    sweep's.  dJ/dM is a difference of parts ~1e7 times larger than itself
+    (the 1/(M lambda dt) term against the S(M) term), so FP64 rounding of
+    either code leaves ~1e-9 relative: the bound is 1e-6."""
+    w, vel, _ = case(3)
+    n = 6
+    for obj in (binding.PF_OBJ_WETTED, binding.PF_OBJ_CENTROID_Z):
+        s = binding.Solver(w.grid, w.params, binding.PF_FP64)
+        s.load_state(wl.initial_phi(w), vel)
+        _, dm_t = s.tangent(n, binding.PF_PARAM_MOBILITY, obj, binding.PF_STEP_CH_ONLY)
+        _, _, dm_a, _ = s.adjoint(n, 2, obj, want_phi=False)
+        assert abs(dm_t - dm_a) <= 1e-6 * abs(dm_a), (dm_t, dm_a)
