@@ -271,6 +271,11 @@ int pf_tangent(pf_ctx* ctx, int nsteps, int param, int objective, double out[2])
  * dir is ignored for the other parameters. */
 int pf_tangent_ex(pf_ctx* ctx, int nsteps, int param, int objective, int flags, const void* dir, int dir_on_device,
                   double out[2]);
+/* pf_tangent_ex on one problem of a batch (its state, grid and parameters);
+ * the problem is not advanced.  Errors as pf_tangent_ex, PF_ERR_ARG for a bad
+ * index. */
+int pf_batch_tangent(pf_batch* b, int problem, int nsteps, int param, int objective, int flags, const void* dir,
+                     int dir_on_device, double out[2]);
 
 /* Launch-shape knobs picked by the autotuner (paper_2111_04577_gb300/autotune.py);
  * 0 restores the built-in default.  They change only how the work is tiled,

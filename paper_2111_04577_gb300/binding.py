@@ -27,7 +27,7 @@ EXPORTS = ["pf_init_grid", "pf_set_params", "pf_field_info", "pf_set_fields", "p
            "pf_get_fields", "pf_diagnostics", "pf_profile", "pf_diagnostics_noalloc", "pf_last_error",
            "pf_destroy", "pf_batch_create", "pf_batch_field_info", "pf_batch_set_fields", "pf_batch_get_fields",
            "pf_batch_step", "pf_batch_diagnostics", "pf_batch_last_error", "pf_batch_destroy", "pf_set_tuning",
-           "pf_get_tuning", "pf_adjoint", "pf_batch_adjoint", "pf_tangent", "pf_tangent_ex"]
+           "pf_get_tuning", "pf_adjoint", "pf_batch_adjoint", "pf_tangent", "pf_tangent_ex", "pf_batch_tangent"]
 PF_OBJ_WETTED, PF_OBJ_CENTROID_Z = 0, 1
 PF_PARAM_WI, PF_PARAM_THETA_BOT, PF_PARAM_PHI0, PF_PARAM_MOBILITY = 0, 1, 2, 3
 PROFILE_NAME = 48
@@ -94,6 +94,9 @@ def load(path: str = LIB_PATH):
         lib.pf_tangent.restype = C.c_int
         lib.pf_tangent_ex.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int, C.POINTER(C.c_double)]
         lib.pf_tangent_ex.restype = C.c_int
+        lib.pf_batch_tangent.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int,
+                                         C.POINTER(C.c_double)]
+        lib.pf_batch_tangent.restype = C.c_int
         lib.pf_set_tuning.argtypes = [vp, C.c_int, C.c_int]
         lib.pf_get_tuning.argtypes = [vp, C.c_int, C.POINTER(C.c_int)]
         lib.pf_set_tuning.restype = C.c_int
@@ -320,6 +323,17 @@ class Batch:
 
     def step(self, n=1):
         self._chk(self.lib.pf_batch_step(self.h, int(n)))
+
+    def tangent(self, b, nsteps, param=PF_PARAM_WI, objective=PF_OBJ_WETTED, flags=0, direction=None):
+        """Solver.tangent for problem b of the batch (not advanced)."""
+        out = (C.c_double * 2)()
+        ptr = None
+        if direction is not None:
+            direction = np.ascontiguousarray(direction, dtype=np.float64).ravel()
+            ptr = direction.ctypes.data_as(C.c_void_p)
+        self._chk(self.lib.pf_batch_tangent(self.h, int(b), int(nsteps), int(param), int(objective), int(flags),
+                                            ptr, 0, out))
+        return out[0], out[1]
 
     def adjoint(self, b, nsteps, ckpt_every=50, objective=PF_OBJ_WETTED, want_phi=True):
         """Solver.adjoint for problem b of the batch; leaves that problem at phi^N."""

@@ -101,31 +101,48 @@ struct TangentRun {
 
 }  // namespace pf
 
+namespace pf {
+
+static void tangent_run(ImplBase& src, cudaStream_t stream, int nsteps, int param, int objective, int flags,
+                        const void* dir, int dir_on_device, double out[2]) {
+  if (nsteps < 1) throw ApiError(PF_ERR_ARG, "nsteps must be >= 1");
+  if (objective != PF_OBJ_WETTED && objective != PF_OBJ_CENTROID_Z)
+    throw ApiError(PF_ERR_ARG, "objective must be PF_OBJ_WETTED or PF_OBJ_CENTROID_Z");
+  if (flags & ~PF_STEP_CH_ONLY) throw ApiError(PF_ERR_ARG, "flags: 0 or PF_STEP_CH_ONLY");
+  if (param == PF_PARAM_WI && (flags & PF_STEP_CH_ONLY))
+    throw ApiError(PF_ERR_ARG, "Wi has no effect on CH steps with the velocity fixed");
+  TangentRun run(src, stream);
+  run.seed(param, dir, dir_on_device);
+  run.impl->step(nsteps, flags);
+  Dual w[6];
+  run.impl->diagnostics_wide(w);
+  const Dual J = objective == PF_OBJ_WETTED ? w[2] : w[5];
+  out[0] = J.v;
+  out[1] = param == PF_PARAM_THETA_BOT ? J.d * M_PI / 180.0 : J.d;  // theta per degree, as pf_adjoint
+}
+
+}  // namespace pf
+
 extern "C" {
 
 int pf_tangent_ex(pf_ctx* ctx, int nsteps, int param, int objective, int flags, const void* dir, int dir_on_device,
                   double out[2]) {
   if (!ctx || !out) return PF_ERR_ARG;
   return guarded(ctx, [&] {
-    if (nsteps < 1) throw pf::ApiError(PF_ERR_ARG, "nsteps must be >= 1");
-    if (objective != PF_OBJ_WETTED && objective != PF_OBJ_CENTROID_Z)
-      throw pf::ApiError(PF_ERR_ARG, "objective must be PF_OBJ_WETTED or PF_OBJ_CENTROID_Z");
-    if (flags & ~PF_STEP_CH_ONLY) throw pf::ApiError(PF_ERR_ARG, "flags: 0 or PF_STEP_CH_ONLY");
-    if (param == PF_PARAM_WI && (flags & PF_STEP_CH_ONLY))
-      throw pf::ApiError(PF_ERR_ARG, "Wi has no effect on CH steps with the velocity fixed");
-    pf::TangentRun run(*ctx->impl, ctx->stream);
-    run.seed(param, dir, dir_on_device);
-    run.impl->step(nsteps, flags);
-    pf::Dual w[6];
-    run.impl->diagnostics_wide(w);
-    const pf::Dual J = objective == PF_OBJ_WETTED ? w[2] : w[5];
-    out[0] = J.v;
-    out[1] = param == PF_PARAM_THETA_BOT ? J.d * M_PI / 180.0 : J.d;  // theta per degree, as pf_adjoint
+    pf::tangent_run(*ctx->impl, ctx->stream, nsteps, param, objective, flags, dir, dir_on_device, out);
   });
 }
 
 int pf_tangent(pf_ctx* ctx, int nsteps, int param, int objective, double out[2]) {
   return pf_tangent_ex(ctx, nsteps, param, objective, 0, nullptr, 0, out);
+}
+
+int pf_batch_tangent(pf_batch* b, int problem, int nsteps, int param, int objective, int flags, const void* dir,
+                     int dir_on_device, double out[2]) {
+  if (!b || !out) return PF_ERR_ARG;
+  return bguarded(b, [&] {
+    pf::tangent_run(*b->impl->problem(problem), b->stream, nsteps, param, objective, flags, dir, dir_on_device, out);
+  });
 }
 
 }  // extern "C"

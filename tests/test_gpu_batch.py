@@ -108,3 +108,28 @@ def test_batch_adjoint_matches_single_problem_adjoint():
         assert np.array_equal(got[3], ref[3])
         s.close()
     bt.close()
+
+
+def test_batch_tangent_matches_single_problem_tangent():
+    """pf_batch_tangent on a problem of the batch equals pf_tangent_ex on a
+    standalone context holding the same state, for each parameter: the
+    derivative-carrying copy is built from the same fields and parameters."""
+    ws = problems()[:2]
+    bt = binding.Batch([w.grid for w in ws], [w.params for w in ws], binding.PF_FP64)
+    for b, w in enumerate(ws):
+        vel = wl.random_velocity(w.grid, 30 + b, 0.2)
+        phi0 = wl.initial_phi(w)
+        bt.set(b, "phi", phi0)
+        bt.set(b, "phi_old", phi0)
+        for name, a in zip(("u", "w"), (vel[0], vel[2])):
+            bt.set(b, name, a)
+            bt.set(b, name + "_old", a)
+        s = binding.Solver(w.grid, w.params, binding.PF_FP64)
+        s.load_state(phi0, vel)
+        params = [binding.PF_PARAM_THETA_BOT, binding.PF_PARAM_MOBILITY]
+        if w.params.wi > 0 and w.params.beta < 1:
+            params.append(binding.PF_PARAM_WI)
+        for prm in params:
+            assert bt.tangent(b, 4, prm) == s.tangent(4, prm), prm
+        s.close()
+    bt.close()
