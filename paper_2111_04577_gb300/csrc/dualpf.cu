@@ -481,7 +481,9 @@ struct Impl : ImplBase {
   template <class Pro>
   void rfft_x(Pro pro, cpx<T>* out, int n, int nlines, int pitch, const FftPlan& pl, const cpx<T>* tw) {
     if (reg_fft_size(n)) {
-      const int lpc = reg_lpc(n), pairs = (nlines + 1) / 2;
+      int lpc = reg_lpc(n);
+      const int pairs = (nlines + 1) / 2;
+      while (lpc > 1 && (size_t)lpc * fft_pad_len(n) * sizeof(cpx<T>) > (size_t)kMaxSmem) lpc /= 2;
       const size_t sm = (size_t)lpc * fft_pad_len(n) * sizeof(cpx<T>);
       mark(Pro::name);
       reg_fft_dispatch(n, [&](auto NN) {
@@ -500,8 +502,11 @@ struct Impl : ImplBase {
   template <class Epi>
   void irfft_x(const cpx<T>* in, Epi epi, int n, int nlines, int pitch, const FftPlan& pl, const cpx<T>* tw, T scale) {
     if (reg_fft_size(n)) {
-      const int lpc = reg_lpc(n), pairs = (nlines + 1) / 2;
-      const size_t sm = (size_t)lpc * n * (sizeof(cpx<T>) + (Epi::kPre ? 4 * sizeof(T) : 0));
+      int lpc = reg_lpc(n);
+      const int pairs = (nlines + 1) / 2;
+      const size_t per_line = (size_t)n * (sizeof(cpx<T>) + (Epi::kPre ? 4 * sizeof(T) : 0));
+      while (lpc > 1 && (size_t)lpc * per_line > (size_t)kMaxSmem) lpc /= 2;
+      const size_t sm = (size_t)lpc * per_line;
       mark(Epi::name);
       reg_fft_dispatch(n, [&](auto NN) {
         constexpr int N = decltype(NN)::value;
@@ -521,8 +526,10 @@ struct Impl : ImplBase {
       constexpr int E = 16;  // elements a thread: 16-column tiles read 128-byte rows
       const int nt = ny / E;
       const int want = tune[PF_TUNE_YFFT_COLS] > 0 ? tune[PF_TUNE_YFFT_COLS] : 16;
-      const int txc = std::max(1, std::min(want, 512 / nt));
-      const size_t sm = (size_t)txc * fft_pad_len(ny) * sizeof(cpx<T>);
+      int txc = std::max(1, std::min(want, 512 / nt));
+      const size_t line = (size_t)fft_pad_len(ny) * sizeof(cpx<T>);
+      while (txc > 1 && (size_t)txc * line > (size_t)kMaxSmem) txc /= 2;  // wide elements (Dual)
+      const size_t sm = (size_t)txc * line;
       mark(ny == d.fny && levels == d.fnz && d.r > 1 ? "fft_y_fine" : "fft_y_coarse");
       reg_fft_dispatch(ny, [&](auto NN) {
         constexpr int N = decltype(NN)::value;
