@@ -1,6 +1,6 @@
 """The hand-written GPU adjoint of the CH step (velocity fixed) against the FP64
 CPU adjoint (autograd of the oracle restatement) and central finite
-differences of the GPU forward (the benchmark spec tolerance 1e-3)."""
+differences of the GPU forward (tolerance 1e-3 for finite differences)."""
 import numpy as np
 import pytest
 import torch

@@ -1,5 +1,5 @@
 """Forward-mode sensitivities through the whole coupled step (pf_tangent)
-against central finite differences of the FP64 oracle (the benchmark spec tolerance
+against central finite differences of the FP64 oracle (tolerance
 1e-3 for finite differences) and of the GPU's own FP64 path; the objective's
 value against the oracle at the FP64 parity tolerance."""
 import numpy as np
@@ -143,7 +143,7 @@ def test_adjoint_dot_product_with_tangent(dim):
     """The classical adjoint check, between two independent codes: the
     hand-written reverse sweep of the CH step (velocity fixed) and forward-mode
     derivatives of the forward kernels.  <dJ/dphi^0, v> and dJ/dtheta agree to
-    FP64 rounding (the benchmark spec: 1e-10 for adjoint against adjoint)."""
+    FP64 rounding (tolerance 1e-10 for adjoint against adjoint)."""
     w, vel, _ = case(dim)
     n = 8
     rng = np.random.default_rng(5)
