@@ -407,8 +407,10 @@ __device__ __forceinline__ void k_polymer_b(const PolyIn<T>& P, const Dims& d, c
   else polymer_cell<T, N, 2>(P, d, q, x);
 }
 
+// FP32: 48 registers, ten 128-thread CTAs per SM (stage 2 measured 2 % faster
+// than at 56 registers)
 template <class T, int N, int STAGE>
-__global__ void k_polymer(const __grid_constant__ PolyIn<T> P, const Dims d, const PhysT<T> q) {
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 10 : 1) k_polymer(const __grid_constant__ PolyIn<T> P, const Dims d, const PhysT<T> q) {
   RowIdx x;
   if (!row_index(d.nx, d.ny, x)) return;
   polymer_cell<T, N, STAGE>(P, d, q, x);
