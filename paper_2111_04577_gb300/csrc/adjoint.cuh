@@ -58,6 +58,24 @@ __global__ void k_lapN_axpy(const T* __restrict__ a, const T* __restrict__ b, T 
   out[id] = lap * q.ih2 + (b ? s * b[id] : (T)0);
 }
 
+// one stencil pass for both: lap = L_N a, out_l = lap, out_s = lap + s a
+template <class T>
+__global__ void k_lapN_two(const T* __restrict__ a, T s, T* __restrict__ out_l, T* __restrict__ out_s, Dims d,
+                           PhysT<T> q) {
+  RowIdx x;
+  if (!row_index(d.fnx, d.fny, x)) return;
+  const int i = x.i, j = x.j, k = x.k;
+  const size_t id = (size_t)x.row * d.fnx + i;
+  const size_t plane = (size_t)d.fnx * d.fny;
+  const T c0 = a[id];
+  T lap = a[id - i + wrap(i + 1, d.fnx)] + a[id - i + wrap(i - 1, d.fnx)] - 2 * c0;
+  if (d.dim == 3) lap += a[fidx(d, i, wrap(j + 1, d.fny), k)] + a[fidx(d, i, wrap(j - 1, d.fny), k)] - 2 * c0;
+  lap += (k + 1 < d.fnz ? a[id + plane] : c0) + (k > 0 ? a[id - plane] : c0) - 2 * c0;
+  const T L = lap * q.ih2;
+  out_l[id] = L;
+  out_s[id] = L + s * c0;
+}
+
 // out = x + y
 template <class T>
 __global__ void k_add(const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ out, size_t n) {
@@ -72,17 +90,19 @@ __global__ void k_sub(const T* __restrict__ a, const T* __restrict__ b, T* __res
     out[i] = a[i] - b[i];
 }
 
-// FP64 partial dot products of up to 4 pairs
+// FP64 partial dot products of up to 4 pairs; with y2b, the third pair's y is
+// y2 - y2b (formed in T)
 template <class T>
 __global__ void k_dots(const T* __restrict__ x0, const T* __restrict__ y0, const T* __restrict__ x1,
                        const T* __restrict__ y1, const T* __restrict__ x2, const T* __restrict__ y2,
-                       const T* __restrict__ x3, const T* __restrict__ y3, size_t n, double* __restrict__ partial) {
+                       const T* __restrict__ x3, const T* __restrict__ y3, size_t n, double* __restrict__ partial,
+                       const T* __restrict__ y2b = nullptr) {
   __shared__ double sh[4][256];
   double a[4] = {0, 0, 0, 0};
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     a[0] += (double)x0[i] * (double)y0[i];
     a[1] += (double)x1[i] * (double)y1[i];
-    a[2] += (double)x2[i] * (double)y2[i];
+    a[2] += (double)x2[i] * (double)(y2b ? (T)(y2[i] - y2b[i]) : y2[i]);
     a[3] += (double)x3[i] * (double)y3[i];
   }
   for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] = a[q];

@@ -1030,10 +1030,8 @@ struct Impl : ImplBase {
     // commute, so R_bar is the forward step's paired solve of phi_bar^{n+1}, and
     // eps_bar = (L_N - c) R_bar is one stencil pass instead of a second solve
     fine_solve_pair(a_next, a_rbar);
-    k_lapN_axpy<T><<<lf.grid, lf.block, 0, st>>>(a_rbar, a_rbar, (T)(-p.c), a_ebar, d, q);
-    k_lapN_axpy<T><<<lf.grid, lf.block, 0, st>>>(a_rbar, (const T*)nullptr, (T)0, a_mubar, d, q);
-    k_sub<T><<<nb, 256, 0, st>>>(po, pn, a_tmp, nf);
-    k_dots<T><<<nb, 256, 0, st>>>(a_ebar, a_delta, a_rbar, a_eps, a_rbar, a_tmp, a_rbar, a_adv, nf, part);
+    k_lapN_two<T><<<lf.grid, lf.block, 0, st>>>(a_rbar, (T)(-p.c), a_mubar, a_ebar, d, q);  // mu_bar, eps_bar
+    k_dots<T><<<nb, 256, 0, st>>>(a_ebar, a_delta, a_rbar, a_eps, a_rbar, po, a_rbar, a_adv, nf, part, pn);
     k_adj_phibar<T><<<lf.grid, lf.block, 0, st>>>(a_phis, a_rbar, a_mubar, a_next, a_cur, a_next2, a_cur2, a_thb, vel,
                                                   d, p, q, a1, a2);
     k_sum_d<<<nb, 256, 0, st>>>(a_thb, (size_t)d.fnx * d.fny, part + (size_t)4 * nb);
