@@ -518,10 +518,6 @@ namespace pf {
 // straddle the periodic seam).  RS = log2 of the refinement ratio (fine/coarse).
 // Planes carry 4 floats of padding on both ends: the halo chunks read one
 // float beyond their row, and only lanes that are never used depend on it.
-// Shared memory: five phi* planes (ring), three mu* planes (ring), one coarse
-// velocity box (u, v, w below and above), and the landing area of the next
-// plane's phi^n and phi^{n-1} chunks (cp.async).  The x neighbours of a chunk
-// come from the adjacent lanes by shuffle.
 // ---------------------------------------------------------------------------
 struct March4 {
   static constexpr int TX = 64, TY = 16, NT = 256, CH = TX / 4;  // 16 chunks per row
@@ -533,7 +529,7 @@ struct March4 {
   static constexpr int KS = (NSC + NT - 1) / NT, KM = (NMC + NT - 1) / NT;
   __host__ __device__ static constexpr int VX(int rs) { return (TX >> rs) + 2; }
   __host__ __device__ static constexpr int VY(int rs) { return (TY >> rs) + 2; }
-  __host__ __device__ static constexpr int smem_floats(int rs) {  // rings, velocity box, landing area
+  __host__ __device__ static constexpr int smem_floats(int rs) {
     return NPS * SPF + NMS * MPF + 4 * VX(rs) * VY(rs) + 8 * NSC;
   }
 };
