@@ -18,8 +18,9 @@ class Derived:
         p = dict(prm)
         if p.get("dw", 0.0) != 0.0:
             raise ValueError("dynamic contact angle (D_w != 0) is not part of this scheme")
-        if p.get("alpha_giesekus", 0.0) != 0.0:
-            raise ValueError("Giesekus alpha != 0 is not part of this scheme")
+        ag = p.get("alpha_giesekus", 0.0)
+        if not (0.0 <= ag < 1.0):
+            raise ValueError("the Giesekus mobility must lie in [0, 1)")
         self.p = p
         self.gamma0 = 1.5
         self.dt = p["dt"]
@@ -43,6 +44,7 @@ class Derived:
         self.mu_p1 = (1.0 - beta) * p["mu1"]
         self.mu_s2 = p["mu2"]
         self.lam_h = p.get("wi", 0.0)
+        self.alpha_g = ag  # Giesekus mobility (Eqs. NS18, NS22); 0 is Oldroyd-B
         self.rho1, self.rho2 = p["rho1"], p["rho2"]
         self.rho0 = min(self.rho1, self.rho2)
         self.nu_m = p.get("nu_m", 0.0) or 0.5 * max(self.mu_s1, self.mu_s2) / self.rho0

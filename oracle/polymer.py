@@ -1,4 +1,4 @@
-"""Log-conformation Oldroyd-B update on coarse centres (oracle; test infrastructure only).
+"""Log-conformation Giesekus / Oldroyd-B update on coarse centres (oracle; test infrastructure only).
 
 Section 2.2 (Eqs. NS17-NS24) and Section 3.2.3 (Eqs. NS40-NS46):
   tau_p = (mu_p/lambda_H)(c - I)                                         NS17
@@ -6,7 +6,11 @@ Section 2.2 (Eqs. NS17-NS24) and Section 3.2.3 (Eqs. NS40-NS46):
   M~ = R^T (grad u)^T R, omega_ab = (l_b m_ab + l_a m_ba)/(l_b - l_a),
   Omega = R [omega] R^T (antisymmetric), B = R diag(m_aa) R^T              NS23, NS24
   dTheta/dt = RH = -div(u Theta) + (Omega Theta - Theta Omega) + 2 B
-                   + (1/lambda_H)(e^{-Theta} - I)       (Oldroyd-B, alpha = 0)
+                   - (1/lambda_H) e^{-Theta} [I + alpha (e^Theta - I)] (e^Theta - I)
+  (Eqs. NS22, NS41, Giesekus mobility alpha; alpha = 0 is Oldroyd-B, whose
+  relaxation is (1/lambda_H)(e^{-Theta} - I)).  The three factors are functions
+  of Theta, so the term is diagonal in its eigenbasis:
+  (1/lambda_H) [(e^{-theta} - 1) - alpha (e^{theta} - 1)(1 - e^{-theta})].
   RK2-TVD: Theta1 = Theta^n + dt RH(Theta^n; R^n, Lambda^n)                NS42
            diagonalise Theta1                                             NS43
            Theta^{n+1} = Theta^n/2 + (Theta1 + dt RH(Theta1; R1, Lambda1))/2 NS44
@@ -79,7 +83,7 @@ def decompose(T):
     return th, R
 
 
-def rh(T, L, adv, lam_h):
+def rh(T, L, adv, lam_h, alpha_g=0.0):
     """Right-hand side RH of Eq. NS41 with the diagonalisation of T (Eq. NS23-NS24)."""
     n = T.shape[-1]
     th, R = decompose(T)
@@ -103,17 +107,22 @@ def rh(T, L, adv, lam_h):
     RT = np.swapaxes(R, -1, -2)
     Omega = R @ Om @ RT
     B = R @ Bt @ RT
-    einv = R @ (np.exp(-th)[..., :, None] * RT)
     I = np.eye(n)
-    return -adv + (Omega @ T - T @ Omega) + 2.0 * B + (einv - I) / lam_h
+    if alpha_g == 0.0:
+        relax = R @ (np.exp(-th)[..., :, None] * RT) - I
+    else:
+        em, ep = np.exp(-th), np.exp(th)
+        relax = R @ (((em - 1.0) - alpha_g * (ep - 1.0) * (1.0 - em))[..., :, None] * RT)
+    return -adv + (Omega @ T - T @ Omega) + 2.0 * B + relax / lam_h
 
 
 def polymer_step(T, u, v, w, phic, d, grid):
     """RK2-TVD of Eqs. NS42-NS46.  Returns (Theta^{n+1}, weighted tau tensor)."""
     L = velocity_gradient(u, v, w, d, grid)
     dt = d.dt
-    T1 = T + dt * rh(T, L, advection(T, u, v, w, grid), d.lam_h)
-    T2 = 0.5 * T + 0.5 * (T1 + dt * rh(T1, L, advection(T1, u, v, w, grid), d.lam_h))
+    ag = getattr(d, "alpha_g", 0.0)
+    T1 = T + dt * rh(T, L, advection(T, u, v, w, grid), d.lam_h, ag)
+    T2 = 0.5 * T + 0.5 * (T1 + dt * rh(T1, L, advection(T1, u, v, w, grid), d.lam_h, ag))
     th, R = decompose(T2)
     n = T.shape[-1]
     c = R @ (np.exp(th)[..., :, None] * np.swapaxes(R, -1, -2))

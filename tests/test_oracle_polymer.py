@@ -60,10 +60,11 @@ def test_zero_stress_rule_and_degenerate_limit(n):
         assert np.max(np.abs(a - b)) < 20 * eps
 
 
-def _startup(dim, dt, t_end, gam=1.3, lam_h=0.8):
+def _startup(dim, dt, t_end, gam=1.3, lam_h=0.8, alpha_g=0.0):
     n = 8
     g = wl.Grid(4, 1 if dim == 2 else 4, n, 0.5, 0.125 if dim == 2 else 0.5, 1.0, 1)
     prm = wl.params_from_groups(Wi=lam_h, beta=0.4, dt=dt)
+    prm.alpha_giesekus = alpha_g
     prm.uw_bot, prm.uw_top = -gam * 0.5, gam * 0.5
     d = Derived(prm.as_dict())
     nz, ny, nx = g.coarse_shape
@@ -101,3 +102,47 @@ def test_oldroyd_b_startup_shear(dim):
     assert errs[-1] < 2e-4
     r = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert np.all(np.abs(r - 2) < 0.2), (errs, r)
+
+
+def _giesekus_steady_shear(gam, lam_h, alpha_g):
+    """Steady conformation of homogeneous shear u = gam z, solved as an
+    algebraic system independent of the log-conformation scheme: with
+    L = grad u^T = [[0, gam], [0, 0]] (x, z), the steady Eq. NS18 (relaxing
+    sign) reads L c + c L^T = (1/lambda_H)[(c - I) + alpha (c - I)^2]."""
+    from scipy.optimize import fsolve
+
+    def F(x):
+        cxx, cxz, czz = x
+        c = np.array([[cxx, cxz], [cxz, czz]])
+        L = np.array([[0.0, gam], [0.0, 0.0]])
+        e = c - np.eye(2)
+        r = L @ c + c @ L.T - (e + alpha_g * e @ e) / lam_h
+        return [r[0, 0], r[0, 1], r[1, 1]]
+
+    wi = gam * lam_h
+    x0 = [1.0 + 2.0 * wi * wi, wi, 1.0]  # the Oldroyd-B solution
+    x = fsolve(F, x0, xtol=1e-13)
+    assert max(abs(r) for r in F(x)) < 1e-12  # converged to round-off
+    return x
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("alpha_g", [0.2, 0.5])
+def test_giesekus_shear_reaches_the_algebraic_steady_state(dim, alpha_g):
+    """Giesekus mobility (Eqs. NS18, NS22): uniform shear from rest, run to
+    steady state by the RK2-TVD log-conformation scheme, gives the stress of the
+    steady algebraic solution; the shear-thinning (tau_xz below mu_p gam) and
+    tau_zz != 0 separate it from Oldroyd-B.  A fixed point of the RK2 map is a
+    zero of RH, so only the decaying transient remains."""
+    gam, lam_h = 1.3, 0.8
+    tau, d = _startup(dim, 0.02, 24.0, gam, lam_h, alpha_g)
+    cxx, cxz, czz = _giesekus_steady_shear(gam, lam_h, alpha_g)
+    mp = d.mu_p1
+    iz = 1 if dim == 2 else 2
+    want = {"xx": mp / lam_h * (cxx - 1), "xz": mp / lam_h * cxz, "zz": mp / lam_h * (czz - 1)}
+    got = {"xx": tau[..., 0, 0], "xz": tau[..., 0, iz], "zz": tau[..., iz, iz]}
+    scale = abs(want["xx"])
+    for k in want:
+        assert np.max(np.abs(got[k] - want[k])) < 1e-8 * scale, (k, got[k].ravel()[:2], want[k])
+    assert want["xz"] < mp * gam * (1 - 1e-3)   # shear thinning
+    assert abs(want["zz"]) > 1e-3 * scale       # second normal stress difference
