@@ -101,7 +101,8 @@ typedef struct {
  * (Eq. NS12, second approach).  mobility: M of Eq. NS1.  sigma, eta: Eq. NS7.
  * theta_*_deg: equilibrium angles of Eq. NS16 at z = 0 and z = lz, measured
  * through phase 1.  dw: must be 0 (static contact angle).  alpha_giesekus:
- * must be 0 (Oldroyd-B).  S = 0 selects the smallest S of Eq. NS30; nu_m = 0
+ * the Giesekus mobility alpha of Eqs. NS18/NS22 in [0, 1), constant in the
+ * viscoelastic phase (0: Oldroyd-B).  S = 0 selects the smallest S of Eq. NS30; nu_m = 0
  * selects nu_m = max(mu_s)/(2 min(rho)) (text after Eq. NS39).  uw_*: x
  * velocity of the walls.  g*: body acceleration (f_ext = rho g). */
 typedef struct {
@@ -123,9 +124,9 @@ int pf_init_grid(pf_ctx** out, const pf_grid_desc* g, void* stream);
 /* Set the physical parameters and derive the scheme's constants:
  * lambda (Eq. NS7), S (Eq. NS30), alpha (Eq. NS29), c = alpha + S/eta^2,
  * rho0 and nu_m (text after Eq. NS39).  May be called again between steps.
- * Errors: PF_ERR_ARG (non-positive rho, sigma, eta, mobility, dt, or an
- * angle outside [0, 180]), PF_ERR_DISCRIMINANT (S below Eq. NS30),
- * PF_ERR_UNSUPPORTED (dw != 0 or alpha_giesekus != 0). */
+ * Errors: PF_ERR_ARG (non-positive rho, sigma, eta, mobility, dt, an angle
+ * outside [0, 180], or alpha_giesekus outside [0, 1)), PF_ERR_DISCRIMINANT (S
+ * below Eq. NS30), PF_ERR_UNSUPPORTED (dw != 0). */
 int pf_set_params(pf_ctx* ctx, const pf_params* prm);
 
 /* Number of elements and element size (bytes) of a field. */

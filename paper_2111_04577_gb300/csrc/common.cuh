@@ -60,6 +60,7 @@ struct Phys {
   double eta, lam, mob, Ml, S, alpha, c;
   double cos_bot, cos_top;
   double rho1, rho2, rho0, mu_s1, mu_s2, mu_p1, lam_h, nu_m;
+  double alpha_g;  // Giesekus mobility (0: Oldroyd-B)
   double uw_bot, uw_top, gx, gy, gz;
   int visco;
 };
@@ -76,6 +77,7 @@ struct PhysT {
   T ih, ih2, iD, iD2;                 // fine and coarse inverse spacings
   T ie2, lam;                         // 1/eta^2, lambda
   T dt, ilh, wtau;                    // dt, 1/lambda_H, mu_p/lambda_H
+  T ag;                               // Giesekus mobility alpha (0: Oldroyd-B)
   Wide<T> cbot, ctop;                 // cos(theta_s) of the two walls (FP64, or carrying a derivative)
 };
 

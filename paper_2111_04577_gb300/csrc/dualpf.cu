@@ -160,7 +160,8 @@ static Phys derive(const pf_params& q, const pf_grid_desc& g) {
   if (q.theta_bot_deg < 0 || q.theta_bot_deg > 180 || q.theta_top_deg < 0 || q.theta_top_deg > 180)
     throw ApiError(PF_ERR_ARG, "contact angles must lie in [0, 180] degrees");
   if (q.dw != 0.0) throw ApiError(PF_ERR_UNSUPPORTED, "dynamic contact angle D_w != 0 is not supported");
-  if (q.alpha_giesekus != 0.0) throw ApiError(PF_ERR_UNSUPPORTED, "Giesekus alpha != 0 is not supported");
+  if (!(q.alpha_giesekus >= 0.0 && q.alpha_giesekus < 1.0))
+    throw ApiError(PF_ERR_ARG, "the Giesekus mobility must lie in [0, 1)");
   Phys p{};
   p.dt = q.dt;
   p.gamma0 = 1.5;
@@ -187,6 +188,7 @@ static Phys derive(const pf_params& q, const pf_grid_desc& g) {
   p.mu_p1 = (1.0 - beta) * q.mu1;
   p.mu_s2 = q.mu2;
   p.lam_h = q.wi;
+  p.alpha_g = q.alpha_giesekus;
   p.nu_m = q.nu_m > 0 ? q.nu_m : 0.5 * std::max(p.mu_s1, p.mu_s2) / p.rho0;
   if (!(p.nu_m > 0)) throw ApiError(PF_ERR_ARG, "nu_m must be > 0 (give a viscosity)");
   p.uw_bot = q.uw_bot;
@@ -795,6 +797,7 @@ struct Impl : ImplBase {
     q.dt = (T)p.dt;
     q.ilh = p.visco ? (T)(1.0 / p.lam_h) : (T)0;
     q.wtau = p.visco ? (T)(p.mu_p1 / p.lam_h) : (T)0;
+    q.ag = (T)p.alpha_g;
     q.cbot = p.cos_bot;
     q.ctop = p.cos_top;
     have_params = true;

@@ -1,11 +1,13 @@
-// Log-conformation Oldroyd-B update on coarse centres (Section 3.2.3).
+// Log-conformation Giesekus / Oldroyd-B update on coarse centres (Section 3.2.3).
 //
-// RH of Eq. NS41 with alpha = 0 and the relaxation acting toward Theta = 0:
-//   RH = -div(u Theta) + (Omega Theta - Theta Omega) + 2 B + (e^{-Theta} - I)/lambda_H,
+// RH of Eq. NS41 with the relaxation acting toward Theta = 0:
+//   RH = -div(u Theta) + (Omega Theta - Theta Omega) + 2 B
+//        - e^{-Theta} [I + alpha (e^Theta - I)] (e^Theta - I)/lambda_H,
+// (Giesekus mobility alpha; alpha = 0 is Oldroyd-B, (e^{-Theta} - I)/lambda_H),
 // Omega and B from the decomposition of Eqs. NS21-NS24 with
 // Theta = R diag(theta) R^T, lambda = e^theta, M~ = R^T (grad u)^T R.
 // In the eigenbasis RH~ = R^T (RH + div(u Theta)) R is symmetric with
-//   RH~_aa = 2 m_aa + (e^{-theta_a} - 1)/lambda_H,
+//   RH~_aa = 2 m_aa + [(e^{-theta_a} - 1) - alpha (e^{theta_a} - 1)(1 - e^{-theta_a})]/lambda_H,
 //   RH~_ab = omega_ab (theta_b - theta_a)
 //          = (lambda_b m_ab + lambda_a m_ba) (theta_b - theta_a)/(lambda_b - lambda_a),
 // evaluated as (e^d m_ab + m_ba) d/expm1(d), d = theta_b - theta_a, which is
@@ -289,7 +291,10 @@ __device__ __forceinline__ void polymer_cell(const PolyIn<T>& P, const Dims& d, 
   T H[N][N];
 #pragma unroll
   for (int a = 0; a < N; ++a) {
-    H[a][a] = 2 * Mt[a][a] + (fexp<T>(-dg[a]) - (T)1) * q.ilh;
+    const T em = fexp<T>(-dg[a]);
+    T relax = em - (T)1;  // Oldroyd-B: e^{-theta} - 1
+    if (q.ag != (T)0) relax -= q.ag * (fexp<T>(dg[a]) - (T)1) * ((T)1 - em);  // Giesekus
+    H[a][a] = 2 * Mt[a][a] + relax * q.ilh;
 #pragma unroll
     for (int b = a + 1; b < N; ++b) {
       const T dd = dg[b] - dg[a];

@@ -233,3 +233,55 @@ def test_degenerate_cases_fp64(dim, nx, nz, theta):
     assert rel(s.fine("phi"), ref.phi) < FP64_TOL
     assert rel(s.coarse("u"), ref.vel[0]) < FP64_TOL
     assert rel(s.coarse("w"), ref.vel[2]) < FP64_TOL
+
+
+@pytest.mark.parametrize("cfg,nx,nz", [("c2", 16, 8), ("c4", 12, 6)])
+@pytest.mark.parametrize("alpha_g", [0.3])
+def test_giesekus_fp64_and_mixed_vs_oracle(cfg, nx, nz, alpha_g):
+    """Giesekus mobility (Eqs. NS18, NS22) in the polymer update: FP64 GPU path
+    against the oracle at 1e-10 (Theta 1e-9), mixed at the viscoelastic
+    tolerances, after steps from a seeded velocity and a seeded Theta of order
+    one (so that the alpha term, quadratic in e^Theta - I, is not small)."""
+    w = wl.scaled(wl.config(cfg), nx, nz)
+    w.params.alpha_giesekus = alpha_g
+    g = w.grid
+    phi0 = wl.initial_phi(w)
+    vel = wl.random_velocity(g, 13, 0.2)
+    nz_, ny_, nx_ = g.coarse_shape
+    m = 2 if g.dim == 2 else 3
+    rng = np.random.default_rng(21)
+    a = 0.25 * rng.standard_normal((nz_, ny_, nx_, m, m))
+    theta0 = a + np.swapaxes(a, -1, -2)
+    idx = [(0, 0), (0, 1), (1, 1)] if g.dim == 2 else [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    theta_comp = np.stack([theta0[..., i, j] for i, j in idx])
+    n = 6
+
+    def oracle(params):
+        ref = ostep.State(g, params.as_dict(), phi0, vel0=vel, theta0=theta0)
+        for _ in range(n):
+            ref.step()
+        return ref
+
+    ref = oracle(w.params)
+    for prec in (binding.PF_FP64, binding.PF_MIXED):
+        s = binding.Solver(g, w.params, prec)
+        s.load_state(phi0, vel)
+        s.set("theta", theta_comp)
+        s.step(n)
+        th = s.coarse("theta")
+        if prec == binding.PF_FP64:
+            assert rel(s.fine("phi"), ref.phi) < FP64_TOL
+            assert rel(s.coarse("u"), ref.vel[0]) < FP64_TOL
+            assert rel(s.coarse("w"), ref.vel[2]) < FP64_TOL
+            for q, (i, j) in enumerate(idx):
+                assert rel(th[q], ref.theta[..., i, j]) < 1e-9, q
+        else:
+            assert np.max(np.abs(s.fine("phi") - ref.phi)) < 2e-4
+            assert rel(s.coarse("u"), ref.vel[0]) < 1e-3
+            scale = max(np.max(np.abs(ref.theta)), 1e-300)
+            for q, (i, j) in enumerate(idx):
+                assert np.max(np.abs(th[q] - ref.theta[..., i, j])) < 1e-3 * scale, q
+        s.close()
+    # the mobility changes the answer: Oldroyd-B (alpha = 0) gives another Theta
+    ref0 = oracle(wl.scaled(wl.config(cfg), nx, nz).params)
+    assert rel(ref0.theta, ref.theta) > 1e-4
