@@ -991,15 +991,6 @@ struct Impl : ImplBase {
     if (d.dim == 3) fft_y(spF, d.fny, pF, d.fnx / 2 + 1, d.fnz, plFy, twFy, +1);
     irfft_x(spF, ArrEpi<T>{out, d.fnx}, d.fnx, nlf, pF, plFx, twFx, (T)1);
   }
-  void fine_solve(const T* in, T* out, double shift) {
-    const int nlf = d.fny * d.fnz;
-    rfft_x(FineArrPro<T>{in, d.fnx}, spF, d.fnx, nlf, pF, plFx, twFx);
-    if (d.dim == 3) fft_y(spF, d.fny, pF, d.fnx / 2 + 1, d.fnz, plFy, twFy, -1);
-    zsolve(spF, d.fnz, d.fny, pF, d.fnx / 2 + 1, eFx, eFy, Z_NEUMANN, d.h * d.h, shift, shift, false,
-           1.0 / ((double)d.fnx * d.fny), false);
-    if (d.dim == 3) fft_y(spF, d.fny, pF, d.fnx / 2 + 1, d.fnz, plFy, twFy, +1);
-    irfft_x(spF, ArrEpi<T>{out, d.fnx}, d.fnx, nlf, pF, plFx, twFx, (T)1);
-  }
 
   // d c/d M and d alpha/d M of Eq. NS29 (S at its minimum moves with M)
   void dshift_dM(double& dc, double& da) const {
