@@ -1,0 +1,65 @@
+"""Pins of the WENO5-Z fluxes (oracle/weno.py): fifth-order accuracy on
+smooth data, exact conservation, near-boundedness at a step, and the mirror
+symmetry between the two upwind directions."""
+import numpy as np
+
+from oracle import weno
+
+
+def test_fifth_order_on_smooth_periodic_data():
+    """Cell averages of sin in, face values out: the face-value error of the
+    WENO-Z reconstruction is O(h^5) for smooth data (the ideal-weight limit)."""
+    errs = []
+    for n in (16, 32, 64, 128):
+        h = 1.0 / n
+        xl = np.arange(n) * h
+        avg = (np.cos(2 * np.pi * xl) - np.cos(2 * np.pi * (xl + h))) / (2 * np.pi * h)  # exact cell averages
+        left, right = weno.face_values(avg[None, None, :], axis=2, periodic=True)
+        xf = (np.arange(n) + 1) * h
+        exact = np.sin(2 * np.pi * xf)
+        errs.append(max(np.max(np.abs(left[0, 0] - exact)), np.max(np.abs(right[0, 0] - exact))))
+    r = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(r[1:] > 4.6), (errs, r)
+
+
+def test_conservation_periodic_and_walls():
+    rng = np.random.default_rng(3)
+    nz, ny, nx = 8, 6, 10
+    h = 0.1
+    q = rng.standard_normal((nz, ny, nx))
+    uf = rng.standard_normal((nz, ny, nx))
+    vf = rng.standard_normal((nz, ny, nx))
+    wf = rng.standard_normal((nz + 1, ny, nx))
+    wf[0] = wf[-1] = 0.0
+    for dim in (2, 3):
+        div = weno.advection(q, uf, vf if dim == 3 else None, wf, h, dim)
+        assert abs(np.sum(div)) < 1e-12 * np.sum(np.abs(div))
+
+
+def test_bounded_at_a_step():
+    """Essentially non-oscillatory: at a unit step the face values leave
+    [0, 1] by at most 1e-3 (the linear fifth-order scheme overshoots by ~10 %)."""
+    n = 64
+    v = (np.arange(n) >= n // 2).astype(float)
+    left, right = weno.face_values(v[None, None, :], axis=2, periodic=True)
+    for f in (left, right):
+        assert f.min() > -1e-3 and f.max() < 1 + 1e-3
+    # the ideal-weight (linear) combination does overshoot: the weights matter
+    g = lambda o: np.roll(v, -o)
+    lin = (0.1 * (2 * g(-2) - 7 * g(-1) + 11 * g(0)) + 0.6 * (-g(-1) + 5 * g(0) + 2 * g(1))
+           + 0.3 * (2 * g(0) + 5 * g(1) - g(2))) / 6
+    assert lin.max() > 1.05 or lin.min() < -0.05
+
+
+def test_upwind_direction_mirror_symmetry():
+    """Reversing the velocity and mirroring the data mirrors the fluxes."""
+    rng = np.random.default_rng(4)
+    n = 20
+    v = rng.standard_normal(n)
+    u = np.abs(rng.standard_normal(n))
+    f = weno.upwind_flux(v[None, None, :], u[None, None, :], axis=2, periodic=True)[0, 0]
+    # mirrored problem: cell j -> n-1-j, face i+1/2 -> face (n-2-i)+1/2, velocity -> -velocity
+    vm = v[::-1]
+    um = -np.roll(u[::-1], -1)
+    fm = weno.upwind_flux(vm[None, None, :], um[None, None, :], axis=2, periodic=True)[0, 0]
+    assert np.allclose(np.roll(fm[::-1], -1), -f, rtol=1e-13, atol=1e-14)
