@@ -26,7 +26,7 @@ import math
 
 import numpy as np
 
-from . import operators as op
+from . import operators as op, weno
 from . import spectral
 
 
@@ -75,7 +75,10 @@ def ch_step(phi_n, phi_nm1, vel_n, vel_nm1, d, grid):
     phih = 2.0 * phi_n - 0.5 * phi_nm1
     us = [2.0 * a - b for a, b in zip(vel_n, vel_nm1)]
     uf, vf, wf = op.prolong_velocity(us[0], us[1], us[2], r, ry, dim)
-    A = advection(phis, uf, vf, wf, h, dim)
+    if getattr(d, "advection", "central") == "weno5z":  # the paper's scheme (Section 3.2.1)
+        A = weno.advection(phis, uf, vf, wf, h, dim)
+    else:
+        A = advection(phis, uf, vf, wf, h, dim)
     hh = f_bulk(phis, eta) - d.S / eta ** 2 * phis
     gb, gt = wall_flux(phis, d)
     B = wall_term(phis.shape, gb, gt, h)
@@ -98,7 +101,10 @@ def ch_step_two_ghost(phi_n, phi_nm1, vel_n, vel_nm1, d, grid, ghb, ght):
     phih = 2.0 * phi_n - 0.5 * phi_nm1
     us = [2.0 * a - b for a, b in zip(vel_n, vel_nm1)]
     uf, vf, wf = op.prolong_velocity(us[0], us[1], us[2], r, ry, dim)
-    A = advection(phis, uf, vf, wf, h, dim)
+    if getattr(d, "advection", "central") == "weno5z":  # the paper's scheme (Section 3.2.1)
+        A = weno.advection(phis, uf, vf, wf, h, dim)
+    else:
+        A = advection(phis, uf, vf, wf, h, dim)
     hh = f_bulk(phis, eta) - d.S / eta ** 2 * phis
     gb, gt = wall_flux(phis, d)
     Bh = wall_term(phis.shape, ghb, ght, h)

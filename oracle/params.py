@@ -45,6 +45,10 @@ class Derived:
         self.mu_s2 = p["mu2"]
         self.lam_h = p.get("wi", 0.0)
         self.alpha_g = ag  # Giesekus mobility (Eqs. NS18, NS22); 0 is Oldroyd-B
+        # convective flux of the CH step: "central" (the GPU path's) or "weno5z" (the paper's)
+        self.advection = p.get("advection", "central")
+        if self.advection not in ("central", "weno5z"):
+            raise ValueError("advection must be 'central' or 'weno5z'")
         self.rho1, self.rho2 = p["rho1"], p["rho2"]
         self.rho0 = min(self.rho1, self.rho2)
         self.nu_m = p.get("nu_m", 0.0) or 0.5 * max(self.mu_s1, self.mu_s2) / self.rho0

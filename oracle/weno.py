@@ -3,7 +3,8 @@
 The paper advects phi (CH) and Theta (LCR) with the fifth-order WENO-Z
 scheme of Borges et al. (2008) (Section 3.2.1 and the text before Eq. NS40);
 the GPU path uses second-order central fluxes.  This is the oracle form of
-the WENO-Z alternative.  It is not yet used by the oracle's step.
+the WENO-Z alternative; the oracle's CH step takes it when the parameter
+"advection" is "weno5z" (default "central", as the GPU path).
 
 Face value at i+1/2 from the upwind side (velocity > 0: cells i-2..i+2):
   candidates  q0 = ( 2 v[i-2] - 7 v[i-1] + 11 v[i]) / 6
