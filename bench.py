@@ -501,9 +501,10 @@ def main():
 
     extra = {}
     if rank == 0 and not args.no_compare:
-        # accuracy of the mixed paths against the FP64 GPU path on the same input, per field
-        nst = 20
-        fields = ("phi", "u", "w", "p", "tau")
+        # accuracy of the mixed paths against the FP64 GPU path on the same input,
+        # per field, after the workload's stated number of steps
+        nst = w.steps if not args.nx else 20
+        fields = ("phi", "u", "v", "w", "p", "theta", "tau")
 
         def run_fields(prec, x0):
             sv = binding.Solver(g, w.params, prec, stream=stream.cuda_stream)

@@ -52,8 +52,8 @@ enum {
   PF_OK = 0,
   PF_ERR_ARG = -1,          /* invalid argument or call order                 */
   PF_ERR_DISCRIMINANT = -2, /* S below the bound of Eq. NS30                  */
-  PF_ERR_UNSUPPORTED = -3,  /* D_w != 0, Giesekus alpha != 0, size not 2^a3^b5^c7^d */
-  PF_ERR_NONFINITE = -4,    /* the FP64 phi-mass check saw NaN/Inf            */
+  PF_ERR_UNSUPPORTED = -3,  /* D_w != 0, size not 2^a3^b5^c7^d                 */
+  PF_ERR_NONFINITE = -4,    /* the phi-sum check (FP64 accumulator) saw NaN/Inf */
   PF_ERR_TIMEOUT = -5,      /* a bounded device-side wait expired             */
   PF_ERR_CUDA = -6,         /* a CUDA runtime call failed                     */
   PF_ERR_NOMEM = -7         /* device allocation failed                       */
@@ -141,7 +141,8 @@ int pf_set_fields(pf_ctx* ctx, int field_id, const void* src, size_t bytes, int 
 
 /* Advance nsteps time steps (Section 3.2 order: CH, restriction, NS,
  * polymer), replaying a captured CUDA graph per step.  Every 50 steps and
- * at the end, the FP64 phi-mass is checked; NaN/Inf -> PF_ERR_NONFINITE.
+ * at the end, a sum of phi (float4 loads, FP64 accumulator) is checked for
+ * NaN/Inf -> PF_ERR_NONFINITE.
  * Asynchronous otherwise. */
 int pf_step(pf_ctx* ctx, int nsteps);
 int pf_step_ex(pf_ctx* ctx, int nsteps, int flags);
@@ -207,14 +208,15 @@ void pf_batch_destroy(pf_batch* b);
  * It computes the six FP64 reductions of pf_diagnostics from a phase field
  * the caller already holds on the current device -- phi_device points to the
  * fine mesh of *g in the element type of g->precision (double for PF_FP64,
- * float for PF_MIXED), layout as above -- with no context and no allocation
+ * float for PF_MIXED and PF_MIXED_Z64), layout as above -- with no context and no allocation
  * of any kind.  Its scratch is one file-scope device array of 1 MiB that
  * every GPU which loads the library holds until the process exits; the
  * phase field may have at most 134,217,728 fine cells, larger fields are
  * rejected with PF_ERR_UNSUPPORTED.  Work is enqueued on `stream` (a
  * cudaStream_t, NULL for the legacy stream) and the call synchronises it.
- * The first call on a device resolves the array's device address; make that
- * first call before any stream capture.  All calls share the array: calls
+ * Every call resolves the array's device address with cudaGetSymbolAddress
+ * (cheap; no allocation); make the first call on a device before any stream
+ * capture, since the runtime may load the module at that call.  All calls share the array: calls
  * that overlap on the GPU (other streams, other threads) race and must be
  * serialised by the caller.  Each call overwrites every slot it reads, so
  * the contents left by an earlier call never matter.  Errors: PF_ERR_ARG,

@@ -6,10 +6,10 @@
 // pf_diagnostics_noalloc computes the same six FP64 reductions as
 // pf_diagnostics directly from a phase field the caller already holds on the
 // device, with no context and no allocation: the per-block partial sums live in
-// one file-scope device array of fixed size that the library reserves once per
-// GPU when it is loaded.
+// one file-scope device array of fixed size, which the CUDA runtime reserves on
+// each GPU by the time of the library's first call there (with lazy module
+// loading, at that first call).
 #include <cmath>
-#include <mutex>
 
 #include "../../include/dualpf.h"
 #include "reduce.cuh"
@@ -40,9 +40,6 @@ __global__ void k_noalloc_final(double* __restrict__ scratch, int nblocks) {
     for (int q = 0; q < RED_N; ++q) scratch[(size_t)kNoAllocBlocks * RED_N + q] = sh[q][0];
 }
 
-static std::mutex g_noalloc_mu;
-static double* g_noalloc_ptr[64] = {nullptr};
-
 }  // namespace pf
 
 extern "C" int pf_diagnostics_noalloc(const pf_grid_desc* g, const pf_params* prm, const void* phi_device,
@@ -51,7 +48,9 @@ extern "C" int pf_diagnostics_noalloc(const pf_grid_desc* g, const pf_params* pr
   auto fail = [](int code, const char*) { return code; };
   if (!g || !prm || !phi_device || !out) return fail(PF_ERR_ARG, "null argument");
   if (g->nx < 2 || g->ny < 1 || g->nz < 2 || !(g->lx > 0)) return fail(PF_ERR_ARG, "bad grid");
-  if (g->precision != PF_FP64 && g->precision != PF_MIXED) return fail(PF_ERR_ARG, "bad precision");
+  // PF_MIXED_Z64 stores phi as float, like PF_MIXED
+  if (g->precision != PF_FP64 && g->precision != PF_MIXED && g->precision != PF_MIXED_Z64)
+    return fail(PF_ERR_ARG, "bad precision");
   if (!(prm->eta > 0) || !(prm->sigma > 0)) return fail(PF_ERR_ARG, "eta and sigma must be > 0");
   Dims d{};
   d.nx = g->nx;
@@ -77,22 +76,18 @@ extern "C" int pf_diagnostics_noalloc(const pf_grid_desc* g, const pf_params* pr
   p.lam = 3.0 * prm->sigma * prm->eta / (2.0 * std::sqrt(2.0));
   p.cos_bot = std::cos(prm->theta_bot_deg * M_PI / 180.0);
   p.cos_top = std::cos(prm->theta_top_deg * M_PI / 180.0);
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return fail(PF_ERR_CUDA, "cudaGetDevice failed");
+  // Resolve the device address of the array on every call: it is cheap,
+  // allocates nothing, and stays right after a cudaDeviceReset (which starts
+  // a new context in which the array has a new address).
   double* scratch = nullptr;
   {
-    // first call on this device: resolve the device address of the array
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-      void* ptr = nullptr;
-      const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-      if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(PF_ERR_CUDA, cudaGetErrorString(e));
-      }
-      g_noalloc_ptr[dev] = static_cast<double*>(ptr);
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PF_ERR_CUDA, cudaGetErrorString(e));
     }
-    scratch = g_noalloc_ptr[dev];
+    scratch = static_cast<double*>(ptr);
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const double dy = d.dim == 3 ? d.h : g->ly;

@@ -119,7 +119,7 @@ def test_full_step_fp64(dim, nx, nz, dual, groups):
         th = s.coarse("theta")
         idx = [(0, 0), (0, 1), (1, 1)] if dim == 2 else [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
         for q, (a, b) in enumerate(idx):
-            assert rel(th[q], ref.theta[..., a, b]) < 1e-9, q
+            assert rel(th[q], ref.theta[..., a, b]) < FP64_TOL, q
 
 
 def test_config1_fp64_full_run():
@@ -239,7 +239,7 @@ def test_degenerate_cases_fp64(dim, nx, nz, theta):
 @pytest.mark.parametrize("alpha_g", [0.3])
 def test_giesekus_fp64_and_mixed_vs_oracle(cfg, nx, nz, alpha_g):
     """Giesekus mobility (Eqs. NS18, NS22) in the polymer update: FP64 GPU path
-    against the oracle at 1e-10 (Theta 1e-9), mixed at the viscoelastic
+    against the oracle at 1e-10, mixed at the viscoelastic
     tolerances, after steps from a seeded velocity and a seeded Theta of order
     one (so that the alpha term, quadratic in e^Theta - I, is not small)."""
     w = wl.scaled(wl.config(cfg), nx, nz)
@@ -274,7 +274,7 @@ def test_giesekus_fp64_and_mixed_vs_oracle(cfg, nx, nz, alpha_g):
             assert rel(s.coarse("u"), ref.vel[0]) < FP64_TOL
             assert rel(s.coarse("w"), ref.vel[2]) < FP64_TOL
             for q, (i, j) in enumerate(idx):
-                assert rel(th[q], ref.theta[..., i, j]) < 1e-9, q
+                assert rel(th[q], ref.theta[..., i, j]) < FP64_TOL, q
         else:
             assert np.max(np.abs(s.fine("phi") - ref.phi)) < 2e-4
             assert rel(s.coarse("u"), ref.vel[0]) < 1e-3

@@ -4,9 +4,9 @@ pf_diagnostics_noalloc exists for callers that cannot allocate device memory
 (an application whose pool owns the GPU, an allocator that forbids cudaMalloc,
 a real-time loop that must not stall on an allocation).  It reduces a phase
 field the caller already holds on the device, using only a fixed device array
-the library reserved when it was loaded.  Here it must give what
+the CUDA runtime reserves on the GPU by the library's first call there.  Here it must give what
 pf_diagnostics gives for the same field, on two calls in a row (the shared
-array keeps the previous call's contents), in both precisions, and it must
+array keeps the previous call's contents), in every precision, and it must
 refuse a field larger than its fixed array.
 
 This file is collected last on purpose: it runs after every other test.
@@ -27,7 +27,7 @@ def _close(a, b, scale):
     return abs(a - b) <= TOL * (abs(b) + scale)
 
 
-@pytest.mark.parametrize("prec", [binding.PF_FP64, binding.PF_MIXED])
+@pytest.mark.parametrize("prec", [binding.PF_FP64, binding.PF_MIXED, binding.PF_MIXED_Z64])
 @pytest.mark.parametrize("case", ["2d", "3d"])
 def test_noalloc_diagnostics_match_context_twice(prec, case):
     import torch
