@@ -116,11 +116,15 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def alg_bytes(grid, esize, visco=True):
+def alg_bytes(grid, esize, visco=True, compensated=None):
     """Algorithmic bytes per step of each kernel (all its launches in one step).
 
     Minimal traffic of the operation: each input read once, each output
-    written once (no halos, no re-reads)."""
+    written once (no halos, no re-reads).  FP32 contexts keep phi as a
+    compensated pair (value and rounding remainder): the CH right side reads
+    both remainders, the finishing transform reads both and writes one."""
+    if compensated is None:
+        compensated = esize == 4
     nzf, nyf, nxf = grid.fine_shape
     nf = nzf * nyf * nxf
     nz, ny, nx = grid.coarse_shape
@@ -134,11 +138,11 @@ def alg_bytes(grid, esize, visco=True):
     ncomp = 6 if d3 else 3
     nsolve = nvel + 1                        # velocity components + pressure
     b = {
-        "ch_rhs": 3 * E * nf + 2 * nvel * E * nc,
+        "ch_rhs": 3 * E * nf + 2 * nvel * E * nc + (2 * E * nf if compensated else 0),
         "rfft_x_fine": E * nf + 2 * E * sf,
         "fft_y_fine": 2 * 2 * (2 * E * sf) if d3 else 0,
         "zsolve_pair": 2 * 2 * E * sf,
-        "ch_ifftx_finish": 2 * E * sf + 3 * E * nf,
+        "ch_ifftx_finish": 2 * E * sf + 3 * E * nf + (3 * E * nf if compensated else 0),
         "ch_G_restrict": E * nf + (11 if d3 else 7) * E * nc,
         "ns_rhs": (2 * (nvel + 1) + (2 * ncomp if visco else 0) + (11 if d3 else 7) + nvel) * E * nc,
         "rfft_x_coarse": nvel * (E * nc + 2 * E * sc),
@@ -146,7 +150,8 @@ def alg_bytes(grid, esize, visco=True):
         "fft_y_coarse": (2 * nsolve * 2 * (2 * E * sc)) if d3 else 0,
         "zsolve": nsolve * 2 * (2 * E * sc),
         "zero_mode": 0,
-        "irfft_x_coarse": nsolve * (2 * E * sc + E * nc),
+        # the velocity solves' epilogue adds u* = 2 u^n - u^{n-1} back to the increment
+        "irfft_x_coarse": nsolve * (2 * E * sc + E * nc) + nvel * 2 * E * nc,
         "correct": (2 * nvel + 3) * E * nc,
         "polymer_stage1": (2 * ncomp + nvel) * E * nc,
         "polymer_stage2": (4 * ncomp + nvel + 1) * E * nc,

@@ -25,7 +25,7 @@ KNOBS = {
     5: ("ch_minb", [2, 3, 4], ("ch_rhs",)),
     6: ("ns_minb", [3, 4], ("ns_rhs",)),
     7: ("g_zchunk", [4, 8, 16], ("ch_G_restrict",)),
-    8: ("ns_kz", [1, 2, 4], ("ns_rhs",)),
+    8: ("ns_kz", [4, 8, 16, 32], ("ns_rhs",)),
 }
 
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "tuning.json")

@@ -36,7 +36,7 @@ struct FinePro {
 template <class T>
 struct PlainEpi {
   static constexpr const char* name = "irfft_x";
-  static constexpr bool kPre = false;
+  static constexpr int kNPre = 0;
   T* a;
   int n;
   __device__ __forceinline__ void operator()(int line, int x, T v) const { a[(size_t)line * n + x] = v; }
@@ -50,6 +50,7 @@ struct BatchProb {
   PhysT<T> q;
   T inv_mldt, inv_ml, div_coef, corr_coef;
   T* phi[2];
+  T* philo[2];  // remainders of phi (compensated FP32 storage) or null
   T *u[2], *v[2], *w[2], *pr[2];
   T *R, *ru, *rw, *wt, *pp, *dv;
   double *gwall, *zwork;
@@ -80,7 +81,7 @@ __device__ __forceinline__ void batch_run_item(const BatchProb<T>& B, int pass, 
   const int po = pc ^ 1, fo = fc ^ 1;
   switch (pass) {
     case BP_CH_RHS: {
-      const FineView<T> fv{B.phi[pc], B.phi[po]};
+      const FineView<T> fv{B.phi[pc], B.phi[po], B.philo[pc], B.philo[po]};
       const CoarseVel<T> vel{B.u[fc], B.u[fo], B.v[fc], B.v[fo], B.w[fc], B.w[fo]};
       k_ch_rhs_b<T, 2>(fv, vel, B.R, B.gwall, d, B.p, B.q, B.inv_mldt, B.inv_ml, bid, sm);
       break;
@@ -90,8 +91,8 @@ __device__ __forceinline__ void batch_run_item(const BatchProb<T>& B, int pass, 
       break;
     case BP_ZPAIR: k_zsolve_b<T, T>(B.spF, B.eFx, B.eFy, B.zpair, B.tx, bid, sm); break;
     case BP_IFFT_F:
-      k_irfft_x_b<T, ChFinish<T>>(B.spF, ChFinish<T>{B.phi[pc], B.phi[po], d.fnx}, d.fnx, d.fnz, B.pF, B.plFx, B.twFx,
-                                  B.npairF, (T)1, bid, sm);
+      k_irfft_x_b<T, ChFinish<T>>(B.spF, ChFinish<T>{B.phi[pc], B.phi[po], d.fnx, B.philo[pc], B.philo[po]}, d.fnx,
+                                  d.fnz, B.pF, B.plFx, B.twFx, B.npairF, (T)1, bid, sm);
       break;
     case BP_GRES:
       if (d.r == 2) k_ch_G_restrict_b<T, 2, 2>(B.phi[po], B.gwall, B.rs, d, B.q, bid, sm);
@@ -103,8 +104,8 @@ __device__ __forceinline__ void batch_run_item(const BatchProb<T>& B, int pass, 
       break;
     case BP_U_Z: k_zsolve_b<T, T>(B.spU, B.eCx, B.eCy, B.zu, B.tx, bid, sm); break;
     case BP_U_IFFT:
-      k_irfft_x_b<T, PlainEpi<T>>(B.spU, PlainEpi<T>{B.u[fo], d.nx}, d.nx, d.nz, B.pC, B.plCx, B.twCx, B.npairC, (T)1,
-                                  bid, sm);
+      k_irfft_x_b<T, IncEpi<T>>(B.spU, IncEpi<T>{B.u[fo], B.u[fc], B.u[fo], d.nx, 0}, d.nx, d.nz, B.pC, B.plCx,
+                                B.twCx, B.npairC, (T)1, bid, sm);
       break;
     case BP_W_RFFT:
       k_rfft_x_b<T, FinePro<T>>(FinePro<T>{B.rw, d.nx}, B.spW, d.nx, d.nz - 1, B.pC, B.plCx, B.twCx, B.npairC, bid,
@@ -112,8 +113,8 @@ __device__ __forceinline__ void batch_run_item(const BatchProb<T>& B, int pass, 
       break;
     case BP_W_Z: k_zsolve_b<T, T>(B.spW, B.eCx, B.eCy, B.zw, B.tx, bid, sm); break;
     case BP_W_IFFT:
-      k_irfft_x_b<T, PlainEpi<T>>(B.spW, PlainEpi<T>{B.wt, d.nx}, d.nx, d.nz - 1, B.pC, B.plCx, B.twCx, B.npairC, (T)1,
-                                  bid, sm);
+      k_irfft_x_b<T, IncEpi<T>>(B.spW, IncEpi<T>{B.wt, B.w[fc], B.w[fo], d.nx, (size_t)d.nx * d.ny}, d.nx, d.nz - 1,
+                                B.pC, B.plCx, B.twCx, B.npairC, (T)1, bid, sm);
       break;
     case BP_DIV: k_div_b<T>(B.u[fo], B.v[fo], B.wt, B.dv, d, B.div_coef, bid, sm); break;
     case BP_P_RFFT:

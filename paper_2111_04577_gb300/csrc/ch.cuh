@@ -17,6 +17,7 @@
 // B(g) = g/h on the wall layers, g = n.grad(phi) of the contact-angle law
 // (Eq. NS34), evaluated in FP64 at phi*_w = 1.5 phi*_0 - 0.5 phi*_1.
 #pragma once
+#include <type_traits>
 #include "common.cuh"
 
 namespace pf {
@@ -25,7 +26,19 @@ template <class T>
 struct FineView {
   const T* pn;   // phi^n
   const T* po;   // phi^{n-1}
+  // Compensated storage (FP32 contexts): the rounding remainders of phi^n and
+  // phi^{n-1} (phi = value + remainder to about 2^-48 relative), or null.  Only
+  // the BDF2 difference phi^{n-1} - phi^n, of the size of one step's change,
+  // needs them; phi* and every stencil take the stored values.
+  const T* ln = nullptr;
+  const T* lo = nullptr;
   __device__ __forceinline__ T star(size_t i) const { return (T)2 * pn[i] - po[i]; }
+  // phi^{n-1} - phi^n at i, given the stored values a = phi^n[i], b = phi^{n-1}[i]
+  __device__ __forceinline__ T back(size_t i, T a, T b) const {
+    T r = b - a;
+    if (ln) r += lo[i] - ln[i];
+    return r;
+  }
 };
 
 // Contact-angle flux (Eqs. NS15-NS16, NS34 with D_w = 0), in W = Wide<T>
@@ -73,19 +86,33 @@ struct CoarseVel {
 template <class T>
 struct ChFinish {
   static constexpr const char* name = "ch_ifftx_finish";
-  static constexpr bool kPre = true;  // phi^n, phi^{n-1} are staged before the transform
+  // phi^n, phi^{n-1} -- and in FP32 contexts their remainders (compensated
+  // storage, see FineView) -- are staged into shared memory before the transform
+  static constexpr int kNPre = std::is_same<T, float>::value ? 4 : 2;
   const T* pn;
   T* po_new;  // holds phi^{n-1} on entry, phi^{n+1} on exit
   int fnx;
-  __device__ __forceinline__ const T* pre0() const { return pn; }
-  __device__ __forceinline__ const T* pre1() const { return po_new; }
+  const T* ln = nullptr;  // remainder of phi^n (FP32: required)
+  T* lo_new = nullptr;    // remainder of phi^{n-1} on entry, of phi^{n+1} on exit
+  __device__ __forceinline__ const T* pre(int j) const { return j == 0 ? pn : (j == 1 ? po_new : (j == 2 ? ln : lo_new)); }
   __device__ __forceinline__ int pre_n() const { return fnx; }
-  __device__ __forceinline__ void apply(int line, int i, T delta, T vn, T vo) const {
-    po_new[(size_t)line * fnx + i] = (T)2 * vn - vo + delta;
-  }
-  __device__ __forceinline__ void operator()(int line, int i, T delta) const {
+  // pv[j * stride]: the staged value of array j at (line, i)
+  __device__ __forceinline__ void apply(int line, int i, T delta, const T* pv, int stride) const {
     const size_t id = (size_t)line * fnx + i;
-    po_new[id] = (T)2 * pn[id] - po_new[id] + delta;
+    const T vn = pv[0], vo = pv[stride];
+    if constexpr (kNPre == 2) {
+      po_new[id] = (T)2 * vn - vo + delta;
+    } else {
+      // phi^{n+1} = 2 phi^n - phi^{n-1} + delta with the remainders carried: the
+      // exact sum 2 vn - vo is split by TwoSum, the small terms are added to its
+      // error, and the total is split again into value and remainder
+      T s, e, hi, lo;
+      two_sum((T)2 * vn, -vo, s, e);
+      const T t = e + ((T)2 * pv[2 * stride] - pv[3 * stride]) + delta;
+      two_sum(s, t, hi, lo);
+      po_new[id] = hi;
+      lo_new[id] = lo;
+    }
   }
 };
 

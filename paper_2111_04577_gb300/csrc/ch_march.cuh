@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(MarchTile::NT, MINB) k_ch_rhs_march(const Fine
         const size_t o = zo + sxy[k];
         const T a = f.pn[o], b = f.po[o];
         reg[k] = (T)2 * a - b;
-        dreg[k] = b - a;
+        dreg[k] = f.back(o, a, b);
       }
     }
   };
@@ -694,11 +694,18 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
   star_load(zb + 2);
   // owned phi^n and phi^{n-1} of the plane being formed, read one plane ahead
   // (an L2 hit: the plane was staged three planes earlier)
-  float4 an = make_float4(0.f, 0.f, 0.f, 0.f), bo = an;
-  if (act) {
-    an = *reinterpret_cast<const float4*>(f.pn + (size_t)zb * plane + gof);
-    bo = *reinterpret_cast<const float4*>(f.po + (size_t)zb * plane + gof);
-  }
+  // (with compensated storage also the remainders' difference dl = lo - ln)
+  float4 an = make_float4(0.f, 0.f, 0.f, 0.f), bo = an, dl = an;
+  auto own_load = [&](int zz) {
+    const size_t o = (size_t)zz * plane + gof;
+    an = *reinterpret_cast<const float4*>(f.pn + o);
+    bo = *reinterpret_cast<const float4*>(f.po + o);
+    if (f.ln) {
+      const float4 a = *reinterpret_cast<const float4*>(f.ln + o), b = *reinterpret_cast<const float4*>(f.lo + o);
+      dl = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, b.w - a.w);
+    }
+  };
+  if (act) own_load(zb);
   int kc_loaded = -1;
   // ring positions m % 5 and m % 3, advanced per plane (no integer division in the loop)
   int m5 = 0, m3 = 0;
@@ -774,7 +781,9 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
     const float4 mzm4 = *reinterpret_cast<const float4*>(mmm + mo);
     const float muv[4] = {mu4.x, mu4.y, mu4.z, mu4.w}, mdv[4] = {md4.x, md4.y, md4.z, md4.w};
     const float mzpv[4] = {mzp4.x, mzp4.y, mzp4.z, mzp4.w}, mzmv[4] = {mzm4.x, mzm4.y, mzm4.z, mzm4.w};
-    const float dv[4] = {bo.x - an.x, bo.y - an.y, bo.z - an.z, bo.w - an.w};
+    // phi^{n-1} - phi^n: the stored values' difference first (exact when they are
+    // close), then the remainders' (zero without compensated storage)
+    const float dv[4] = {(bo.x - an.x) + dl.x, (bo.y - an.y) + dl.y, (bo.z - an.z) + dl.z, (bo.w - an.w) + dl.w};
     float out[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -794,10 +803,7 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
     }
     if (!act) continue;
     *reinterpret_cast<float4*>(R + (size_t)z * plane + gof) = make_float4(out[0], out[1], out[2], out[3]);
-    if (z + 1 < ze) {
-      an = *reinterpret_cast<const float4*>(f.pn + (size_t)(z + 1) * plane + gof);
-      bo = *reinterpret_cast<const float4*>(f.po + (size_t)(z + 1) * plane + gof);
-    }
+    if (z + 1 < ze) own_load(z + 1);
   }
 }
 

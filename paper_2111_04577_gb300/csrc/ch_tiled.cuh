@@ -171,7 +171,7 @@ __device__ __forceinline__ void k_ch_rhs_b(const FineView<T> f, const CoarseVel<
     const T mzm = gz > 0 ? M(mz - 1, my, mx) : m0;
     lap = (lap + mzp + mzm - 2 * m0) * q.ih2;
     const size_t o = (size_t)gz * plane + (size_t)gy * fnx + gx;
-    R[o] = (f.po[o] - f.pn[o]) * inv_mldt - adv * inv_ml + lap;
+    R[o] = f.back(o, f.pn[o], f.po[o]) * inv_mldt - adv * inv_ml + lap;
   }
 }
 

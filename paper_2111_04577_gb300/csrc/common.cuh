@@ -115,6 +115,15 @@ __host__ __device__ __forceinline__ size_t fidx(const Dims& d, int i, int j, int
 __host__ __device__ __forceinline__ size_t cidx(const Dims& d, int i, int j, int k) {
   return ((size_t)k * d.ny + j) * d.nx + i;
 }
+// Knuth's TwoSum (The Art of Computer Programming, Vol. 2, 4.2.2): s = fl(a + b)
+// and e with s + e = a + b exactly, for any a, b, in round-to-nearest.
+template <class T>
+__host__ __device__ __forceinline__ void two_sum(T a, T b, T& s, T& e) {
+  s = a + b;
+  const T bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
 __host__ __device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
 // ---------------------------------------------------------------------------

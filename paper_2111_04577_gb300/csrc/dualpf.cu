@@ -27,6 +27,7 @@
 #include "fft_reg.cuh"
 #include "ns.cuh"
 #include "ns_rhs.cuh"
+#include "ns_march.cuh"
 #include "polymer.cuh"
 #include "reduce.cuh"
 #include "spectral.cuh"
@@ -128,7 +129,7 @@ struct FineArrPro {
 template <class T>
 struct ArrEpi {
   static constexpr const char* name = "irfft_x_coarse";
-  static constexpr bool kPre = false;
+  static constexpr int kNPre = 0;
   T* a;
   int n;
   __device__ __forceinline__ void operator()(int line, int x, T v) const { a[(size_t)line * n + x] = v; }
@@ -218,6 +219,9 @@ struct Impl : ImplBase {
   int ncomp;
   // fields
   T *phi[2], *u[2], *v[2], *w[2], *pr[2];
+  // FP32 contexts: the rounding remainders of phi at both parities (compensated
+  // storage, phi = phi + philo to about 2^-48 relative); null otherwise
+  T* philo[2] = {nullptr, nullptr};
   T *theta[6], *theta1[6], *tau[2][6];
   T *mu, *G;
   Wide<T>* gwall;  // contact-line flux g of both walls (FP64; Dual when derivatives are carried)
@@ -275,6 +279,7 @@ struct Impl : ImplBase {
     const size_t ncw = (size_t)d.nx * d.ny * (d.nz + 1);
     for (int q = 0; q < 2; ++q) {
       phi[q] = ar.get<T>(nf);
+      if constexpr (std::is_same<T, float>::value) philo[q] = ar.get<T>(nf);
       u[q] = ar.get<T>(nc);
       v[q] = d.dim == 3 ? ar.get<T>(nc) : ar.get<T>(1);
       w[q] = ar.get<T>(ncw);
@@ -441,6 +446,8 @@ struct Impl : ImplBase {
       PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march4<0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     }
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict_march<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PF_CUDA_TRY(cudaFuncSetAttribute(k_ns_rhs_march3<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PF_CUDA_TRY(cudaFuncSetAttribute(k_ns_rhs_march3<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_zero_mode_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     for (int n : {64, 128, 256, 512, 1024})
       reg_fft_dispatch(n, [&](auto NN) {
@@ -450,6 +457,7 @@ struct Impl : ImplBase {
         PF_CUDA_TRY(cudaFuncSetAttribute(k_rfft_x_reg<T, N, DivPro<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
         PF_CUDA_TRY(cudaFuncSetAttribute(k_irfft_x_reg<T, N, ChFinish<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
         PF_CUDA_TRY(cudaFuncSetAttribute(k_irfft_x_reg<T, N, ArrEpi<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+        PF_CUDA_TRY(cudaFuncSetAttribute(k_irfft_x_reg<T, N, IncEpi<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
         PF_CUDA_TRY(cudaFuncSetAttribute(k_fft_y_reg<T, N, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
       });
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict<T, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
@@ -458,6 +466,7 @@ struct Impl : ImplBase {
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict<T, 3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_irfft_x<T, ChFinish<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_irfft_x<T, ArrEpi<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+    PF_CUDA_TRY(cudaFuncSetAttribute(k_irfft_x<T, IncEpi<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
   }
 
   // ------------------------------------------------------------------ launches
@@ -506,7 +515,7 @@ struct Impl : ImplBase {
     if (reg_fft_size(n)) {
       int lpc = reg_lpc(n);
       const int pairs = (nlines + 1) / 2;
-      const size_t per_line = (size_t)n * (sizeof(cpx<T>) + (Epi::kPre ? 4 * sizeof(T) : 0));
+      const size_t per_line = (size_t)n * (sizeof(cpx<T>) + 2 * Epi::kNPre * sizeof(T));
       while (lpc > 1 && (size_t)lpc * per_line > (size_t)kMaxSmem) lpc /= 2;
       const size_t sm = (size_t)lpc * per_line;
       mark(Epi::name);
@@ -601,17 +610,22 @@ struct Impl : ImplBase {
 
   // one transform solve on the coarse mesh: rhs (real, lines of nx) -> out
   void coarse_solve(const T* rhs, T* out, cpx<T>* sp, int rows, int bc, double shift, bool poisson) {
-    coarse_solve_pro(ArrPro<T>{rhs, d.nx}, out, sp, rows, bc, shift, poisson);
+    coarse_solve_pro(ArrPro<T>{rhs, d.nx}, ArrEpi<T>{out, d.nx}, sp, rows, bc, shift, poisson);
   }
-  template <class Pro>
-  void coarse_solve_pro(Pro pro, T* out, cpx<T>* sp, int rows, int bc, double shift, bool poisson) {
+  // velocity solve for the increment u~ - u*; out = u~ (IncEpi adds u* back)
+  void velocity_solve(const T* rhs, T* out, const T* un, const T* uo, size_t off, cpx<T>* sp, int rows, int bc,
+                      double shift) {
+    coarse_solve_pro(ArrPro<T>{rhs, d.nx}, IncEpi<T>{out, un, uo, d.nx, off}, sp, rows, bc, shift, false);
+  }
+  template <class Pro, class Epi>
+  void coarse_solve_pro(Pro pro, Epi epi, cpx<T>* sp, int rows, int bc, double shift, bool poisson) {
     const int nlines = d.ny * rows;
     rfft_x(pro, sp, d.nx, nlines, pC, plCx, twCx);
     if (d.dim == 3) fft_y(sp, d.ny, pC, d.nx / 2 + 1, rows, plCy, twCy, -1);
     zsolve(sp, rows, d.ny, pC, d.nx / 2 + 1, eCx, eCy, bc, d.dx * d.dx, shift, shift, false,
            1.0 / ((double)d.nx * d.ny), poisson);
     if (d.dim == 3) fft_y(sp, d.ny, pC, d.nx / 2 + 1, rows, plCy, twCy, +1);
-    irfft_x(sp, ArrEpi<T>{out, d.nx}, d.nx, nlines, pC, plCx, twCx, (T)1);
+    irfft_x(sp, epi, d.nx, nlines, pC, plCx, twCx, (T)1);
   }
 
   // pend_in: first run the owed polymer update (parity fc) on the side stream,
@@ -625,7 +639,7 @@ struct Impl : ImplBase {
       PF_CUDA_TRY(cudaEventRecord(ev_join, st2));
     }
     // ---- Cahn-Hilliard on the fine mesh ----
-    FineView<T> fv{phi[pc], phi[po]};
+    FineView<T> fv{phi[pc], phi[po], philo[pc], philo[po]};
     const CoarseVel<T> vel{u[fc], u[fo], v[fc], v[fo], w[fc], w[fo]};
     T inv_mldt = (T)(1.0 / (p.Ml * p.dt)), inv_ml = (T)(1.0 / p.Ml);
     if constexpr (IsDual<T>::value) {
@@ -671,7 +685,7 @@ struct Impl : ImplBase {
     zsolve(spF, d.fnz, d.fny, pF, d.fnx / 2 + 1, eFx, eFy, Z_NEUMANN, d.h * d.h, p.c, -p.alpha, true,
            1.0 / ((double)d.fnx * d.fny), false, dseed.c, -dseed.alpha);
     if (d.dim == 3) fft_y(spF, d.fny, pF, d.fnx / 2 + 1, d.fnz, plFy, twFy, +1);
-    irfft_x(spF, ChFinish<T>{phi[pc], phi[po], d.fnx}, d.fnx, nlf, pF, plFx, twFx, (T)1);
+    irfft_x(spF, ChFinish<T>{phi[pc], phi[po], d.fnx, philo[pc], philo[po]}, d.fnx, nlf, pF, plFx, twFx, (T)1);
     if (flags & PF_STEP_CH_ONLY) return;
     if (pend_in) PF_CUDA_TRY(cudaStreamWaitEvent(st, ev_join, 0));  // the update read the restricted phi
     // ---- chemical potential and restriction to the coarse mesh ----
@@ -720,6 +734,14 @@ struct Impl : ImplBase {
       if (d.dim == 2) {
         if (ns3) k_ns_rhs_v2z<T, 2, 3><<<gz, lc.block, 0, st>>>(A, d, q, ru, rv, rw, p.visco, kz);
         else k_ns_rhs_v2z<T, 2, 4><<<gz, lc.block, 0, st>>>(A, d, q, ru, rv, rw, p.visco, kz);
+      } else if (d.nx >= NsMarch::TX && d.ny >= NsMarch::TY) {
+        // z-march through shared memory; the chunk is the same knob (layers per CTA)
+        const int kc = tune[PF_TUNE_NS_KZ] > 1 ? tune[PF_TUNE_NS_KZ] : 16;
+        const dim3 gm((d.nx + NsMarch::TX - 1) / NsMarch::TX, (d.ny + NsMarch::TY - 1) / NsMarch::TY,
+                      (d.nz + kc - 1) / kc);
+        const size_t sm = NsMarch::smem_elems() * sizeof(T);
+        if (ns3) k_ns_rhs_march3<T, 3><<<gm, NsMarch::NT, sm, st>>>(A, d, q, ru, rv, rw, p.visco, kc);
+        else k_ns_rhs_march3<T, 4><<<gm, NsMarch::NT, sm, st>>>(A, d, q, ru, rv, rw, p.visco, kc);
       } else {
         if (ns3) k_ns_rhs_v2z<T, 3, 3><<<gz, lc.block, 0, st>>>(A, d, q, ru, rv, rw, p.visco, kz);
         else k_ns_rhs_v2z<T, 3, 4><<<gz, lc.block, 0, st>>>(A, d, q, ru, rv, rw, p.visco, kz);
@@ -729,32 +751,33 @@ struct Impl : ImplBase {
     // u~, v~ land in the n-1 buffers (free once the right sides exist).  The
     // three solves share nothing but their inputs, so outside pf_profile (which
     // times kernels one after another) they run on three streams.
+    const size_t P = (size_t)d.nx * d.ny;
     if (!prof) {
       ensure_side_stream();
       PF_CUDA_TRY(cudaEventRecord(ev_ns, st));
       PF_CUDA_TRY(cudaStreamWaitEvent(st2, ev_ns, 0));
       {
         OnStream on(st, st2);
-        coarse_solve(rw, wt, spW, d.nz - 1, Z_FACES, kk, false);
+        velocity_solve(rw, wt, w[fc], w[fo], P, spW, d.nz - 1, Z_FACES, kk);
         PF_CUDA_TRY(cudaEventRecord(ev_w, st));
       }
       if (d.dim == 3) {
         PF_CUDA_TRY(cudaStreamWaitEvent(st3, ev_ns, 0));
         OnStream on(st, st3);
-        coarse_solve(rv, v[fo], spV, d.nz, Z_DIRICH, kk, false);
+        velocity_solve(rv, v[fo], v[fc], v[fo], 0, spV, d.nz, Z_DIRICH, kk);
         PF_CUDA_TRY(cudaEventRecord(ev_v, st));
       }
-      coarse_solve(ru, u[fo], spU, d.nz, Z_DIRICH, kk, false);
+      velocity_solve(ru, u[fo], u[fc], u[fo], 0, spU, d.nz, Z_DIRICH, kk);
       PF_CUDA_TRY(cudaStreamWaitEvent(st, ev_w, 0));
       if (d.dim == 3) PF_CUDA_TRY(cudaStreamWaitEvent(st, ev_v, 0));
     } else {
-      coarse_solve(ru, u[fo], spU, d.nz, Z_DIRICH, kk, false);
-      if (d.dim == 3) coarse_solve(rv, v[fo], spV, d.nz, Z_DIRICH, kk, false);
-      coarse_solve(rw, wt, spW, d.nz - 1, Z_FACES, kk, false);
+      velocity_solve(ru, u[fo], u[fc], u[fo], 0, spU, d.nz, Z_DIRICH, kk);
+      if (d.dim == 3) velocity_solve(rv, v[fo], v[fc], v[fo], 0, spV, d.nz, Z_DIRICH, kk);
+      velocity_solve(rw, wt, w[fc], w[fo], P, spW, d.nz - 1, Z_FACES, kk);
     }
     // pressure Poisson (Eq. NS37), its right side formed inside the first transform
-    coarse_solve_pro(DivPro<T>{u[fo], v[fo], wt, d, (T)(p.gamma0 * p.rho0 / p.dt), (T)(1.0 / d.dx)}, pp, spP, d.nz,
-                     Z_NEUMANN, 0.0, true);
+    coarse_solve_pro(DivPro<T>{u[fo], v[fo], wt, d, (T)(p.gamma0 * p.rho0 / p.dt), (T)(1.0 / d.dx)},
+                     ArrEpi<T>{pp, d.nx}, spP, d.nz, Z_NEUMANN, 0.0, true);
     mark("correct");
     {
       constexpr int kzc = 8;
@@ -859,6 +882,12 @@ struct Impl : ImplBase {
     flush_polymer();
     if (f == PF_G) throw ApiError(PF_ERR_ARG, "PF_G is read-only");
     copy_field(f, src, bytes, on_dev);
+    // phi set from outside carries no remainder
+    const size_t nfb = (size_t)d.fnx * d.fny * d.fnz * sizeof(T);
+    if (philo[0] && (f == PF_PHI || f == PF_PHI_OLD)) {
+      PF_CUDA_TRY(cudaMemsetAsync(philo[f == PF_PHI ? pc : pc ^ 1], 0, nfb, st));
+      if (f == PF_PHI) PF_CUDA_TRY(cudaMemsetAsync(philo[pc ^ 1], 0, nfb, st));
+    }
     int twin = -1;
     if (f == PF_PHI) twin = PF_PHI_OLD;
     if (f == PF_U) twin = PF_U_OLD;
@@ -952,7 +981,8 @@ struct Impl : ImplBase {
   std::vector<T*> ck_n, ck_o, st_buf;
   T *a_phis = nullptr, *a_adv = nullptr, *a_delta = nullptr, *a_eps = nullptr, *a_ebar = nullptr,
     *a_rbar = nullptr, *a_mubar = nullptr, *a_tmp = nullptr, *a_next = nullptr, *a_cur = nullptr,
-    *a_next2 = nullptr, *a_cur2 = nullptr, *a_fin_n = nullptr, *a_fin_o = nullptr;
+    *a_next2 = nullptr, *a_cur2 = nullptr, *a_fin_n = nullptr, *a_fin_o = nullptr, *a_fin_nl = nullptr,
+    *a_fin_ol = nullptr;
   double *a_thb = nullptr, *a_part = nullptr;
 
   void adj_alloc(int K, int nseg) {
@@ -961,10 +991,13 @@ struct Impl : ImplBase {
     const size_t nf = (size_t)d.fnx * d.fny * d.fnz;
     ck_n.assign(nseg, nullptr);
     ck_o.assign(nseg, nullptr);
+    const size_t per = philo[0] ? 2 * nf : nf;  // value, then remainder
     for (int s = 0; s < nseg; ++s) {
-      ck_n[s] = adj_ar->get<T>(nf);
-      ck_o[s] = adj_ar->get<T>(nf);
+      ck_n[s] = adj_ar->get<T>(per);
+      ck_o[s] = adj_ar->get<T>(per);
     }
+    a_fin_nl = philo[0] ? adj_ar->get<T>(nf) : nullptr;
+    a_fin_ol = philo[0] ? adj_ar->get<T>(nf) : nullptr;
     st_buf.assign(K + 2, nullptr);
     for (int m = 0; m < K + 2; ++m) st_buf[m] = adj_ar->get<T>(nf);
     T** ws[] = {&a_phis, &a_adv, &a_delta, &a_eps, &a_ebar, &a_rbar, &a_mubar, &a_tmp,
@@ -979,6 +1012,16 @@ struct Impl : ImplBase {
   void dcopy(T* dst, const T* src) {
     const size_t nf = (size_t)d.fnx * d.fny * d.fnz;
     PF_CUDA_TRY(cudaMemcpyAsync(dst, src, nf * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  }
+  // phi of parity q with its remainder (compensated storage) to or from a
+  // checkpoint of 2 nf elements (nf without remainders)
+  void save_phi(T* ck, int q) {
+    dcopy(ck, phi[q]);
+    if (philo[q]) dcopy(ck + (size_t)d.fnx * d.fny * d.fnz, philo[q]);
+  }
+  void load_phi(int q, const T* ck) {
+    dcopy(phi[q], ck);
+    if (philo[q]) dcopy(philo[q], ck + (size_t)d.fnx * d.fny * d.fnz);
   }
 
   // out = (L_N - c)^-1 (L_N + alpha)^-1 in: the forward step's paired transform solve
@@ -1068,8 +1111,8 @@ struct Impl : ImplBase {
       const size_t nf = (size_t)d.fnx * d.fny * d.fnz;
       // forward sweep with checkpoints of the BDF2 state (phi^n, phi^{n-1})
       for (int s = 0; s < nseg; ++s) {
-        dcopy(ck_n[s], phi[pc]);
-        dcopy(ck_o[s], phi[pc ^ 1]);
+        save_phi(ck_n[s], pc);
+        save_phi(ck_o[s], pc ^ 1);
         step(std::min(K, nsteps - s * K), PF_STEP_CH_ONLY);
       }
       double dg[6];
@@ -1077,6 +1120,10 @@ struct Impl : ImplBase {
       const double J = which == 0 ? dg[2] : dg[5];
       dcopy(a_fin_n, phi[pc]);
       dcopy(a_fin_o, phi[pc ^ 1]);
+      if (philo[0]) {
+        dcopy(a_fin_nl, philo[pc]);
+        dcopy(a_fin_ol, philo[pc ^ 1]);
+      }
       const RowLaunch lf = rows(d.fny * d.fnz, d.fnx);
       const double D = 0.5 * ((double)nf + dg[0] / std::pow(d.h, d.dim));
       k_obj_seed<T><<<lf.grid, lf.block, 0, st>>>(a_next, d, which, dg[5], D);
@@ -1085,8 +1132,8 @@ struct Impl : ImplBase {
       for (int s = nseg - 1; s >= 0; --s) {
         const int len = std::min(K, nsteps - s * K);
         // recompute the segment: st_buf[0] = phi^{sK-1}, st_buf[m+1] = phi^{sK+m}
-        dcopy(phi[pc], ck_n[s]);
-        dcopy(phi[pc ^ 1], ck_o[s]);
+        load_phi(pc, ck_n[s]);
+        load_phi(pc ^ 1, ck_o[s]);
         dcopy(st_buf[0], ck_o[s]);
         dcopy(st_buf[1], ck_n[s]);
         for (int m = 1; m <= len; ++m) {
@@ -1111,6 +1158,10 @@ struct Impl : ImplBase {
       // leave the context at phi^N, as pf_step would
       dcopy(phi[pc], a_fin_n);
       dcopy(phi[pc ^ 1], a_fin_o);
+      if (philo[0]) {
+        dcopy(philo[pc], a_fin_nl);
+        dcopy(philo[pc ^ 1], a_fin_ol);
+      }
       PF_CUDA_TRY(cudaStreamSynchronize(st));
       out[0] = J;
       out[1] = thb * M_PI / 180.0;
@@ -1296,6 +1347,7 @@ struct Batch : BatchBase {
       B.corr_coef = (T)(I.p.dt / (I.p.gamma0 * I.p.rho0));
       for (int k = 0; k < 2; ++k) {
         B.phi[k] = I.phi[k];
+        B.philo[k] = I.philo[k];
         B.u[k] = I.u[k];
         B.v[k] = I.v[k];
         B.w[k] = I.w[k];

@@ -155,32 +155,35 @@ __global__ void __launch_bounds__(1024) __maxnreg__(sizeof(T) == 4 ? 48 : 64) k_
 // ---------------------------------------------------------------------------
 // Inverse real FFT along x (as k_irfft_x): the input A + iB of each line pair
 // is built in registers from the two half spectra, the output goes from
-// registers to the epilogue.  An epilogue with kPre has its two arrays copied
-// into shared memory by cp.async before the transform (smem after the line
-// buffers: LPC * 4 * N elements of T).  Line buffers: LPC * N complex.
+// registers to the epilogue.  An epilogue with kNPre > 0 has its kNPre arrays
+// copied into shared memory by cp.async before the transform (smem after the
+// line buffers: LPC * 2 * kNPre * N elements of T).  Line buffers: LPC * N complex.
 // ---------------------------------------------------------------------------
 template <class T, int N, class Epi>
 __global__ void __launch_bounds__(1024) k_irfft_x_reg(const cpx<T>* __restrict__ in, Epi epi, int nlines, int pitch,
                                                       const cpx<T>* __restrict__ tw, T scale) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int NT = N / 8;
+  constexpr int NP = Epi::kNPre;
   const int m = threadIdx.x / NT, t = threadIdx.x % NT;
   const int lpc = blockDim.x / NT;
   const int l0 = 2 * (blockIdx.x * lpc + m), l1 = l0 + 1;
   cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw) + (size_t)m * N;  // unpadded line buffers
-  T* pre = reinterpret_cast<T*>(reinterpret_cast<cpx<T>*>(smraw) + (size_t)lpc * N) + (size_t)m * 4 * N;
-  if constexpr (Epi::kPre) {
+  // [line of the pair][array][N]
+  T* pre = reinterpret_cast<T*>(reinterpret_cast<cpx<T>*>(smraw) + (size_t)lpc * N) + (size_t)m * 2 * NP * N;
+  if constexpr (NP > 0) {
 #pragma unroll
     for (int li = 0; li < 2; ++li) {
       const int l = l0 + li;
       if (l >= nlines) continue;
-      const T* s0 = epi.pre0() + (size_t)l * epi.pre_n();
-      const T* s1 = epi.pre1() + (size_t)l * epi.pre_n();
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int x = t + NT * q;
-        cp_async_elem(pre + (size_t)(2 * li) * N + x, s0 + x);
-        cp_async_elem(pre + (size_t)(2 * li + 1) * N + x, s1 + x);
+      for (int j = 0; j < NP; ++j) {
+        const T* src = epi.pre(j) + (size_t)l * epi.pre_n();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int x = t + NT * q;
+          cp_async_elem(pre + (size_t)(li * NP + j) * N + x, src + x);
+        }
       }
     }
     cp_async_commit();
@@ -200,14 +203,14 @@ __global__ void __launch_bounds__(1024) k_irfft_x_reg(const cpx<T>* __restrict__
     v[c] = mk(A.re - B.im, A.im + B.re);  // A + i B
   }
   reg_fft<T, N, 8, false>(v, sm, tw, +1, t);  // unpadded here: fewer registers measured faster
-  if constexpr (Epi::kPre) cp_async_wait_all();  // this thread's own copies
+  if constexpr (NP > 0) cp_async_wait_all();  // this thread's own copies
   if (l0 >= nlines) return;
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const int x = t + NT * q;
-    if constexpr (Epi::kPre) {
-      epi.apply(l0, x, v[q].re * scale, pre[x], pre[N + x]);
-      if (l1 < nlines) epi.apply(l1, x, v[q].im * scale, pre[2 * N + x], pre[3 * N + x]);
+    if constexpr (NP > 0) {
+      epi.apply(l0, x, v[q].re * scale, pre + x, N);
+      if (l1 < nlines) epi.apply(l1, x, v[q].im * scale, pre + (size_t)NP * N + x, N);
     } else {
       epi(l0, x, v[q].re * scale);
       if (l1 < nlines) epi(l1, x, v[q].im * scale);

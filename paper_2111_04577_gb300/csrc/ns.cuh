@@ -9,14 +9,40 @@
 // from the restricted phi^{n+1} (Eqs. dual2, dual3), second-order central
 // differences on the staggered mesh, 4-point averages for quantities needed
 // off their home location, no-slip ghosts 2 u_w - u, mirror ghosts for tau.
-// k_ns_rhs writes the right side divided by nu_m (minus the wall-velocity
-// ghost term), ready for (L - gamma0/(dt nu_m)) u~ = rhs.
+// The solve is taken for the increment delta = u~ - u*: with L the discrete
+// Laplacian with the walls' homogeneous ghosts and k = gamma0/(dt nu_m),
+// (L - k) delta = R/nu_m - (L - k) u* (R and its wall-velocity ghost term as
+// above), where nu_m lap(u*) cancels against L u* and -u_hat/dt + gamma0 u*/dt
+// = (u^n - u^{n-1})/dt.  k_ns_rhs therefore writes
+//   [(u^n - u^{n-1})/dt + div(u* u*) + (1/rho) J.grad(u*) + ... - g]/nu_m
+// (the terms above less the two), and the inverse transform of the solve adds
+// u* back (IncEpi).  The discrete u~ is the same; the working-precision right
+// side no longer carries u/dt-sized terms that cancel to the increment.
 // Step 2 (Eq. NS37 with coefficient gamma0 rho0/dt): k_div feeds the Neumann
 // Poisson solve; step 3 (Eqs. NS38-NS39): k_correct.
 #pragma once
 #include "ch.cuh"
 
 namespace pf {
+
+// Epilogue of the velocity solves' inverse x transform: out = delta + u*,
+// u* = 2 u^n - u^{n-1} read at offset `off` (one plane for the w faces, whose
+// solve rows 0..nz-2 hold faces 1..nz-1).  `o` may be `a` itself (u~ lands in
+// the u^{n-1} buffer): each element is read before it is written, by one thread.
+template <class T>
+struct IncEpi {
+  static constexpr const char* name = "irfft_x_coarse";
+  static constexpr int kNPre = 0;
+  T* a;
+  const T* n;
+  const T* o;
+  int nx;
+  size_t off;
+  __device__ __forceinline__ void operator()(int line, int x, T v) const {
+    const size_t i = (size_t)line * nx + x;
+    a[i] = v + ((T)2 * n[i + off] - o[i + off]);
+  }
+};
 
 template <class T>
 struct NsIn {

@@ -6,7 +6,9 @@
 // 4-point face averages of J = -(rho1 - rho2)/2 M grad(G), pressure split with
 // rho0, nu_m lap(u*), div(tau*) with 4-point edge averages of the centre stress
 // (mirror ghost at the walls), div(mu (grad u* + grad u*^T)) with mu at centres
-// and edges, surface force G_face grad(phi_c), body acceleration g.
+// and edges, surface force G_face grad(phi_c), body acceleration g.  It is the
+// right side of the increment delta = u~ - u* (ns.cuh), so u_hat/dt and
+// nu_m lap(u*) do not appear: (u^n - u^{n-1})/dt stands in their place.
 #pragma once
 #include "ns.cuh"
 
@@ -44,7 +46,11 @@ __device__ __forceinline__ void k_ns_rhs_v2_b(const NsIn<T>& a, const Dims d, co
   const T Wxm_zp = S(a.wn, a.wo, zpw + r0 + xm);
   const T Wzm = hasb ? S(a.wn, a.wo, zm + r0 + x0) : (T)0;
   // ---- pressure ----
-  const T Pn_c = a.pn[c], Ps_c = S(a.pn, a.po, c);
+  // The pressure split (1/rho0) grad p^n + (1/rho - 1/rho0) grad p* is formed
+  // as (1/rho0) grad(p^{n-1} - p^n) + (1/rho) grad p* (p^n - p* = p^{n-1} - p^n):
+  // the same value, without cancelling two terms of size 1/rho0 (1000x the
+  // result at density ratio 1000) in the working precision.
+  const T Dp_c = a.po[c] - a.pn[c], Ps_c = S(a.pn, a.po, c);
   // ---- restricted fields ----
   const T phc = a.rs.phic[c], phc_xm = a.rs.phic[z0 + r0 + xm];
   const T Gc_c = a.rs.Gc[c], Gc_xm = a.rs.Gc[z0 + r0 + xm], Gc_xp = a.rs.Gc[z0 + r0 + xp];
@@ -71,7 +77,6 @@ __device__ __forceinline__ void k_ns_rhs_v2_b(const NsIn<T>& a, const Dims d, co
     T adv = (cxx0 - cxx1 + Exz_p - Exz_0) * iD;
     const T Jzu = (T)0.25 * (Jz_xm + Jz_c + Jz_xm_zp + Jz_zp);
     T jg = (Jx_c * (Uxp - Uxm) + Jzu * (Uzp - Uzm)) * h * iD;
-    T lap = (Uxp + Uxm + Uzp + Uzm - 4 * Uc) * iD2;
     const T sxx0 = 2 * muc * (Uxp - Uc), sxx1 = 2 * muc_xm * (Uc - Uxm);
     const T sxz_p = muexz_zp * ((Uzp - Uc) + (Wzp - Wxm_zp));
     const T sxz_0 = muexz * ((Uc - Uzm) + (Wc - Wxm));
@@ -106,21 +111,15 @@ __device__ __forceinline__ void k_ns_rhs_v2_b(const NsIn<T>& a, const Dims d, co
       const T Jy_yp = cj * (Gc_yp - Gc_c), Jy_xm_yp = cj * (Gc_xm_yp - Gc_xm);
       const T Jyu = (T)0.25 * (Jy_xm + Jy_c + Jy_xm_yp + Jy_yp);
       jg += Jyu * (Uyp - Uym) * h * iD;
-      lap += (Uyp + Uym - 2 * Uc) * iD2;
       const T muexy = mu_of(a.rs.phiexy[c]), muexy_yp = mu_of(a.rs.phiexy[z0 + rp + x0]);
       const T sxy_p = muexy_yp * ((Uyp - Uc) + (Vyp - Vxm_yp));
       const T sxy_0 = muexy * ((Uc - Uym) + (Vc - Vxm));
       visc += (sxy_p - sxy_0) * iD2;
     }
     const T st = a.rs.Gfx[c] * (phc - phc_xm) * iD;
-    const T gp = (Pn_c - a.pn[z0 + r0 + xm]) * iD * q.irho0 +
-                 ((T)1 / rho - q.irho0) * (Ps_c - S(a.pn, a.po, z0 + r0 + xm)) * iD;
-    const T R = -((T)2 * a.un[c] - h * a.uo[c]) * q.idt + adv +
-                (jg - divt - visc - st) / rho + gp + q.num * lap - q.gx;
-    T out = R * q.inum;
-    if (k == 0) out -= q.uw2_bot * iD2;
-    if (k == nz - 1) out -= q.uw2_top * iD2;
-    ru[c] = out;
+    const T gdp = (Dp_c - (a.po[z0 + r0 + xm] - a.pn[z0 + r0 + xm])) * iD, gps = (Ps_c - S(a.pn, a.po, z0 + r0 + xm)) * iD;
+    const T R = (a.un[c] - a.uo[c]) * q.idt + adv + (jg - divt - visc - st + gps) / rho + gdp * q.irho0 - q.gx;
+    ru[c] = R * q.inum;
   }
   // ================= y momentum at the v-face (i, j, k), 3D =================
   if constexpr (D3) {
@@ -146,7 +145,6 @@ __device__ __forceinline__ void k_ns_rhs_v2_b(const NsIn<T>& a, const Dims d, co
     const T Jz_ym_zp = hast ? cj * (Gc_ym_zp - Gc_ym) : (T)0;
     const T Jzv = (T)0.25 * (Jz_ym + Jz_c + Jz_ym_zp + Jz_zp);
     const T jg = (Jxv * (Vxp - Vxm) + Jy_c * (Vyp - Vym) + Jzv * (Vzp - Vzm)) * h * iD;
-    const T lap = (Vxp + Vxm + Vyp + Vym + Vzp + Vzm - 6 * Vc) * iD2;
     const T muc_ym = mu_of(a.rs.phic[z0 + rm + x0]);
     const T syy0 = 2 * muc * (Vyp - Vc), syy1 = 2 * muc_ym * (Vc - Vym);
     const T muexy = mu_of(a.rs.phiexy[c]), muexy_xp = mu_of(a.rs.phiexy[z0 + r0 + xp]);
@@ -169,10 +167,8 @@ __device__ __forceinline__ void k_ns_rhs_v2_b(const NsIn<T>& a, const Dims d, co
       divt = (tau(YY, c) - tau(YY, z0 + rm + x0) + Txy_xp - Txy_0 + Tyz_p - Tyz_0) * iD;
     }
     const T st = a.rs.Gfy[c] * (phc - a.rs.phic[z0 + rm + x0]) * iD;
-    const T gp = (Pn_c - a.pn[z0 + rm + x0]) * iD * q.irho0 +
-                 ((T)1 / rho - q.irho0) * (Ps_c - S(a.pn, a.po, z0 + rm + x0)) * iD;
-    const T R = -((T)2 * a.vn[c] - h * a.vo[c]) * q.idt + adv + (jg - divt - visc - st) / rho + gp + q.num * lap -
-                q.gy;
+    const T gdp = (Dp_c - (a.po[z0 + rm + x0] - a.pn[z0 + rm + x0])) * iD, gps = (Ps_c - S(a.pn, a.po, z0 + rm + x0)) * iD;
+    const T R = (a.vn[c] - a.vo[c]) * q.idt + adv + (jg - divt - visc - st + gps) / rho + gdp * q.irho0 - q.gy;
     rv[c] = R * q.inum;
   }
   // ================= z momentum at the w-face k (interior faces 1..nz-1) =================
@@ -187,7 +183,6 @@ __device__ __forceinline__ void k_ns_rhs_v2_b(const NsIn<T>& a, const Dims d, co
     const T Jx_zm = cj * (Gc_zm - Gc_xm_zm), Jx_xp_zm = cj * (Gc_xp_zm - Gc_zm), Jx_xp = cj * (Gc_xp - Gc_c);
     const T Jxw = (T)0.25 * (Jx_zm + Jx_xp_zm + Jx_c + Jx_xp);
     T jg = (Jxw * (Wxp - Wxm) + Jz_c * (Wzp - Wzm)) * h * iD;
-    T lap = (Wxp + Wxm + Wzp + Wzm - 4 * Wc) * iD2;
     const T muc_zm = mu_of(a.rs.phic[zm + r0 + x0]);
     const T szz0 = 2 * muc * (Wzp - Wc), szz1 = 2 * muc_zm * (Wc - Wzm);
     const T sxz_xp = muexz_xp * ((Uxp - Uxp_zm) + (Wxp - Wc));
@@ -221,17 +216,14 @@ __device__ __forceinline__ void k_ns_rhs_v2_b(const NsIn<T>& a, const Dims d, co
       const T Jy_c = cj * (Gc_c - Gc_ym), Jy_yp = cj * (Gc_yp - Gc_c);
       const T Jyw = (T)0.25 * (Jy_zm + Jy_yp_zm + Jy_c + Jy_yp);
       jg += Jyw * (Wyp - Wym) * h * iD;
-      lap += (Wyp + Wym - 2 * Wc) * iD2;
       const T mueyz = mu_of(a.rs.phieyz[c]), mueyz_yp = mu_of(a.rs.phieyz[z0 + rp + x0]);
       const T syz_yp = mueyz_yp * ((Vyp - Vyp_zm) + (Wyp - Wc));
       const T syz_0 = mueyz * ((Vc - Vzm) + (Wc - Wym));
       visc += (syz_yp - syz_0) * iD2;
     }
     const T st = a.rs.Gfz[c] * (phc - a.rs.phic[zm + r0 + x0]) * iD;
-    const T gp = (Pn_c - a.pn[zm + r0 + x0]) * iD * q.irho0 +
-                 ((T)1 / rho - q.irho0) * (Ps_c - S(a.pn, a.po, zm + r0 + x0)) * iD;
-    const T R = -((T)2 * a.wn[c] - h * a.wo[c]) * q.idt + adv + (jg - divt - visc - st) / rho + gp + q.num * lap -
-                q.gz;
+    const T gdp = (Dp_c - (a.po[zm + r0 + x0] - a.pn[zm + r0 + x0])) * iD, gps = (Ps_c - S(a.pn, a.po, zm + r0 + x0)) * iD;
+    const T R = (a.wn[c] - a.wo[c]) * q.idt + adv + (jg - divt - visc - st + gps) / rho + gdp * q.irho0 - q.gz;
     rw[c - P] = R * q.inum;  // face rows 0..nz-2 hold faces 1..nz-1
   }
 }

@@ -104,28 +104,28 @@ __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// An epilogue with kPre = true names two arrays (pre0(), pre1(), row length
-// pre_n()) whose elements at (line, x) it combines with the transform output
-// (apply(line, x, value, a0, a1)); the kernel copies them into shared memory
-// with cp.async before the transform, so their latency hides behind it.
+// An epilogue with kNPre > 0 names kNPre arrays (pre(j), row length pre_n())
+// whose elements at (line, x) it combines with the transform output
+// (apply(line, x, value, staged values, stride)); the kernel copies them into
+// shared memory with cp.async before the transform, so their latency hides
+// behind it.
 template <class T, class Epi>
 __device__ __forceinline__ void k_irfft_x_b(const cpx<T>* __restrict__ in, Epi epi, int n, int nlines, int pitch, FftPlan pl, const cpx<T>* __restrict__ tw, int npair, T scale, const int3 bid, unsigned char* smraw) {
+  constexpr int NP = Epi::kNPre;
   cpx<T>* a = reinterpret_cast<cpx<T>*>(smraw);
   cpx<T>* b = a + (size_t)npair * n;
-  T* pre = reinterpret_cast<T*>(b + (size_t)npair * n);  // [npair][2 lines][2 arrays][n]
+  T* pre = reinterpret_cast<T*>(b + (size_t)npair * n);  // [npair][2 lines][NP arrays][n]
   const int pair0 = bid.x * npair;
   const int nh = n / 2;
-  if constexpr (Epi::kPre) {
+  if constexpr (NP > 0) {
     for (int m = 0; m < npair; ++m)
       for (int li = 0; li < 2; ++li) {
         const int l = 2 * (pair0 + m) + li;
         if (l >= nlines) continue;
-        const T* s0 = epi.pre0() + (size_t)l * epi.pre_n();
-        const T* s1 = epi.pre1() + (size_t)l * epi.pre_n();
-        T* d0 = pre + ((size_t)(m * 2 + li) * 2) * n;
-        for (int x = threadIdx.x; x < n; x += blockDim.x) {
-          cp_async_elem(d0 + x, s0 + x);
-          cp_async_elem(d0 + n + x, s1 + x);
+        for (int j = 0; j < NP; ++j) {
+          const T* src = epi.pre(j) + (size_t)l * epi.pre_n();
+          T* dst = pre + ((size_t)(m * 2 + li) * NP + j) * n;
+          for (int x = threadIdx.x; x < n; x += blockDim.x) cp_async_elem(dst + x, src + x);
         }
       }
     cp_async_commit();
@@ -146,7 +146,7 @@ __device__ __forceinline__ void k_irfft_x_b(const cpx<T>* __restrict__ in, Epi e
   }
   __syncthreads();
   cpx<T>* z = fft_lines<T>(a, b, pl, tw, +1, npair, 1, n);
-  if constexpr (Epi::kPre) {
+  if constexpr (NP > 0) {
     cp_async_wait_all();
     __syncthreads();
   }
@@ -155,10 +155,10 @@ __device__ __forceinline__ void k_irfft_x_b(const cpx<T>* __restrict__ in, Epi e
     if (l0 >= nlines) break;
     for (int x = threadIdx.x; x < n; x += blockDim.x) {
       const cpx<T> v = z[m * n + x];
-      if constexpr (Epi::kPre) {
-        const T* p0 = pre + ((size_t)(m * 2) * 2) * n;
-        epi.apply(l0, x, v.re * scale, p0[x], p0[n + x]);
-        if (l1 < nlines) epi.apply(l1, x, v.im * scale, p0[2 * n + x], p0[3 * n + x]);
+      if constexpr (NP > 0) {
+        const T* p0 = pre + ((size_t)(m * 2) * NP) * n;
+        epi.apply(l0, x, v.re * scale, p0 + x, n);
+        if (l1 < nlines) epi.apply(l1, x, v.im * scale, p0 + (size_t)NP * n + x, n);
       } else {
         epi(l0, x, v.re * scale);
         if (l1 < nlines) epi(l1, x, v.im * scale);
@@ -170,7 +170,7 @@ __device__ __forceinline__ void k_irfft_x_b(const cpx<T>* __restrict__ in, Epi e
 // shared memory of k_irfft_x for epilogue Epi
 template <class T, class Epi>
 inline size_t irfft_x_smem(int n, int npair) {
-  return (size_t)npair * n * (2 * sizeof(cpx<T>) + (Epi::kPre ? 4 * sizeof(T) : 0));
+  return (size_t)npair * n * (2 * sizeof(cpx<T>) + 2 * Epi::kNPre * sizeof(T));
 }
 
 template <class T, class Epi>

@@ -196,13 +196,7 @@ def test_c5_batch_stated_steps(oracle):
         m, d = res[binding.PF_MIXED][b], res[binding.PF_FP64][b]
         assert np.max(np.abs(m["phi"] - d["phi"])) < PHI_ABS, b
         for n in ("u", "w"):
-            # relative to the larger of the field's maximum and 1 % of the velocity
-            # unit U = 1: droplets that start near their equilibrium angle barely
-            # move (max |u| down to 2.6e-3 after 500 steps), and there the FP32
-            # rounding of the balanced capillary and pressure forces (an absolute
-            # 3e-6 to 9e-6 in every problem) is not a relative error of the flow
-            scale = max(np.max(np.abs(d[n])), 1e-2)
-            assert np.max(np.abs(m[n] - d[n])) < REL * scale, (b, n)
+            assert rel(m[n], d[n]) < REL, (b, n)
         if "theta" in d:
             scale = max(np.max(np.abs(d["theta"])), 1e-300)
             assert np.max(np.abs(m["theta"] - d["theta"])) < REL * scale, b
