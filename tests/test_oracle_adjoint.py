@@ -82,3 +82,66 @@ def test_split_mobility_parts_add_up():
     assert abs(J2.item() - J.item()) < 1e-15
     total = sum(p.grad.item() for p in parts)
     assert abs(total - mob.grad.item()) < 1e-12 * sum(abs(p.grad.item()) for p in parts)
+
+
+# ---------------------------------------------------------------------------
+# the coupled 2D step (CH, restriction, NS, polymer) in torch: oracle.step_torch
+# ---------------------------------------------------------------------------
+def _coupled_case():
+    from paper_2111_04577_gb300 import workloads as wl
+    w = wl.scaled(wl.config("c2"), 8, 4)
+    w.params.dt = 1e-3
+    g = w.grid
+    phi0 = wl.initial_phi(w)
+    vel = wl.random_velocity(g, 3, 0.2)
+    nz, ny, nx = g.coarse_shape
+    rng = np.random.default_rng(5)
+    a = 0.3 * rng.standard_normal((nz, ny, nx, 2, 2))
+    th0 = a + np.swapaxes(a, -1, -2)  # distinct eigenvalues (torch.linalg.eigh's derivative)
+    return g, w.params.as_dict(), phi0, vel, th0
+
+
+def test_coupled_torch_forward_equals_oracle():
+    from oracle import step as ostep, step_torch as stt
+    g, prm, phi0, vel, th0 = _coupled_case()
+    _, _, s = stt.run(g, prm, phi0, 5, "wetted", vel0=vel, theta0=th0)
+    ref = ostep.State(g, prm, phi0, vel0=vel, theta0=th0)
+    for _ in range(5):
+        ref.step()
+    rel = lambda a, b: np.max(np.abs(a.detach().numpy() - b)) / np.max(np.abs(b))
+    assert rel(s["phi"], ref.phi) < 1e-12
+    assert rel(s["u"], ref.vel[0]) < 1e-11 and rel(s["w"], ref.vel[2]) < 1e-11
+    assert rel(s["p"], ref.p) < 1e-11
+    assert rel(s["theta"], ref.theta) < 1e-12 and rel(s["tau"], ref.tau) < 1e-12
+
+
+@pytest.mark.parametrize("which", ["wetted", "centroid"])
+def test_coupled_torch_gradients_equal_oracle_central_differences(which):
+    """dJ/dtheta_s, dJ/dM, dJ/dWi and <dJ/dphi0, v> of the coupled step's
+    autograd adjoint against central differences of the FP64 oracle."""
+    from oracle import step as ostep, step_torch as stt
+    g, prm, phi0, vel, th0 = _coupled_case()
+    J, leaves, _ = stt.run(g, prm, phi0, 5, which, vel0=vel, theta0=th0)
+    J.backward()
+
+    def Jor(p0=phi0, **kw):
+        p2 = dict(prm)
+        p2.update(kw)
+        r = ostep.State(g, p2, p0, vel0=vel, theta0=th0)
+        for _ in range(5):
+            r.step()
+        return ob.wetted(r.phi, g) if which == "wetted" else ob.centroid(r.phi, g)[2]
+
+    assert abs(J.item() - Jor()) < 1e-12 * abs(J.item())
+    # dJ/dM is a small difference of large parts (the 1/(M lambda dt) term against
+    # S(M)): its differences take a wider step (truncation O(h^2)) and 1e-3
+    for key, h, ad, tol in (("theta_bot_deg", 0.1, leaves["theta"].grad.item(), 1e-4),
+                            ("wi", 1e-4, leaves["wi"].grad.item(), 1e-4),
+                            ("mobility", prm["mobility"] * 1e-2, leaves["mobility"].grad.item(), 1e-3)):
+        fd = (Jor(**{key: prm[key] + h}) - Jor(**{key: prm[key] - h})) / (2 * h)
+        assert abs(fd - ad) <= tol * abs(fd), (key, fd, ad)
+    v = np.random.default_rng(8).uniform(-1, 1, phi0.shape)
+    eps = 1e-6
+    fd = (Jor(phi0 + eps * v) - Jor(phi0 - eps * v)) / (2 * eps)
+    ad = float(np.sum(leaves["phi0"].grad.numpy() * v))
+    assert abs(fd - ad) <= 1e-6 * abs(fd), (fd, ad)
