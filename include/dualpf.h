@@ -198,6 +198,11 @@ int pf_batch_diagnostics(pf_batch* b, int problem, double out[6]);
  * problem holds phi^N.  Errors as pf_adjoint, PF_ERR_ARG for a bad index. */
 int pf_batch_adjoint(pf_batch* b, int problem, int nsteps, int ckpt_every, int objective, double out[3], void* dphi0,
                      int dphi0_on_device);
+/* pf_adjoint_ex on one problem of the batch (its own buffers, parameters and
+ * the single-problem kernels); afterwards the problem holds step N.  Errors as
+ * pf_adjoint_ex, PF_ERR_ARG for a bad index. */
+int pf_batch_adjoint_ex(pf_batch* b, int problem, int nsteps, int ckpt_every, int objective, int flags, double out[4],
+                        void* dphi0, int dphi0_on_device);
 const char* pf_batch_last_error(const pf_batch* b);
 void pf_batch_destroy(pf_batch* b);
 
@@ -241,6 +246,31 @@ int pf_diagnostics_noalloc(const pf_grid_desc* g, const pf_params* prm, const vo
 enum { PF_OBJ_WETTED = 0, PF_OBJ_CENTROID_Z = 1 };
 int pf_adjoint(pf_ctx* ctx, int nsteps, int ckpt_every, int objective, double out[3], void* dphi0,
                int dphi0_on_device);
+
+/* Discrete adjoint of the whole coupled step (Sections 3.2.1-3.2.3: the CH
+ * update, the restriction of Eqs. dual2-dual3, the NS projection of Eqs.
+ * NS35-NS39 and the log-conformation update of Eqs. NS40-NS46), on a 2D
+ * context: gradients of an objective of phi^N after nsteps coupled steps from
+ * the context's current state (phi^{-1} = phi^0, u^{-1} = u^0, p^{-1} = p^0,
+ * tau^{-1} = tau^0), in one reverse sweep.
+ *   flags: PF_ADJ_COUPLED (required; 0 is reserved for pf_adjoint's CH-only
+ *   sweep, which this call then runs with out[3] = 0).
+ * out[0] = J, out[1] = dJ/d theta_bot (per degree), out[2] = dJ/d mobility,
+ * out[3] = dJ/d lambda_H (the Weissenberg number; 0 for a Newtonian droplet).
+ * dphi0 (may be NULL) receives dJ/d phi^0 as for pf_adjoint.  The forward
+ * sweep stores the whole state every ckpt_every steps; each segment is
+ * recomputed, keeping the state of each of its steps (memory: ckpt_every + 1
+ * states), and each reverse step re-runs its forward step for the restricted
+ * fields, the polymer's first stage and the wall flux.  The linear parts
+ * (projection, solves, restriction, prolongation, advection and velocity
+ * gradient stencils) are transposed; the nonlinear per-cell parts (momentum
+ * right side, the polymer's right side and stress) are differentiated exactly
+ * with dual numbers.  The context is left at step N.
+ * Errors: PF_ERR_ARG, PF_ERR_UNSUPPORTED (a 3D context, PF_ADJ_COUPLED on a
+ * derivative-carrying context), PF_ERR_CUDA, PF_ERR_NOMEM. */
+enum { PF_ADJ_COUPLED = 1 };
+int pf_adjoint_ex(pf_ctx* ctx, int nsteps, int ckpt_every, int objective, int flags, double out[4], void* dphi0,
+                  int dphi0_on_device);
 
 /* Sensitivity of an objective to one scalar parameter through the whole
  * coupled step of Section 3.2 (forward mode): the Cahn-Hilliard step with its

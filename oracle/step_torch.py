@@ -127,10 +127,13 @@ class CoupledTorch2D:
 
     # ---------------- Cahn-Hilliard (Eqs. NS25-NS34) ----------------
     def ch(self, pn, po, us, ws, theta_bot, mob):
+        """mob: the mobility, or copies (M_a, M_b, M_s) of it entering the time
+        term 1/(M lambda dt), the advection term 1/(M lambda) and S."""
         p, h = self.p, self.h
         eta, dt, g0 = p["eta"], self.dt, self.gamma0
         lam = self.lam
-        S = eta ** 2 * torch.sqrt(4.0 * g0 / (mob * lam * dt))   # Eq. NS30, equality
+        Ma, Mb, Ms = mob if isinstance(mob, tuple) else (mob,) * 3
+        S = eta ** 2 * torch.sqrt(4.0 * g0 / (Ms * lam * dt))   # Eq. NS30, equality
         alpha = -S / (2.0 * eta ** 2)
         c = alpha + S / eta ** 2
         phs = 2 * pn - po
@@ -153,7 +156,7 @@ class CoupledTorch2D:
         zero = torch.zeros_like(phs[1:-1])
         B = torch.cat([(gb / h)[None], zero, (gt / h)[None]], 0)
         lap = lambda a: (self.Lf @ a.reshape(-1)).reshape(self.fshape)
-        R1 = phh / (dt * mob * lam) - A / (mob * lam) + lap(hh) - c * B
+        R1 = phh / (dt * Ma * lam) - A / (Mb * lam) + lap(hh) - c * B
         psi = torch.linalg.solve(self.Lf - c * self.If, R1.reshape(-1)).reshape(self.fshape)
         phi = torch.linalg.solve(self.Lf + alpha * self.If, (psi - B).reshape(-1)).reshape(self.fshape)
         G = lam * (-(lap(phi) + B) + phi * (phi * phi - 1) / eta ** 2)
@@ -290,13 +293,16 @@ class CoupledTorch2D:
 
     # ---------------- one coupled step (oracle.step.State.step) ----------------
     def step(self, s, theta_bot, mob, lam_h):
-        phi, G = self.ch(s["phi"], s["phi_old"], 2 * s["u"] - s["u_old"], 2 * s["w"] - s["w_old"], theta_bot, mob)
+        """mob: the mobility, or four copies of it (CH time term, CH advection, S,
+        the flux J of the momentum equation)."""
+        mch, mj = (mob[:3], mob[3]) if isinstance(mob, tuple) else (mob, mob)
+        phi, G = self.ch(s["phi"], s["phi_old"], 2 * s["u"] - s["u_old"], 2 * s["w"] - s["w_old"], theta_bot, mch)
         rphi, rG = self.restrict(phi), self.restrict(G)
         tau_s = None
         if self.visco:
             t = 2 * s["tau"] - s["tau_old"]
             tau_s = {"xx": t[..., 0, 0], "xz": t[..., 0, 1], "zz": t[..., 1, 1]}
-        u, w, p = self.ns(s["u"], s["u_old"], s["w"], s["w_old"], s["p"], s["p_old"], tau_s, rphi, rG, mob)
+        u, w, p = self.ns(s["u"], s["u_old"], s["w"], s["w_old"], s["p"], s["p_old"], tau_s, rphi, rG, mj)
         n = dict(phi=phi, phi_old=s["phi"], u=u, u_old=s["u"], w=w, w_old=s["w"], p=p, p_old=s["p"],
                  theta=s["theta"], tau=s["tau"], tau_old=s["tau_old"])
         if self.visco:
@@ -316,14 +322,19 @@ def objective(phi, grid, which):
     return torch.sum(wgt * z[:, None, None]) / torch.sum(wgt)
 
 
-def run(grid, prm, phi0, steps, which, vel0=None, theta0=None):
+def run(grid, prm, phi0, steps, which, vel0=None, theta0=None, split_mobility=False):
     """J after `steps` coupled steps from phi^{-1} = phi^0 (u^{-1} = u^0, ...),
-    and the leaf tensors (phi0, theta_bot, M, lambda_H) whose .grad are dJ/d*."""
+    and the leaf tensors (phi0, theta_bot, M, lambda_H) whose .grad are dJ/d*.
+    With split_mobility, M is four leaves (see CoupledTorch2D.step): dJ/dM is
+    the sum of their gradients, and their sizes show its cancellation."""
     m = CoupledTorch2D(grid, prm)
     nz, _, nx = grid.coarse_shape
     ph0 = torch.tensor(phi0, dtype=F64, requires_grad=True)
     th = torch.tensor(float(prm["theta_bot_deg"]), dtype=F64, requires_grad=True)
-    mob = torch.tensor(float(prm["mobility"]), dtype=F64, requires_grad=True)
+    if split_mobility:
+        mob = tuple(torch.tensor(float(prm["mobility"]), dtype=F64, requires_grad=True) for _ in range(4))
+    else:
+        mob = torch.tensor(float(prm["mobility"]), dtype=F64, requires_grad=True)
     lh = torch.tensor(float(prm.get("wi", 0.0)) or 1.0, dtype=F64, requires_grad=True)
     if vel0 is None:
         u0, w0 = np.zeros((nz, 1, nx)), np.zeros((nz + 1, 1, nx))

@@ -2,13 +2,18 @@
 
     J = CHObjective.apply(phi0, theta_bot_deg, mobility, solver, nsteps, ckpt_every, objective)
     J = CoupledObjective.apply(wi, theta_bot_deg, solver, params, nsteps, objective)
+    J = CoupledAdjointObjective.apply(phi0, theta_bot_deg, mobility, wi, solver, params, nsteps, ckpt_every,
+                                      objective)
 
 CHObjective.forward loads phi0 (phi^{-1} = phi^0) into the solver and runs
 nsteps CH steps on the GPU (velocity fixed) to evaluate the objective; its
 backward reloads phi0 and calls pf_adjoint, which re-runs the forward with
 checkpoints and returns dJ/dphi0, dJ/dtheta_bot (per degree) and
 dJ/dmobility.  CoupledObjective takes the whole coupled step through
-pf_tangent (forward-mode derivatives in Wi and theta_bot).
+pf_tangent (forward-mode derivatives in Wi and theta_bot, 2D or 3D).
+CoupledAdjointObjective takes the whole coupled 2D step through one reverse
+sweep (pf_adjoint_ex): dJ/dphi0, dJ/dtheta_bot, dJ/dmobility and dJ/dWi at
+once.
 """
 from __future__ import annotations
 
@@ -75,3 +80,33 @@ class CoupledObjective(torch.autograd.Function):
         g = float(gJ)
         return (torch.tensor(ctx.grads[0] * g, dtype=torch.float64),
                 torch.tensor(ctx.grads[1] * g, dtype=torch.float64), None, None, None, None)
+
+
+class CoupledAdjointObjective(torch.autograd.Function):
+    """J after nsteps coupled 2D steps (CH, restriction, NS, LCR) from phi0 and
+    the solver's current flow and polymer state, as a function of phi0,
+    theta_bot (degrees), the mobility and Wi.  forward loads phi0 and runs the
+    reverse sweep once (it yields J and every gradient); backward scales the
+    gradients.  The solver is left at step nsteps."""
+
+    @staticmethod
+    def forward(ctx, phi0, theta_bot_deg, mobility, wi, solver, params, nsteps, ckpt_every, objective):
+        p = params.__class__(**params.as_dict())
+        p.theta_bot_deg = float(theta_bot_deg)
+        p.mobility = float(mobility)
+        p.wi = float(wi)
+        solver.set_params(p)
+        solver.set("phi", phi0.detach().cpu().numpy().astype(solver.dtype))
+        J, dth, dm, dwi, dphi = solver.adjoint_coupled(int(nsteps), int(ckpt_every), int(objective))
+        ctx.grads = (dphi, dth, dm, dwi)
+        ctx.dtypes = (phi0.dtype, phi0.device)
+        return torch.tensor(J, dtype=torch.float64)
+
+    @staticmethod
+    def backward(ctx, gJ):
+        dphi, dth, dm, dwi = ctx.grads
+        dt, dev = ctx.dtypes
+        g = float(gJ)
+        dphi_t = torch.from_numpy(np.asarray(dphi, dtype=np.float64) * g).to(dtype=dt, device=dev)
+        return (dphi_t, torch.tensor(dth * g, dtype=torch.float64), torch.tensor(dm * g, dtype=torch.float64),
+                torch.tensor(dwi * g, dtype=torch.float64), None, None, None, None, None)

@@ -27,8 +27,10 @@ EXPORTS = ["pf_init_grid", "pf_set_params", "pf_field_info", "pf_set_fields", "p
            "pf_get_fields", "pf_diagnostics", "pf_profile", "pf_diagnostics_noalloc", "pf_last_error",
            "pf_destroy", "pf_batch_create", "pf_batch_field_info", "pf_batch_set_fields", "pf_batch_get_fields",
            "pf_batch_step", "pf_batch_diagnostics", "pf_batch_last_error", "pf_batch_destroy", "pf_set_tuning",
-           "pf_get_tuning", "pf_adjoint", "pf_batch_adjoint", "pf_tangent", "pf_tangent_ex", "pf_batch_tangent"]
+           "pf_get_tuning", "pf_adjoint", "pf_batch_adjoint", "pf_tangent", "pf_tangent_ex", "pf_batch_tangent",
+           "pf_adjoint_ex", "pf_batch_adjoint_ex"]
 PF_OBJ_WETTED, PF_OBJ_CENTROID_Z = 0, 1
+PF_ADJ_COUPLED = 1
 PF_PARAM_WI, PF_PARAM_THETA_BOT, PF_PARAM_PHI0, PF_PARAM_MOBILITY = 0, 1, 2, 3
 PROFILE_NAME = 48
 
@@ -88,6 +90,11 @@ def load(path: str = LIB_PATH):
             getattr(lib, f).restype = C.c_int
         lib.pf_adjoint.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), vp, C.c_int]
         lib.pf_adjoint.restype = C.c_int
+        lib.pf_adjoint_ex.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), vp, C.c_int]
+        lib.pf_adjoint_ex.restype = C.c_int
+        lib.pf_batch_adjoint_ex.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
+                                            vp, C.c_int]
+        lib.pf_batch_adjoint_ex.restype = C.c_int
         lib.pf_batch_adjoint.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), vp, C.c_int]
         lib.pf_batch_adjoint.restype = C.c_int
         lib.pf_tangent.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double)]
@@ -215,6 +222,23 @@ class Solver:
         if g is not None:
             g = g.reshape(self.grid.fine_shape)
         return out[0], out[1], out[2], g
+
+    def adjoint_coupled(self, nsteps, ckpt_every=50, objective=PF_OBJ_WETTED, want_phi=True):
+        """(J, dJ/dtheta_bot [per degree], dJ/dmobility, dJ/dWi, dJ/dphi0 or None)
+        through the whole coupled step (2D), by one reverse sweep from the
+        current state; leaves the context at step N."""
+        out = (C.c_double * 4)()
+        g = None
+        ptr = None
+        if want_phi:
+            cnt, _ = self.info("phi")
+            g = np.empty(cnt, dtype=self.dtype)
+            ptr = g.ctypes.data_as(C.c_void_p)
+        self._chk(self.lib.pf_adjoint_ex(self.h, int(nsteps), int(ckpt_every), int(objective), PF_ADJ_COUPLED, out,
+                                         ptr, 0))
+        if g is not None:
+            g = g.reshape(self.grid.fine_shape)
+        return out[0], out[1], out[2], out[3], g
 
     def tangent(self, nsteps, param=PF_PARAM_WI, objective=PF_OBJ_WETTED, flags=0, direction=None):
         """(J, dJ/dparam) after nsteps steps from the current state, by forward-mode
@@ -348,6 +372,21 @@ class Batch:
         if g is not None:
             g = g.reshape(self.grids[b].fine_shape)
         return out[0], out[1], out[2], g
+
+    def adjoint_coupled(self, b, nsteps, ckpt_every=50, objective=PF_OBJ_WETTED, want_phi=True):
+        """Solver.adjoint_coupled for problem b of the batch; leaves it at step N."""
+        out = (C.c_double * 4)()
+        g = None
+        ptr = None
+        if want_phi:
+            cnt, _ = self.info(b, "phi")
+            g = np.empty(cnt, dtype=self.dtype)
+            ptr = g.ctypes.data_as(C.c_void_p)
+        self._chk(self.lib.pf_batch_adjoint_ex(self.h, int(b), int(nsteps), int(ckpt_every), int(objective),
+                                               PF_ADJ_COUPLED, out, ptr, 0))
+        if g is not None:
+            g = g.reshape(self.grids[b].fine_shape)
+        return out[0], out[1], out[2], out[3], g
 
     def diagnostics(self, b):
         out = (C.c_double * 6)()

@@ -124,7 +124,7 @@ template <class T>
 __global__ void k_adj_phibar(const T* __restrict__ phis, const T* __restrict__ rbar, const T* __restrict__ mubar,
                              const T* __restrict__ pbar_next, const T* __restrict__ acur, T* __restrict__ an_new,
                              T* __restrict__ acur_new, double* __restrict__ thb_col, CoarseVel<T> vel, Dims d,
-                             Phys p, PhysT<T> q, T a1, T a2) {
+                             Phys p, PhysT<T> q, T a1, T a2, const double* __restrict__ gbx = nullptr) {
   RowIdx x;
   if (!row_index(d.fnx, d.fny, x)) return;
   const int i = x.i, j = x.j, k = x.k;
@@ -154,7 +154,8 @@ __global__ void k_adj_phibar(const T* __restrict__ phis, const T* __restrict__ r
   if (k <= 1) {
     const size_t b0 = col, b1 = plane + col;  // cells 0 and 1 of this column
     const double w = 1.5 * (double)phis[b0] - 0.5 * (double)phis[b1];
-    const double gbar = -(double)mubar[b0] / d.h;
+    // gbx: the wall flux's adjoint from elsewhere in the step (G's wall term, coupled sweep)
+    const double gbar = -(double)mubar[b0] / d.h + (gbx ? gbx[col] : 0.0);
     const double wbar = gbar * p.cos_bot * (-2.0 * w) / s2eta;
     sb += (T)(k == 0 ? 1.5 * wbar : -0.5 * wbar);
     if (k == 0) thb_col[col] = gbar * (-sqrt(fmax(0.0, 1.0 - p.cos_bot * p.cos_bot))) * (1.0 - w * w) / s2eta;
@@ -162,7 +163,7 @@ __global__ void k_adj_phibar(const T* __restrict__ phis, const T* __restrict__ r
   if (k >= d.fnz - 2) {
     const size_t t0 = (size_t)(d.fnz - 1) * plane + col, t1 = (size_t)(d.fnz - 2) * plane + col;
     const double w = 1.5 * (double)phis[t0] - 0.5 * (double)phis[t1];
-    const double gbar = -(double)mubar[t0] / d.h;
+    const double gbar = -(double)mubar[t0] / d.h + (gbx ? gbx[plane + col] : 0.0);
     const double wbar = gbar * p.cos_top * (-2.0 * w) / s2eta;
     sb += (T)(k == d.fnz - 1 ? 1.5 * wbar : -0.5 * wbar);
   }

@@ -33,6 +33,7 @@
 #include "spectral.cuh"
 #include "batch.cuh"
 #include "adjoint.cuh"
+#include "adjoint_ns.cuh"
 
 namespace pf {
 
@@ -150,6 +151,7 @@ struct ImplBase {
                        std::vector<int>& counts, int& per_step) = 0;
   virtual void set_tuning(int knob, int value) = 0;
   virtual void adjoint(int nsteps, int K, int which, double out[3], void* dphi0, int on_dev) = 0;
+  virtual void adjoint_coupled(int nsteps, int K, int which, double out[4], void* dphi0, int on_dev) = 0;
   virtual int get_tuning(int knob) const = 0;
 };
 
@@ -792,37 +794,44 @@ struct Impl : ImplBase {
   // ------------------------------------------------------------------ API
   const pf_grid_desc& grid_desc() const override { return g; }
   bool params_ready() const override { return have_params; }
+  // the scheme's constants in arithmetic type TT, from the FP64 derived ones
+  template <class TT>
+  PhysT<TT> phys_of() const {
+    PhysT<TT> r{};
+    r.idt = (TT)(1.0 / p.dt);
+    r.irho0 = (TT)(1.0 / p.rho0);
+    r.inum = (TT)(1.0 / p.nu_m);
+    r.num = (TT)p.nu_m;
+    r.rho1 = (TT)p.rho1;
+    r.rho2 = (TT)p.rho2;
+    r.mu_s1 = (TT)p.mu_s1;
+    r.mu_s2 = (TT)p.mu_s2;
+    r.uw2_bot = (TT)(2 * p.uw_bot);
+    r.uw2_top = (TT)(2 * p.uw_top);
+    r.cj_dx = (TT)(-0.5 * (p.rho1 - p.rho2) * p.mob / d.dx);
+    r.gx = (TT)p.gx;
+    r.gy = (TT)p.gy;
+    r.gz = (TT)p.gz;
+    r.ih = (TT)(1.0 / d.h);
+    r.ih2 = (TT)(1.0 / (d.h * d.h));
+    r.iD = (TT)(1.0 / d.dx);
+    r.iD2 = (TT)(1.0 / (d.dx * d.dx));
+    r.ie2 = (TT)(1.0 / (p.eta * p.eta));
+    r.lam = (TT)p.lam;
+    r.dt = (TT)p.dt;
+    r.ilh = p.visco ? (TT)(1.0 / p.lam_h) : (TT)0;
+    r.wtau = p.visco ? (TT)(p.mu_p1 / p.lam_h) : (TT)0;
+    r.ag = (TT)p.alpha_g;
+    r.cbot = p.cos_bot;
+    r.ctop = p.cos_top;
+    return r;
+  }
   void set_params(const pf_params& prm) override {
     p = derive(prm, g);
     raw_prm = prm;
     sigma = prm.sigma;
     prm_S = prm.S;
-    q.idt = (T)(1.0 / p.dt);
-    q.irho0 = (T)(1.0 / p.rho0);
-    q.inum = (T)(1.0 / p.nu_m);
-    q.num = (T)p.nu_m;
-    q.rho1 = (T)p.rho1;
-    q.rho2 = (T)p.rho2;
-    q.mu_s1 = (T)p.mu_s1;
-    q.mu_s2 = (T)p.mu_s2;
-    q.uw2_bot = (T)(2 * p.uw_bot);
-    q.uw2_top = (T)(2 * p.uw_top);
-    q.cj_dx = (T)(-0.5 * (p.rho1 - p.rho2) * p.mob / d.dx);
-    q.gx = (T)p.gx;
-    q.gy = (T)p.gy;
-    q.gz = (T)p.gz;
-    q.ih = (T)(1.0 / d.h);
-    q.ih2 = (T)(1.0 / (d.h * d.h));
-    q.iD = (T)(1.0 / d.dx);
-    q.iD2 = (T)(1.0 / (d.dx * d.dx));
-    q.ie2 = (T)(1.0 / (p.eta * p.eta));
-    q.lam = (T)p.lam;
-    q.dt = (T)p.dt;
-    q.ilh = p.visco ? (T)(1.0 / p.lam_h) : (T)0;
-    q.wtau = p.visco ? (T)(p.mu_p1 / p.lam_h) : (T)0;
-    q.ag = (T)p.alpha_g;
-    q.cbot = p.cos_bot;
-    q.ctop = p.cos_top;
+    q = phys_of<T>();
     have_params = true;
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
     graphs.clear();
@@ -1053,11 +1062,16 @@ struct Impl : ImplBase {
 
   // one reverse step; its FP64 partial sums go to part[0 .. 5 nb) (read by adjoint_accumulate)
   void adjoint_step(const T* pn, const T* po, const T* pnew, double* part) {
+    const int fo = fc ^ 1;
+    adjoint_step_v(pn, po, pnew, part, CoarseVel<T>{u[fc], u[fo], v[fc], v[fo], w[fc], w[fo]}, nullptr);
+  }
+  // the same with the step's velocity given, and an extra wall-flux adjoint gbx
+  // (per wall column, bottom then top; null for none)
+  void adjoint_step_v(const T* pn, const T* po, const T* pnew, double* part, const CoarseVel<T> vel,
+                      const double* gbx) {
     const size_t nf = (size_t)d.fnx * d.fny * d.fnz;
     const RowLaunch lf = rows(d.fny * d.fnz, d.fnx);
     const FineView<T> fv{pn, po};
-    const int fo = fc ^ 1;
-    const CoarseVel<T> vel{u[fc], u[fo], v[fc], v[fo], w[fc], w[fo]};
     const T a1 = (T)(1.0 / (p.Ml * p.dt)), a2 = (T)(1.0 / p.Ml);
     const int nb = nred_blocks;
     k_adj_prep<T><<<lf.grid, lf.block, 0, st>>>(fv, vel, a_phis, a_adv, d, q);
@@ -1070,7 +1084,7 @@ struct Impl : ImplBase {
     k_lapN_two<T><<<lf.grid, lf.block, 0, st>>>(a_rbar, (T)(-p.c), a_mubar, a_ebar, d, q);  // mu_bar, eps_bar
     k_dots<T><<<nb, 256, 0, st>>>(a_ebar, a_delta, a_rbar, a_eps, a_rbar, po, a_rbar, a_adv, nf, part, pn);
     k_adj_phibar<T><<<lf.grid, lf.block, 0, st>>>(a_phis, a_rbar, a_mubar, a_next, a_cur, a_next2, a_cur2, a_thb, vel,
-                                                  d, p, q, a1, a2);
+                                                  d, p, q, a1, a2, gbx);
     k_sum_d<<<nb, 256, 0, st>>>(a_thb, (size_t)d.fnx * d.fny, part + (size_t)4 * nb);
     check_launch();
     std::swap(a_next, a_next2);
@@ -1167,6 +1181,311 @@ struct Impl : ImplBase {
       out[1] = thb * M_PI / 180.0;
       out[2] = mb;
     }
+  }
+
+  // ------------------------------------------------------------------
+  // Reverse sweep of the coupled 2D step (CH, restriction, NS, LCR).
+  // out[0] = J, out[1] = dJ/d theta_bot (per degree), out[2] = dJ/d M,
+  // out[3] = dJ/d lambda_H (the Weissenberg number); dphi0 (optional)
+  // receives dJ/d phi^0.  Checkpoints of the whole state every K steps; each
+  // segment is recomputed forward, storing the state of every step, and each
+  // reverse step re-runs its forward step for the intermediates (restricted
+  // fields, Theta1, the wall flux).
+  // ------------------------------------------------------------------
+  std::unique_ptr<Arena> cadj_ar;
+  int cadj_K = 0, cadj_nseg = 0;
+  std::vector<T*> cck, csb;  // checkpoints and the segment's per-step states
+  T *cb[32] = {nullptr};      // coarse adjoint buffers (see cadj_alloc)
+  T *cGb = nullptr, *cwork[6] = {nullptr}, *cpoly[9] = {nullptr}, *crf[7] = {nullptr}, *cfin = nullptr;
+  double *cgbx = nullptr, *cmpart = nullptr, *cwpart = nullptr;
+
+  size_t state_elems() const {
+    const size_t nf = (size_t)d.fnx * d.fny * d.fnz, nc = (size_t)d.nx * d.ny * d.nz,
+                 ncw = (size_t)d.nx * d.ny * (d.nz + 1);
+    return nf * (philo[0] ? 4 : 2) + nc * 4 + ncw * 2 + (size_t)nc * ncomp * 3;
+  }
+  // copy the state (current and old levels in that order) to or from b
+  void state_io(T* b, bool save) {
+    const size_t nf = (size_t)d.fnx * d.fny * d.fnz, nc = (size_t)d.nx * d.ny * d.nz,
+                 ncw = (size_t)d.nx * d.ny * (d.nz + 1);
+    size_t o = 0;
+    auto io = [&](T* a, size_t n) {
+      if (save) PF_CUDA_TRY(cudaMemcpyAsync(b + o, a, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+      else PF_CUDA_TRY(cudaMemcpyAsync(a, b + o, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+      o += n;
+    };
+    io(phi[pc], nf);
+    io(phi[pc ^ 1], nf);
+    if (philo[0]) {
+      io(philo[pc], nf);
+      io(philo[pc ^ 1], nf);
+    }
+    io(u[fc], nc);
+    io(u[fc ^ 1], nc);
+    io(w[fc], ncw);
+    io(w[fc ^ 1], ncw);
+    io(pr[fc], nc);
+    io(pr[fc ^ 1], nc);
+    for (int c = 0; c < ncomp; ++c) io(theta[c], nc);
+    for (int c = 0; c < ncomp; ++c) io(tau[fc][c], nc);
+    for (int c = 0; c < ncomp; ++c) io(tau[fc ^ 1][c], nc);
+  }
+  struct StateView {
+    const T *phi_n, *phi_o, *u_n, *u_o, *w_n, *w_o, *p_n, *p_o, *th[3], *tau_n[3], *tau_o[3];
+  };
+  StateView state_view(const T* b) const {
+    const size_t nf = (size_t)d.fnx * d.fny * d.fnz, nc = (size_t)d.nx * d.ny * d.nz,
+                 ncw = (size_t)d.nx * d.ny * (d.nz + 1);
+    StateView v{};
+    size_t o = 0;
+    v.phi_n = b + o, o += nf;
+    v.phi_o = b + o, o += nf;
+    if (philo[0]) o += 2 * nf;
+    v.u_n = b + o, o += nc;
+    v.u_o = b + o, o += nc;
+    v.w_n = b + o, o += ncw;
+    v.w_o = b + o, o += ncw;
+    v.p_n = b + o, o += nc;
+    v.p_o = b + o, o += nc;
+    for (int c = 0; c < 3; ++c) v.th[c] = c < ncomp ? b + o + (size_t)c * nc : nullptr;
+    o += (size_t)nc * ncomp;
+    for (int c = 0; c < 3; ++c) v.tau_n[c] = c < ncomp ? b + o + (size_t)c * nc : nullptr;
+    o += (size_t)nc * ncomp;
+    for (int c = 0; c < 3; ++c) v.tau_o[c] = c < ncomp ? b + o + (size_t)c * nc : nullptr;
+    return v;
+  }
+
+  // coarse adjoint buffers, by index:
+  //  0 ub1  1 ub0p  2 wb1  3 wb0p  4 pb1  5 pb0p  6-8 thb1  9-11 taub1  12-14 taub0p
+  // 15 ub0 16 ubm 17 wb0 18 wbm 19 pb0 20 pbm 21-23 thb0 24-26 taub0 27-29 taubm
+  // work: ppb, divb, utb, wtb, rbu, rbw, rphib (c, fx, fz, exz), rGb (c, fx, fz)
+  void cadj_alloc(int K, int nseg) {
+    if (cadj_ar && cadj_K >= K && cadj_nseg >= nseg) return;
+    cadj_ar.reset(new Arena());
+    const size_t nf = (size_t)d.fnx * d.fny * d.fnz, nc = (size_t)d.nx * d.ny * d.nz,
+                 ncw = (size_t)d.nx * d.ny * (d.nz + 1);
+    const size_t se = state_elems();
+    cck.assign(nseg, nullptr);
+    for (int s = 0; s < nseg; ++s) cck[s] = cadj_ar->get<T>(se);
+    csb.assign(K + 1, nullptr);
+    for (int m = 0; m <= K; ++m) csb[m] = cadj_ar->get<T>(se);
+    for (int b = 0; b < 30; ++b) cb[b] = cadj_ar->get<T>(ncw);  // ncw >= nc: one size for all
+    for (int b = 0; b < 6; ++b) cwork[b] = cadj_ar->get<T>(ncw);
+    for (int b = 0; b < 9; ++b) cpoly[b] = cadj_ar->get<T>(nc);
+    for (int b = 0; b < 7; ++b) crf[b] = cadj_ar->get<T>(ncw);
+    cfin = cadj_ar->get<T>(se);
+    cGb = cadj_ar->get<T>(nf);
+    cgbx = cadj_ar->get<double>(2 * (size_t)d.fnx * d.fny);
+    const int nblk = (int)((nc + 127) / 128);
+    cmpart = cadj_ar->get<double>(nblk);
+    cwpart = cadj_ar->get<double>(nblk);
+    for (int b = 0; b < 30; ++b) PF_CUDA_TRY(cudaMemsetAsync(cb[b], 0, ncw * sizeof(T), st));
+    cadj_K = K;
+    cadj_nseg = nseg;
+  }
+
+  void adjoint_coupled(int nsteps, int K, int which, double out[4], void* dphi0, int on_dev) override {
+    if constexpr (IsDual<T>::value) {
+      (void)nsteps, (void)K, (void)which, (void)out, (void)dphi0, (void)on_dev;
+      throw ApiError(PF_ERR_UNSUPPORTED, "the adjoint runs on PF_FP64, PF_MIXED and PF_MIXED_Z64 contexts");
+    } else {
+      flush_polymer();
+      if (!have_params) throw ApiError(PF_ERR_ARG, "pf_set_params must precede pf_adjoint_ex");
+      if (d.dim != 2) throw ApiError(PF_ERR_UNSUPPORTED, "the coupled reverse sweep is built for 2D meshes");
+      if (nsteps < 1 || K < 1) throw ApiError(PF_ERR_ARG, "nsteps and ckpt_every must be >= 1");
+      if (which != 0 && which != 1) throw ApiError(PF_ERR_ARG, "objective must be PF_OBJ_WETTED or PF_OBJ_CENTROID_Z");
+      const int nseg = (nsteps + K - 1) / K;
+      adj_alloc(K, nseg);  // the CH adjoint's buffers
+      cadj_alloc(K, nseg);
+      const size_t nf = (size_t)d.fnx * d.fny * d.fnz, nc = (size_t)d.nx * d.ny * d.nz,
+                   ncw = (size_t)d.nx * d.ny * (d.nz + 1);
+      const int nblk = (int)((nc + 127) / 128);
+      const int nbf = (int)((nf + 255) / 256);
+      const int nbc = (int)((nc + 255) / 256);
+      // forward sweep with checkpoints of the whole state
+      for (int s = 0; s < nseg; ++s) {
+        state_io(cck[s], true);
+        step(std::min(K, nsteps - s * K), 0);
+      }
+      double dg[6];
+      diagnostics(dg);
+      const double J = which == 0 ? dg[2] : dg[5];
+      state_io(cfin, true);  // the final state, put back at the end
+      // adjoint seeds
+      const RowLaunch lf = rows(d.fny * d.fnz, d.fnx);
+      const double D = 0.5 * ((double)nf + dg[0] / std::pow(d.h, d.dim));
+      k_obj_seed<T><<<lf.grid, lf.block, 0, st>>>(a_next, d, which, dg[5], D);
+      PF_CUDA_TRY(cudaMemsetAsync(a_cur, 0, nf * sizeof(T), st));
+      for (int b = 0; b < 30; ++b) PF_CUDA_TRY(cudaMemsetAsync(cb[b], 0, ncw * sizeof(T), st));
+      PF_CUDA_TRY(cudaMemsetAsync(cmpart, 0, nblk * sizeof(double), st));
+      PF_CUDA_TRY(cudaMemsetAsync(cwpart, 0, nblk * sizeof(double), st));
+      const PhysT<Dual> qd = phys_of<Dual>();
+      PhysT<Dual> qm = qd, qw = qd;
+      qm.cj_dx.d = -0.5 * (p.rho1 - p.rho2) / d.dx;                       // d(cj_dx)/dM
+      if (p.visco) {
+        qw.ilh.d = -1.0 / (p.lam_h * p.lam_h);                          // d(1/lambda_H)/d lambda_H
+        qw.wtau.d = -p.mu_p1 / (p.lam_h * p.lam_h);                     // d(mu_p/lambda_H)/d lambda_H
+      }
+      const double kk = p.gamma0 / (p.dt * p.nu_m);
+      const T cfD = (T)(p.dt / (p.gamma0 * p.rho0) / d.dx);
+      const T coefD = (T)(p.gamma0 * p.rho0 / p.dt / d.dx);
+      double thb = 0, mb = 0;
+      for (int s = nseg - 1; s >= 0; --s) {
+        const int len = std::min(K, nsteps - s * K);
+        state_io(cck[s], false);
+        state_io(csb[0], true);
+        for (int m = 1; m <= len; ++m) {
+          step(1, 0);
+          state_io(csb[m], true);
+        }
+        const size_t slot = (size_t)5 * nred_blocks;
+        for (int m = len; m >= 1; --m) {
+          // re-run step n (state csb[m-1]) for its intermediates; the context then holds state n+1
+          state_io(csb[m - 1], false);
+          step(1, 0);
+          coupled_reverse_step(state_view(csb[m - 1]), a_part + (len - m) * slot, qd, qm, qw, kk, cfD, coefD, nbf,
+                               nbc, nblk);
+        }
+        std::vector<double> h(len * slot);
+        PF_CUDA_TRY(cudaMemcpyAsync(h.data(), a_part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        PF_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int m = len; m >= 1; --m) adjoint_accumulate(h.data() + (len - m) * slot, thb, mb);
+      }
+      if (dphi0) {  // phi^{-1} = phi^0: both adjoints land on phi^0
+        k_add<T><<<nred_blocks, 256, 0, st>>>(a_next, a_cur, a_tmp, nf);
+        check_launch();
+        PF_CUDA_TRY(cudaMemcpyAsync(dphi0, a_tmp, nf * sizeof(T), on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+      }
+      std::vector<double> hm(nblk), hw(nblk);
+      PF_CUDA_TRY(cudaMemcpyAsync(hm.data(), cmpart, nblk * sizeof(double), cudaMemcpyDeviceToHost, st));
+      PF_CUDA_TRY(cudaMemcpyAsync(hw.data(), cwpart, nblk * sizeof(double), cudaMemcpyDeviceToHost, st));
+      state_io(cfin, false);  // leave the context at step N, as pf_step would
+      PF_CUDA_TRY(cudaStreamSynchronize(st));
+      double mns = 0, wi = 0;
+      for (int b = 0; b < nblk; ++b) {
+        mns += hm[b];
+        wi += hw[b];
+      }
+      out[0] = J;
+      out[1] = thb * M_PI / 180.0;
+      out[2] = mb + mns;
+      out[3] = wi;
+    }
+  }
+
+  // One reverse step of the coupled step n.  sv: the state of step n; the
+  // context holds state n+1 and the step's intermediates (rs, theta1, gwall).
+  void coupled_reverse_step(const StateView& sv, double* part, const PhysT<Dual>& qd, const PhysT<Dual>& qm,
+                            const PhysT<Dual>& qw, double kk, T cfD, T coefD, int nbf, int nbc, int nblk) {
+    const size_t nf = (size_t)d.fnx * d.fny * d.fnz, nc = (size_t)d.nx * d.ny * d.nz,
+                 ncw = (size_t)d.nx * d.ny * (d.nz + 1);
+    T *ub1 = cb[0], *ub0p = cb[1], *wb1 = cb[2], *wb0p = cb[3], *pb1 = cb[4], *pb0p = cb[5];
+    T *ub0 = cb[15], *ubm = cb[16], *wb0 = cb[17], *wbm = cb[18], *pb0 = cb[19], *pbm = cb[20];
+    T *ppb = cwork[0], *divb = cwork[1], *utb = cwork[2], *wtb = cwork[3], *rbu = cwork[4], *rbw = cwork[5];
+    NsBar<T> bar{};
+    // restricted-field adjoints: phic, phifx, phifz, phiexz, Gc, Gfx, Gfz
+    T* const* rfield = crf;
+    for (int f = 0; f < 7; ++f) PF_CUDA_TRY(cudaMemsetAsync(rfield[f], 0, ncw * sizeof(T), st));
+    bar.phic = rfield[0];
+    bar.phifx = rfield[1];
+    bar.phifz = rfield[2];
+    bar.phiexz = rfield[3];
+    bar.Gc = rfield[4];
+    bar.Gfx = rfield[5];
+    bar.Gfz = rfield[6];
+    // ---- 1. LCR update ----
+    if (p.visco) {
+      PolyAdj<T> P{};
+      for (int c = 0; c < 3; ++c) {
+        P.th0[c] = sv.th[c];
+        P.th1[c] = theta1[c];
+        P.thb_in[c] = cb[6 + c];
+        P.taub[c] = cb[9 + c];
+        P.thb_out[c] = cb[21 + c];
+        P.th1b[c] = cpoly[c];
+        P.ab1[c] = cpoly[3 + c];
+        P.ab0[c] = cpoly[6 + c];
+      }
+      P.U = u[fc];
+      P.W = w[fc];
+      P.phic = rs.phic;
+      P.ub = ub1;
+      P.wb = wb1;
+      P.phicb = bar.phic;
+      P.wipart = cwpart;
+      k_adj_poly2_a<T><<<nblk, 128, 0, st>>>(P, d, q, qd, qw);
+      k_adj_poly2_b<T><<<nblk, 128, 0, st>>>(P, d, q, qd, qw);
+      k_adj_poly2_c<T><<<nbc, 256, 0, st>>>(P, d, q);
+      check_launch();
+    }
+    // ---- 2. projection ----
+    k_adj_correct2<T><<<nbc, 256, 0, st>>>(ub1, wb1, pb1, ppb, d, cfD);
+    coarse_solve(ppb, divb, spP, d.nz, Z_NEUMANN, 0.0, true);   // P+ is symmetric
+    PF_CUDA_TRY(cudaMemcpyAsync(utb, ub1, nc * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    PF_CUDA_TRY(cudaMemcpyAsync(wtb, wb1, ncw * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    k_adj_div2<T><<<nbc, 256, 0, st>>>(divb, utb, wtb, d, coefD);
+    coarse_solve(utb, rbu, spU, d.nz, Z_DIRICH, kk, false);     // H^{-1}, symmetric
+    coarse_solve(wtb + d.nx, rbw, spW, d.nz - 1, Z_FACES, kk, false);
+    PF_CUDA_TRY(cudaMemcpyAsync(ub0, ub0p, nc * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    PF_CUDA_TRY(cudaMemsetAsync(ubm, 0, nc * sizeof(T), st));
+    PF_CUDA_TRY(cudaMemcpyAsync(wb0, wb0p, ncw * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    PF_CUDA_TRY(cudaMemsetAsync(wbm, 0, ncw * sizeof(T), st));
+    k_adj_ustar<T><<<nbc, 256, 0, st>>>(utb, ub0, ubm, 0, nc);
+    k_adj_ustar<T><<<nbc, 256, 0, st>>>(wtb, wb0, wbm, (size_t)d.nx, (size_t)d.nx * d.nz);
+    k_add<T><<<nbc, 256, 0, st>>>(pb0p, pb1, pb0, nc);          // p^{n+1} = p^n + p'
+    PF_CUDA_TRY(cudaMemsetAsync(pbm, 0, nc * sizeof(T), st));
+    for (int c = 0; c < 3; ++c) {
+      PF_CUDA_TRY(cudaMemcpyAsync(cb[24 + c], cb[12 + c], nc * sizeof(T), cudaMemcpyDeviceToDevice, st));
+      PF_CUDA_TRY(cudaMemsetAsync(cb[27 + c], 0, nc * sizeof(T), st));
+    }
+    // ---- 3. momentum right side ----
+    NsIn<T> A{};
+    A.un = sv.u_n;
+    A.uo = sv.u_o;
+    A.vn = A.vo = sv.u_n;
+    A.wn = sv.w_n;
+    A.wo = sv.w_o;
+    A.pn = sv.p_n;
+    A.po = sv.p_o;
+    for (int c = 0; c < 6; ++c) {
+      A.tn[c] = c < 3 ? sv.tau_n[c] : nullptr;
+      A.to[c] = c < 3 ? sv.tau_o[c] : nullptr;
+    }
+    A.rs = rs;
+    bar.un = ub0;
+    bar.uo = ubm;
+    bar.wn = wb0;
+    bar.wo = wbm;
+    bar.pn = pb0;
+    bar.po = pbm;
+    for (int c = 0; c < 3; ++c) {
+      bar.tn[c] = cb[24 + c];
+      bar.to[c] = cb[27 + c];
+    }
+    k_adj_ns_rhs2<T><<<nblk, 128, 0, st>>>(A, d, qd, qm, rbu, rbw, bar, p.visco, cmpart);
+    check_launch();
+    // ---- 4. restriction and chemical potential ----
+    k_adj_restrict2<T><<<nbf, 256, 0, st>>>(bar, a_next, cGb, d);
+    k_adj_G2<T><<<nbf, 256, 0, st>>>(phi[pc], cGb, a_next, cgbx, d, q);
+    check_launch();
+    // ---- 5. CH step, velocity from step n ----
+    const CoarseVel<T> vel{sv.u_n, sv.u_o, sv.u_n, sv.u_o, sv.w_n, sv.w_o};
+    adjoint_step_v(sv.phi_n, sv.phi_o, phi[pc], part, vel, cgbx);
+    k_adj_ch_vel2<T><<<nbc, 256, 0, st>>>(a_phis, a_rbar, ub0, ubm, wb0, wbm, d, -1.0 / (p.Ml * 2.0 * d.h));
+    check_launch();
+    // ---- 6. the adjoints of step n become the incoming ones ----
+    std::swap(cb[0], cb[15]);   // ub1 <- ub0
+    std::swap(cb[1], cb[16]);   // ub0p <- ubm
+    std::swap(cb[2], cb[17]);
+    std::swap(cb[3], cb[18]);
+    std::swap(cb[4], cb[19]);
+    std::swap(cb[5], cb[20]);
+    for (int c = 0; c < 3; ++c) {
+      std::swap(cb[6 + c], cb[21 + c]);   // thb1 <- thb0
+      std::swap(cb[9 + c], cb[24 + c]);   // taub1 <- taub0
+      std::swap(cb[12 + c], cb[27 + c]);  // taub0p <- taubm
+    }
+    (void)nf;
   }
 
   // per-kernel average device time over nsteps direct (non-graph) steps
@@ -1672,6 +1991,20 @@ int pf_adjoint(pf_ctx* ctx, int nsteps, int ckpt_every, int objective, double ou
   return guarded(ctx, [&] { ctx->impl->adjoint(nsteps, ckpt_every, objective, out, dphi0, dphi0_on_device); });
 }
 
+int pf_adjoint_ex(pf_ctx* ctx, int nsteps, int ckpt_every, int objective, int flags, double out[4], void* dphi0,
+                  int dphi0_on_device) {
+  if (!ctx || !out) return PF_ERR_ARG;
+  if (flags & ~PF_ADJ_COUPLED) return PF_ERR_ARG;
+  return guarded(ctx, [&] {
+    if (flags & PF_ADJ_COUPLED) {
+      ctx->impl->adjoint_coupled(nsteps, ckpt_every, objective, out, dphi0, dphi0_on_device);
+    } else {
+      ctx->impl->adjoint(nsteps, ckpt_every, objective, out, dphi0, dphi0_on_device);
+      out[3] = 0.0;
+    }
+  });
+}
+
 const char* pf_last_error(const pf_ctx* ctx) { return ctx ? ctx->err.c_str() : g_init_err.c_str(); }
 
 }  // extern "C"
@@ -1760,6 +2093,21 @@ int pf_batch_adjoint(pf_batch* b, int problem, int nsteps, int ckpt_every, int o
                      int dphi0_on_device) {
   if (!b || !out) return PF_ERR_ARG;
   return bguarded(b, [&] { b->impl->problem(problem)->adjoint(nsteps, ckpt_every, objective, out, dphi0, dphi0_on_device); });
+}
+
+int pf_batch_adjoint_ex(pf_batch* b, int problem, int nsteps, int ckpt_every, int objective, int flags, double out[4],
+                        void* dphi0, int dphi0_on_device) {
+  if (!b || !out) return PF_ERR_ARG;
+  if (flags & ~PF_ADJ_COUPLED) return PF_ERR_ARG;
+  return bguarded(b, [&] {
+    auto* I = b->impl->problem(problem);
+    if (flags & PF_ADJ_COUPLED) {
+      I->adjoint_coupled(nsteps, ckpt_every, objective, out, dphi0, dphi0_on_device);
+    } else {
+      I->adjoint(nsteps, ckpt_every, objective, out, dphi0, dphi0_on_device);
+      out[3] = 0.0;
+    }
+  });
 }
 
 const char* pf_batch_last_error(const pf_batch* b) { return b ? b->err.c_str() : g_init_err.c_str(); }

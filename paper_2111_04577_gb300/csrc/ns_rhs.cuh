@@ -14,6 +14,126 @@
 
 namespace pf {
 
+// The two momentum rows of 2D cell (i, k): x at its u-face, z at its w-face k
+// (k >= 1).  T is the arithmetic type (float, double, or Dual for the
+// derivatives the adjoint takes of it); the accessor A supplies the inputs by
+// offset from the cell: U, W (extrapolated u*, w*; W's dz is relative to face
+// k), DP = p^{n-1} - p^n, PS = p*, PHC, G (centres), EXZ (x-z edges, dz relative
+// to face k), TXX, TXZ, TZZ (extrapolated tau*; layers beyond a wall read as the
+// wall layer, the mirror ghost), and at the cell's own faces phifx, phifz, gfx,
+// gfz, du = u^n - u^{n-1}, dw = w^n - w^{n-1}.  Terms as in k_ns_rhs_v2_b.
+template <class T, class Acc>
+__device__ __forceinline__ void ns_rhs_cell2(const Acc& A, const PhysT<T>& q, const int k, const int nz,
+                                             const int have_tau, T& ru, T& rw) {
+  const bool hasb = k > 0, hast = k < nz - 1;
+  const T iD = q.iD, iD2 = q.iD2, h = (T)0.5;
+  auto mu_of = [&](T ph) { return h * ((T)1 + ph) * q.mu_s1 + h * ((T)1 - ph) * q.mu_s2; };
+  auto rho_of = [&](T ph) { return h * ((T)1 + ph) * q.rho1 + h * ((T)1 - ph) * q.rho2; };
+  const T Uc = A.U(0, 0), Uxp = A.U(1, 0), Uxm = A.U(-1, 0);
+  const T Uzp = hast ? A.U(0, 1) : q.uw2_top - Uc;
+  const T Uzm = hasb ? A.U(0, -1) : q.uw2_bot - Uc;
+  const T Uxp_zm = hasb ? A.U(1, -1) : (T)0;
+  const T Wc = A.W(0, 0), Wzp = A.W(0, 1), Wxm = A.W(-1, 0), Wxp = A.W(1, 0), Wxm_zp = A.W(-1, 1);
+  const T Wzm = hasb ? A.W(0, -1) : (T)0;
+  const T Dp_c = A.DP(0, 0), Ps_c = A.PS(0, 0);
+  const T phc = A.PHC(0, 0), phc_xm = A.PHC(-1, 0);
+  const T Gc_c = A.G(0, 0), Gc_xm = A.G(-1, 0), Gc_xp = A.G(1, 0);
+  const T muc = mu_of(phc), muc_xm = mu_of(phc_xm);
+  const T muexz = mu_of(A.EXZ(0, 0)), muexz_zp = mu_of(A.EXZ(0, 1)), muexz_xp = mu_of(A.EXZ(1, 0));
+  const T cj = q.cj_dx;
+  const T Jx_c = cj * (Gc_c - Gc_xm);
+  const T Gc_zp = hast ? A.G(0, 1) : (T)0, Gc_xm_zp = hast ? A.G(-1, 1) : (T)0;
+  const T Gc_zm = hasb ? A.G(0, -1) : (T)0, Gc_xm_zm = hasb ? A.G(-1, -1) : (T)0;
+  const T Jz_c = hasb ? cj * (Gc_c - Gc_zm) : (T)0;
+  const T Jz_xm = hasb ? cj * (Gc_xm - Gc_xm_zm) : (T)0;
+  const T Jz_zp = hast ? cj * (Gc_zp - Gc_c) : (T)0;
+  const T Jz_xm_zp = hast ? cj * (Gc_xm_zp - Gc_xm) : (T)0;
+  {  // x momentum at the u-face
+    const T rho = rho_of(A.phifx());
+    const T cxx0 = (T)0.25 * (Uc + Uxp) * (Uc + Uxp), cxx1 = (T)0.25 * (Uxm + Uc) * (Uxm + Uc);
+    const T Exz_p = (T)0.25 * (Uc + Uzp) * (Wxm_zp + Wzp);
+    const T Exz_0 = (T)0.25 * (Uzm + Uc) * (Wxm + Wc);
+    const T adv = (cxx0 - cxx1 + Exz_p - Exz_0) * iD;
+    const T Jzu = (T)0.25 * (Jz_xm + Jz_c + Jz_xm_zp + Jz_zp);
+    const T jg = (Jx_c * (Uxp - Uxm) + Jzu * (Uzp - Uzm)) * h * iD;
+    const T sxx0 = 2 * muc * (Uxp - Uc), sxx1 = 2 * muc_xm * (Uc - Uxm);
+    const T sxz_p = muexz_zp * ((Uzp - Uc) + (Wzp - Wxm_zp));
+    const T sxz_0 = muexz * ((Uc - Uzm) + (Wc - Wxm));
+    const T visc = (sxx0 - sxx1 + sxz_p - sxz_0) * iD2;
+    T divt = 0;
+    if (have_tau) {
+      const T tzc = A.TXZ(0, 0), tzxm = A.TXZ(-1, 0);
+      const T tzzp = A.TXZ(0, 1), tzxmzp = A.TXZ(-1, 1);
+      const T tzzm = A.TXZ(0, -1), tzxmzm = A.TXZ(-1, -1);
+      const T Txz_p = (T)0.25 * (tzxm + tzc + tzxmzp + tzzp);
+      const T Txz_0 = (T)0.25 * (tzxmzm + tzzm + tzxm + tzc);
+      divt = (A.TXX(0, 0) - A.TXX(-1, 0) + Txz_p - Txz_0) * iD;
+    }
+    const T st = A.gfx() * (phc - phc_xm) * iD;
+    const T gdp = (Dp_c - A.DP(-1, 0)) * iD, gps = (Ps_c - A.PS(-1, 0)) * iD;
+    const T R = A.du() * q.idt + adv + (jg - divt - visc - st + gps) / rho + gdp * q.irho0 - q.gx;
+    ru = R * q.inum;
+  }
+  if (hasb) {  // z momentum at the w-face k
+    const T rho = rho_of(A.phifz());
+    const T Exz_xp = (T)0.25 * (Uxp_zm + Uxp) * (Wc + Wxp);
+    const T Exz_0 = (T)0.25 * (Uzm + Uc) * (Wxm + Wc);
+    const T czz0 = (T)0.25 * (Wc + Wzp) * (Wc + Wzp), czz1 = (T)0.25 * (Wzm + Wc) * (Wzm + Wc);
+    const T adv = (Exz_xp - Exz_0 + czz0 - czz1) * iD;
+    const T Gc_xp_zm = A.G(1, -1);
+    const T Jx_zm = cj * (Gc_zm - Gc_xm_zm), Jx_xp_zm = cj * (Gc_xp_zm - Gc_zm), Jx_xp = cj * (Gc_xp - Gc_c);
+    const T Jxw = (T)0.25 * (Jx_zm + Jx_xp_zm + Jx_c + Jx_xp);
+    const T jg = (Jxw * (Wxp - Wxm) + Jz_c * (Wzp - Wzm)) * h * iD;
+    const T muc_zm = mu_of(A.PHC(0, -1));
+    const T szz0 = 2 * muc * (Wzp - Wc), szz1 = 2 * muc_zm * (Wc - Wzm);
+    const T sxz_xp = muexz_xp * ((Uxp - Uxp_zm) + (Wxp - Wc));
+    const T sxz_0 = muexz * ((Uc - Uzm) + (Wc - Wxm));
+    const T visc = (sxz_xp - sxz_0 + szz0 - szz1) * iD2;
+    T divt = 0;
+    if (have_tau) {
+      const T e00 = A.TXZ(0, 0), e0m = A.TXZ(0, -1), ep0 = A.TXZ(1, 0), epm = A.TXZ(1, -1), em0 = A.TXZ(-1, 0),
+              emm = A.TXZ(-1, -1);
+      const T Txz_xp = (T)0.25 * (e0m + epm + e00 + ep0), Txz_0 = (T)0.25 * (emm + e0m + em0 + e00);
+      divt = (Txz_xp - Txz_0 + A.TZZ(0, 0) - A.TZZ(0, -1)) * iD;
+    }
+    const T st = A.gfz() * (phc - A.PHC(0, -1)) * iD;
+    const T gdp = (Dp_c - A.DP(0, -1)) * iD, gps = (Ps_c - A.PS(0, -1)) * iD;
+    const T R = A.dw() * q.idt + adv + (jg - divt - visc - st + gps) / rho + gdp * q.irho0 - q.gz;
+    rw = R * q.inum;
+  }
+}
+
+// The inputs of ns_rhs_cell2 read from the fields of step n (arithmetic type
+// R; storage type T).
+template <class T, class R = T>
+struct NsGlobalAcc2 {
+  const NsIn<T>* a;
+  int nx, nz, i, k;
+  __device__ __forceinline__ int x(int dx) const { return wrap(i + dx, nx); }
+  __device__ __forceinline__ int zc(int dz) const { return min(max(k + dz, 0), nz - 1) * nx; }
+  __device__ __forceinline__ int zf(int dz) const { return (k + dz) * nx; }
+  __device__ __forceinline__ R ex(const T* n, const T* o, int o_) const { return (R)((T)2 * n[o_] - o[o_]); }
+  __device__ __forceinline__ R U(int dx, int dz) const { return ex(a->un, a->uo, zc(dz) + x(dx)); }
+  __device__ __forceinline__ R W(int dx, int dz) const { return ex(a->wn, a->wo, zf(dz) + x(dx)); }
+  __device__ __forceinline__ R DP(int dx, int dz) const {
+    const int o = zc(dz) + x(dx);
+    return (R)(a->po[o] - a->pn[o]);
+  }
+  __device__ __forceinline__ R PS(int dx, int dz) const { return ex(a->pn, a->po, zc(dz) + x(dx)); }
+  __device__ __forceinline__ R PHC(int dx, int dz) const { return (R)a->rs.phic[zc(dz) + x(dx)]; }
+  __device__ __forceinline__ R G(int dx, int dz) const { return (R)a->rs.Gc[zc(dz) + x(dx)]; }
+  __device__ __forceinline__ R EXZ(int dx, int dz) const { return (R)a->rs.phiexz[zf(dz) + x(dx)]; }
+  __device__ __forceinline__ R phifx() const { return (R)a->rs.phifx[k * nx + i]; }
+  __device__ __forceinline__ R phifz() const { return (R)a->rs.phifz[k * nx + i]; }
+  __device__ __forceinline__ R gfx() const { return (R)a->rs.Gfx[k * nx + i]; }
+  __device__ __forceinline__ R gfz() const { return (R)a->rs.Gfz[k * nx + i]; }
+  __device__ __forceinline__ R TXX(int dx, int dz) const { return ex(a->tn[0], a->to[0], zc(dz) + x(dx)); }
+  __device__ __forceinline__ R TXZ(int dx, int dz) const { return ex(a->tn[1], a->to[1], zc(dz) + x(dx)); }
+  __device__ __forceinline__ R TZZ(int dx, int dz) const { return ex(a->tn[2], a->to[2], zc(dz) + x(dx)); }
+  __device__ __forceinline__ R du() const { return (R)(a->un[k * nx + i] - a->uo[k * nx + i]); }
+  __device__ __forceinline__ R dw() const { return (R)(a->wn[k * nx + i] - a->wo[k * nx + i]); }
+};
+
 template <class T, int DIM>
 __device__ __forceinline__ void k_ns_rhs_v2_b(const NsIn<T>& a, const Dims d, const PhysT<T> q, T* __restrict__ ru, T* __restrict__ rv, T* __restrict__ rw, const int have_tau, const int3 bid) {
   constexpr bool D3 = DIM == 3;
@@ -22,6 +142,14 @@ __device__ __forceinline__ void k_ns_rhs_v2_b(const NsIn<T>& a, const Dims d, co
   const int i = ix.i, j = ix.j, k = ix.k;
   const int nx = d.nx, ny = d.ny, nz = d.nz;
   const int P = nx * ny;
+  if constexpr (!D3) {
+    const NsGlobalAcc2<T> acc{&a, nx, nz, i, k};
+    T oru = 0, orw = 0;
+    ns_rhs_cell2<T>(acc, q, k, nz, have_tau, oru, orw);
+    ru[k * nx + i] = oru;
+    if (k > 0) rw[(k - 1) * nx + i] = orw;  // face rows 0..nz-2 hold faces 1..nz-1
+    return;
+  }
   // 32-bit neighbour offsets (fields are smaller than 2^31 elements)
   const int x0 = i, xm = i == 0 ? nx - 1 : i - 1, xp = i == nx - 1 ? 0 : i + 1;
   const int r0 = j * nx;

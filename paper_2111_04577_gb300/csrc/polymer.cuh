@@ -191,6 +191,116 @@ __device__ __forceinline__ int comp_of(int a, int b) {
   return s == 1 ? 3 : (s == 2 ? 4 : 5);
 }
 
+// The local part of RH at one cell: R H R^T of Eq. NS41 (everything but the
+// advection), from Theta's unique components th0 and the velocity gradient
+// L[a][b] = du_a/dx_b.  Returns it per component in s_out, and Theta's
+// eigenbasis R and eigenvalues dg.
+template <class T, int N>
+__device__ __forceinline__ void lcr_rhs_local(const T (&th0)[N == 2 ? 3 : 6], const T (&L)[N][N], const PhysT<T>& q,
+                                              T (&s_out)[N == 2 ? 3 : 6], T (&R)[N][N], T (&dg)[N]) {
+  T of[N == 2 ? 1 : 3];
+#pragma unroll
+  for (int a = 0; a < N; ++a) dg[a] = th0[comp_of<N>(a, a)];
+  if (N == 2) of[0] = th0[comp_of<N>(0, 1)];
+  else {
+    of[0] = th0[comp_of<N>(0, 1)];
+    of[1] = th0[comp_of<N>(0, 2)];
+    of[2] = th0[comp_of<N>(1, 2)];
+  }
+  eig_sym<T, N>(dg, of, R);
+  // M~ = R^T L R
+  T LR[N][N], Mt[N][N];
+#pragma unroll
+  for (int a = 0; a < N; ++a)
+#pragma unroll
+    for (int b = 0; b < N; ++b) {
+      T s = 0;
+#pragma unroll
+      for (int c = 0; c < N; ++c) s += L[a][c] * R[c][b];
+      LR[a][b] = s;
+    }
+#pragma unroll
+  for (int a = 0; a < N; ++a)
+#pragma unroll
+    for (int b = 0; b < N; ++b) {
+      T s = 0;
+#pragma unroll
+      for (int c = 0; c < N; ++c) s += R[c][a] * LR[c][b];
+      Mt[a][b] = s;
+    }
+  // RH in the eigenbasis
+  T H[N][N];
+#pragma unroll
+  for (int a = 0; a < N; ++a) {
+    const T em = fexp<T>(-dg[a]);
+    T relax = em - (T)1;  // Oldroyd-B: e^{-theta} - 1
+    if (q.ag != (T)0) relax -= q.ag * (fexp<T>(dg[a]) - (T)1) * ((T)1 - em);  // Giesekus
+    H[a][a] = 2 * Mt[a][a] + relax * q.ilh;
+#pragma unroll
+    for (int b = a + 1; b < N; ++b) {
+      const T dd = dg[b] - dg[a];
+      T o;
+      const T x = dd > 0 ? -dd : dd;  // -|dd|
+      const T ex = fexp<T>(x);
+      const T wgt = dexpm1_e<T>(x, ex);
+      if (dd > 0) o = (Mt[a][b] + ex * Mt[b][a]) * wgt;
+      else o = (ex * Mt[a][b] + Mt[b][a]) * wgt;
+      H[a][b] = o;
+      H[b][a] = o;
+    }
+  }
+  // back to the physical basis: R H R^T
+  T HR[N][N];
+#pragma unroll
+  for (int a = 0; a < N; ++a)
+#pragma unroll
+    for (int b = 0; b < N; ++b) {
+      T s = 0;
+#pragma unroll
+      for (int c = 0; c < N; ++c) s += H[a][c] * R[b][c];
+      HR[a][b] = s;
+    }
+#pragma unroll
+  for (int a = 0; a < N; ++a)
+#pragma unroll
+    for (int b = a; b < N; ++b) {
+      T s = 0;
+#pragma unroll
+      for (int c = 0; c < N; ++c) s += R[a][c] * HR[c][b];
+      s_out[comp_of<N>(a, b)] = s;
+    }
+}
+
+// tau = (1 + phi)/2 (mu_p/lambda_H) (W e^theta W^T - I) from Theta's unique
+// components (Eqs. NS12, NS46), with a decomposition of its own
+template <class T, int N>
+__device__ __forceinline__ void lcr_tau(const T (&th)[N == 2 ? 3 : 6], T phic, const PhysT<T>& q,
+                                        T (&tau)[N == 2 ? 3 : 6]) {
+  T dg[N], of[N == 2 ? 1 : 3], R[N][N];
+#pragma unroll
+  for (int a = 0; a < N; ++a) dg[a] = th[comp_of<N>(a, a)];
+  if (N == 2) of[0] = th[comp_of<N>(0, 1)];
+  else {
+    of[0] = th[comp_of<N>(0, 1)];
+    of[1] = th[comp_of<N>(0, 2)];
+    of[2] = th[comp_of<N>(1, 2)];
+  }
+  eig_sym<T, N>(dg, of, R);
+  T ex[N];
+#pragma unroll
+  for (int c = 0; c < N; ++c) ex[c] = fexp<T>(dg[c]);
+  const T wgt = (T)0.5 * ((T)1 + phic) * q.wtau;
+#pragma unroll
+  for (int a = 0; a < N; ++a)
+#pragma unroll
+    for (int b = a; b < N; ++b) {
+      T s = 0;
+#pragma unroll
+      for (int c = 0; c < N; ++c) s += R[a][c] * ex[c] * R[b][c];
+      tau[comp_of<N>(a, b)] = wgt * (s - (a == b ? (T)1 : (T)0));
+    }
+}
+
 // one RK2-TVD stage at one coarse cell; STAGE 2 also forms tau
 template <class T, int N, int STAGE>
 __device__ __forceinline__ void polymer_cell(const PolyIn<T>& P, const Dims& d, const PhysT<T>& q, const RowIdx& x) {
@@ -256,83 +366,17 @@ __device__ __forceinline__ void polymer_cell(const PolyIn<T>& P, const Dims& d, 
       th0[cq] = t0;
     }
   }
-  // eigen-decomposition of Theta at the cell
-  T dg[N], of[N == 2 ? 1 : 3], R[N][N];
-#pragma unroll
-  for (int a = 0; a < N; ++a) dg[a] = th0[comp_of<N>(a, a)];
-  if (N == 2) of[0] = th0[comp_of<N>(0, 1)];
-  else {
-    of[0] = th0[comp_of<N>(0, 1)];
-    of[1] = th0[comp_of<N>(0, 2)];
-    of[2] = th0[comp_of<N>(1, 2)];
-  }
-  eig_sym<T, N>(dg, of, R);
-  // M~ = R^T L R
-  T LR[N][N], Mt[N][N];
-#pragma unroll
-  for (int a = 0; a < N; ++a)
-#pragma unroll
-    for (int b = 0; b < N; ++b) {
-      T s = 0;
-#pragma unroll
-      for (int c = 0; c < N; ++c) s += L[a][c] * R[c][b];
-      LR[a][b] = s;
-    }
-#pragma unroll
-  for (int a = 0; a < N; ++a)
-#pragma unroll
-    for (int b = 0; b < N; ++b) {
-      T s = 0;
-#pragma unroll
-      for (int c = 0; c < N; ++c) s += R[c][a] * LR[c][b];
-      Mt[a][b] = s;
-    }
-  // RH in the eigenbasis
-  T H[N][N];
-#pragma unroll
-  for (int a = 0; a < N; ++a) {
-    const T em = fexp<T>(-dg[a]);
-    T relax = em - (T)1;  // Oldroyd-B: e^{-theta} - 1
-    if (q.ag != (T)0) relax -= q.ag * (fexp<T>(dg[a]) - (T)1) * ((T)1 - em);  // Giesekus
-    H[a][a] = 2 * Mt[a][a] + relax * q.ilh;
-#pragma unroll
-    for (int b = a + 1; b < N; ++b) {
-      const T dd = dg[b] - dg[a];
-      T o;
-      const T x = dd > 0 ? -dd : dd;  // -|dd|
-      const T ex = fexp<T>(x);
-      const T wgt = dexpm1_e<T>(x, ex);
-      if (dd > 0) o = (Mt[a][b] + ex * Mt[b][a]) * wgt;
-      else o = (ex * Mt[a][b] + Mt[b][a]) * wgt;
-      H[a][b] = o;
-      H[b][a] = o;
-    }
-  }
-  // back to the physical basis: R H R^T
-  T HR[N][N];
-#pragma unroll
-  for (int a = 0; a < N; ++a)
-#pragma unroll
-    for (int b = 0; b < N; ++b) {
-      T s = 0;
-#pragma unroll
-      for (int c = 0; c < N; ++c) s += H[a][c] * R[b][c];
-      HR[a][b] = s;
-    }
+  // local part of RH at the cell (eigen-decomposition of Theta, Eqs. NS21-NS24)
+  T dg[N], of[N == 2 ? 1 : 3], R[N][N], rl[NC];
+  lcr_rhs_local<T, N>(th0, L, q, rl, R, dg);
   const T dt = q.dt;
   T newth[NC];
 #pragma unroll
-  for (int a = 0; a < N; ++a)
-#pragma unroll
-    for (int b = a; b < N; ++b) {
-      T s = 0;
-#pragma unroll
-      for (int c = 0; c < N; ++c) s += R[a][c] * HR[c][b];
-      const int cq = comp_of<N>(a, b);
-      const T rh = s - adv[cq];
-      const T t0 = th0[cq];
-      newth[cq] = STAGE == 1 ? t0 + dt * rh : (T)0.5 * P.base[cq][id] + (T)0.5 * (t0 + dt * rh);
-    }
+  for (int cq = 0; cq < NC; ++cq) {
+    const T rh = rl[cq] - adv[cq];
+    const T t0 = th0[cq];
+    newth[cq] = STAGE == 1 ? t0 + dt * rh : (T)0.5 * P.base[cq][id] + (T)0.5 * (t0 + dt * rh);
+  }
 #pragma unroll
   for (int cq = 0; cq < NC; ++cq) P.out[cq][id] = newth[cq];
   if (STAGE == 2) {
