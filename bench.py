@@ -334,6 +334,7 @@ def gradients_leg(w, stream, nx=128, steps=10):
     b.record(stream)
     b.synchronize()
     t_ch = a.elapsed_time(b) / 1e3
+    out["coupled_adjoint"] = coupled_adjoint_leg(stream)
     out["ch_adjoint"] = {"ms_per_step": t_adj / steps * 1e3, "ch_step_ms": t_ch / steps * 1e3,
                          "ratio": t_adj / t_ch, "ckpt_every": 5,
                          "ms_per_step_without_dphi0_to_host": t_adj_nophi / steps * 1e3,
@@ -343,6 +344,35 @@ def gradients_leg(w, stream, nx=128, steps=10):
     gc.collect()
     torch.cuda.synchronize()
     return out
+
+
+def coupled_adjoint_leg(stream, problem=8, steps=500, ckpt=50):
+    """The reverse sweep through the whole coupled 2D step (pf_adjoint_ex) on
+    one problem of the 64-problem sweep (coarse 128 x 64, its contact angle and
+    Wi), mixed precision, over the stated 500 steps with checkpoints every 50:
+    dJ/dphi0, dJ/dtheta, dJ/dM and dJ/dWi of the final wetted length in one
+    sweep, against the forward steps alone."""
+    import time
+    import torch
+    from paper_2111_04577_gb300 import binding, workloads as wl
+    w = wl.batch_problems(64, seed=0)[problem]
+    s = binding.Solver(w.grid, w.params, binding.PF_MIXED, stream=stream.cuda_stream)
+    phi0 = wl.initial_phi(w)
+    s.load_state(phi0)
+    s.adjoint_coupled(10, 5, binding.PF_OBJ_WETTED)  # warm-up (allocations, graphs)
+    s.load_state(phi0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J, dth, dm, dwi, dphi = s.adjoint_coupled(steps, ckpt, binding.PF_OBJ_WETTED)
+    t_adj = time.perf_counter() - t0
+    s.load_state(phi0)
+    t_fwd = time_steps(s, stream, steps)
+    s.close()
+    return {"grid": f"coarse {w.grid.nx}x{w.grid.nz} / fine {2 * w.grid.nx}x{2 * w.grid.nz} (2D)",
+            "theta_deg": w.params.theta_bot_deg, "wi": w.params.wi, "steps": steps, "ckpt_every": ckpt,
+            "precision": "mixed", "ms_per_step": t_adj / steps * 1e3, "forward_ms_per_step": t_fwd / steps * 1e3,
+            "ratio": t_adj / t_fwd, "J": J, "dJ_dtheta_per_deg": dth, "dJ_dM": dm, "dJ_dWi": dwi,
+            "dJ_dphi0_norm": float(np.sqrt(np.sum(np.asarray(dphi, dtype=np.float64) ** 2)))}
 
 
 def batch_leg(stream, nprob=64, steps=20):

@@ -1335,14 +1335,14 @@ struct Impl : ImplBase {
         state_io(cck[s], false);
         state_io(csb[0], true);
         for (int m = 1; m <= len; ++m) {
-          step(1, 0);
+          fwd1();
           state_io(csb[m], true);
         }
         const size_t slot = (size_t)5 * nred_blocks;
         for (int m = len; m >= 1; --m) {
           // re-run step n (state csb[m-1]) for its intermediates; the context then holds state n+1
           state_io(csb[m - 1], false);
-          step(1, 0);
+          fwd1();
           coupled_reverse_step(state_view(csb[m - 1]), a_part + (len - m) * slot, qd, qm, qw, kk, cfD, coefD, nbf,
                                nbc, nblk);
         }
@@ -1375,6 +1375,15 @@ struct Impl : ImplBase {
 
   // One reverse step of the coupled step n.  sv: the state of step n; the
   // context holds state n+1 and the step's intermediates (rs, theta1, gwall).
+  // one coupled step with the polymer update in place (no deferral, no
+  // finiteness check): the adjoint's recomputation
+  void fwd1() {
+    run_one(0, false, false);
+    pc ^= 1;
+    fc ^= 1;
+    ++steps_done;
+  }
+
   void coupled_reverse_step(const StateView& sv, double* part, const PhysT<Dual>& qd, const PhysT<Dual>& qm,
                             const PhysT<Dual>& qw, double kk, T cfD, T coefD, int nbf, int nbc, int nblk) {
     const size_t nf = (size_t)d.fnx * d.fny * d.fnz, nc = (size_t)d.nx * d.ny * d.nz,
