@@ -375,6 +375,94 @@ def coupled_adjoint_leg(stream, problem=8, steps=500, ckpt=50):
             "dJ_dphi0_norm": float(np.sqrt(np.sum(np.asarray(dphi, dtype=np.float64) ** 2)))}
 
 
+def accuracy_leg(stream, steps=200):
+    """Section 4.1's comparison on the 3D Newtonian droplet (coarse 128^2 x 64,
+    mixed): dual resolution (DR), single resolution with phi on the coarse
+    mesh (CSR) and with every field on the fine mesh (RSR), from the same
+    droplet, after `steps` steps of the same dt.  RSR is the reference: DR's phi
+    is compared on the fine mesh, CSR's against RSR's phi averaged over each
+    coarse cell; velocities on the coarse faces against RSR's face velocities
+    averaged over the fine faces that tile each coarse face."""
+    import gc
+    import torch
+    from paper_2111_04577_gb300 import binding, workloads as wl
+    w = wl.config("c3")
+    g = w.grid
+    grids = {"dr": g, "csr": wl.Grid(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, 0),
+             "rsr": wl.Grid(2 * g.nx, 2 * g.ny, 2 * g.nz, g.lx, g.ly, g.lz, 0)}
+    out = {}
+    for name, gg in grids.items():
+        ww = wl.Workload(w.name, gg, w.params, w.steps, w.R0, w.seed, 0.0)  # no seeded noise: one droplet
+        s = binding.Solver(gg, w.params, binding.PF_MIXED, stream=stream.cuda_stream)
+        s.load_state(wl.initial_phi(ww).astype(s.dtype))
+        s.step(steps)
+        out[name] = {"phi": s.fine("phi"), "u": s.coarse("u"), "v": s.coarse("v"), "w": s.coarse("w")}
+        s.close()
+        del s
+        gc.collect()
+        torch.cuda.synchronize()
+    r = out["rsr"]
+    nz, ny, nx = g.coarse_shape
+    phi_c = r["phi"].reshape(nz, 2, ny, 2, nx, 2).mean(axis=(1, 3, 5))
+    u_c = r["u"][:, :, 0::2].reshape(nz, 2, ny, 2, nx).mean(axis=(1, 3))
+    v_c = r["v"][:, 0::2, :].reshape(nz, 2, ny, nx, 2).mean(axis=(1, 4))
+    w_c = r["w"][0::2].reshape(nz + 1, ny, 2, nx, 2).mean(axis=(2, 4))
+
+    def rel(a, b):
+        return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+    res = {"steps": steps, "time": steps * w.params.dt, "grid": f"coarse {g.nx}x{g.ny}x{g.nz} / fine 2x",
+           "reference": "RSR (every field on the fine mesh)"}
+    for name in ("dr", "csr"):
+        o = out[name]
+        dphi = o["phi"] - (r["phi"] if name == "dr" else phi_c)
+        res[name] = {"phi_maxabs": float(np.max(np.abs(dphi))),
+                     "phi_rms": float(np.sqrt(np.mean(dphi ** 2))),
+                     "u_rel": rel(o["u"], u_c), "v_rel": rel(o["v"], v_c), "w_rel": rel(o["w"], w_c)}
+    return res
+
+
+def paper_case_leg(stream, steps=5, warm=2):
+    """Section 4.5's performance case at its size: two coalescing drops on a
+    180 deg wall in a 6^3 box, dual resolution 384^3 (phase field 768^3)
+    against single resolution 768^3, Newtonian and Oldroyd-B (Wi = 10,
+    beta = 0.1), mixed precision, built-in launch shapes.  Time per step of
+    each, and the ratio the paper reports (about 2 Newtonian, above 2
+    viscoelastic, on 256-2304 CPU cores)."""
+    import gc
+    import torch
+    from paper_2111_04577_gb300 import binding, workloads as wl
+    res = {"box": "6 x 6 x 6, periodic x, y; walls z (180 / 90 deg)", "steps": steps}
+    phi = None
+    for visco in (False, True):
+        key = "viscoelastic" if visco else "newtonian"
+        res[key] = {}
+        for dual, n in ((1, 384), (0, 768)):
+            w = wl.config("e9", dual=dual, visco=visco, n=n)
+            if phi is None:
+                phi = wl.drops_phi(w, np.float32)  # the same 768^3 field for both meshes
+            try:
+                s = binding.Solver(w.grid, w.params, binding.PF_MIXED, stream=stream.cuda_stream)
+            except binding.PFError as e:
+                res[key]["dr" if dual else "sr"] = {"unavailable": str(e)}
+                continue
+            s.load_state(phi)
+            s.step(warm)
+            t = time_steps(s, stream, steps)
+            s.close()
+            del s
+            gc.collect()
+            torch.cuda.synchronize()
+            res[key]["dr" if dual else "sr"] = {"grid": f"{n}^3" + (" (phase field 768^3)" if dual else ""),
+                                                "ms_per_step": t / steps * 1e3,
+                                                "fine_cell_steps_per_s": 768 ** 3 * steps / t}
+        if "ms_per_step" in res[key].get("dr", {}) and "ms_per_step" in res[key].get("sr", {}):
+            res[key]["sr_over_dr"] = res[key]["sr"]["ms_per_step"] / res[key]["dr"]["ms_per_step"]
+    res["paper_sr_over_dr"] = {"newtonian": "about 2", "viscoelastic": "above 2 (above 3 on few cores)",
+                               "hardware": "CPU cluster, 256-2304 cores"}
+    return res
+
+
 def batch_leg(stream, nprob=64, steps=20):
     """64 uneven 2D droplets (coarse 64x32 .. 256x128, fine 2x, theta ~ U(30,150),
     Wi ~ U(0,2), beta = 0.5, mixed precision): one persistent launch per step
@@ -588,6 +676,8 @@ def main():
                     "dual_speedup_at_same_phi_resolution": ms_rsr / ms_per_step},
         }
     if rank == 0 and not args.no_compare:
+        extra["accuracy_dr_csr_vs_rsr"] = accuracy_leg(stream)
+        extra["paper_case_coalescing_drops"] = paper_case_leg(stream)
         extra["batch_sweep"] = batch_leg(stream)
         if w.params.wi > 0:
             extra["gradients"] = gradients_leg(w, stream)

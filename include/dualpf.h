@@ -117,7 +117,8 @@ typedef struct {
 /* Create a context for grid *g and allocate all fields on the current CUDA
  * device (all zero).  stream: a cudaStream_t, or NULL for a private one.  On success *out owns
  * the context; release it with pf_destroy.  Errors: PF_ERR_ARG (bad sizes,
- * non-cubic cells), PF_ERR_UNSUPPORTED (a size with a prime factor > 7),
+ * non-cubic cells), PF_ERR_UNSUPPORTED (a size with a prime factor > 7, or more than 4096
+ * fine z rows),
  * PF_ERR_NOMEM, PF_ERR_CUDA. */
 int pf_init_grid(pf_ctx** out, const pf_grid_desc* g, void* stream);
 
@@ -315,7 +316,9 @@ int pf_batch_tangent(pf_batch* b, int problem, int nsteps, int param, int object
  * never the arithmetic of a cell.
  *   PF_TUNE_XFFT_PAIRS   pairs of x-lines per CTA of the x transforms (1..16)
  *   PF_TUNE_YFFT_COLS    kx columns per CTA of the y transforms (power of two <= 32)
- *   PF_TUNE_ZSOLVE_COLS  kx columns per CTA of the z solves (multiple of 16, <= 64)
+ *   PF_TUNE_ZSOLVE_COLS  kx columns per CTA of the z solves (multiple of 16, <= 64); halved
+ *                        for a long z line until its CTA fits (two threads per column and
+ *                        16-row segment, at most 512)
  *   PF_TUNE_ROW_BLOCK    threads per CTA of the row kernels (multiple of 32)
  *   PF_TUNE_CH_ZCHUNK    fine z planes one CTA of the 3D CH right side walks (>= 2)
  *   PF_TUNE_CH_MINB      CTAs per SM the 3D CH right side's registers are sized for (2, 3, 4)

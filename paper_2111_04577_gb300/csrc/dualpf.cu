@@ -276,6 +276,8 @@ struct Impl : ImplBase {
     d.dx = g.lx / g.nx;
     d.h = d.dx / d.r;
     ncomp = d.dim == 2 ? 3 : 6;
+    if (zsolve_cols(std::max(d.fnz, d.nz + 1), true) == 0)
+      throw ApiError(PF_ERR_UNSUPPORTED, "z lines too long for the segmented z solve (at most 4096 rows)");
     const size_t nf = (size_t)d.fnx * d.fny * d.fnz;
     const size_t nc = (size_t)d.nx * d.ny * d.nz;
     const size_t ncw = (size_t)d.nx * d.ny * (d.nz + 1);
@@ -432,7 +434,6 @@ struct Impl : ImplBase {
   static constexpr int kMaxSmem = 200 * 1024;
   void set_smem_limits() {
     PF_CUDA_TRY(cudaFuncSetAttribute(k_fft_y<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
-    PF_CUDA_TRY(cudaFuncSetAttribute(k_zsolve<T, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_zsolve_seg<T, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_rfft_x<T, ArrPro<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_rfft_x<T, DivPro<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
@@ -556,6 +557,16 @@ struct Impl : ImplBase {
     mark(ny == d.fny && levels == d.fnz && d.r > 1 ? "fft_y_fine" : "fft_y_coarse");
     k_fft_y<T><<<grid, 256, sm, st>>>(data, ny, pitch, ncol, pl, tw, sign, tx);
   }
+  // kx columns per CTA of a z solve over `rows` rows: the tuned (else 16)
+  // count, halved until the CTA's threads (two per column and segment, at most
+  // 512) and its shared memory fit; 0 if not even one column fits
+  int zsolve_cols(int rows, bool dual) const {
+    const int nseg = (rows + ZSEG - 1) / ZSEG;
+    for (int t = tune[PF_TUNE_ZSOLVE_COLS] > 0 ? tune[PF_TUNE_ZSOLVE_COLS] : 16; t >= 1; t >>= 1)
+      if (2 * t * nseg <= 512 && zsolve_seg_smem<TC>(rows, t, dual) <= (size_t)kMaxSmem) return t;
+    return 0;
+  }
+
   void zsolve(cpx<T>* data, int rows, int ny, int pitch, int ncol, const double* ex, const double* ey, int bc,
               double h2, double s1, double s2, bool two, double scale, bool poisson, double ds1 = 0.0,
               double ds2 = 0.0) {
@@ -594,18 +605,10 @@ struct Impl : ImplBase {
       PF_CUDA_TRY(cudaEventRecord(ev_z1, st3));
     }
     mark(two ? "zsolve_pair" : "zsolve");
-    const int txs = tune[PF_TUNE_ZSOLVE_COLS] > 0 ? tune[PF_TUNE_ZSOLVE_COLS] : 16;
+    const int txs = zsolve_cols(rows, two && !zs.same);
     const int nseg = (rows + ZSEG - 1) / ZSEG;
-    const size_t sms = zsolve_seg_smem<TC>(rows, txs, two && !zs.same);
-    if ((size_t)2 * txs * nseg <= 512 && sms <= (size_t)kMaxSmem) {
-      dim3 grid((ncol + txs - 1) / txs, ny);
-      k_zsolve_seg<T, TC><<<grid, 2 * txs * nseg, sms, st>>>(data, ex, ey, zs, txs);
-    } else {  // very long z lines: one sequential lane pair per column
-      const int tx = sizeof(T) == 4 ? 32 : 16;
-      const size_t sm = (size_t)rows * tx * (sizeof(cpx<T>) + sizeof(TC) * (zs.same ? 1 : 2));
-      dim3 grid((ncol + tx - 1) / tx, ny);
-      k_zsolve<T, TC><<<grid, 256, sm, st>>>(data, ex, ey, zs, tx);
-    }
+    dim3 grid((ncol + txs - 1) / txs, ny);
+    k_zsolve_seg<T, TC><<<grid, 2 * txs * nseg, zsolve_seg_smem<TC>(rows, txs, two && !zs.same), st>>>(data, ex, ey, zs, txs);
     if (zside) PF_CUDA_TRY(cudaStreamWaitEvent(st, ev_z1, 0));
     else if (poisson) zero_mode();
   }
@@ -964,9 +967,8 @@ struct Impl : ImplBase {
         throw ApiError(PF_ERR_ARG, "x-transform line pairs do not fit in shared memory");
       if (knob == PF_TUNE_YFFT_COLS && (!pow2(value) || value > 32 || 2 * (size_t)value * std::max(d.fny, d.ny) * sizeof(cpx<T>) > (size_t)kMaxSmem))
         throw ApiError(PF_ERR_ARG, "y-transform columns must be a power of two that fits in shared memory");
-      // two solver lanes per column: whole warps (the solve phase synchronises with __syncwarp)
-      if (knob == PF_TUNE_ZSOLVE_COLS && (value % 16 || value > 64 || (size_t)std::max(d.fnz, d.nz) * value * (sizeof(cpx<T>) + 2 * sizeof(TC)) > (size_t)kMaxSmem))
-        throw ApiError(PF_ERR_ARG, "z-solve columns must be a multiple of 16 that fits in shared memory");
+      if (knob == PF_TUNE_ZSOLVE_COLS && (value % 16 || value > 64))
+        throw ApiError(PF_ERR_ARG, "z-solve columns must be a multiple of 16, at most 64");
       if (knob == PF_TUNE_ROW_BLOCK && (value % 32 || value > 1024)) throw ApiError(PF_ERR_ARG, "row block must be a multiple of 32");
       if (knob == PF_TUNE_CH_ZCHUNK && value < 2) throw ApiError(PF_ERR_ARG, "z chunk must be at least 2 planes");
       if (knob == PF_TUNE_G_ZCHUNK && value < 1) throw ApiError(PF_ERR_ARG, "z chunk must be at least 1 layer");

@@ -211,8 +211,9 @@ __global__ void k_fft_y(cpx<T>* __restrict__ data, int ny, int pitch, int ncol, 
 }
 
 // ---------------------------------------------------------------------------
-// z solves.  TX must be a multiple of 16: the 2 TX solver lanes then form whole
-// warps, which the __syncwarp of the solve phase requires.
+// z solves of the batched sweep's persistent kernel.  TX must be a multiple of
+// 16: the 2 TX solver lanes then form whole warps, which the __syncwarp of the
+// solve phase requires.
 // One CTA: a tile of TX kx-columns x all z rows at one ky, staged
 // in shared memory with coalesced row loads; thread t < 2 TX then solves column
 // t/2, component t%2 (real and imaginary parts are independent real systems)
@@ -355,12 +356,6 @@ __device__ __forceinline__ void k_zsolve_b(cpx<T>* __restrict__ data, const doub
     const int colc = col0 + cc;
     if (cc < ncol && !(zs.skip_zero && colc == 0 && ky == 0)) gbase[(size_t)k * zstride + cc] = tile[e];
   }
-}
-
-template <class T, class TC>
-__global__ void k_zsolve(cpx<T>* __restrict__ data, const double* __restrict__ eigx, const double* __restrict__ eigy, ZSolve zs, int tx) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  k_zsolve_b<T, TC>(data, eigx, eigy, zs, tx, make_int3(blockIdx.x, blockIdx.y, blockIdx.z), smraw);
 }
 
 // The (kx, ky) = (0, 0) column of a pure Neumann Poisson problem is singular

@@ -285,3 +285,59 @@ def test_giesekus_fp64_and_mixed_vs_oracle(cfg, nx, nz, alpha_g):
     # the mobility changes the answer: Oldroyd-B (alpha = 0) gives another Theta
     ref0 = oracle(wl.scaled(wl.config(cfg), nx, nz).params)
     assert rel(ref0.theta, ref.theta) > 1e-4
+
+
+@pytest.mark.parametrize("visco", [True, False])
+def test_coalescing_drops_case_fp64(visco):
+    """The performance case of Section 4.5 (two tangent drops on a 180 deg wall,
+    Oh = 0.118, Cn = 0.015, density ratio 1/0.00119, Wi = 10, beta = 0.1) at
+    coarse 16^3 / fine 32^3 on its 6 x 6 x 6 box, FP64 against the oracle."""
+    w = wl.scaled(wl.config("e9", visco=visco), 16, 16)
+    g = w.grid
+    phi0 = wl.drops_phi(w)
+    vel = wl.random_velocity(g, 12, 0.05)
+    s = binding.Solver(g, w.params, binding.PF_FP64)
+    s.load_state(phi0, vel)
+    ref = ostep.State(g, w.params.as_dict(), phi0, vel0=vel)
+    for _ in range(3):
+        s.step(1)
+        ref.step()
+    assert rel(s.fine("phi"), ref.phi) < FP64_TOL
+    for name, a in (("u", ref.vel[0]), ("v", ref.vel[1]), ("w", ref.vel[2]), ("p", ref.p)):
+        assert rel(s.coarse(name), a) < FP64_TOL, name
+    if visco:
+        th = s.coarse("theta")
+        for q, (a, b) in enumerate([(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]):
+            assert rel(th[q], ref.theta[..., a, b]) < FP64_TOL, q
+
+
+@pytest.mark.parametrize("dim,nx,nz", [(2, 8, 400), (3, 4, 384)])
+def test_long_z_lines_vs_oracle(dim, nx, nz):
+    """z lines of 800 and 768 fine rows (400 and 384 coarse): more 16-row
+    segments than a 16-column CTA holds, so the solves run with the columns per
+    CTA halved (8 and 4).  FP64 at 1e-10, both mixed paths at the mixed
+    tolerances, against the oracle after 3 steps from a seeded velocity."""
+    g = grid(dim, nx, nz, 1, lx=2.0)
+    w = workload(g, ratio_rho=1000.0, ratio_mu=20.0, theta_deg=120.0, Wi=1.0, beta=0.3)
+    phi0 = wl.initial_phi(w)
+    vel = wl.random_velocity(g, 9, 0.1)
+    ref = ostep.State(g, w.params.as_dict(), phi0, vel0=vel)
+    for _ in range(3):
+        ref.step()
+    names = ["u", "w", "p"] + (["v"] if dim == 3 else [])
+    refs = {"u": ref.vel[0], "v": ref.vel[1] if dim == 3 else None, "w": ref.vel[2], "p": ref.p}
+    for prec in (binding.PF_FP64, binding.PF_MIXED, binding.PF_MIXED_Z64):
+        s = binding.Solver(g, w.params, prec)
+        s.load_state(phi0, vel)
+        s.step(3)
+        phi = s.fine("phi").astype(np.float64)
+        out = {n: s.coarse(n).astype(np.float64) for n in names}
+        s.close()
+        if prec == binding.PF_FP64:
+            assert rel(phi, ref.phi) < FP64_TOL
+            for n in names:
+                assert rel(out[n], refs[n]) < FP64_TOL, n
+        else:
+            assert np.max(np.abs(phi - ref.phi)) < 2e-4, prec
+            for n in ("u", "w"):
+                assert rel(out[n], refs[n]) < 1e-3, (prec, n)
