@@ -37,9 +37,28 @@ class Derived:
         self.S = S
         self.alpha = -S / (2.0 * self.eta ** 2) * (1.0 + math.sqrt(disc))
         self.c = self.alpha + S / self.eta ** 2
-        # polymer (approach 2 of Eq. NS12: constant polymer parameters, droplet only)
-        self.visco = p.get("wi", 0.0) > 0.0 and p.get("beta", 1.0) < 1.0
-        beta = p.get("beta", 1.0) if self.visco else 1.0
+        # polymer.  Approach 2 of Eq. NS12 (polymer_approach 0, the default): constant
+        # polymer parameters, the droplet phase viscoelastic, tau = (1 + phi)/2 tau_p.
+        # Approach 1 (polymer_approach 1): mu_p, lambda_H and alpha linear in phi
+        # (Eq. NS11) between the droplet's (mu_p1, wi, alpha_giesekus) and the
+        # ambient's (mu_p2, wi2, alpha_giesekus2); tau = tau_p.
+        self.approach1 = int(p.get("polymer_approach", 0)) == 1
+        if int(p.get("polymer_approach", 0)) not in (0, 1):
+            raise ValueError("polymer_approach must be 0 (Eq. NS12) or 1 (Eq. NS11)")
+        if self.approach1:
+            beta = p.get("beta", 1.0)
+            self.mu_p2 = p.get("mu_p2", 0.0)
+            self.visco = (beta < 1.0 and p["mu1"] > 0.0) or self.mu_p2 > 0.0
+            if self.visco and not (p.get("wi", 0.0) > 0.0 and p.get("wi2", 0.0) > 0.0):
+                raise ValueError("approach 1 needs both relaxation times wi, wi2 > 0")
+            ag2 = p.get("alpha_giesekus2", 0.0)
+            if not (0.0 <= ag2 < 1.0):
+                raise ValueError("the Giesekus mobility must lie in [0, 1)")
+            self.lam_h2 = p.get("wi2", 0.0)
+            self.alpha_g2 = ag2
+        else:
+            self.visco = p.get("wi", 0.0) > 0.0 and p.get("beta", 1.0) < 1.0
+            beta = p.get("beta", 1.0) if self.visco else 1.0
         self.mu_s1 = beta * p["mu1"]
         self.mu_p1 = (1.0 - beta) * p["mu1"]
         self.mu_s2 = p["mu2"]
@@ -65,3 +84,12 @@ class Derived:
     def mu(self, phi):
         """Eq. NS9 / dual3 (solvent viscosity)."""
         return 0.5 * (1.0 + phi) * self.mu_s1 + 0.5 * (1.0 - phi) * self.mu_s2
+
+    def polymer_props(self, phic):
+        """(mu_p, lambda_H, alpha) at coarse centres: Eq. NS11 in approach 1, the
+        droplet's constants in approach 2."""
+        if not self.approach1:
+            return self.mu_p1, self.lam_h, self.alpha_g
+        a, b = 0.5 * (1.0 + phic), 0.5 * (1.0 - phic)
+        return (a * self.mu_p1 + b * self.mu_p2, a * self.lam_h + b * self.lam_h2,
+                a * self.alpha_g + b * self.alpha_g2)

@@ -15,7 +15,9 @@ Section 2.2 (Eqs. NS17-NS24) and Section 3.2.3 (Eqs. NS40-NS46):
            diagonalise Theta1                                             NS43
            Theta^{n+1} = Theta^n/2 + (Theta1 + dt RH(Theta1; R1, Lambda1))/2 NS44
            diagonalise, tau_p^{n+1} = (mu_p/lambda_H)(R Lambda R^T - I)   NS45, NS46
-  tau = (1 + phi)/2 tau_p  (approach 2, Eq. NS12: the droplet phi = +1 is viscoelastic)
+  tau = (1 + phi)/2 tau_p  (approach 2, Eq. NS12: the droplet phi = +1 is viscoelastic);
+  approach 1 (Eq. NS11): mu_p, lambda_H and alpha are linear in phi at each
+  centre (the restricted phi^{n+1}) in both stages, and tau = tau_p.
 
 Readings: the printed sign of the relaxation term in Eqs. NS18/NS22/NS41 is
 reversed (as printed it would grow, not relax); the oracle relaxes.  For
@@ -108,11 +110,13 @@ def rh(T, L, adv, lam_h, alpha_g=0.0):
     Omega = R @ Om @ RT
     B = R @ Bt @ RT
     I = np.eye(n)
-    if alpha_g == 0.0:
+    lam_h = np.asarray(lam_h, dtype=np.float64)[..., None, None]
+    if np.ndim(alpha_g) == 0 and alpha_g == 0.0:
         relax = R @ (np.exp(-th)[..., :, None] * RT) - I
     else:
+        ag = np.asarray(alpha_g, dtype=np.float64)[..., None]
         em, ep = np.exp(-th), np.exp(th)
-        relax = R @ (((em - 1.0) - alpha_g * (ep - 1.0) * (1.0 - em))[..., :, None] * RT)
+        relax = R @ (((em - 1.0) - ag * (ep - 1.0) * (1.0 - em))[..., :, None] * RT)
     return -adv + (Omega @ T - T @ Omega) + 2.0 * B + relax / lam_h
 
 
@@ -120,13 +124,15 @@ def polymer_step(T, u, v, w, phic, d, grid):
     """RK2-TVD of Eqs. NS42-NS46.  Returns (Theta^{n+1}, weighted tau tensor)."""
     L = velocity_gradient(u, v, w, d, grid)
     dt = d.dt
-    ag = getattr(d, "alpha_g", 0.0)
-    T1 = T + dt * rh(T, L, advection(T, u, v, w, grid), d.lam_h, ag)
-    T2 = 0.5 * T + 0.5 * (T1 + dt * rh(T1, L, advection(T1, u, v, w, grid), d.lam_h, ag))
+    mu_p, lam_h, ag = d.polymer_props(phic)
+    T1 = T + dt * rh(T, L, advection(T, u, v, w, grid), lam_h, ag)
+    T2 = 0.5 * T + 0.5 * (T1 + dt * rh(T1, L, advection(T1, u, v, w, grid), lam_h, ag))
     th, R = decompose(T2)
     n = T.shape[-1]
     c = R @ (np.exp(th)[..., :, None] * np.swapaxes(R, -1, -2))
-    taup = d.mu_p1 / d.lam_h * (c - np.eye(n))
+    taup = np.asarray(mu_p / lam_h)[..., None, None] * (c - np.eye(n))
+    if d.approach1:
+        return T2, taup
     tau = 0.5 * (1.0 + phic)[..., None, None] * taup
     return T2, tau
 

@@ -108,6 +108,10 @@ class Params:
     gx: float = 0.0
     gy: float = 0.0
     gz: float = 0.0
+    mu_p2: float = 0.0            # approach 1: polymer viscosity of phase 2
+    wi2: float = 0.0              # approach 1: relaxation time of phase 2
+    alpha_giesekus2: float = 0.0  # approach 1: Giesekus mobility of phase 2
+    polymer_approach: int = 0     # 0: Eq. NS12 (droplet only), 1: Eq. NS11 (linear in phi)
 
     def as_dict(self):
         return asdict(self)

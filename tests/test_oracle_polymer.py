@@ -60,11 +60,13 @@ def test_zero_stress_rule_and_degenerate_limit(n):
         assert np.max(np.abs(a - b)) < 20 * eps
 
 
-def _startup(dim, dt, t_end, gam=1.3, lam_h=0.8, alpha_g=0.0):
+def _startup(dim, dt, t_end, gam=1.3, lam_h=0.8, alpha_g=0.0, phi=1.0, **extra):
     n = 8
     g = wl.Grid(4, 1 if dim == 2 else 4, n, 0.5, 0.125 if dim == 2 else 0.5, 1.0, 1)
     prm = wl.params_from_groups(Wi=lam_h, beta=0.4, dt=dt)
     prm.alpha_giesekus = alpha_g
+    for k, val in extra.items():
+        setattr(prm, k, val)
     prm.uw_bot, prm.uw_top = -gam * 0.5, gam * 0.5
     d = Derived(prm.as_dict())
     nz, ny, nx = g.coarse_shape
@@ -74,7 +76,7 @@ def _startup(dim, dt, t_end, gam=1.3, lam_h=0.8, alpha_g=0.0):
     w = np.zeros((nz + 1, ny, nx))
     m = 2 if dim == 2 else 3
     T = np.zeros((nz, ny, nx, m, m))
-    phic = np.ones((nz, ny, nx))
+    phic = np.full((nz, ny, nx), float(phi))
     steps = int(round(t_end / dt))
     for _ in range(steps):
         T, tau = polymer.polymer_step(T, u, v, w, phic, d, g)
@@ -146,3 +148,76 @@ def test_giesekus_shear_reaches_the_algebraic_steady_state(dim, alpha_g):
         assert np.max(np.abs(got[k] - want[k])) < 1e-8 * scale, (k, got[k].ravel()[:2], want[k])
     assert want["xz"] < mp * gam * (1 - 1e-3)   # shear thinning
     assert abs(want["zz"]) > 1e-3 * scale       # second normal stress difference
+
+
+# Approach 1 of Section 2.1 (Eq. NS11): mu_p, lambda_H and alpha linear in phi,
+# tau = tau_p unweighted.  Phase 2 gets its own polymer: mu_p2, wi2, alpha2.
+AP1 = dict(polymer_approach=1, mu_p2=0.05, wi2=0.3)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_approach1_startup_shear_uses_the_phase_averaged_parameters(dim):
+    """Uniform shear from rest at a constant phi = 0.4: the closed-form
+    Oldroyd-B start-up with lambda_H = 0.7 lambda_1 + 0.3 lambda_2 and
+    mu_p = 0.7 mu_p1 + 0.3 mu_p2 (Eq. NS11), and no (1 + phi)/2 weight.
+    Swapped phases (lambda_H 0.45, mu_p 0.3/0.7 mix) or the weight of Eq. NS12
+    (0.7) miss it by tens of per cent."""
+    gam, lam1, t, phi = 1.3, 0.8, 1.6, 0.4
+    a, b = 0.5 * (1 + phi), 0.5 * (1 - phi)
+    tau, d = _startup(dim, 0.005, t, gam, lam1, phi=phi, **AP1)
+    lam = a * lam1 + b * AP1["wi2"]
+    mp = a * d.mu_p1 + b * AP1["mu_p2"]
+    e = math.exp(-t / lam)
+    xz = mp * gam * (1 - e)
+    xx = 2 * mp * lam * gam ** 2 * (1 - (1 + t / lam) * e)
+    iz = 1 if dim == 2 else 2
+    assert np.max(np.abs(tau[..., 0, iz] - xz)) < 1e-4 * xz
+    assert np.max(np.abs(tau[..., 0, 0] - xx)) < 1e-4 * xx
+    assert np.max(np.abs(tau[..., iz, iz])) < 1e-4 * xx
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_approach1_giesekus_steady_shear_at_intermediate_phi(dim):
+    """The algebraic Giesekus steady state (independent fsolve) with the
+    interpolated alpha = 0.4 alpha_1 + 0.6 alpha_2 and lambda_H at phi = -0.2."""
+    gam, lam1, phi = 1.3, 0.8, -0.2
+    a, b = 0.5 * (1 + phi), 0.5 * (1 - phi)
+    extra = dict(AP1, alpha_giesekus2=0.1)
+    tau, d = _startup(dim, 0.02, 24.0, gam, lam1, 0.5, phi=phi, **extra)
+    lam = a * lam1 + b * extra["wi2"]
+    ag = a * 0.5 + b * 0.1
+    mp = a * d.mu_p1 + b * extra["mu_p2"]
+    cxx, cxz, czz = _giesekus_steady_shear(gam, lam, ag)
+    iz = 1 if dim == 2 else 2
+    want = {"xx": mp / lam * (cxx - 1), "xz": mp / lam * cxz, "zz": mp / lam * (czz - 1)}
+    got = {"xx": tau[..., 0, 0], "xz": tau[..., 0, iz], "zz": tau[..., iz, iz]}
+    for k in want:
+        assert np.max(np.abs(got[k] - want[k])) < 1e-8 * abs(want["xx"]), k
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_approach1_reduces_to_approach2_in_the_droplet_and_vanishes_in_a_newtonian_ambient(dim):
+    """phi = +1: both approaches give tau_p of the droplet's constants; phi = -1
+    with mu_p2 = 0: no stress at all, whatever the ambient's relaxation time."""
+    t1, _ = _startup(dim, 0.02, 0.4, phi=1.0, **AP1)
+    t2, _ = _startup(dim, 0.02, 0.4, phi=1.0)
+    assert np.allclose(t1, t2, rtol=0, atol=1e-14 * np.max(np.abs(t2)))
+    t3, _ = _startup(dim, 0.02, 0.4, phi=-1.0, **dict(AP1, mu_p2=0.0))
+    assert np.max(np.abs(t3)) == 0.0
+
+
+@pytest.mark.parametrize("plant", ["swap_phases", "weight"])
+def test_approach1_pin_catches_planted_mistakes(monkeypatch, plant):
+    """The start-up pin fails with the phases swapped in Eq. NS11, and with the
+    (1 + phi)/2 weight of Eq. NS12 applied in approach 1."""
+    from mutate import mutated
+    from oracle.params import Derived as D
+    if plant == "swap_phases":
+        bad = mutated(D, "polymer_props", "a, b = 0.5 * (1.0 + phic), 0.5 * (1.0 - phic)",
+                      "b, a = 0.5 * (1.0 + phic), 0.5 * (1.0 - phic)")
+        monkeypatch.setattr(D, "polymer_props", bad)
+    else:
+        bad = mutated(polymer, "polymer_step", "if d.approach1:", "if False:")
+        monkeypatch.setattr(polymer, "polymer_step", bad)
+    with pytest.raises(AssertionError):
+        test_approach1_startup_shear_uses_the_phase_averaged_parameters(2)
