@@ -67,21 +67,21 @@ def replica_value(cells, steps, world, elapsed):
 # sha256 of the source files that define the kernel when the counters were
 # taken: once a kernel changes its traffic reads null until it is measured again.
 TRAFFIC = {
-    "ch_rhs": (14.306, ["paper_2111_04577_gb300/csrc/ch_march.cuh", "paper_2111_04577_gb300/csrc/ch.cuh"], "cb5956e04c2e5ada"),
-    "ns_rhs": (16.766, ["paper_2111_04577_gb300/csrc/ns_rhs.cuh", "paper_2111_04577_gb300/csrc/ns.cuh"], "66032cbf66bfe48a"),
-    "polymer_stage2": (13.689, ["paper_2111_04577_gb300/csrc/polymer.cuh"], "a904305d60909ba6"),
-    "polymer_stage1": (7.056, ["paper_2111_04577_gb300/csrc/polymer.cuh"], "a904305d60909ba6"),
-    "fft_y_fine": (10.577, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "20a07416dcdf5429"),
-    "fft_y_coarse": (4.041, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "20a07416dcdf5429"),
-    "ch_G_restrict": (6.728, ["paper_2111_04577_gb300/csrc/ch_march.cuh", "paper_2111_04577_gb300/csrc/ch.cuh"], "cb5956e04c2e5ada"),
-    "ch_ifftx_finish": (14.034, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "20a07416dcdf5429"),
-    "zsolve_pair": (4.655, ["paper_2111_04577_gb300/csrc/zsolve_seg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh"], "a1a5065b5d451308"),
-    "zsolve": (2.031, ["paper_2111_04577_gb300/csrc/zsolve_seg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh"], "a1a5065b5d451308"),
-    "irfft_x_coarse": (2.018, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "20a07416dcdf5429"),
-    "rfft_x_fine": (4.994, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "20a07416dcdf5429"),
-    "rfft_x_coarse": (1.487, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "20a07416dcdf5429"),
-    "correct": (2.485, ["paper_2111_04577_gb300/csrc/ns.cuh"], "23a9f2ee44332b71"),
-    "div_rfft_x_coarse": (1.486, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "20a07416dcdf5429"),
+    "ch_rhs": (23.070, ["paper_2111_04577_gb300/csrc/ch_march.cuh", "paper_2111_04577_gb300/csrc/ch.cuh"], "3f15bc88c404391e"),
+    "ns_rhs": (17.566, ["paper_2111_04577_gb300/csrc/ns_rhs.cuh", "paper_2111_04577_gb300/csrc/ns.cuh"], "3eca06039157fe4b"),
+    "polymer_stage2": (13.312, ["paper_2111_04577_gb300/csrc/polymer.cuh"], "0121b0cd026e185a"),
+    "polymer_stage1": (7.033, ["paper_2111_04577_gb300/csrc/polymer.cuh"], "0121b0cd026e185a"),
+    "fft_y_fine": (10.566, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "5054e326fcfd8551"),
+    "fft_y_coarse": (4.041, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "5054e326fcfd8551"),
+    "ch_G_restrict": (6.726, ["paper_2111_04577_gb300/csrc/ch_march.cuh", "paper_2111_04577_gb300/csrc/ch.cuh"], "3f15bc88c404391e"),
+    "ch_ifftx_finish": (25.814, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "5054e326fcfd8551"),
+    "zsolve_pair": (4.646, ["paper_2111_04577_gb300/csrc/zsolve_seg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh"], "0948c8f74c76bf52"),
+    "zsolve": (2.031, ["paper_2111_04577_gb300/csrc/zsolve_seg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh"], "0948c8f74c76bf52"),
+    "irfft_x_coarse": (4.987, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "5054e326fcfd8551"),
+    "rfft_x_fine": (5.000, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "5054e326fcfd8551"),
+    "rfft_x_coarse": (1.486, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "5054e326fcfd8551"),
+    "correct": (2.485, ["paper_2111_04577_gb300/csrc/ns.cuh"], "68dabd490b962e39"),
+    "div_rfft_x_coarse": (1.486, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "5054e326fcfd8551"),
 }
 
 
@@ -218,14 +218,16 @@ def cpu_sample(w, steps, nx=64):
     phi0 = wl.initial_phi(ws)
     st = ostep.State(ws.grid, ws.params.as_dict(), phi0)
     st.step()  # warm caches / FFT plans
-    t0 = time.perf_counter()
+    t0, c0 = time.perf_counter(), time.process_time()
     for _ in range(steps):
         st.step()
-    dt = time.perf_counter() - t0
+    dt, cpu = time.perf_counter() - t0, time.process_time() - c0
     cells = ws.grid.fine_cells()
-    return {"value": cells * steps / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+    # cores actually used: the process's CPU time over the wall time of the sample
+    return {"value": cells * steps / dt, "unit": UNIT, "cores": round(cpu / dt, 1), "kind": "oracle",
             "sample": f"FP64 NumPy/SciPy oracle, same physics at coarse {nx}x{nx}x{nx // 2} / fine "
-                      f"{2 * nx}x{2 * nx}x{nx}, {steps} steps, {dt:.1f} s"}
+                      f"{2 * nx}x{2 * nx}x{nx}, {steps} steps, {dt:.1f} s wall, {cpu:.1f} s CPU "
+                      f"({os.cpu_count()} host cores)"}
 
 
 def run_reference(args):
@@ -241,10 +243,10 @@ def run_reference(args):
     st = ostep.State(ws.grid, ws.params.as_dict(), wl.initial_phi(ws))
     for _ in range(warm):
         st.step()
-    t0 = time.perf_counter()
+    t0, c0 = time.perf_counter(), time.process_time()
     for _ in range(steps):
         st.step()
-    dt = time.perf_counter() - t0
+    dt, cpu = time.perf_counter() - t0, time.process_time() - c0
     val = ws.grid.fine_cells() * steps / dt
     sample = (f"FP64 NumPy/SciPy oracle, workload physics at coarse {nx}x{nx}x{nx // 2} / fine "
               f"{2 * nx}x{2 * nx}x{nx}, one oracle time step per step")
@@ -252,7 +254,7 @@ def run_reference(args):
             "steps": steps, "warmup": warm, "ms_per_step": dt / steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name + f" (sampled at {nx}x{nx}x{nx // 2})", "precision": "fp64"},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": round(cpu / dt, 1), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -681,7 +683,7 @@ def main():
         extra["batch_sweep"] = batch_leg(stream)
         if w.params.wi > 0:
             extra["gradients"] = gradients_leg(w, stream)
-    cpu = cpu_sample(workload(args.config), 2, 64) if (rank == 0 and not args.no_cpu) else None
+    cpu = cpu_sample(workload(args.config), 12, 64) if (rank == 0 and not args.no_cpu) else None
 
     if rank == 0:
         line = {
