@@ -69,8 +69,8 @@ def replica_value(cells, steps, world, elapsed):
 TRAFFIC = {
     "ch_rhs": (23.070, ["paper_2111_04577_gb300/csrc/ch_march.cuh", "paper_2111_04577_gb300/csrc/ch.cuh"], "3f15bc88c404391e"),
     "ns_rhs": (17.566, ["paper_2111_04577_gb300/csrc/ns_rhs.cuh", "paper_2111_04577_gb300/csrc/ns.cuh"], "3eca06039157fe4b"),
-    "polymer_stage2": (13.312, ["paper_2111_04577_gb300/csrc/polymer.cuh"], "0121b0cd026e185a"),
-    "polymer_stage1": (7.033, ["paper_2111_04577_gb300/csrc/polymer.cuh"], "0121b0cd026e185a"),
+    "polymer_stage2": (13.620, ["paper_2111_04577_gb300/csrc/polymer.cuh"], "543640f3a9bccb20"),
+    "polymer_stage1": (7.153, ["paper_2111_04577_gb300/csrc/polymer.cuh"], "543640f3a9bccb20"),
     "fft_y_fine": (10.566, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "5054e326fcfd8551"),
     "fft_y_coarse": (4.041, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "5054e326fcfd8551"),
     "ch_G_restrict": (6.726, ["paper_2111_04577_gb300/csrc/ch_march.cuh", "paper_2111_04577_gb300/csrc/ch.cuh"], "3f15bc88c404391e"),

@@ -98,7 +98,12 @@ typedef struct {
 /* Physical parameters (Section 2.1; the droplet phase phi = +1 is fluid 1).
  * mu1, mu2: total viscosities; the droplet is viscoelastic when wi > 0 and
  * beta < 1, with solvent mu_s1 = beta mu1 and polymer mu_p1 = (1-beta) mu1
- * (Eq. NS12, second approach).  mobility: M of Eq. NS1.  sigma, eta: Eq. NS7.
+ * (Eq. NS12, second approach).  polymer_approach = 1 selects the first
+ * approach instead (Eq. NS11): mu_p, lambda_H and alpha are linear in phi
+ * between the droplet's (mu_p1, wi, alpha_giesekus) and phase 2's (mu_p2,
+ * wi2, alpha_giesekus2) at each coarse centre, tau = tau_p (no phase weight),
+ * phase 2's solvent viscosity stays mu2; it needs wi, wi2 > 0 when either
+ * phase has a polymer.  mobility: M of Eq. NS1.  sigma, eta: Eq. NS7.
  * theta_*_deg: equilibrium angles of Eq. NS16 at z = 0 and z = lz, measured
  * through phase 1.  dw: must be 0 (static contact angle).  alpha_giesekus:
  * the Giesekus mobility alpha of Eqs. NS18/NS22 in [0, 1), constant in the
@@ -112,6 +117,8 @@ typedef struct {
   double wi, beta, alpha_giesekus;
   double dt, S, nu_m;
   double uw_bot, uw_top, gx, gy, gz;
+  double mu_p2, wi2, alpha_giesekus2; /* phase 2's polymer (polymer_approach 1)      */
+  int polymer_approach;               /* 0: Eq. NS12 (default), 1: Eq. NS11            */
 } pf_params;
 
 /* Create a context for grid *g and allocate all fields on the current CUDA
@@ -126,8 +133,9 @@ int pf_init_grid(pf_ctx** out, const pf_grid_desc* g, void* stream);
  * lambda (Eq. NS7), S (Eq. NS30), alpha (Eq. NS29), c = alpha + S/eta^2,
  * rho0 and nu_m (text after Eq. NS39).  May be called again between steps.
  * Errors: PF_ERR_ARG (non-positive rho, sigma, eta, mobility, dt, an angle
- * outside [0, 180], or alpha_giesekus outside [0, 1)), PF_ERR_DISCRIMINANT (S
- * below Eq. NS30), PF_ERR_UNSUPPORTED (dw != 0). */
+ * outside [0, 180], alpha_giesekus or alpha_giesekus2 outside [0, 1),
+ * polymer_approach not 0 or 1, approach 1 without wi, wi2 > 0),
+ * PF_ERR_DISCRIMINANT (S below Eq. NS30), PF_ERR_UNSUPPORTED (dw != 0). */
 int pf_set_params(pf_ctx* ctx, const pf_params* prm);
 
 /* Number of elements and element size (bytes) of a field. */
@@ -268,7 +276,7 @@ int pf_adjoint(pf_ctx* ctx, int nsteps, int ckpt_every, int objective, double ou
  * right side, the polymer's right side and stress) are differentiated exactly
  * with dual numbers.  The context is left at step N.
  * Errors: PF_ERR_ARG, PF_ERR_UNSUPPORTED (a 3D context, PF_ADJ_COUPLED on a
- * derivative-carrying context), PF_ERR_CUDA, PF_ERR_NOMEM. */
+ * derivative-carrying context, polymer approach 1), PF_ERR_CUDA, PF_ERR_NOMEM. */
 enum { PF_ADJ_COUPLED = 1 };
 int pf_adjoint_ex(pf_ctx* ctx, int nsteps, int ckpt_every, int objective, int flags, double out[4], void* dphi0,
                   int dphi0_on_device);

@@ -63,6 +63,8 @@ struct Phys {
   double alpha_g;  // Giesekus mobility (0: Oldroyd-B)
   double uw_bot, uw_top, gx, gy, gz;
   int visco;
+  int approach1;                    // Eq. NS11: polymer parameters linear in phi, tau = tau_p
+  double mu_p2, lam_h2, alpha_g2;   // phase 2's polymer (approach 1)
 };
 
 // Scheme constants converted once to the arithmetic type of the kernels, so
@@ -79,6 +81,10 @@ struct PhysT {
   T dt, ilh, wtau;                    // dt, 1/lambda_H, mu_p/lambda_H
   T ag;                               // Giesekus mobility alpha (0: Oldroyd-B)
   Wide<T> cbot, ctop;                 // cos(theta_s) of the two walls (FP64, or carrying a derivative)
+  // approach 1 (Eq. NS11): lambda_H, mu_p and alpha of the two phases, mixed
+  // per coarse centre by the restricted phi; ilh, wtau and ag above unused
+  T lh1, lh2, mp1, mp2, ag2;
+  int ap1;
 };
 
 // Kernels over rows of a mesh use a 2D grid: blockIdx.x = row (y, z pair),

@@ -182,8 +182,26 @@ static Phys derive(const pf_params& q, const pf_grid_desc& g) {
   p.c = p.alpha + S / (q.eta * q.eta);
   p.cos_bot = std::cos(q.theta_bot_deg * M_PI / 180.0);
   p.cos_top = std::cos(q.theta_top_deg * M_PI / 180.0);
-  p.visco = (q.wi > 0 && q.beta < 1.0) ? 1 : 0;
-  const double beta = p.visco ? q.beta : 1.0;
+  if (q.polymer_approach != 0 && q.polymer_approach != 1)
+    throw ApiError(PF_ERR_ARG, "polymer_approach must be 0 (Eq. NS12) or 1 (Eq. NS11)");
+  p.approach1 = q.polymer_approach;
+  double beta;
+  if (p.approach1) {
+    if (!(q.beta > 0 && q.beta <= 1.0) || !(q.mu_p2 >= 0))
+      throw ApiError(PF_ERR_ARG, "approach 1 needs beta in (0, 1] and mu_p2 >= 0");
+    p.visco = ((q.beta < 1.0 && q.mu1 > 0) || q.mu_p2 > 0) ? 1 : 0;
+    if (p.visco && !(q.wi > 0 && q.wi2 > 0))
+      throw ApiError(PF_ERR_ARG, "approach 1 needs both relaxation times wi, wi2 > 0");
+    if (!(q.alpha_giesekus2 >= 0.0 && q.alpha_giesekus2 < 1.0))
+      throw ApiError(PF_ERR_ARG, "the Giesekus mobility must lie in [0, 1)");
+    beta = q.beta;
+    p.mu_p2 = q.mu_p2;
+    p.lam_h2 = q.wi2;
+    p.alpha_g2 = q.alpha_giesekus2;
+  } else {
+    p.visco = (q.wi > 0 && q.beta < 1.0) ? 1 : 0;
+    beta = p.visco ? q.beta : 1.0;
+  }
   p.rho1 = q.rho1;
   p.rho2 = q.rho2;
   p.rho0 = std::min(q.rho1, q.rho2);
@@ -825,6 +843,12 @@ struct Impl : ImplBase {
     r.ilh = p.visco ? (TT)(1.0 / p.lam_h) : (TT)0;
     r.wtau = p.visco ? (TT)(p.mu_p1 / p.lam_h) : (TT)0;
     r.ag = (TT)p.alpha_g;
+    r.ap1 = p.approach1;
+    r.lh1 = (TT)p.lam_h;
+    r.lh2 = (TT)p.lam_h2;
+    r.mp1 = (TT)p.mu_p1;
+    r.mp2 = (TT)p.mu_p2;
+    r.ag2 = (TT)p.alpha_g2;
     r.cbot = p.cos_bot;
     r.ctop = p.cos_top;
     return r;
@@ -1294,6 +1318,8 @@ struct Impl : ImplBase {
       flush_polymer();
       if (!have_params) throw ApiError(PF_ERR_ARG, "pf_set_params must precede pf_adjoint_ex");
       if (d.dim != 2) throw ApiError(PF_ERR_UNSUPPORTED, "the coupled reverse sweep is built for 2D meshes");
+      if (p.approach1)
+        throw ApiError(PF_ERR_UNSUPPORTED, "the coupled reverse sweep is built for polymer approach 2 (Eq. NS12)");
       if (nsteps < 1 || K < 1) throw ApiError(PF_ERR_ARG, "nsteps and ckpt_every must be >= 1");
       if (which != 0 && which != 1) throw ApiError(PF_ERR_ARG, "objective must be PF_OBJ_WETTED or PF_OBJ_CENTROID_Z");
       const int nseg = (nsteps + K - 1) / K;

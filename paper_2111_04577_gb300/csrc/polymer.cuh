@@ -16,7 +16,9 @@
 // RK2-TVD: Theta1 = Theta^n + dt RH(Theta^n) (Eq. NS42); Theta^{n+1} =
 // Theta^n/2 + (Theta1 + dt RH(Theta1))/2 (Eq. NS44); tau_p = (mu_p/lambda_H)
 // (R e^Lambda R^T - I) (Eq. NS46); the momentum equation receives
-// tau = (1 + phi)/2 tau_p (Eq. NS12, droplet phase viscoelastic).
+// tau = (1 + phi)/2 tau_p (Eq. NS12, droplet phase viscoelastic); in approach 1
+// (Eq. NS11) lambda_H, mu_p and alpha are linear in the restricted phi at each
+// centre and tau = tau_p.
 #pragma once
 #include <type_traits>
 
@@ -271,8 +273,30 @@ __device__ __forceinline__ void lcr_rhs_local(const T (&th0)[N == 2 ? 3 : 6], co
     }
 }
 
+// The polymer constants at a coarse centre with restricted phi `ph`: in
+// approach 1 (Eq. NS11) lambda_H, mu_p and alpha are linear in phi, and the
+// stress weight is 1; otherwise the droplet's constants, weight (1 + phi)/2
+// (Eq. NS12).  Returns the constants with ilh, ag and wtau set, and the
+// weight of tau_p in `wgt`.
+template <class T>
+__device__ __forceinline__ PhysT<T> poly_at(const PhysT<T>& q, T ph, T& wgt) {
+  PhysT<T> qc = q;
+  if (q.ap1) {
+    const T a = (T)0.5 * ((T)1 + ph), b = (T)0.5 * ((T)1 - ph);
+    const T lh = a * q.lh1 + b * q.lh2;
+    qc.ilh = (T)1 / lh;
+    qc.ag = a * q.ag + b * q.ag2;
+    qc.wtau = (a * q.mp1 + b * q.mp2) * qc.ilh;
+    wgt = qc.wtau;
+  } else {
+    wgt = (T)0.5 * ((T)1 + ph) * q.wtau;
+  }
+  return qc;
+}
+
 // tau = (1 + phi)/2 (mu_p/lambda_H) (W e^theta W^T - I) from Theta's unique
-// components (Eqs. NS12, NS46), with a decomposition of its own
+// components (Eqs. NS12, NS46; Eq. NS11 in approach 1), with a decomposition
+// of its own
 template <class T, int N>
 __device__ __forceinline__ void lcr_tau(const T (&th)[N == 2 ? 3 : 6], T phic, const PhysT<T>& q,
                                         T (&tau)[N == 2 ? 3 : 6]) {
@@ -289,7 +313,8 @@ __device__ __forceinline__ void lcr_tau(const T (&th)[N == 2 ? 3 : 6], T phic, c
   T ex[N];
 #pragma unroll
   for (int c = 0; c < N; ++c) ex[c] = fexp<T>(dg[c]);
-  const T wgt = (T)0.5 * ((T)1 + phic) * q.wtau;
+  T wgt;
+  (void)poly_at<T>(q, phic, wgt);
 #pragma unroll
   for (int a = 0; a < N; ++a)
 #pragma unroll
@@ -366,9 +391,12 @@ __device__ __forceinline__ void polymer_cell(const PolyIn<T>& P, const Dims& d, 
       th0[cq] = t0;
     }
   }
+  // polymer constants of this centre (Eq. NS11 in approach 1)
+  T wgt = (T)0;
+  const PhysT<T> qc = q.ap1 ? poly_at<T>(q, P.phic[id], wgt) : q;
   // local part of RH at the cell (eigen-decomposition of Theta, Eqs. NS21-NS24)
   T dg[N], of[N == 2 ? 1 : 3], R[N][N], rl[NC];
-  lcr_rhs_local<T, N>(th0, L, q, rl, R, dg);
+  lcr_rhs_local<T, N>(th0, L, qc, rl, R, dg);
   const T dt = q.dt;
   T newth[NC];
 #pragma unroll
@@ -435,7 +463,7 @@ __device__ __forceinline__ void polymer_cell(const PolyIn<T>& P, const Dims& d, 
     T ex[N];
 #pragma unroll
     for (int c = 0; c < N; ++c) ex[c] = fexp<T>(dg[c]);
-    const T wgt = (T)0.5 * ((T)1 + P.phic[id]) * q.wtau;
+    if (!q.ap1) wgt = (T)0.5 * ((T)1 + P.phic[id]) * q.wtau;
 #pragma unroll
     for (int a = 0; a < N; ++a)
 #pragma unroll

@@ -81,6 +81,7 @@ struct TangentRun {
       const double lh = I.p.lam_h;
       I.q.ilh = Dual(1.0 / lh, -1.0 / (lh * lh));
       I.q.wtau = Dual(I.p.mu_p1 / lh, -I.p.mu_p1 / (lh * lh));
+      I.q.lh1 = Dual(lh, 1.0);  // approach 1: the droplet's lambda_H, mixed per cell
     } else if (param == PF_PARAM_MOBILITY) {
       const double M = I.p.mob;
       double dc = 0, da = 0;

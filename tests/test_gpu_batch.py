@@ -1,7 +1,8 @@
 """The batched persistent sweep against the single-problem GPU path and the oracle.
 
 Uneven 2D problems (radix-2, 3, 5 and 7 sizes, different contact angles and
-Weissenberg numbers, Newtonian and Oldroyd-B) advanced together by one
+Weissenberg numbers, Newtonian, Oldroyd-B and one problem in polymer
+approach 1 with a Giesekus ambient) advanced together by one
 persistent launch per step must reproduce, problem by problem, the fields of
 the single-problem path (same device code: agreement to round-off) and the
 FP64 oracle (1e-10 relative).
@@ -23,6 +24,8 @@ def problems():
     for b, ((nx, nz), th, wi) in enumerate(zip(sizes, thetas, wis)):
         g = wl.Grid(nx, 1, nz, 4.0, 4.0 / nx, 2.0, 1)
         prm = wl.params_from_groups(theta_deg=th, Wi=wi, beta=0.5 if wi > 0 else 1.0, ratio_rho=10.0, ratio_mu=5.0)
+        if b == 3:  # polymer approach 1 (Eq. NS11): both phases viscoelastic, parameters linear in phi
+            prm.polymer_approach, prm.mu_p2, prm.wi2, prm.alpha_giesekus2 = 1, 0.01, 0.7, 0.2
         out.append(wl.Workload(f"b{b}", g, prm, 3, seed=b))
     return out
 

@@ -341,3 +341,68 @@ def test_long_z_lines_vs_oracle(dim, nx, nz):
             assert np.max(np.abs(phi - ref.phi)) < 2e-4, prec
             for n in ("u", "w"):
                 assert rel(out[n], refs[n]) < 1e-3, (prec, n)
+
+
+AP1 = dict(polymer_approach=1, mu_p2=0.02, wi2=0.4, alpha_giesekus2=0.1)
+
+
+@pytest.mark.parametrize("cfg,nx,nz", [("c2", 16, 8), ("c4", 12, 6)])
+def test_polymer_approach1_fp64_and_mixed_vs_oracle(cfg, nx, nz):
+    """Approach 1 of Section 2.1 (Eq. NS11): mu_p, lambda_H and alpha linear in
+    the restricted phi at every centre, both phases viscoelastic, tau = tau_p.
+    FP64 against the oracle at 1e-10, mixed at the viscoelastic tolerances,
+    after 6 steps from a seeded velocity and Theta; the answer differs from
+    approach 2 (Eq. NS12) on the same inputs."""
+    w = wl.scaled(wl.config(cfg), nx, nz)
+    w.params.alpha_giesekus = 0.2
+    for k, v in AP1.items():
+        setattr(w.params, k, v)
+    g = w.grid
+    phi0 = wl.initial_phi(w)
+    vel = wl.random_velocity(g, 14, 0.2)
+    nz_, ny_, nx_ = g.coarse_shape
+    m = 2 if g.dim == 2 else 3
+    a = 0.25 * np.random.default_rng(22).standard_normal((nz_, ny_, nx_, m, m))
+    theta0 = a + np.swapaxes(a, -1, -2)
+    idx = [(0, 0), (0, 1), (1, 1)] if g.dim == 2 else [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    theta_comp = np.stack([theta0[..., i, j] for i, j in idx])
+    n = 6
+
+    def oracle(params):
+        ref = ostep.State(g, params.as_dict(), phi0, vel0=vel, theta0=theta0)
+        for _ in range(n):
+            ref.step()
+        return ref
+
+    ref = oracle(w.params)
+    for prec in (binding.PF_FP64, binding.PF_MIXED):
+        s = binding.Solver(g, w.params, prec)
+        s.load_state(phi0, vel)
+        s.set("theta", theta_comp)
+        s.step(n)
+        th = s.coarse("theta")
+        if prec == binding.PF_FP64:
+            assert rel(s.fine("phi"), ref.phi) < FP64_TOL
+            for name, r in (("u", ref.vel[0]), ("w", ref.vel[2]), ("p", ref.p)):
+                assert rel(s.coarse(name), r) < FP64_TOL, name
+            for q, (i, j) in enumerate(idx):
+                assert rel(th[q], ref.theta[..., i, j]) < FP64_TOL, q
+        else:
+            assert np.max(np.abs(s.fine("phi") - ref.phi)) < 2e-4
+            assert rel(s.coarse("u"), ref.vel[0]) < 1e-3
+            scale = max(np.max(np.abs(ref.theta)), 1e-300)
+            for q, (i, j) in enumerate(idx):
+                assert np.max(np.abs(th[q] - ref.theta[..., i, j])) < 1e-3 * scale, q
+        s.close()
+    p2 = wl.Params(**{**w.params.as_dict(), "polymer_approach": 0})
+    assert rel(oracle(p2).vel[0], ref.vel[0]) > 1e-6
+
+
+def test_polymer_approach1_argument_errors():
+    w = wl.scaled(wl.config("c2"), 16, 8)
+    for over in (dict(polymer_approach=2), dict(polymer_approach=1, wi2=0.0, mu_p2=0.1),
+                 dict(polymer_approach=1, wi2=0.5, alpha_giesekus2=1.0)):
+        prm = wl.Params(**{**w.params.as_dict(), **over})
+        with pytest.raises(binding.PFError) as e:
+            binding.Solver(w.grid, prm, binding.PF_FP64)
+        assert e.value.code == -1, over

@@ -186,3 +186,19 @@ def test_mobility_tangent_equals_adjoint_velocity_fixed():
         _, dm_t = s.tangent(n, binding.PF_PARAM_MOBILITY, obj, binding.PF_STEP_CH_ONLY)
         _, _, dm_a, _ = s.adjoint(n, 2, obj, want_phi=False)
         assert abs(dm_t - dm_a) <= 1e-6 * abs(dm_a), (dm_t, dm_a)
+
+
+def test_wi_sensitivity_in_polymer_approach1():
+    """Eq. NS11 (approach 1): d/dWi moves the droplet's relaxation time, which
+    the polymer update mixes with phase 2's at every centre; against central
+    differences of the oracle."""
+    w, vel, n = case(2)
+    w.params.polymer_approach = 1
+    w.params.mu_p2 = 0.02
+    w.params.wi2 = 0.4
+    J, dJ = tangents(w, vel, n, binding.PF_PARAM_WI)
+    wi = w.params.wi
+    h = 1e-3 * wi
+    fd = (oracle_J(w, vel, n, wi=wi + h) - oracle_J(w, vel, n, wi=wi - h)) / (2 * h)
+    assert close(J, oracle_J(w, vel, n), 1e-10)
+    assert close(dJ, fd, 1e-3), (dJ, fd)
