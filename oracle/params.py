@@ -65,9 +65,12 @@ class Derived:
         self.lam_h = p.get("wi", 0.0)
         self.alpha_g = ag  # Giesekus mobility (Eqs. NS18, NS22); 0 is Oldroyd-B
         # convective flux of the CH step: "central" (the GPU path's) or "weno5z" (the paper's)
-        self.advection = p.get("advection", "central")
+        # convective flux of phi (CH) and Theta (LCR): "central" (0, the default) or
+        # "weno5z" (1, the paper's scheme, Section 3.2.1 and before Eq. NS40)
+        adv = p.get("advection", "central")
+        self.advection = {0: "central", 1: "weno5z"}.get(adv, adv)
         if self.advection not in ("central", "weno5z"):
-            raise ValueError("advection must be 'central' or 'weno5z'")
+            raise ValueError("advection must be 'central' (0) or 'weno5z' (1)")
         self.rho1, self.rho2 = p["rho1"], p["rho2"]
         self.rho0 = min(self.rho1, self.rho2)
         self.nu_m = p.get("nu_m", 0.0) or 0.5 * max(self.mu_s1, self.mu_s2) / self.rho0

@@ -27,7 +27,9 @@ the commutator term; with tau_p = 0 this is Omega = 0, B = sym(grad u^T), as the
 paper states).  The convective term is the central conservative flux with zero
 flux through the walls (w = 0 there).  The velocity gradient at the centre uses
 face differences along the face normal and, across, central differences of the
-centre-averaged velocity (no-slip ghosts 2 u_w - u at the walls).
+centre-averaged velocity (no-slip ghosts 2 u_w - u at the walls).  With the
+paper's WENO5-Z option (advection "weno5z") the convective term takes the
+WENO5-Z face values of oracle.weno per component instead of the central flux.
 (grad u)^T has entries L[a, b] = d u_a / d x_b.
 """
 import numpy as np
@@ -65,8 +67,25 @@ def velocity_gradient(u, v, w, d, grid):
     return L
 
 
-def advection(T, u, v, w, grid):
+def advection_weno(T, u, v, w, grid):
+    """div(u Theta) per component with the WENO5-Z face values of oracle.weno
+    (the paper's scheme for the convective term, before Eq. NS40): u, v, w are
+    the coarse face velocities (left x face and y face of each cell, z faces
+    with both walls), the same arrays the central flux takes."""
+    from . import weno
+    out = np.empty_like(T)
+    n = T.shape[-1]
+    for a in range(n):
+        for b in range(a, n):
+            out[..., a, b] = weno.advection(T[..., a, b], u, v if grid.dim == 3 else None, w, grid.dx, grid.dim)
+            out[..., b, a] = out[..., a, b]
+    return out
+
+
+def advection(T, u, v, w, grid, scheme="central"):
     """div(u Theta) per component; T has shape (nz, ny, nx, n, n)."""
+    if scheme == "weno5z":
+        return advection_weno(T, u, v, w, grid)
     D = grid.dx
     ex = (Ellipsis, None, None)
     Fx = u[ex] * 0.5 * (np.roll(T, 1, axis=2) + T)
@@ -125,8 +144,9 @@ def polymer_step(T, u, v, w, phic, d, grid):
     L = velocity_gradient(u, v, w, d, grid)
     dt = d.dt
     mu_p, lam_h, ag = d.polymer_props(phic)
-    T1 = T + dt * rh(T, L, advection(T, u, v, w, grid), lam_h, ag)
-    T2 = 0.5 * T + 0.5 * (T1 + dt * rh(T1, L, advection(T1, u, v, w, grid), lam_h, ag))
+    sch = getattr(d, "advection", "central")
+    T1 = T + dt * rh(T, L, advection(T, u, v, w, grid, sch), lam_h, ag)
+    T2 = 0.5 * T + 0.5 * (T1 + dt * rh(T1, L, advection(T1, u, v, w, grid, sch), lam_h, ag))
     th, R = decompose(T2)
     n = T.shape[-1]
     c = R @ (np.exp(th)[..., :, None] * np.swapaxes(R, -1, -2))

@@ -2,6 +2,7 @@
 smooth data, exact conservation, near-boundedness at a step, and the mirror
 symmetry between the two upwind directions."""
 import numpy as np
+import pytest
 
 from oracle import weno
 
@@ -89,3 +90,79 @@ def test_ch_step_with_weno_conserves_mass_and_stays_close_to_central():
         out[adv] = st.phi
     d = np.max(np.abs(out["weno5z"] - out["central"]))
     assert 0 < d < 1e-2
+
+
+def _theta_case(n, axis):
+    """One Theta component varying along x (periodic) or z (walls), with a
+    non-uniform face velocity along that axis; the exact d(u Theta)/dx_axis at
+    the centres.  3D coarse grid n cells along the axis, 4 across."""
+    from paper_2111_04577_gb300 import workloads as wl
+    L = 1.0
+    h = L / n
+    if axis == "x":
+        g = wl.Grid(n, 4, 4, L, 4 * h, 4 * h, 1)
+        xc = (np.arange(n) + 0.5) * h
+        xf = np.arange(n) * h  # left faces
+        th = np.sin(2 * np.pi * xc)
+        T = np.zeros((4, 4, n, 3, 3))
+        T[..., 0, 1] = T[..., 1, 0] = th[None, None, :]
+        u = np.broadcast_to(1.0 + 0.5 * np.cos(2 * np.pi * xf), (4, 4, n)).copy()
+        v = np.zeros((4, 4, n))
+        w = np.zeros((5, 4, n))
+        exact = (-np.pi * np.sin(2 * np.pi * xc) * np.sin(2 * np.pi * xc)
+                 + 2 * np.pi * np.cos(2 * np.pi * xc) * (1.0 + 0.5 * np.cos(2 * np.pi * xc)))
+        return g, T, u, v, w, exact[None, None, :], (0, 1)
+    g = wl.Grid(4, 4, n, 4 * h, 4 * h, L, 1)
+    zc = (np.arange(n) + 0.5) * h
+    zf = np.arange(n + 1) * h
+    s = 0.08
+    th = np.exp(-((zc - 0.5) / s) ** 2)
+    T = np.zeros((n, 4, 4, 3, 3))
+    T[..., 2, 2] = th[:, None, None]
+    u = np.zeros((n, 4, 4))
+    v = np.zeros((n, 4, 4))
+    w = np.broadcast_to(np.sin(np.pi * zf)[:, None, None], (n + 1, 4, 4)).copy()
+    wc, dwc = np.sin(np.pi * zc), np.pi * np.cos(np.pi * zc)
+    dth = -2 * (zc - 0.5) / s ** 2 * th
+    exact = dwc * th + wc * dth
+    return g, T, u, v, w, exact[:, None, None], (2, 2)
+
+
+@pytest.mark.parametrize("axis", ["x", "z"])
+def test_theta_weno_advection_converges_to_the_divergence(axis):
+    """The polymer's WENO5-Z convective term, per component with the coarse
+    face velocities: with a non-uniform face velocity it converges to the
+    exact d(u Theta)/dx at (at least) second order along x (periodic) and z
+    (walls, mirror ghosts); a face velocity taken one face off converges at
+    first order only (see the planted-mistake test)."""
+    from oracle import polymer
+    errs = []
+    for n in (32, 64, 128):
+        g, T, u, v, w, exact, (a, b) = _theta_case(n, axis)
+        A = polymer.advection(T, u, v, w, g, "weno5z")
+        errs.append(np.max(np.abs(A[..., a, b] - exact)))
+    r = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(r > 1.8), (errs, r)
+
+
+def test_theta_weno_advection_of_a_uniform_state_is_zero():
+    """A uniform Theta under a discretely divergence-free velocity (uniform
+    along x, zero w) is not advected: every face value is the constant."""
+    from oracle import polymer
+    from paper_2111_04577_gb300 import workloads as wl
+    g = wl.Grid(8, 8, 8, 1.0, 1.0, 1.0, 1)
+    T = np.broadcast_to(np.array([[0.3, 0.1, -0.2], [0.1, 0.5, 0.05], [-0.2, 0.05, -0.4]]), (8, 8, 8, 3, 3)).copy()
+    u = np.full((8, 8, 8), 0.7)
+    v = np.full((8, 8, 8), -0.3)
+    w = np.zeros((9, 8, 8))
+    assert np.max(np.abs(polymer.advection(T, u, v, w, g, "weno5z"))) < 1e-13
+
+
+def test_theta_weno_pin_catches_a_shifted_face_velocity(monkeypatch):
+    from mutate import mutated
+    from oracle import polymer
+    bad = mutated(polymer, "advection_weno", "weno.advection(T[..., a, b], u,",
+                  "weno.advection(T[..., a, b], np.roll(u, 1, axis=2),")
+    monkeypatch.setattr(polymer, "advection_weno", bad)
+    with pytest.raises(AssertionError):
+        test_theta_weno_advection_converges_to_the_divergence("x")
