@@ -103,7 +103,11 @@ typedef struct {
  * between the droplet's (mu_p1, wi, alpha_giesekus) and phase 2's (mu_p2,
  * wi2, alpha_giesekus2) at each coarse centre, tau = tau_p (no phase weight),
  * phase 2's solvent viscosity stays mu2; it needs wi, wi2 > 0 when either
- * phase has a polymer.  mobility: M of Eq. NS1.  sigma, eta: Eq. NS7.
+ * phase has a polymer.  advection = 1 takes the paper's WENO5-Z face values
+ * (Section 3.2.1; before Eq. NS40) for div(u phi) of the CH step and div(u Theta)
+ * of the polymer update instead of the central flux; it needs at least 4
+ * coarse cells along every axis, and the batch and the reverse sweeps reject
+ * it.  mobility: M of Eq. NS1.  sigma, eta: Eq. NS7.
  * theta_*_deg: equilibrium angles of Eq. NS16 at z = 0 and z = lz, measured
  * through phase 1.  dw: must be 0 (static contact angle).  alpha_giesekus:
  * the Giesekus mobility alpha of Eqs. NS18/NS22 in [0, 1), constant in the
@@ -119,6 +123,7 @@ typedef struct {
   double uw_bot, uw_top, gx, gy, gz;
   double mu_p2, wi2, alpha_giesekus2; /* phase 2's polymer (polymer_approach 1)      */
   int polymer_approach;               /* 0: Eq. NS12 (default), 1: Eq. NS11            */
+  int advection;                      /* 0: central second order (default), 1: WENO5-Z */
 } pf_params;
 
 /* Create a context for grid *g and allocate all fields on the current CUDA
@@ -134,7 +139,8 @@ int pf_init_grid(pf_ctx** out, const pf_grid_desc* g, void* stream);
  * rho0 and nu_m (text after Eq. NS39).  May be called again between steps.
  * Errors: PF_ERR_ARG (non-positive rho, sigma, eta, mobility, dt, an angle
  * outside [0, 180], alpha_giesekus or alpha_giesekus2 outside [0, 1),
- * polymer_approach not 0 or 1, approach 1 without wi, wi2 > 0),
+ * polymer_approach or advection not 0 or 1, approach 1 without wi, wi2 > 0,
+ * WENO5-Z on fewer than 4 coarse cells along an axis),
  * PF_ERR_DISCRIMINANT (S below Eq. NS30), PF_ERR_UNSUPPORTED (dw != 0). */
 int pf_set_params(pf_ctx* ctx, const pf_params* prm);
 
@@ -192,7 +198,8 @@ int pf_profile(pf_ctx* ctx, int nsteps, int flags, int max_entries, char* names,
  * makes pf_batch_step return PF_ERR_TIMEOUT (the status is sticky).
  * Field access and diagnostics take a problem index 0..nproblems-1 and
  * behave as pf_set_fields / pf_get_fields / pf_diagnostics on that problem.
- * Precision PF_FP64 or PF_MIXED (PF_MIXED_Z64: PF_ERR_UNSUPPORTED).
+ * Precision PF_FP64 or PF_MIXED (PF_MIXED_Z64: PF_ERR_UNSUPPORTED); the
+ * central advection flux only (advection = 1: PF_ERR_UNSUPPORTED).
  * ------------------------------------------------------------------------ */
 typedef struct pf_batch pf_batch;
 int pf_batch_create(pf_batch** out, int nproblems, const pf_grid_desc* grids, const pf_params* params,
@@ -251,7 +258,8 @@ int pf_diagnostics_noalloc(const pf_grid_desc* g, const pf_params* prm, const vo
  * each segment, then runs the transposed kernels and the same (symmetric)
  * transform solves.  The context is left at phi^N.  The mobility derivative
  * follows S when S = 0 selects the bound of Eq. NS30.
- * Errors: PF_ERR_ARG, PF_ERR_DISCRIMINANT, PF_ERR_CUDA, PF_ERR_NOMEM. */
+ * Errors: PF_ERR_ARG, PF_ERR_DISCRIMINANT, PF_ERR_UNSUPPORTED (WENO5-Z
+ * advection), PF_ERR_CUDA, PF_ERR_NOMEM. */
 enum { PF_OBJ_WETTED = 0, PF_OBJ_CENTROID_Z = 1 };
 int pf_adjoint(pf_ctx* ctx, int nsteps, int ckpt_every, int objective, double out[3], void* dphi0,
                int dphi0_on_device);
@@ -276,7 +284,8 @@ int pf_adjoint(pf_ctx* ctx, int nsteps, int ckpt_every, int objective, double ou
  * right side, the polymer's right side and stress) are differentiated exactly
  * with dual numbers.  The context is left at step N.
  * Errors: PF_ERR_ARG, PF_ERR_UNSUPPORTED (a 3D context, PF_ADJ_COUPLED on a
- * derivative-carrying context, polymer approach 1), PF_ERR_CUDA, PF_ERR_NOMEM. */
+ * derivative-carrying context, polymer approach 1, WENO5-Z advection),
+ * PF_ERR_CUDA, PF_ERR_NOMEM. */
 enum { PF_ADJ_COUPLED = 1 };
 int pf_adjoint_ex(pf_ctx* ctx, int nsteps, int ckpt_every, int objective, int flags, double out[4], void* dphi0,
                   int dphi0_on_device);

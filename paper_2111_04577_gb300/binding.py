@@ -44,7 +44,7 @@ class ParamsC(C.Structure):
     _fields_ = [(n, C.c_double) for n in
                 ("rho1", "rho2", "mu1", "mu2", "sigma", "eta", "mobility", "theta_bot_deg", "theta_top_deg",
                  "dw", "wi", "beta", "alpha_giesekus", "dt", "S", "nu_m", "uw_bot", "uw_top", "gx", "gy", "gz",
-                 "mu_p2", "wi2", "alpha_giesekus2")] + [("polymer_approach", C.c_int)]
+                 "mu_p2", "wi2", "alpha_giesekus2")] + [("polymer_approach", C.c_int), ("advection", C.c_int)]
 
 
 class PFError(RuntimeError):

@@ -32,6 +32,9 @@ struct FineView {
   // needs them; phi* and every stencil take the stored values.
   const T* ln = nullptr;
   const T* lo = nullptr;
+  // div(u* phi*) precomputed with the WENO5-Z fluxes (csrc/weno.cuh), or null
+  // for the central second-order flux formed in the right-side kernels
+  const T* aw = nullptr;
   __device__ __forceinline__ T star(size_t i) const { return (T)2 * pn[i] - po[i]; }
   // phi^{n-1} - phi^n at i, given the stored values a = phi^n[i], b = phi^{n-1}[i]
   __device__ __forceinline__ T back(size_t i, T a, T b) const {

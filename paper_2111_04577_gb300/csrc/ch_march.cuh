@@ -256,6 +256,8 @@ __global__ void __launch_bounds__(MarchTile::NT, MINB) k_ch_rhs_march(const Fine
       if (z + 1 < fnz) adv += w1 * (c0 + pq[so]);
       if (z > 0) adv -= w0 * (pm[so] + c0);
       adv *= (T)0.5 * q.ih;
+      const size_t o = (size_t)z * plane + (size_t)gy * fnx + gx;
+      if (f.aw) adv = f.aw[o];
       const int mo = (ty + 1) * TL::MX + (tx + 1);
       const T m0 = mmc[mo];
       T lap = mmc[mo + 1] + mmc[mo - 1] - 2 * m0;
@@ -263,7 +265,6 @@ __global__ void __launch_bounds__(MarchTile::NT, MINB) k_ch_rhs_march(const Fine
       const T mzp = z + 1 < fnz ? mmp[mo] : m0;
       const T mzm = z > 0 ? mmm[mo] : m0;
       lap = (lap + mzp + mzm - 2 * m0) * q.ih2;
-      const size_t o = (size_t)z * plane + (size_t)gy * fnx + gx;
       R[o] = dd[ty * TL::TX + tx] * inv_mldt - adv * inv_ml + lap;
     }
   }
@@ -784,6 +785,11 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
     // phi^{n-1} - phi^n: the stored values' difference first (exact when they are
     // close), then the remainders' (zero without compensated storage)
     const float dv[4] = {(bo.x - an.x) + dl.x, (bo.y - an.y) + dl.y, (bo.z - an.z) + dl.z, (bo.w - an.w) + dl.w};
+    float awv[4] = {0.f, 0.f, 0.f, 0.f};
+    if (f.aw && act) {
+      const float4 a = *reinterpret_cast<const float4*>(f.aw + (size_t)z * plane + gof);
+      awv[0] = a.x, awv[1] = a.y, awv[2] = a.z, awv[3] = a.w;
+    }
     float out[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -793,6 +799,7 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
       if (z + 1 < fnz) adv += whi[i] * (c0 + zpp[i]);
       if (z > 0) adv -= wlo[i] * (zmp[i] + c0);
       adv *= 0.5f * q.ih;
+      if (f.aw) adv = awv[i];
       const float m0 = mv[i + 1];
       float lap = mv[i + 2] + mv[i] - 2 * m0;
       lap += muv[i] + mdv[i] - 2 * m0;

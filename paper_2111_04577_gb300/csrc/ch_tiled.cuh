@@ -163,6 +163,8 @@ __device__ __forceinline__ void k_ch_rhs_b(const FineView<T> f, const CoarseVel<
     if (gz + 1 < fnz) adv += wface(gx, gy, gz + 1) * (c0 + P(sz + 1, sy, sx));
     if (gz > 0) adv -= wface(gx, gy, gz) * (P(sz - 1, sy, sx) + c0);
     adv *= (T)0.5 * q.ih;
+    const size_t o = (size_t)gz * plane + (size_t)gy * fnx + gx;
+    if (f.aw) adv = f.aw[o];
     const int mx = tx + 1, my = ty + (DIM == 3 ? 1 : 0), mz = tz + 1;
     const T m0 = M(mz, my, mx);
     T lap = M(mz, my, mx + 1) + M(mz, my, mx - 1) - 2 * m0;
@@ -170,7 +172,6 @@ __device__ __forceinline__ void k_ch_rhs_b(const FineView<T> f, const CoarseVel<
     const T mzp = gz + 1 < fnz ? M(mz + 1, my, mx) : m0;
     const T mzm = gz > 0 ? M(mz - 1, my, mx) : m0;
     lap = (lap + mzp + mzm - 2 * m0) * q.ih2;
-    const size_t o = (size_t)gz * plane + (size_t)gy * fnx + gx;
     R[o] = f.back(o, f.pn[o], f.po[o]) * inv_mldt - adv * inv_ml + lap;
   }
 }

@@ -65,6 +65,7 @@ struct Phys {
   int visco;
   int approach1;                    // Eq. NS11: polymer parameters linear in phi, tau = tau_p
   double mu_p2, lam_h2, alpha_g2;   // phase 2's polymer (approach 1)
+  int weno;                         // WENO5-Z convective fluxes for phi and Theta (else central)
 };
 
 // Scheme constants converted once to the arithmetic type of the kernels, so
@@ -85,6 +86,7 @@ struct PhysT {
   // per coarse centre by the restricted phi; ilh, wtau and ag above unused
   T lh1, lh2, mp1, mp2, ag2;
   int ap1;
+  int weno;  // WENO5-Z advection of phi and Theta (csrc/weno.cuh), else central
 };
 
 // Kernels over rows of a mesh use a 2D grid: blockIdx.x = row (y, z pair),

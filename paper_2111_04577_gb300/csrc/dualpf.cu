@@ -156,7 +156,6 @@ struct ImplBase {
 };
 
 static Phys derive(const pf_params& q, const pf_grid_desc& g) {
-  (void)g;
   if (!(q.rho1 > 0 && q.rho2 > 0 && q.sigma > 0 && q.eta > 0 && q.mobility > 0 && q.dt > 0 && q.mu1 >= 0 &&
         q.mu2 >= 0))
     throw ApiError(PF_ERR_ARG, "rho1, rho2, sigma, eta, mobility, dt must be > 0 and mu1, mu2 >= 0");
@@ -182,9 +181,14 @@ static Phys derive(const pf_params& q, const pf_grid_desc& g) {
   p.c = p.alpha + S / (q.eta * q.eta);
   p.cos_bot = std::cos(q.theta_bot_deg * M_PI / 180.0);
   p.cos_top = std::cos(q.theta_top_deg * M_PI / 180.0);
+  if (q.advection != 0 && q.advection != 1)
+    throw ApiError(PF_ERR_ARG, "advection must be 0 (central) or 1 (WENO5-Z)");
+  if (q.advection == 1 && (g.nx < 4 || g.nz < 4 || (g.ny > 1 && g.ny < 4)))
+    throw ApiError(PF_ERR_ARG, "WENO5-Z advection needs at least 4 coarse cells along every axis");
   if (q.polymer_approach != 0 && q.polymer_approach != 1)
     throw ApiError(PF_ERR_ARG, "polymer_approach must be 0 (Eq. NS12) or 1 (Eq. NS11)");
   p.approach1 = q.polymer_approach;
+  p.weno = q.advection;
   double beta;
   if (p.approach1) {
     if (!(q.beta > 0 && q.beta <= 1.0) || !(q.mu_p2 >= 0))
@@ -664,6 +668,12 @@ struct Impl : ImplBase {
     // ---- Cahn-Hilliard on the fine mesh ----
     FineView<T> fv{phi[pc], phi[po], philo[pc], philo[po]};
     const CoarseVel<T> vel{u[fc], u[fo], v[fc], v[fo], w[fc], w[fo]};
+    if (p.weno) {  // div(u* phi*) with WENO5-Z fluxes, read by the right side
+      mark("weno_adv");
+      const RowLaunch lw = rows(d.fny * d.fnz, d.fnx);
+      k_weno_adv_fine<T><<<lw.grid, lw.block, 0, st>>>(fv, vel, wadv, d, q);
+      fv.aw = wadv;
+    }
     T inv_mldt = (T)(1.0 / (p.Ml * p.dt)), inv_ml = (T)(1.0 / p.Ml);
     if constexpr (IsDual<T>::value) {
       inv_mldt.d = dseed.inv_mldt;
@@ -844,6 +854,7 @@ struct Impl : ImplBase {
     r.wtau = p.visco ? (TT)(p.mu_p1 / p.lam_h) : (TT)0;
     r.ag = (TT)p.alpha_g;
     r.ap1 = p.approach1;
+    r.weno = p.weno;
     r.lh1 = (TT)p.lam_h;
     r.lh2 = (TT)p.lam_h2;
     r.mp1 = (TT)p.mu_p1;
@@ -862,7 +873,13 @@ struct Impl : ImplBase {
     have_params = true;
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
     graphs.clear();
+    if (p.weno && !wadv) {  // the WENO5-Z advection of phi*: one fine array, made on first use
+      weno_ar.reset(new Arena());
+      wadv = weno_ar->get<T>((size_t)d.fnx * d.fny * d.fnz);
+    }
   }
+  std::unique_ptr<Arena> weno_ar;
+  T* wadv = nullptr;
 
   void field_info(int f, size_t* count, size_t* eb) const override {
     const size_t nf = (size_t)d.fnx * d.fny * d.fnz;
@@ -1144,6 +1161,7 @@ struct Impl : ImplBase {
     } else {
       flush_polymer();
       if (!have_params) throw ApiError(PF_ERR_ARG, "pf_set_params must precede pf_adjoint");
+      if (p.weno) throw ApiError(PF_ERR_UNSUPPORTED, "the reverse sweep transposes the central advection flux");
       if (nsteps < 1 || K < 1) throw ApiError(PF_ERR_ARG, "nsteps and ckpt_every must be >= 1");
       if (which != 0 && which != 1) throw ApiError(PF_ERR_ARG, "objective must be PF_OBJ_WETTED or PF_OBJ_CENTROID_Z");
       const int nseg = (nsteps + K - 1) / K;
@@ -1320,6 +1338,7 @@ struct Impl : ImplBase {
       if (d.dim != 2) throw ApiError(PF_ERR_UNSUPPORTED, "the coupled reverse sweep is built for 2D meshes");
       if (p.approach1)
         throw ApiError(PF_ERR_UNSUPPORTED, "the coupled reverse sweep is built for polymer approach 2 (Eq. NS12)");
+      if (p.weno) throw ApiError(PF_ERR_UNSUPPORTED, "the reverse sweep transposes the central advection flux");
       if (nsteps < 1 || K < 1) throw ApiError(PF_ERR_ARG, "nsteps and ckpt_every must be >= 1");
       if (which != 0 && which != 1) throw ApiError(PF_ERR_ARG, "objective must be PF_OBJ_WETTED or PF_OBJ_CENTROID_Z");
       const int nseg = (nsteps + K - 1) / K;
@@ -1673,6 +1692,7 @@ struct Batch : BatchBase {
     for (int i = 0; i < n; ++i) {
       if (g[i].ny != 1) throw ApiError(PF_ERR_UNSUPPORTED, "batched problems must be two-dimensional (ny = 1)");
       if (g[i].precision != g[0].precision) throw ApiError(PF_ERR_ARG, "all batched problems share one precision");
+      if (prm[i].advection != 0) throw ApiError(PF_ERR_UNSUPPORTED, "batched problems use the central advection flux");
       probs.emplace_back(new Impl<T, T>(g[i], st));
       probs.back()->set_params(prm[i]);
     }

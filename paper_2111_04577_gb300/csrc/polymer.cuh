@@ -23,6 +23,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "weno.cuh"
 
 namespace pf {
 
@@ -373,9 +374,16 @@ __device__ __forceinline__ void polymer_cell(const PolyIn<T>& P, const Dims& d, 
     L[N - 1][1] = (wc(id + oy) - wc(id + oym)) * (T)0.5 * iD;
     L[N - 1][N - 1] = dwdz;
   }
-  // advection div(u Theta), central conservative fluxes, no wall flux
+  // advection div(u Theta), conservative, no wall flux: WENO5-Z face values
+  // (the paper's scheme) when selected, else central
   T adv[NC], th0[NC];
-  {
+  if (q.weno) {
+#pragma unroll
+    for (int cq = 0; cq < NC; ++cq) {
+      adv[cq] = weno_div_coarse<T>(P.th[cq], U, Vv, W, i, j, k, d, iD);
+      th0[cq] = P.th[cq][id];
+    }
+  } else {
     const T ul = U[id], ur = U[id + ox];
     const T wb = W[id], wt = W[id + plane];
     const T vl = N == 3 ? Vv[id] : (T)0, vr = N == 3 ? Vv[id + oy] : (T)0;

@@ -112,6 +112,7 @@ class Params:
     wi2: float = 0.0              # approach 1: relaxation time of phase 2
     alpha_giesekus2: float = 0.0  # approach 1: Giesekus mobility of phase 2
     polymer_approach: int = 0     # 0: Eq. NS12 (droplet only), 1: Eq. NS11 (linear in phi)
+    advection: int = 0            # 0: central second order, 1: WENO5-Z (phi and Theta)
 
     def as_dict(self):
         return asdict(self)

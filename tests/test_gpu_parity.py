@@ -406,3 +406,76 @@ def test_polymer_approach1_argument_errors():
         with pytest.raises(binding.PFError) as e:
             binding.Solver(w.grid, prm, binding.PF_FP64)
         assert e.value.code == -1, over
+
+
+@pytest.mark.parametrize("cfg,nx,nz", [("c2", 16, 8), ("c4", 12, 6), ("c4", 16, 4)])
+def test_weno5z_advection_fp64_and_mixed_vs_oracle(cfg, nx, nz):
+    """The paper's WENO5-Z convective fluxes (advection = 1) for phi in the CH
+    step (2D tiled, 3D scalar march in FP64, 3D float4 march in FP32) and for
+    Theta in the polymer update: FP64 against the oracle at 1e-10, mixed at
+    the mixed tolerances, after 4 steps from a seeded velocity and Theta; the
+    fluxes change the answer against the central scheme."""
+    w = wl.scaled(wl.config(cfg), nx, nz)
+    w.params.advection = 1
+    g = w.grid
+    phi0 = wl.initial_phi(w)
+    vel = wl.random_velocity(g, 15, 0.3)
+    nz_, ny_, nx_ = g.coarse_shape
+    m = 2 if g.dim == 2 else 3
+    a = 0.25 * np.random.default_rng(23).standard_normal((nz_, ny_, nx_, m, m))
+    theta0 = a + np.swapaxes(a, -1, -2)
+    idx = [(0, 0), (0, 1), (1, 1)] if g.dim == 2 else [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    theta_comp = np.stack([theta0[..., i, j] for i, j in idx])
+    n = 4
+
+    def oracle(params):
+        ref = ostep.State(g, params.as_dict(), phi0, vel0=vel, theta0=theta0)
+        for _ in range(n):
+            ref.step()
+        return ref
+
+    ref = oracle(w.params)
+    for prec in (binding.PF_FP64, binding.PF_MIXED):
+        s = binding.Solver(g, w.params, prec)
+        s.load_state(phi0, vel)
+        s.set("theta", theta_comp)
+        s.step(n)
+        th = s.coarse("theta")
+        if prec == binding.PF_FP64:
+            assert rel(s.fine("phi"), ref.phi) < FP64_TOL
+            for name, r in (("u", ref.vel[0]), ("w", ref.vel[2]), ("p", ref.p)):
+                assert rel(s.coarse(name), r) < FP64_TOL, name
+            for q, (i, j) in enumerate(idx):
+                assert rel(th[q], ref.theta[..., i, j]) < FP64_TOL, q
+        else:
+            assert np.max(np.abs(s.fine("phi") - ref.phi)) < 2e-4
+            assert rel(s.coarse("u"), ref.vel[0]) < 1e-3
+            scale = max(np.max(np.abs(ref.theta)), 1e-300)
+            for q, (i, j) in enumerate(idx):
+                assert np.max(np.abs(th[q] - ref.theta[..., i, j])) < 1e-3 * scale, q
+        s.close()
+    central = oracle(wl.Params(**{**w.params.as_dict(), "advection": 0}))
+    assert rel(central.phi, ref.phi) > 1e-9
+    assert rel(central.theta, ref.theta) > 1e-6
+
+
+def test_weno5z_argument_errors():
+    w = wl.scaled(wl.config("c2"), 16, 8)
+    bad = wl.Params(**{**w.params.as_dict(), "advection": 2})
+    with pytest.raises(binding.PFError) as e:
+        binding.Solver(w.grid, bad, binding.PF_FP64)
+    assert e.value.code == -1
+    thin = wl.scaled(wl.config("c2"), 16, 2)
+    with pytest.raises(binding.PFError) as e:
+        binding.Solver(thin.grid, wl.Params(**{**thin.params.as_dict(), "advection": 1}), binding.PF_FP64)
+    assert e.value.code == -1
+    we = wl.Params(**{**w.params.as_dict(), "advection": 1})
+    s = binding.Solver(w.grid, we, binding.PF_FP64)
+    s.load_state(wl.initial_phi(w))
+    with pytest.raises(binding.PFError) as e:
+        s.adjoint(2, 1, binding.PF_OBJ_WETTED)
+    assert e.value.code == -3
+    s.close()
+    with pytest.raises(binding.PFError) as e:
+        binding.Batch([w.grid], [we], binding.PF_FP64)
+    assert e.value.code == -3

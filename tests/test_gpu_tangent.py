@@ -202,3 +202,16 @@ def test_wi_sensitivity_in_polymer_approach1():
     fd = (oracle_J(w, vel, n, wi=wi + h) - oracle_J(w, vel, n, wi=wi - h)) / (2 * h)
     assert close(J, oracle_J(w, vel, n), 1e-10)
     assert close(dJ, fd, 1e-3), (dJ, fd)
+
+
+def test_theta_sensitivity_with_weno5z_advection():
+    """Forward mode through the WENO5-Z fluxes (phi and Theta): dJ/dtheta_s
+    against central differences of the oracle with the same scheme."""
+    w, vel, n = case(2)
+    w.params.advection = 1
+    J, dJ = tangents(w, vel, n, binding.PF_PARAM_THETA_BOT)
+    th = w.params.theta_bot_deg
+    hd = 1e-2
+    fd = (oracle_J(w, vel, n, theta_bot_deg=th + hd) - oracle_J(w, vel, n, theta_bot_deg=th - hd)) / (2 * hd)
+    assert close(J, oracle_J(w, vel, n), 1e-10)
+    assert close(dJ, fd, 1e-3), (dJ, fd)
