@@ -535,7 +535,9 @@ struct March4 {
   }
 };
 
-template <int RS, int MINB>
+// AW: take div(u* phi*) from f.aw (WENO5-Z) instead of the central flux; a
+// template flag, so that the default form carries no trace of it
+template <int RS, int MINB, bool AW = false>
 __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineView<float> f, const CoarseVel<float> vel,
                                                                      float* __restrict__ R, double* __restrict__ gwall,
                                                                      const Dims d, const Phys p, const PhysT<float> q,
@@ -786,9 +788,11 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
     // close), then the remainders' (zero without compensated storage)
     const float dv[4] = {(bo.x - an.x) + dl.x, (bo.y - an.y) + dl.y, (bo.z - an.z) + dl.z, (bo.w - an.w) + dl.w};
     float awv[4] = {0.f, 0.f, 0.f, 0.f};
-    if (f.aw && act) {
-      const float4 a = *reinterpret_cast<const float4*>(f.aw + (size_t)z * plane + gof);
-      awv[0] = a.x, awv[1] = a.y, awv[2] = a.z, awv[3] = a.w;
+    if constexpr (AW) {
+      if (act) {
+        const float4 a = *reinterpret_cast<const float4*>(f.aw + (size_t)z * plane + gof);
+        awv[0] = a.x, awv[1] = a.y, awv[2] = a.z, awv[3] = a.w;
+      }
     }
     float out[4];
 #pragma unroll
@@ -799,7 +803,7 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
       if (z + 1 < fnz) adv += whi[i] * (c0 + zpp[i]);
       if (z > 0) adv -= wlo[i] * (zmp[i] + c0);
       adv *= 0.5f * q.ih;
-      if (f.aw) adv = awv[i];
+      if constexpr (AW) adv = awv[i];
       const float m0 = mv[i + 1];
       float lap = mv[i + 2] + mv[i] - 2 * m0;
       lap += muv[i] + mdv[i] - 2 * m0;

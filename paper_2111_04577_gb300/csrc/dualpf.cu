@@ -469,6 +469,8 @@ struct Impl : ImplBase {
       PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march4<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
       PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march4<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
       PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march4<0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+      PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march4<1, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+      PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march4<0, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     }
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_G_restrict_march<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
     PF_CUDA_TRY(cudaFuncSetAttribute(k_ns_rhs_march3<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
@@ -695,7 +697,10 @@ struct Impl : ImplBase {
           dim3 g4((d.fnx + T4::TX - 1) / T4::TX, (d.fny + T4::TY - 1) / T4::TY, (d.fnz + nzc - 1) / nzc);
           const size_t s4 = (size_t)T4::smem_floats(d.rs) * sizeof(float);
           const int mb = tune[PF_TUNE_CH_MINB];
-          if (d.rs == 1) {
+          if (fv.aw) {  // WENO5-Z advection: the precomputed divergence, default register budget
+            if (d.rs == 1) k_ch_rhs_march4<1, 3, true><<<g4, T4::NT, s4, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml, nzc);
+            else k_ch_rhs_march4<0, 2, true><<<g4, T4::NT, s4, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml, nzc);
+          } else if (d.rs == 1) {
             if (mb == 2) k_ch_rhs_march4<1, 2><<<g4, T4::NT, s4, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml, nzc);
             else if (mb == 4) k_ch_rhs_march4<1, 4><<<g4, T4::NT, s4, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml, nzc);
             else k_ch_rhs_march4<1, 3><<<g4, T4::NT, s4, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml, nzc);
