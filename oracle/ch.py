@@ -10,6 +10,9 @@ Follows Section 3.2.1 in the paper's order:
   Eq. NS27       (lap + alpha) phi^{n+1} = Psi                with Eq. NS34 on the walls;
   Eq. NS15/16/34 with D_w = 0: n.grad(phi^{n+1}) = -f_w'(phi*)/lambda
                  = cos(theta_s) (1 - phi*_w^2)/(sqrt(2) eta), n the outward normal;
+                 with D_w > 0 the flux also holds -D_w (dphi/dt + u.grad phi*) at
+                 the wall, implicit in phi^{n+1}: the two solves are then one
+                 system per Fourier mode (spectral.solve_ch_robin, wall_explicit);
   Eq. NS5/NS6    G = lambda(-lap phi + f(phi)), f(phi) = phi (phi^2 - 1)/eta^2.
 
 Readings (the paper is silent or ambiguous):
@@ -43,6 +46,26 @@ def wall_flux(phis, d):
     gb = d.cos_bot * (1.0 - wb * wb) / (s2 * d.eta)
     gt = d.cos_top * (1.0 - wt * wt) / (s2 * d.eta)
     return gb, gt
+
+
+def wall_explicit(phis, phih, d, grid):
+    """The explicit part E of the dynamic contact-angle condition, Eq. NS34 with
+    D_w > 0, at the bottom and top walls: the wall flux of phi^{n+1} is
+    g = E - kappa phi_w^{n+1} with kappa = D_w gamma0/dt and
+        E = -f_w'(phi*_w)/lambda - D_w (u_w . grad phi*)_w + (D_w/dt) phi_hat_w,
+    the BDF2 time derivative of Eq. NS31 taken at the wall.  Readings: every
+    wall value (phi*, phi_hat, phi^{n+1}) is the extrapolation 1.5 v_0 - 0.5 v_1;
+    the wall velocity is the no-slip u_w along x (w = 0, v = 0 there), times the
+    central x difference of phi*_w."""
+    gb, gt = wall_flux(phis, d)
+    h = grid.h
+    out = []
+    for g, a, uw in ((gb, (0, 1), d.uw_bot), (gt, (-1, -2), d.uw_top)):
+        ws = 1.5 * phis[a[0]] - 0.5 * phis[a[1]]
+        wh = 1.5 * phih[a[0]] - 0.5 * phih[a[1]]
+        dx = (np.roll(ws, -1, axis=-1) - np.roll(ws, 1, axis=-1)) / (2.0 * h)
+        out.append(g - d.dw * uw * dx + d.dw / d.dt * wh)
+    return out
 
 
 def wall_term(shape, gb, gt, h):
@@ -80,11 +103,20 @@ def ch_step(phi_n, phi_nm1, vel_n, vel_nm1, d, grid):
     else:
         A = advection(phis, uf, vf, wf, h, dim)
     hh = f_bulk(phis, eta) - d.S / eta ** 2 * phis
-    gb, gt = wall_flux(phis, d)
-    B = wall_term(phis.shape, gb, gt, h)
-    R1 = (phih / d.dt - A) / d.Ml + op.lap_neumann(hh, h, dim) - d.c * B
-    psi = spectral.solve(R1, d.c, h, "neumann")
-    phi = spectral.solve(psi - B, -d.alpha, h, "neumann")
+    if d.dw > 0:  # Eq. NS34 with D_w > 0: a Robin condition coupling the two solves
+        Eb, Et = wall_explicit(phis, phih, d, grid)
+        Q = (phih / d.dt - A) / d.Ml + op.lap_neumann(hh, h, dim)
+        psi, phi = spectral.solve_ch_robin(Q, Eb, Et, d.c, d.alpha, d.kappa, h)
+        gb = Eb - d.kappa * (1.5 * phi[0] - 0.5 * phi[1])
+        gt = Et - d.kappa * (1.5 * phi[-1] - 0.5 * phi[-2])
+        B = wall_term(phis.shape, gb, gt, h)
+        R1 = Q - d.c * B
+    else:
+        gb, gt = wall_flux(phis, d)
+        B = wall_term(phis.shape, gb, gt, h)
+        R1 = (phih / d.dt - A) / d.Ml + op.lap_neumann(hh, h, dim) - d.c * B
+        psi = spectral.solve(R1, d.c, h, "neumann")
+        phi = spectral.solve(psi - B, -d.alpha, h, "neumann")
     G = d.lam * (-(op.lap_neumann(phi, h, dim) + B) + f_bulk(phi, eta))
     return dict(phi=phi, psi=psi, G=G, gb=gb, gt=gt, A=A, R1=R1, phis=phis, phih=phih)
 

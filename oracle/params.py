@@ -16,14 +16,16 @@ import math
 class Derived:
     def __init__(self, prm: dict):
         p = dict(prm)
-        if p.get("dw", 0.0) != 0.0:
-            raise ValueError("dynamic contact angle (D_w != 0) is not part of this scheme")
+        self.dw = p.get("dw", 0.0)
+        if self.dw < 0.0:
+            raise ValueError("the wall relaxation D_w of Eq. NS15 must be >= 0")
         ag = p.get("alpha_giesekus", 0.0)
         if not (0.0 <= ag < 1.0):
             raise ValueError("the Giesekus mobility must lie in [0, 1)")
         self.p = p
         self.gamma0 = 1.5
         self.dt = p["dt"]
+        self.kappa = self.dw * self.gamma0 / self.dt  # implicit wall coefficient of Eq. NS34
         self.eta = p["eta"]
         self.lam = 3.0 * p["sigma"] * p["eta"] / (2.0 * math.sqrt(2.0))
         self.mob = p["mobility"]
