@@ -52,7 +52,7 @@ enum {
   PF_OK = 0,
   PF_ERR_ARG = -1,          /* invalid argument or call order                 */
   PF_ERR_DISCRIMINANT = -2, /* S below the bound of Eq. NS30                  */
-  PF_ERR_UNSUPPORTED = -3,  /* D_w != 0, size not 2^a3^b5^c7^d                 */
+  PF_ERR_UNSUPPORTED = -3,  /* a size not 2^a3^b5^c7^d, an option a path lacks  */
   PF_ERR_NONFINITE = -4,    /* the phi-sum check (FP64 accumulator) saw NaN/Inf */
   PF_ERR_TIMEOUT = -5,      /* a bounded device-side wait expired             */
   PF_ERR_CUDA = -6,         /* a CUDA runtime call failed                     */
@@ -109,7 +109,11 @@ typedef struct {
  * coarse cells along every axis, and the batch and the reverse sweeps reject
  * it.  mobility: M of Eq. NS1.  sigma, eta: Eq. NS7.
  * theta_*_deg: equilibrium angles of Eq. NS16 at z = 0 and z = lz, measured
- * through phase 1.  dw: must be 0 (static contact angle).  alpha_giesekus:
+ * through phase 1.  dw: the wall relaxation D_w >= 0 of Eq. NS15 (0: static
+ * contact angle); with D_w > 0 the wall flux of Eq. NS34 holds the BDF2 time
+ * derivative of the wall value (1.5 phi_0 - 0.5 phi_1), implicit, and the wall
+ * advection u_w d_x phi*, and the two CH solves take it as a Robin condition
+ * (the batch, forward mode and the reverse sweeps reject D_w > 0).  alpha_giesekus:
  * the Giesekus mobility alpha of Eqs. NS18/NS22 in [0, 1), constant in the
  * viscoelastic phase (0: Oldroyd-B).  S = 0 selects the smallest S of Eq. NS30; nu_m = 0
  * selects nu_m = max(mu_s)/(2 min(rho)) (text after Eq. NS39).  uw_*: x
@@ -140,8 +144,8 @@ int pf_init_grid(pf_ctx** out, const pf_grid_desc* g, void* stream);
  * Errors: PF_ERR_ARG (non-positive rho, sigma, eta, mobility, dt, an angle
  * outside [0, 180], alpha_giesekus or alpha_giesekus2 outside [0, 1),
  * polymer_approach or advection not 0 or 1, approach 1 without wi, wi2 > 0,
- * WENO5-Z on fewer than 4 coarse cells along an axis),
- * PF_ERR_DISCRIMINANT (S below Eq. NS30), PF_ERR_UNSUPPORTED (dw != 0). */
+ * WENO5-Z on fewer than 4 coarse cells along an axis,
+ * dw < 0), PF_ERR_DISCRIMINANT (S below Eq. NS30). */
 int pf_set_params(pf_ctx* ctx, const pf_params* prm);
 
 /* Number of elements and element size (bytes) of a field. */
@@ -199,7 +203,8 @@ int pf_profile(pf_ctx* ctx, int nsteps, int flags, int max_entries, char* names,
  * Field access and diagnostics take a problem index 0..nproblems-1 and
  * behave as pf_set_fields / pf_get_fields / pf_diagnostics on that problem.
  * Precision PF_FP64 or PF_MIXED (PF_MIXED_Z64: PF_ERR_UNSUPPORTED); the
- * central advection flux only (advection = 1: PF_ERR_UNSUPPORTED).
+ * central advection flux and the static contact angle only (advection = 1 or
+ * dw > 0: PF_ERR_UNSUPPORTED).
  * ------------------------------------------------------------------------ */
 typedef struct pf_batch pf_batch;
 int pf_batch_create(pf_batch** out, int nproblems, const pf_grid_desc* grids, const pf_params* params,
@@ -259,7 +264,7 @@ int pf_diagnostics_noalloc(const pf_grid_desc* g, const pf_params* prm, const vo
  * transform solves.  The context is left at phi^N.  The mobility derivative
  * follows S when S = 0 selects the bound of Eq. NS30.
  * Errors: PF_ERR_ARG, PF_ERR_DISCRIMINANT, PF_ERR_UNSUPPORTED (WENO5-Z
- * advection), PF_ERR_CUDA, PF_ERR_NOMEM. */
+ * advection, D_w > 0), PF_ERR_CUDA, PF_ERR_NOMEM. */
 enum { PF_OBJ_WETTED = 0, PF_OBJ_CENTROID_Z = 1 };
 int pf_adjoint(pf_ctx* ctx, int nsteps, int ckpt_every, int objective, double out[3], void* dphi0,
                int dphi0_on_device);
@@ -284,7 +289,7 @@ int pf_adjoint(pf_ctx* ctx, int nsteps, int ckpt_every, int objective, double ou
  * right side, the polymer's right side and stress) are differentiated exactly
  * with dual numbers.  The context is left at step N.
  * Errors: PF_ERR_ARG, PF_ERR_UNSUPPORTED (a 3D context, PF_ADJ_COUPLED on a
- * derivative-carrying context, polymer approach 1, WENO5-Z advection),
+ * derivative-carrying context, polymer approach 1, WENO5-Z advection, D_w > 0),
  * PF_ERR_CUDA, PF_ERR_NOMEM. */
 enum { PF_ADJ_COUPLED = 1 };
 int pf_adjoint_ex(pf_ctx* ctx, int nsteps, int ckpt_every, int objective, int flags, double out[4], void* dphi0,
@@ -309,7 +314,8 @@ int pf_adjoint_ex(pf_ctx* ctx, int nsteps, int ckpt_every, int objective, int fl
  * out[0] = J after nsteps steps, out[1] = dJ/d param.  The copy holds every
  * field in 16 bytes per value (value and derivative) besides the context's
  * own; its kernels are those of PF_FP64 run on that pair.
- * Errors: PF_ERR_ARG, PF_ERR_NONFINITE, PF_ERR_CUDA, PF_ERR_NOMEM. */
+ * Errors: PF_ERR_ARG, PF_ERR_UNSUPPORTED (D_w > 0), PF_ERR_NONFINITE, PF_ERR_CUDA,
+ * PF_ERR_NOMEM. */
 enum { PF_PARAM_WI = 0, PF_PARAM_THETA_BOT = 1, PF_PARAM_PHI0 = 2, PF_PARAM_MOBILITY = 3 };
 int pf_tangent(pf_ctx* ctx, int nsteps, int param, int objective, double out[2]);
 /* pf_tangent with two more choices.

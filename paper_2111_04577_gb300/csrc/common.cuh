@@ -66,6 +66,7 @@ struct Phys {
   int approach1;                    // Eq. NS11: polymer parameters linear in phi, tau = tau_p
   double mu_p2, lam_h2, alpha_g2;   // phase 2's polymer (approach 1)
   int weno;                         // WENO5-Z convective fluxes for phi and Theta (else central)
+  double dw, kappa;                 // wall relaxation D_w of Eq. NS15 and D_w gamma0/dt
 };
 
 // Scheme constants converted once to the arithmetic type of the kernels, so

@@ -34,6 +34,7 @@
 #include "batch.cuh"
 #include "adjoint.cuh"
 #include "adjoint_ns.cuh"
+#include "robin.cuh"
 
 namespace pf {
 
@@ -161,7 +162,7 @@ static Phys derive(const pf_params& q, const pf_grid_desc& g) {
     throw ApiError(PF_ERR_ARG, "rho1, rho2, sigma, eta, mobility, dt must be > 0 and mu1, mu2 >= 0");
   if (q.theta_bot_deg < 0 || q.theta_bot_deg > 180 || q.theta_top_deg < 0 || q.theta_top_deg > 180)
     throw ApiError(PF_ERR_ARG, "contact angles must lie in [0, 180] degrees");
-  if (q.dw != 0.0) throw ApiError(PF_ERR_UNSUPPORTED, "dynamic contact angle D_w != 0 is not supported");
+  if (!(q.dw >= 0.0)) throw ApiError(PF_ERR_ARG, "the wall relaxation D_w must be >= 0");
   if (!(q.alpha_giesekus >= 0.0 && q.alpha_giesekus < 1.0))
     throw ApiError(PF_ERR_ARG, "the Giesekus mobility must lie in [0, 1)");
   Phys p{};
@@ -189,6 +190,8 @@ static Phys derive(const pf_params& q, const pf_grid_desc& g) {
     throw ApiError(PF_ERR_ARG, "polymer_approach must be 0 (Eq. NS12) or 1 (Eq. NS11)");
   p.approach1 = q.polymer_approach;
   p.weno = q.advection;
+  p.dw = q.dw;
+  p.kappa = q.dw * p.gamma0 / q.dt;  // implicit wall coefficient of Eq. NS34
   double beta;
   if (p.approach1) {
     if (!(q.beta > 0 && q.beta <= 1.0) || !(q.mu_p2 >= 0))
@@ -717,13 +720,37 @@ struct Impl : ImplBase {
       else k_ch_rhs_march<T, 3><<<grid, TL::NT, sm, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml, nzc);
       }
     }
+    const bool robin = !IsDual<T>::value && p.dw > 0;
+    const dim3 rgrid((d.fnx + 127) / 128, d.fny);
+    if constexpr (!IsDual<T>::value) {
+      if (robin) {  // D_w > 0: the flux g* of phi* into the right side (csrc/robin.cuh)
+        mark("robin_wall");
+        k_robin_wall<T><<<rgrid, 128, 0, st>>>(fv, rgE, rdg, d, p, q, p.dw, p.kappa);
+        mark("robin_rhs");
+        k_robin_rhs<T><<<rgrid, 128, 0, st>>>(mu, rdg, d, q);
+      }
+    }
     const int nlf = d.fny * d.fnz;
     rfft_x(FineArrPro<T>{mu, d.fnx}, spF, d.fnx, nlf, pF, plFx, twFx);
     if (d.dim == 3) fft_y(spF, d.fny, pF, d.fnx / 2 + 1, d.fnz, plFy, twFy, -1);
     zsolve(spF, d.fnz, d.fny, pF, d.fnx / 2 + 1, eFx, eFy, Z_NEUMANN, d.h * d.h, p.c, -p.alpha, true,
            1.0 / ((double)d.fnx * d.fny), false, dseed.c, -dseed.alpha);
+    if constexpr (!IsDual<T>::value) {
+      if (robin) {  // the Robin walls: delta = delta0 + b_bot D + b_top D mirrored
+        const int ncol = d.fnx / 2 + 1;
+        mark("robin_correct");
+        k_robin_correct<T, TC><<<dim3((2 * ncol + 127) / 128, d.fny), 128, 0, st>>>(spF, d.fnz, d.fny, pF, ncol, rD,
+                                                                                   rsx, (TC)p.kappa);
+      }
+    }
     if (d.dim == 3) fft_y(spF, d.fny, pF, d.fnx / 2 + 1, d.fnz, plFy, twFy, +1);
     irfft_x(spF, ChFinish<T>{phi[pc], phi[po], d.fnx, philo[pc], philo[po]}, d.fnx, nlf, pF, plFx, twFx, (T)1);
+    if constexpr (!IsDual<T>::value) {
+      if (robin) {  // the flux of phi^{n+1}, for G (Eq. NS5)
+        mark("robin_flux");
+        k_robin_flux<T><<<rgrid, 128, 0, st>>>(phi[po], philo[po], rgE, gwall, d, p.kappa);
+      }
+    }
     if (flags & PF_STEP_CH_ONLY) return;
     if (pend_in) PF_CUDA_TRY(cudaStreamWaitEvent(st, ev_join, 0));  // the update read the restricted phi
     // ---- chemical potential and restriction to the coarse mesh ----
@@ -882,6 +909,62 @@ struct Impl : ImplBase {
       weno_ar.reset(new Arena());
       wadv = weno_ar->get<T>((size_t)d.fnx * d.fny * d.fnz);
     }
+    if constexpr (!IsDual<T>::value) {
+      if (p.dw > 0) robin_tables();
+    }
+  }
+  // ---- dynamic contact angle (D_w > 0): the pair's response to a unit wall flux ----
+  std::unique_ptr<Arena> robin_ar;
+  TC* rD = nullptr;       // [fnz][fny][ncol]: delta of the pair for a unit flux at the bottom wall
+  TC* rsx = nullptr;      // [fny][ncol][2]: its wall values w_bot, w_top
+  Wide<T>* rgE = nullptr; // [2][fny][fnx]: explicit part E of the wall flux
+  Wide<T>* rdg = nullptr; // [2][fny][fnx]: g* - g0
+  void robin_tables() {
+    const int R = d.fnz, ny = d.fny, ncol = d.fnx / 2 + 1;
+    if (!robin_ar) {
+      robin_ar.reset(new Arena());
+      rD = robin_ar->get<TC>((size_t)R * ny * ncol);
+      rsx = robin_ar->get<TC>((size_t)2 * ny * ncol);
+      rgE = robin_ar->get<Wide<T>>((size_t)2 * d.fnx * d.fny);
+      rdg = robin_ar->get<Wide<T>>((size_t)2 * d.fnx * d.fny);
+    }
+    // per mode, with lam the x-y eigenvalue of the Laplacian and L_N the
+    // Neumann tridiagonal along z (all FP64):
+    //   (L_N + lam - c) eps = -(c/h) e_0,   (L_N + lam + alpha) D = eps - (1/h) e_0
+    const double h = d.h, ih2 = 1.0 / (h * h);
+    auto eig = [&](int k, int n) {
+      if (n == 1) return 0.0;
+      const double s = std::sin(M_PI * k / n);
+      return -4.0 * ih2 * s * s;
+    };
+    std::vector<TC> hD((size_t)R * ny * ncol), hs((size_t)2 * ny * ncol);
+    std::vector<double> cp(R), x(R), e(R);
+    // Thomas algorithm for (L_N + sh) x = b (b overwritten with x)
+    auto tri = [&](double sh, std::vector<double>& b) {
+      for (int k = 0; k < R; ++k) {
+        const double diag = -2.0 * ih2 + ((k == 0 || k == R - 1) ? ih2 : 0.0) + sh;
+        const double den = diag - (k > 0 ? ih2 * cp[k - 1] : 0.0);
+        cp[k] = ih2 / den;
+        b[k] = (b[k] - (k > 0 ? ih2 * b[k - 1] : 0.0)) / den;
+      }
+      for (int k = R - 2; k >= 0; --k) b[k] -= cp[k] * b[k + 1];
+    };
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < ncol; ++i) {
+        const double lam = eig(i, d.fnx) + eig(j, ny);
+        std::fill(e.begin(), e.end(), 0.0);
+        e[0] = -p.c / h;
+        tri(lam - p.c, e);
+        x = e;
+        x[0] -= 1.0 / h;
+        tri(lam + p.alpha, x);
+        const size_t m = (size_t)j * ncol + i;
+        for (int k = 0; k < R; ++k) hD[(size_t)k * ny * ncol + m] = (TC)x[k];
+        hs[2 * m] = (TC)(1.5 * x[0] - 0.5 * x[1]);
+        hs[2 * m + 1] = (TC)(1.5 * x[R - 1] - 0.5 * x[R - 2]);
+      }
+    PF_CUDA_TRY(cudaMemcpy(rD, hD.data(), hD.size() * sizeof(TC), cudaMemcpyHostToDevice));
+    PF_CUDA_TRY(cudaMemcpy(rsx, hs.data(), hs.size() * sizeof(TC), cudaMemcpyHostToDevice));
   }
   std::unique_ptr<Arena> weno_ar;
   T* wadv = nullptr;
@@ -1167,6 +1250,7 @@ struct Impl : ImplBase {
       flush_polymer();
       if (!have_params) throw ApiError(PF_ERR_ARG, "pf_set_params must precede pf_adjoint");
       if (p.weno) throw ApiError(PF_ERR_UNSUPPORTED, "the reverse sweep transposes the central advection flux");
+      if (p.dw > 0) throw ApiError(PF_ERR_UNSUPPORTED, "the reverse sweep is built for the static contact angle (D_w = 0)");
       if (nsteps < 1 || K < 1) throw ApiError(PF_ERR_ARG, "nsteps and ckpt_every must be >= 1");
       if (which != 0 && which != 1) throw ApiError(PF_ERR_ARG, "objective must be PF_OBJ_WETTED or PF_OBJ_CENTROID_Z");
       const int nseg = (nsteps + K - 1) / K;
@@ -1344,6 +1428,7 @@ struct Impl : ImplBase {
       if (p.approach1)
         throw ApiError(PF_ERR_UNSUPPORTED, "the coupled reverse sweep is built for polymer approach 2 (Eq. NS12)");
       if (p.weno) throw ApiError(PF_ERR_UNSUPPORTED, "the reverse sweep transposes the central advection flux");
+      if (p.dw > 0) throw ApiError(PF_ERR_UNSUPPORTED, "the reverse sweep is built for the static contact angle (D_w = 0)");
       if (nsteps < 1 || K < 1) throw ApiError(PF_ERR_ARG, "nsteps and ckpt_every must be >= 1");
       if (which != 0 && which != 1) throw ApiError(PF_ERR_ARG, "objective must be PF_OBJ_WETTED or PF_OBJ_CENTROID_Z");
       const int nseg = (nsteps + K - 1) / K;
@@ -1698,6 +1783,7 @@ struct Batch : BatchBase {
       if (g[i].ny != 1) throw ApiError(PF_ERR_UNSUPPORTED, "batched problems must be two-dimensional (ny = 1)");
       if (g[i].precision != g[0].precision) throw ApiError(PF_ERR_ARG, "all batched problems share one precision");
       if (prm[i].advection != 0) throw ApiError(PF_ERR_UNSUPPORTED, "batched problems use the central advection flux");
+      if (prm[i].dw != 0) throw ApiError(PF_ERR_UNSUPPORTED, "batched problems use the static contact angle (D_w = 0)");
       probs.emplace_back(new Impl<T, T>(g[i], st));
       probs.back()->set_params(prm[i]);
     }

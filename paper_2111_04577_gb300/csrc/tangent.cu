@@ -31,6 +31,8 @@ struct TangentRun {
 
   TangentRun(ImplBase& src, cudaStream_t st) {
     if (!src.params_ready()) throw ApiError(PF_ERR_ARG, "pf_set_params must precede pf_tangent");
+    if (src.raw_prm.dw > 0)
+      throw ApiError(PF_ERR_UNSUPPORTED, "forward mode is built for the static contact angle (D_w = 0)");
     impl.reset(new Impl<Dual, Dual>(src.grid_desc(), st));
     impl->set_params(src.raw_prm);
     // PHI before PHI_OLD (setting PHI also sets PHI_OLD), likewise U/V/W/P/TAU

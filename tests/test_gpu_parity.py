@@ -479,3 +479,73 @@ def test_weno5z_argument_errors():
     with pytest.raises(binding.PFError) as e:
         binding.Batch([w.grid], [we], binding.PF_FP64)
     assert e.value.code == -3
+
+
+@pytest.mark.parametrize("cfg,nx,nz", [("c1", 32, 16), ("c3", 12, 6), ("c2", 16, 8)])
+def test_dynamic_contact_angle_fp64_and_mixed_vs_oracle(cfg, nx, nz):
+    """Eq. NS15 / NS34 with D_w = 10 (the Robin walls that couple the two CH
+    solves: the BDF2 time derivative of the wall value, implicit) and a
+    moving top wall (the wall advection term), faster CH dynamics (100x
+    mobility): 4 full steps, FP64 against the oracle at 1e-10 (phi, G and the
+    flow), mixed at the mixed tolerances; 2D tiled, 3D scalar march (FP64)
+    and float4 march (FP32) right sides.  D_w changes the answer."""
+    w = wl.scaled(wl.config(cfg), nx, nz)
+    w.params.mobility *= 100
+    w.params.uw_top = 0.4
+    w.params.dw = 10.0
+    g = w.grid
+    phi0 = wl.initial_phi(w)
+    vel = wl.random_velocity(g, 5, 0.1)
+    n = 4
+    ref = ostep.State(g, w.params.as_dict(), phi0, vel0=vel)
+    for _ in range(n):
+        ref.step()
+    for prec in (binding.PF_FP64, binding.PF_MIXED, binding.PF_MIXED_Z64):
+        s = binding.Solver(g, w.params, prec)
+        s.load_state(phi0, vel)
+        s.step(n)
+        phi = s.fine("phi").astype(np.float64)
+        if prec == binding.PF_FP64:
+            assert rel(phi, ref.phi) < FP64_TOL
+            assert rel(s.fine("G"), ref.G) < FP64_TOL
+            for name, r in (("u", ref.vel[0]), ("w", ref.vel[2]), ("p", ref.p)):
+                assert rel(s.coarse(name), r) < FP64_TOL, name
+        else:
+            assert np.max(np.abs(phi - ref.phi)) < 2e-4, prec
+            assert rel(s.coarse("u").astype(np.float64), ref.vel[0]) < 1e-3, prec
+        s.close()
+    st = ostep.State(g, {**w.params.as_dict(), "dw": 0.0}, phi0, vel0=vel)
+    for _ in range(n):
+        st.step()
+    assert rel(st.G, ref.G) > 1e-2
+
+
+def test_dynamic_contact_angle_ch_only_and_errors():
+    """CH-only steps with D_w > 0 keep G (with the flux of phi^{n+1}) equal to
+    the oracle's; D_w < 0 is an argument error; the batch, forward mode and
+    the reverse sweep reject D_w > 0."""
+    w = wl.scaled(wl.config("c1"), 32, 16)
+    w.params.mobility *= 100
+    w.params.dw = 3.0
+    g = w.grid
+    phi0 = wl.initial_phi(w)
+    vel = wl.random_velocity(g, 6, 0.2)
+    s = binding.Solver(g, w.params, binding.PF_FP64)
+    s.load_state(phi0, vel)
+    ref = ostep.State(g, w.params.as_dict(), phi0, vel0=vel)
+    for k in range(3):
+        s.step(1, binding.PF_STEP_CH_ONLY)
+        ref.step(with_ns=False)
+        assert rel(s.fine("phi"), ref.phi) < FP64_TOL, k
+        assert rel(s.fine("G"), ref.G) < FP64_TOL, k
+    for call in (lambda: s.adjoint(2, 1, binding.PF_OBJ_WETTED), lambda: s.tangent(2, binding.PF_PARAM_THETA_BOT, 0)):
+        with pytest.raises(binding.PFError) as e:
+            call()
+        assert e.value.code == -3
+    s.close()
+    with pytest.raises(binding.PFError) as e:
+        binding.Batch([g], [w.params], binding.PF_FP64)
+    assert e.value.code == -3
+    with pytest.raises(binding.PFError) as e:
+        binding.Solver(g, wl.Params(**{**w.params.as_dict(), "dw": -1.0}), binding.PF_FP64)
+    assert e.value.code == -1
