@@ -144,10 +144,126 @@ __device__ __forceinline__ void jacobi_rot_sym_f(float (&dg)[N], float (&of)[N =
   }
 }
 
-// symmetric eigen-decomposition A = V diag(w) V^T by cyclic Jacobi rotations;
-// on entry (dg, of) hold A, on exit dg holds the eigenvalues w
+// Symmetric 3 x 3 eigen-decomposition A = V diag(w) V^T in closed form (FP32,
+// FP64), V orthonormal to rounding.  The mean m = tr A / 3 is removed and the
+// rest scaled by its largest entry s, B = (A - m I)/s.  Of the roots
+//   2 p cos(psi + 2 pi k/3),  p^2 = tr(B^2)/6,  psi = acos(det(B/p)/2)/3
+// of B's characteristic polynomial (the trigonometric solution of the cubic),
+// only the one farthest from the other two is used: k = 0 for psi < pi/6,
+// else k = 2.  Its gap to the others is at least sqrt(3) p, so its
+// eigenvector, the largest cross product of two rows of B - w I, is well
+// conditioned, and its eigenvalue is taken again as the Rayleigh quotient of
+// that vector.  The other two pairs come from diagonalising B on the plane
+// orthogonal to it (one exact rotation), so a near-double eigenvalue costs no
+// accuracy.  On entry (dg, of) hold A, on exit dg the eigenvalues and V the
+// eigenvectors in columns.
+template <class T>
+__device__ __forceinline__ void eig_sym3_closed(T (&dg)[3], T (&of)[3], T (&V)[3][3]) {
+  const T m = (dg[0] + dg[1] + dg[2]) * (T)(1.0 / 3.0);
+  T b[3][3];
+  b[0][0] = dg[0] - m, b[1][1] = dg[1] - m, b[2][2] = dg[2] - m;
+  b[0][1] = b[1][0] = of[0], b[0][2] = b[2][0] = of[1], b[1][2] = b[2][1] = of[2];
+  T sc = (T)0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = a; c < 3; ++c) sc = fmax(sc, fabs(b[a][c]));
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) V[a][c] = (a == c) ? (T)1 : (T)0;
+  if (sc == (T)0) {  // A = m I
+    dg[0] = dg[1] = dg[2] = m;
+    return;
+  }
+  const T isc = (T)1 / sc;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) b[a][c] *= isc;
+  const T p2 = (b[0][0] * b[0][0] + b[1][1] * b[1][1] + b[2][2] * b[2][2] +
+                (T)2 * (b[0][1] * b[0][1] + b[0][2] * b[0][2] + b[1][2] * b[1][2])) * (T)(1.0 / 6.0);
+  const T p = sqrt(p2), ip = (T)1 / p;
+  const T det = b[0][0] * (b[1][1] * b[2][2] - b[1][2] * b[1][2]) - b[0][1] * (b[0][1] * b[2][2] - b[1][2] * b[0][2]) +
+                b[0][2] * (b[0][1] * b[1][2] - b[1][1] * b[0][2]);
+  T r = (T)0.5 * det * ip * ip * ip;
+  r = fmin(fmax(r, (T)-1), (T)1);
+  const T psi = acos(r) * (T)(1.0 / 3.0);
+  const T lam = (T)2 * p * cos(psi < (T)(3.14159265358979323846 / 6.0) ? psi : psi + (T)(4.0 * 3.14159265358979323846 / 3.0));
+  // eigenvector of lam: the largest cross product of two rows of B - lam I
+  T r0[3] = {b[0][0] - lam, b[0][1], b[0][2]}, r1[3] = {b[0][1], b[1][1] - lam, b[1][2]},
+    r2[3] = {b[0][2], b[1][2], b[2][2] - lam};
+  auto cross = [](const T (&x)[3], const T (&y)[3], T (&z)[3]) {
+    z[0] = x[1] * y[2] - x[2] * y[1];
+    z[1] = x[2] * y[0] - x[0] * y[2];
+    z[2] = x[0] * y[1] - x[1] * y[0];
+  };
+  T v[3], c1[3], c2[3];
+  cross(r0, r1, v);
+  cross(r0, r2, c1);
+  cross(r1, r2, c2);
+  T n0 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  const T n1 = c1[0] * c1[0] + c1[1] * c1[1] + c1[2] * c1[2];
+  const T n2 = c2[0] * c2[0] + c2[1] * c2[1] + c2[2] * c2[2];
+  if (n1 > n0) {
+    v[0] = c1[0], v[1] = c1[1], v[2] = c1[2];
+    n0 = n1;
+  }
+  if (n2 > n0) {
+    v[0] = c2[0], v[1] = c2[1], v[2] = c2[2];
+    n0 = n2;
+  }
+  const T iv = rsqrt(n0);
+  v[0] *= iv, v[1] *= iv, v[2] *= iv;
+  // orthonormal pair spanning the plane orthogonal to v
+  const T ax = fabs(v[0]), ay = fabs(v[1]), az = fabs(v[2]);
+  const bool ex = ax <= ay && ax <= az, ey = !ex && ay <= az;  // the axis least aligned with v
+  T u[3], w[3];
+  // u = v x e (e the unit vector of that axis)
+  u[0] = ex ? (T)0 : (ey ? -v[2] : v[1]);
+  u[1] = ex ? v[2] : (ey ? (T)0 : -v[0]);
+  u[2] = ex ? -v[1] : (ey ? v[0] : (T)0);
+  const T iu = rsqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  u[0] *= iu, u[1] *= iu, u[2] *= iu;
+  cross(v, u, w);
+  auto quad = [&](const T (&x)[3], const T (&y)[3]) {  // x^T B y
+    T t = (T)0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) t += x[a] * (b[a][0] * y[0] + b[a][1] * y[1] + b[a][2] * y[2]);
+    return t;
+  };
+  const T lv = quad(v, v), a11 = quad(u, u), a12 = quad(u, w), a22 = quad(w, w);
+  // one rotation diagonalises the 2 x 2 block [[a11, a12], [a12, a22]]
+  T cs = (T)1, sn = (T)0, t = (T)0;
+  if (a12 != (T)0) {
+    const T th = (a22 - a11) / ((T)2 * a12);
+    const T ath = fabs(th);
+    t = ath > (T)1e15 ? (T)0.5 / ath : (T)1 / (ath + sqrt(ath * ath + (T)1));
+    if (th < (T)0) t = -t;
+    cs = rsqrt(t * t + (T)1);
+    sn = t * cs;
+  }
+  dg[0] = m + sc * lv;
+  dg[1] = m + sc * (a11 - t * a12);
+  dg[2] = m + sc * (a22 + t * a12);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    V[a][0] = v[a];
+    V[a][1] = cs * u[a] - sn * w[a];
+    V[a][2] = sn * u[a] + cs * w[a];
+  }
+}
+
+// symmetric eigen-decomposition A = V diag(w) V^T: in closed form for a 3 x 3
+// in FP32 or FP64, else by cyclic Jacobi rotations (2 x 2: one rotation; the
+// derivative-carrying type); on entry (dg, of) hold A, on exit dg holds the
+// eigenvalues w
 template <class T, int N>
 __device__ __forceinline__ void eig_sym(T (&dg)[N], T (&of)[N == 2 ? 1 : 3], T (&V)[N][N]) {
+  if constexpr (N == 3 && !IsDual<T>::value) {
+    eig_sym3_closed<T>(dg, of, V);
+    return;
+  }
 #pragma unroll
   for (int a = 0; a < N; ++a)
 #pragma unroll
@@ -417,10 +533,15 @@ __device__ __forceinline__ void polymer_cell(const PolyIn<T>& P, const Dims& d, 
   for (int cq = 0; cq < NC; ++cq) P.out[cq][id] = newth[cq];
   if (STAGE == 2) {
     // tau = (1 + phi)/2 (mu_p/lambda_H) (W e^theta W^T - I), W the eigenvectors of
-    // Theta^{n+1}.  Theta^{n+1} differs from the stage's Theta by O(dt), so in 3D
-    // it is first rotated into that Theta's eigenbasis R (R^T Theta^{n+1} R is
-    // nearly diagonal and Jacobi converges in about a sweep); W = R V.
-    if constexpr (N == 3) {
+    // Theta^{n+1}: in closed form in FP32 and FP64.  With Jacobi (the
+    // derivative-carrying type), Theta^{n+1}, which differs from the stage's Theta
+    // by O(dt), is first rotated into that Theta's eigenbasis R (R^T Theta^{n+1} R
+    // is nearly diagonal and Jacobi converges in about a sweep); W = R V.
+    if constexpr (N == 3 && !IsDual<T>::value) {
+      dg[0] = newth[0], dg[1] = newth[1], dg[2] = newth[2];
+      of[0] = newth[3], of[1] = newth[4], of[2] = newth[5];
+      eig_sym<T, N>(dg, of, R);
+    } else if constexpr (N == 3) {
       T A[N][N], B[N][N];
 #pragma unroll
       for (int a = 0; a < N; ++a)
@@ -492,10 +613,13 @@ __device__ __forceinline__ void k_polymer_b(const PolyIn<T>& P, const Dims& d, c
   else polymer_cell<T, N, 2>(P, d, q, x);
 }
 
-// FP32: 48 registers, ten 128-thread CTAs per SM (stage 2 measured 2 % faster
-// than at 56 registers)
+// FP32: 64 registers, eight 128-thread CTAs per SM (with the closed-form
+// eigen-decomposition, stage 1 measured 8 % and stage 2 2 % faster than at 48
+// registers, and 5 % and 10 % faster than at 80).  The budget is fixed, not a
+// tuning knob: the compiler's schedule, and so the rounding, differs between
+// budgets.
 template <class T, int N, int STAGE>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 10 : 1) k_polymer(const __grid_constant__ PolyIn<T> P, const Dims d, const PhysT<T> q) {
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 8 : 1) k_polymer(const __grid_constant__ PolyIn<T> P, const Dims d, const PhysT<T> q) {
   RowIdx x;
   if (!row_index(d.nx, d.ny, x)) return;
   polymer_cell<T, N, STAGE>(P, d, q, x);
