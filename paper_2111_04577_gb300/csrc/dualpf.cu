@@ -371,8 +371,8 @@ struct Impl : ImplBase {
     for (auto e : mark_ev) cudaEventDestroy(e);
     for (cudaEvent_t e : {ev_fork, ev_join, ev_ns, ev_v, ev_w, ev_z0, ev_z1})
       if (e) cudaEventDestroy(e);
-    if (st2) cudaStreamDestroy(st2);
-    if (st3) cudaStreamDestroy(st3);
+    for (cudaStream_t x : {st2, st3, st4})
+      if (x) cudaStreamDestroy(x);
   }
 
   // The polymer update of step n needs u^{n+1}, Theta and the restricted phi
@@ -389,10 +389,12 @@ struct Impl : ImplBase {
   cudaEvent_t ev_ns = nullptr, ev_v = nullptr, ev_w = nullptr;
   // the pressure's mean mode is solved on st3 beside the other columns
   cudaEvent_t ev_z0 = nullptr, ev_z1 = nullptr;
+  cudaStream_t st4 = nullptr;  // the w velocity solve
   void ensure_side_stream() {
     if (st2) return;
     PF_CUDA_TRY(cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
     PF_CUDA_TRY(cudaStreamCreateWithFlags(&st3, cudaStreamNonBlocking));
+    PF_CUDA_TRY(cudaStreamCreateWithFlags(&st4, cudaStreamNonBlocking));
     for (cudaEvent_t* e : {&ev_fork, &ev_join, &ev_ns, &ev_v, &ev_w, &ev_z0, &ev_z1})
       PF_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   }
@@ -664,12 +666,6 @@ struct Impl : ImplBase {
   // joined before the restriction; defer: leave this step's update owed.
   void launch_step(int flags, bool pend_in = false, bool defer = false) {
     const int po = pc ^ 1, fo = fc ^ 1;
-    if (pend_in) {
-      PF_CUDA_TRY(cudaEventRecord(ev_fork, st));
-      PF_CUDA_TRY(cudaStreamWaitEvent(st2, ev_fork, 0));
-      launch_polymer(fc, st2);
-      PF_CUDA_TRY(cudaEventRecord(ev_join, st2));
-    }
     // ---- Cahn-Hilliard on the fine mesh ----
     FineView<T> fv{phi[pc], phi[po], philo[pc], philo[po]};
     const CoarseVel<T> vel{u[fc], u[fo], v[fc], v[fo], w[fc], w[fo]};
@@ -729,6 +725,14 @@ struct Impl : ImplBase {
         mark("robin_rhs");
         k_robin_rhs<T><<<rgrid, 128, 0, st>>>(mu, rdg, d, q);
       }
+    }
+    // the owed polymer update runs beside the memory-bound transform chain (not
+    // beside the CH right side, which fills the SMs' registers and shared memory)
+    if (pend_in) {
+      PF_CUDA_TRY(cudaEventRecord(ev_fork, st));
+      PF_CUDA_TRY(cudaStreamWaitEvent(st2, ev_fork, 0));
+      launch_polymer(fc, st2);
+      PF_CUDA_TRY(cudaEventRecord(ev_join, st2));
     }
     const int nlf = d.fny * d.fnz;
     rfft_x(FineArrPro<T>{mu, d.fnx}, spF, d.fnx, nlf, pF, plFx, twFx);
@@ -820,9 +824,9 @@ struct Impl : ImplBase {
     if (!prof) {
       ensure_side_stream();
       PF_CUDA_TRY(cudaEventRecord(ev_ns, st));
-      PF_CUDA_TRY(cudaStreamWaitEvent(st2, ev_ns, 0));
+      PF_CUDA_TRY(cudaStreamWaitEvent(st4, ev_ns, 0));
       {
-        OnStream on(st, st2);
+        OnStream on(st, st4);
         velocity_solve(rw, wt, w[fc], w[fo], P, spW, d.nz - 1, Z_FACES, kk);
         PF_CUDA_TRY(cudaEventRecord(ev_w, st));
       }
