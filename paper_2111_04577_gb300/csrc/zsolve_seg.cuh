@@ -33,6 +33,11 @@ namespace pf {
 
 constexpr int ZSEG = 16;
 
+// the primal value of a factor (the value itself, or a dual number's value)
+template <class TC>
+__device__ __forceinline__ TC zs_val(TC x) { return x; }
+__device__ __forceinline__ double zs_val(Dual x) { return x.v; }
+
 template <class TC>
 __device__ __forceinline__ TC zs_exp2(TC x) { return exp2(x); }
 template <>
@@ -116,24 +121,63 @@ __global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 2 : 1) k_zsolve_seg(cpx
   const TC sg2 = (k2 + zshift<TC>(zs.shift2, zs.dshift2)) * h2;
   // ---- factors in closed form: the two lanes of a column share the rows ----
   // Each lane forms rows k0 + part, k0 + part + 2, ...; rho^k is advanced by
-  // rho^2 from row to row instead of being raised afresh.
+  // rho^2 from row to row instead of being raised afresh.  In FP64, from row kc
+  // on, |beta rho^k| <= 2^-60: 1 + beta rho^k rounds to 1 and the interior
+  // factor is 1/l1 exactly, so it is stored without the division, and a warp
+  // whose rows all have it takes it from a register in the passes below.
   const int part = lane & 1;
-  auto factors = [&](TC sg, TC* f) {
+  // (the convergence row: a row estimate with one row of margin)
+  auto conv_row = [&](const LuClosed<TC>& lu) {
+    using S = decltype(zs_val(lu.beta));
+    const S lthr = (S)-60;  // log2 of the threshold
+    const S ab = fabs(zs_val(lu.beta)), lr = zs_val(lu.lr);
+    if (ab == (S)0) return 0;
+    const S la = log2(ab);
+    if (la <= lthr) return 0;
+    if (!(lr < (S)-1e-6)) return R;
+    const S k = ceil((lthr - la) / lr) + (S)1;
+    return k >= (S)R ? R : (int)k;
+  };
+  // stores the factors of this lane's rows; returns the convergence row kc and 1/l1.
+  // (Only FP64 factors skip the division and take the constant passes: there an
+  // FP64 division costs far more than the registers the extra paths take; the
+  // FP32 form would spill.)
+  constexpr bool kConst = sizeof(TC) == 8;
+  auto factors = [&](TC sg, TC* f, TC& il) {
     const LuClosed<TC> lu(R, zs.bc, sg);
+    const int kc = kConst ? conv_row(lu) : R;
+    il = lu.il1;
     const TC rho = zs_exp2<TC>(lu.lr), rho2 = rho * rho;
     TC pk = zs_exp2<TC>((TC)(k0 + part) * lu.lr);  // rho^k
     for (int j = part; j < nk; j += 2) {
       const int k = k0 + j;
       TC m;
       if (R == 1) m = (TC)1 / lu.d0;
-      else if (k < R - 1) m = lu.il1 * ((TC)1 + lu.beta * pk) / ((TC)1 + lu.beta * pk * rho);
+      else if (k < R - 1) {
+        if (k >= kc) m = lu.il1;
+        else m = lu.il1 * ((TC)1 + lu.beta * pk) / ((TC)1 + lu.beta * pk * rho);
+      }
       else m = (TC)1 / (lu.d0 - lu.interior(R - 2));
       f[(size_t)k * tx + c] = m;
       pk *= rho2;
     }
+    return kc;
   };
-  factors(sg1, f1);
-  if (dual) factors(sg2, f2);
+  TC il1, il2;
+  const int kc1 = factors(sg1, f1, il1);
+  int kc2 = kc1;
+  il2 = il1;
+  if (dual) kc2 = factors(sg2, f2, il2);
+  // segments whose rows all take the constant factor, per solve (solve 2 reads
+  // its factors mirrored, g_k = m2_{R-1-k}), decided for the whole warp so that
+  // the passes below do not diverge
+  bool c1 = false, c2 = false;
+  if constexpr (kConst) {
+    const unsigned wmask = __activemask();
+    const bool full_seg = nk == ZSEG;
+    c1 = __all_sync(wmask, full_seg && k0 >= kc1 && k0 + nk - 1 <= R - 2);
+    c2 = __all_sync(wmask, full_seg && k0 >= 1 && k0 + nk - 1 <= R - 1 - kc2);
+  }
   __syncthreads();
   const TC rs = (TC)(zs.h2 * zs.scale);
   // carried-in value of a linear recurrence, from the (product, last) pairs of the earlier segments
@@ -154,22 +198,37 @@ __global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 2 : 1) k_zsolve_seg(cpx
   TC* cC = car + (size_t)4 * S * L;
   TC* cD = car + (size_t)6 * S * L;
   // Every pass below runs between barriers; a full segment (all but possibly
-  // the last) takes a copy of the loop without the row-count predicate.
+  // the last) takes a copy of the loop without the row-count predicate, and a
+  // segment of constant factors one that takes them from a register.
   const bool full = nk == ZSEG;
-  auto pass = [&](auto&& body) {
-    if (full) body(std::true_type{});
-    else body(std::false_type{});
+  auto pass = [&](bool cst, auto&& body) {
+    if constexpr (kConst) {
+      if (full && cst) {
+        body(std::true_type{}, std::true_type{});
+        return;
+      }
+    }
+    if (full) body(std::true_type{}, std::false_type{});
+    else body(std::false_type{}, std::false_type{});
   };
   const TC* m1 = f1 + c;                         // m_k at m1[k * tx]
   const TC* g2 = f2 + (size_t)(R - 1) * tx + c;  // g_k = m2_{R-1-k} at g2[-k * tx]
+  auto M1 = [&](auto C, int k) -> TC {
+    if constexpr (decltype(C)::value) return il1;
+    else return m1[(size_t)k * tx];
+  };
+  auto G2 = [&](auto C, int k) -> TC {
+    if constexpr (decltype(C)::value) return il2;
+    else return g2[-(ptrdiff_t)k * tx];
+  };
   // ---- solve 1, forward: d_k = -m_k d_{k-1} + m_k r_k ----
-  pass([&](auto F) {
+  pass(c1, [&](auto F, auto C) {
     constexpr bool FULL = decltype(F)::value;
     TC z = 0, P = 1;
 #pragma unroll
     for (int j = 0; j < ZSEG; ++j)
       if (FULL || j < nk) {
-        const TC m = m1[(size_t)(k0 + j) * tx];
+        const TC m = M1(C, k0 + j);
         z = m * (v[j] * rs - z);
         v[j] = z;
         P *= -m;
@@ -179,21 +238,21 @@ __global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 2 : 1) k_zsolve_seg(cpx
   });
   __syncthreads();
   // ---- fix-up of solve 1 forward, then solve 1 backward: x_k = -m_k x_{k+1} + d_k ----
-  pass([&](auto F) {
+  pass(c1, [&](auto F, auto C) {
     constexpr bool FULL = decltype(F)::value;
     const TC g = carry_fwd(cA);
     TC p = 1;
 #pragma unroll
     for (int j = 0; j < ZSEG; ++j)
       if (FULL || j < nk) {
-        p *= -m1[(size_t)(k0 + j) * tx];
+        p *= -M1(C, k0 + j);
         v[j] += p * g;
       }
     TC z = 0, P = 1;
 #pragma unroll
     for (int j = ZSEG - 1; j >= 0; --j)
       if (FULL || j < nk) {
-        const TC m = m1[(size_t)(k0 + j) * tx];
+        const TC m = M1(C, k0 + j);
         z = v[j] - m * z;
         v[j] = z;
         P *= -m;
@@ -214,14 +273,14 @@ __global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 2 : 1) k_zsolve_seg(cpx
       }
   };
   if (!zs.two) {
-    pass([&](auto F) {
+    pass(c1, [&](auto F, auto C) {
       constexpr bool FULL = decltype(F)::value;
       const TC g = carry_bwd(cB);
       TC p = 1;
 #pragma unroll
       for (int j = ZSEG - 1; j >= 0; --j)
         if (FULL || j < nk) {
-          p *= -m1[(size_t)(k0 + j) * tx];
+          p *= -M1(C, k0 + j);
           v[j] += p * g;
         }
       store(F);
@@ -229,7 +288,7 @@ __global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 2 : 1) k_zsolve_seg(cpx
     return;
   }
   // ---- finish solve 1 and run solve 2's elimination in the same backward pass ----
-  pass([&](auto F) {
+  pass(c1 && c2, [&](auto F, auto C) {
     constexpr bool FULL = decltype(F)::value;
     const TC g = carry_bwd(cB);
     TC p = 1, z = 0, P = 1;
@@ -237,9 +296,9 @@ __global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 2 : 1) k_zsolve_seg(cpx
     for (int j = ZSEG - 1; j >= 0; --j)
       if (FULL || j < nk) {
         const int k = k0 + j;
-        p *= -m1[(size_t)k * tx];
+        p *= -M1(C, k);
         const TC x = v[j] + p * g;
-        const TC gk = g2[-(ptrdiff_t)k * tx];
+        const TC gk = G2(C, k);
         z = gk * (h2 * x - z);
         v[j] = z;
         P *= -gk;
@@ -249,21 +308,21 @@ __global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 2 : 1) k_zsolve_seg(cpx
   });
   __syncthreads();
   // ---- fix-up of solve 2's elimination, then its forward substitution: y_k = -g_k y_{k-1} + q_k ----
-  pass([&](auto F) {
+  pass(c2, [&](auto F, auto C) {
     constexpr bool FULL = decltype(F)::value;
     const TC g = carry_bwd(cC);
     TC p = 1;
 #pragma unroll
     for (int j = ZSEG - 1; j >= 0; --j)
       if (FULL || j < nk) {
-        p *= -g2[-(ptrdiff_t)(k0 + j) * tx];
+        p *= -G2(C, k0 + j);
         v[j] += p * g;
       }
     TC z = 0, P = 1;
 #pragma unroll
     for (int j = 0; j < ZSEG; ++j)
       if (FULL || j < nk) {
-        const TC gk = g2[-(ptrdiff_t)(k0 + j) * tx];
+        const TC gk = G2(C, k0 + j);
         z = v[j] - gk * z;
         v[j] = z;
         P *= -gk;
@@ -272,14 +331,14 @@ __global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 2 : 1) k_zsolve_seg(cpx
     cD[(size_t)(S + s) * L + lane] = z;
   });
   __syncthreads();
-  pass([&](auto F) {
+  pass(c2, [&](auto F, auto C) {
     constexpr bool FULL = decltype(F)::value;
     const TC g = carry_fwd(cD);
     TC p = 1;
 #pragma unroll
     for (int j = 0; j < ZSEG; ++j)
       if (FULL || j < nk) {
-        p *= -g2[-(ptrdiff_t)(k0 + j) * tx];
+        p *= -G2(C, k0 + j);
         v[j] += p * g;
       }
     store(F);
