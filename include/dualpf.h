@@ -73,7 +73,9 @@ enum {
   PF_TAU = 11,     /* weighted polymer stress tau^n = (1+phi)/2 tau_p (Eq. NS12) */
   PF_TAU_OLD = 12,
   PF_G = 13,       /* fine chemical potential G^n (Eq. NS5), read-only */
-  PF_NFIELDS = 14
+  PF_PHI_REM = 14, /* fine, read-only: the rounding remainders of phi^n in FP32
+                      contexts (phi = value + remainder), zeros in PF_FP64     */
+  PF_NFIELDS = 15
 };
 
 /* Step flags for pf_step_ex. */

@@ -122,7 +122,7 @@ def load(path: str = LIB_PATH):
 
 FIELD = {"phi": wl.PHI, "phi_old": wl.PHI_OLD, "u": wl.U, "u_old": wl.U_OLD, "v": wl.V, "v_old": wl.V_OLD,
          "w": wl.W, "w_old": wl.W_OLD, "p": wl.P, "p_old": wl.P_OLD, "theta": wl.THETA, "tau": wl.TAU,
-         "tau_old": wl.TAU_OLD, "G": wl.G_FINE}
+         "tau_old": wl.TAU_OLD, "G": wl.G_FINE, "phi_rem": wl.PHI_REM}
 
 
 class Solver:

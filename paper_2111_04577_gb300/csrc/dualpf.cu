@@ -979,7 +979,7 @@ struct Impl : ImplBase {
     const size_t ncw = (size_t)d.nx * d.ny * (d.nz + 1);
     size_t c = 0;
     switch (f) {
-      case PF_PHI: case PF_PHI_OLD: case PF_G: c = nf; break;
+      case PF_PHI: case PF_PHI_OLD: case PF_G: case PF_PHI_REM: c = nf; break;
       case PF_U: case PF_U_OLD: case PF_P: case PF_P_OLD: c = nc; break;
       case PF_V: case PF_V_OLD: c = d.dim == 3 ? nc : 0; break;
       case PF_W: case PF_W_OLD: c = ncw; break;
@@ -1005,6 +1005,7 @@ struct Impl : ImplBase {
       case PF_P: return {pr[fc]};
       case PF_P_OLD: return {pr[fo]};
       case PF_G: return {G};
+      case PF_PHI_REM: return {philo[pc]};  // null in FP64 contexts (read as zeros)
       case PF_THETA: return std::vector<T*>(theta, theta + ncomp);
       case PF_TAU: return std::vector<T*>(tau[fc], tau[fc] + ncomp);
       case PF_TAU_OLD: return std::vector<T*>(tau[fo], tau[fo] + ncomp);
@@ -1025,7 +1026,7 @@ struct Impl : ImplBase {
 
   void set_field(int f, const void* src, size_t bytes, int on_dev) override {
     flush_polymer();
-    if (f == PF_G) throw ApiError(PF_ERR_ARG, "PF_G is read-only");
+    if (f == PF_G || f == PF_PHI_REM) throw ApiError(PF_ERR_ARG, "PF_G and PF_PHI_REM are read-only");
     copy_field(f, src, bytes, on_dev);
     // phi set from outside carries no remainder
     const size_t nfb = (size_t)d.fnx * d.fny * d.fnz * sizeof(T);
@@ -1056,9 +1057,15 @@ struct Impl : ImplBase {
     if (bytes != cnt * eb) throw ApiError(PF_ERR_ARG, "byte count does not match the field size");
     auto ptrs = field_ptrs(f);
     const size_t per = cnt / ptrs.size();
-    for (size_t q = 0; q < ptrs.size(); ++q)
+    for (size_t q = 0; q < ptrs.size(); ++q) {
+      if (!ptrs[q]) {  // PF_PHI_REM of an FP64 context
+        if (on_dev) PF_CUDA_TRY(cudaMemsetAsync(static_cast<char*>(dst) + q * per * eb, 0, per * eb, st));
+        else std::memset(static_cast<char*>(dst) + q * per * eb, 0, per * eb);
+        continue;
+      }
       PF_CUDA_TRY(cudaMemcpyAsync(static_cast<char*>(dst) + q * per * eb, ptrs[q], per * eb,
                                   on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    }
     PF_CUDA_TRY(cudaStreamSynchronize(st));
   }
 
@@ -1735,7 +1742,7 @@ struct Impl : ImplBase {
   // the six diagnostics in Wide<T> (their derivatives too when T carries them)
   void diagnostics_wide(Wide<T> out[6]) {
     using W = Wide<T>;
-    k_reduce<T><<<nred_blocks, 256, 0, st>>>(phi[pc], d, p, sigma, d.dim == 3 ? d.h : g.ly, wpartial);
+    k_reduce<T><<<nred_blocks, 256, 0, st>>>(phi[pc], d, p, sigma, d.dim == 3 ? d.h : g.ly, wpartial, philo[pc]);
     check_launch();
     std::vector<W> h((size_t)nred_blocks * RED_N);
     PF_CUDA_TRY(cudaMemcpyAsync(h.data(), wpartial, h.size() * sizeof(W), cudaMemcpyDeviceToHost, st));

@@ -16,14 +16,19 @@ constexpr int RED_N = 8;  // sum phi, bulk energy density, wall energy, wetted, 
 constexpr int RGROUP = 8;
 
 // The accumulators are Wide<T>: FP64, or Dual when derivatives are carried.
+// The mass, the sum the method conserves, is accumulated in Wide<T> element by
+// element, and with compensated FP32 storage (lo: the remainders of phi, or
+// null) takes value + remainder: it is the exact sum of the stored field, so
+// a drift it shows is the field's own, not the summation's.
 template <class T>
 __global__ void __launch_bounds__(256) k_reduce(const T* __restrict__ phi, Dims d, Phys p, double sigma, double dy,
-                                                Wide<T>* __restrict__ partial) {
+                                                Wide<T>* __restrict__ partial, const T* __restrict__ lo = nullptr) {
   using W = Wide<T>;
   __shared__ W sh[RED_N][256];
   W acc[RED_N];
 #pragma unroll
   for (int q = 0; q < RED_N; ++q) acc[q] = 0.0;
+  W mass = 0.0;
   const int rows = d.fny * d.fnz, fnx = d.fnx;
   const size_t plane = (size_t)fnx * d.fny;
   const T h = (T)d.h, ih = (T)(1.0 / d.h), ie2 = (T)(1.0 / (p.eta * p.eta)), dyT = (T)dy;
@@ -43,7 +48,8 @@ __global__ void __launch_bounds__(256) k_reduce(const T* __restrict__ phi, Dims 
       const T yj = ((T)j + (T)0.5) * dyT, zk = ((T)k + (T)0.5) * h;
       for (int i = threadIdx.x; i < fnx; i += blockDim.x) {
         const T c = row[i];
-        ga[0] += c;
+        mass += (W)c;
+        if (lo) mass += (W)lo[(size_t)r * fnx + i];
         const T gx = (c - row[i == 0 ? fnx - 1 : i - 1]) * ih;
         T e = (T)0.5 * gx * gx;
         if (d.dim == 3) {
@@ -69,8 +75,9 @@ __global__ void __launch_bounds__(256) k_reduce(const T* __restrict__ phi, Dims 
       }
     }
 #pragma unroll
-    for (int q = 0; q < RED_N; ++q) acc[q] += (W)ga[q];
+    for (int q = 1; q < RED_N; ++q) acc[q] += (W)ga[q];
   }
+  acc[0] = mass;
 #pragma unroll
   for (int q = 0; q < RED_N; ++q) sh[q][threadIdx.x] = acc[q];
   __syncthreads();

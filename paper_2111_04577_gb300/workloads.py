@@ -30,7 +30,7 @@ from dataclasses import dataclass, field, asdict
 import numpy as np
 
 # field identifiers shared by the C-ABI, the binding and the tests
-PHI, PHI_OLD, U, U_OLD, V, V_OLD, W, W_OLD, P, P_OLD, THETA, TAU, TAU_OLD, G_FINE = range(14)
+PHI, PHI_OLD, U, U_OLD, V, V_OLD, W, W_OLD, P, P_OLD, THETA, TAU, TAU_OLD, G_FINE, PHI_REM = range(15)
 
 
 @dataclass
