@@ -157,6 +157,19 @@ __device__ __forceinline__ void jacobi_rot_sym_f(float (&dg)[N], float (&of)[N =
 // orthogonal to it (one exact rotation), so a near-double eigenvalue costs no
 // accuracy.  On entry (dg, of) hold A, on exit dg the eigenvalues and V the
 // eigenvectors in columns.
+// FP32 forms of the closed form's few non-FMA steps (a fast divide, the
+// hardware cosine): they touch only the isolated root, whose eigenvalue is then
+// taken again as a Rayleigh quotient, and the rotation of the pair, which stays
+// orthogonal by construction; FP64 keeps the exact functions.
+template <class T>
+__device__ __forceinline__ T e3_div(T a, T b) { return a / b; }
+template <>
+__device__ __forceinline__ float e3_div<float>(float a, float b) { return __fdividef(a, b); }
+template <class T>
+__device__ __forceinline__ T e3_cos(T x) { return cos(x); }
+template <>
+__device__ __forceinline__ float e3_cos<float>(float x) { return __cosf(x); }
+
 template <class T>
 __device__ __forceinline__ void eig_sym3_closed(T (&dg)[3], T (&of)[3], T (&V)[3][3]) {
   const T m = (dg[0] + dg[1] + dg[2]) * (T)(1.0 / 3.0);
@@ -176,20 +189,20 @@ __device__ __forceinline__ void eig_sym3_closed(T (&dg)[3], T (&of)[3], T (&V)[3
     dg[0] = dg[1] = dg[2] = m;
     return;
   }
-  const T isc = (T)1 / sc;
+  const T isc = e3_div<T>((T)1, sc);
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int c = 0; c < 3; ++c) b[a][c] *= isc;
   const T p2 = (b[0][0] * b[0][0] + b[1][1] * b[1][1] + b[2][2] * b[2][2] +
                 (T)2 * (b[0][1] * b[0][1] + b[0][2] * b[0][2] + b[1][2] * b[1][2])) * (T)(1.0 / 6.0);
-  const T p = sqrt(p2), ip = (T)1 / p;
+  const T ip = rsqrt(p2), p = p2 * ip;
   const T det = b[0][0] * (b[1][1] * b[2][2] - b[1][2] * b[1][2]) - b[0][1] * (b[0][1] * b[2][2] - b[1][2] * b[0][2]) +
                 b[0][2] * (b[0][1] * b[1][2] - b[1][1] * b[0][2]);
   T r = (T)0.5 * det * ip * ip * ip;
   r = fmin(fmax(r, (T)-1), (T)1);
   const T psi = acos(r) * (T)(1.0 / 3.0);
-  const T lam = (T)2 * p * cos(psi < (T)(3.14159265358979323846 / 6.0) ? psi : psi + (T)(4.0 * 3.14159265358979323846 / 3.0));
+  const T lam = (T)2 * p * e3_cos<T>(psi < (T)(3.14159265358979323846 / 6.0) ? psi : psi + (T)(4.0 * 3.14159265358979323846 / 3.0));
   // eigenvector of lam: the largest cross product of two rows of B - lam I
   T r0[3] = {b[0][0] - lam, b[0][1], b[0][2]}, r1[3] = {b[0][1], b[1][1] - lam, b[1][2]},
     r2[3] = {b[0][2], b[1][2], b[2][2] - lam};
@@ -234,12 +247,14 @@ __device__ __forceinline__ void eig_sym3_closed(T (&dg)[3], T (&of)[3], T (&V)[3
   };
   const T lv = quad(v, v), a11 = quad(u, u), a12 = quad(u, w), a22 = quad(w, w);
   // one rotation diagonalises the 2 x 2 block [[a11, a12], [a12, a22]]
+  // t = tan of the rotation angle, g/(|h| + sqrt(h^2 + g^2)) sgn h (h = a22 - a11,
+  // g = 2 a12), the smaller root, without overflow
   T cs = (T)1, sn = (T)0, t = (T)0;
   if (a12 != (T)0) {
-    const T th = (a22 - a11) / ((T)2 * a12);
-    const T ath = fabs(th);
-    t = ath > (T)1e15 ? (T)0.5 / ath : (T)1 / (ath + sqrt(ath * ath + (T)1));
-    if (th < (T)0) t = -t;
+    const T hh = a22 - a11, gg = (T)2 * a12;
+    const T aa = hh * hh + gg * gg;
+    t = e3_div<T>(gg, fabs(hh) + aa * rsqrt(aa));
+    if (hh < (T)0) t = -t;
     cs = rsqrt(t * t + (T)1);
     sn = t * cs;
   }
