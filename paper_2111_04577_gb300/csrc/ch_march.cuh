@@ -698,14 +698,16 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
   // owned phi^n and phi^{n-1} of the plane being formed, read one plane ahead
   // (an L2 hit: the plane was staged three planes earlier)
   // (with compensated storage also the remainders' difference dl = lo - ln)
-  float4 an = make_float4(0.f, 0.f, 0.f, 0.f), bo = an, dl = an;
+  // (the remainders are kept as loaded and differenced where R uses them, so that
+  // no warp waits for these loads at the end of the plane that issues them)
+  float4 an = make_float4(0.f, 0.f, 0.f, 0.f), bo = an, la = an, lb = an;
   auto own_load = [&](int zz) {
     const size_t o = (size_t)zz * plane + gof;
     an = *reinterpret_cast<const float4*>(f.pn + o);
     bo = *reinterpret_cast<const float4*>(f.po + o);
     if (f.ln) {
-      const float4 a = *reinterpret_cast<const float4*>(f.ln + o), b = *reinterpret_cast<const float4*>(f.lo + o);
-      dl = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, b.w - a.w);
+      la = *reinterpret_cast<const float4*>(f.ln + o);
+      lb = *reinterpret_cast<const float4*>(f.lo + o);
     }
   };
   if (act) own_load(zb);
@@ -786,7 +788,8 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
     const float mzpv[4] = {mzp4.x, mzp4.y, mzp4.z, mzp4.w}, mzmv[4] = {mzm4.x, mzm4.y, mzm4.z, mzm4.w};
     // phi^{n-1} - phi^n: the stored values' difference first (exact when they are
     // close), then the remainders' (zero without compensated storage)
-    const float dv[4] = {(bo.x - an.x) + dl.x, (bo.y - an.y) + dl.y, (bo.z - an.z) + dl.z, (bo.w - an.w) + dl.w};
+    const float dv[4] = {(bo.x - an.x) + (lb.x - la.x), (bo.y - an.y) + (lb.y - la.y), (bo.z - an.z) + (lb.z - la.z),
+                         (bo.w - an.w) + (lb.w - la.w)};
     float awv[4] = {0.f, 0.f, 0.f, 0.f};
     if constexpr (AW) {
       if (act) {
