@@ -652,6 +652,11 @@ def main():
         tz = time_steps(sz, stream, 5)
         sz.close()
         del sz
+        sf, ff = run_fields(binding.PF_MIXED_Z2F, phi0_f)
+        sf.step(2)
+        tf = time_steps(sf, stream, 5)
+        sf.close()
+        del sf
         sd, fd = run_fields(binding.PF_FP64, phi0)
         sd.step(2)
         t64 = time_steps(sd, stream, 5)
@@ -665,6 +670,10 @@ def main():
         extra["mixed_z64_path"] = {"what": "mixed with FP64 wall-normal eliminations",
                                    "value": g.fine_cells() * 5 / tz, "ms_per_step": tz / 5 * 1e3,
                                    "err_vs_fp64_after_steps": field_err(fz, fd)}
+        extra["mixed_z2f_path"] = {"what": "mixed with double-float (48-bit significand) wall-normal eliminations",
+                                   "value": g.fine_cells() * 5 / tf, "ms_per_step": tf / 5 * 1e3,
+                                   "err_vs_fp64_after_steps": field_err(ff, fd),
+                                   "err_vs_z64_after_steps": field_err(ff, fz)}
         # single resolution: CSR (phi on the coarse mesh) and RSR (all fields on the fine mesh)
         csr = wl.Grid(g.nx, g.ny, g.nz, g.lx, g.ly, g.lz, 0)
         rsr = wl.Grid(2 * g.nx, 2 * g.ny, 2 * g.nz, g.lx, g.ly, g.lz, 0)

@@ -35,7 +35,10 @@
  *  - Element type: a context computes and stores in double (PF_FP64) or in
  *    float with FP64 kept in the named places (PF_MIXED: the contact-line
  *    flux, the pressure zero mode and the global reductions; PF_MIXED_Z64
- *    adds the wall-normal tridiagonal eliminations of every transform solve).
+ *    adds the wall-normal tridiagonal eliminations of every transform solve;
+ *    PF_MIXED_Z2F runs those eliminations in double-float instead, two FP32
+ *    words per value with error-free transformations: a 48-bit significand,
+ *    relative rounding about 2^-47 against FP64's 2^-53, on the FP32 pipes).
  *    pf_set_fields and pf_get_fields move elements of the context's storage
  *    type: double for PF_FP64, float otherwise (see pf_field_info).
  */
@@ -59,7 +62,7 @@ enum {
   PF_ERR_NOMEM = -7         /* device allocation failed                       */
 };
 
-enum { PF_FP64 = 0, PF_MIXED = 1, PF_MIXED_Z64 = 2 };
+enum { PF_FP64 = 0, PF_MIXED = 1, PF_MIXED_Z64 = 2, PF_MIXED_Z2F = 3 };
 
 /* Field identifiers for pf_set_fields / pf_get_fields. */
 enum {
@@ -93,7 +96,7 @@ typedef struct pf_ctx pf_ctx;
 typedef struct {
   int nx, ny, nz;
   double lx, ly, lz;
-  int precision; /* PF_FP64 | PF_MIXED | PF_MIXED_Z64 */
+  int precision; /* PF_FP64 | PF_MIXED | PF_MIXED_Z64 | PF_MIXED_Z2F */
   int dual;
 } pf_grid_desc;
 
@@ -236,7 +239,7 @@ void pf_batch_destroy(pf_batch* b);
  * It computes the six FP64 reductions of pf_diagnostics from a phase field
  * the caller already holds on the current device -- phi_device points to the
  * fine mesh of *g in the element type of g->precision (double for PF_FP64,
- * float for PF_MIXED and PF_MIXED_Z64), layout as above -- with no context and no allocation
+ * float for the mixed precisions), layout as above -- with no context and no allocation
  * of any kind.  Its scratch is one file-scope device array of 1 MiB that
  * every GPU which loads the library holds until the process exits; the
  * phase field may have at most 134,217,728 fine cells, larger fields are

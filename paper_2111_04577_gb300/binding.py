@@ -17,7 +17,7 @@ from . import workloads as wl
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libdualpf.so")
 
-PF_FP64, PF_MIXED, PF_MIXED_Z64 = 0, 1, 2
+PF_FP64, PF_MIXED, PF_MIXED_Z64, PF_MIXED_Z2F = 0, 1, 2, 3
 PF_STEP_CH_ONLY, PF_STEP_NO_GRAPH = 1, 2
 
 ERRORS = {-1: "PF_ERR_ARG", -2: "PF_ERR_DISCRIMINANT", -3: "PF_ERR_UNSUPPORTED", -4: "PF_ERR_NONFINITE",

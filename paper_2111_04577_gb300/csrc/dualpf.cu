@@ -1256,7 +1256,7 @@ struct Impl : ImplBase {
   void adjoint(int nsteps, int K, int which, double out[3], void* dphi0, int on_dev) override {
     if constexpr (IsDual<T>::value) {  // derivative-carrying steps have no reverse sweep
       (void)nsteps, (void)K, (void)which, (void)out, (void)dphi0, (void)on_dev;
-      throw ApiError(PF_ERR_UNSUPPORTED, "the adjoint runs on PF_FP64, PF_MIXED and PF_MIXED_Z64 contexts");
+      throw ApiError(PF_ERR_UNSUPPORTED, "the adjoint runs on PF_FP64 and the mixed contexts");
     } else {
       flush_polymer();
       if (!have_params) throw ApiError(PF_ERR_ARG, "pf_set_params must precede pf_adjoint");
@@ -1431,7 +1431,7 @@ struct Impl : ImplBase {
   void adjoint_coupled(int nsteps, int K, int which, double out[4], void* dphi0, int on_dev) override {
     if constexpr (IsDual<T>::value) {
       (void)nsteps, (void)K, (void)which, (void)out, (void)dphi0, (void)on_dev;
-      throw ApiError(PF_ERR_UNSUPPORTED, "the adjoint runs on PF_FP64, PF_MIXED and PF_MIXED_Z64 contexts");
+      throw ApiError(PF_ERR_UNSUPPORTED, "the adjoint runs on PF_FP64 and the mixed contexts");
     } else {
       flush_polymer();
       if (!have_params) throw ApiError(PF_ERR_ARG, "pf_set_params must precede pf_adjoint_ex");
@@ -2057,8 +2057,9 @@ int pf_init_grid(pf_ctx** out, const pf_grid_desc* g, void* stream) {
     const double dx = g->lx / g->nx;
     if (std::fabs(g->lz / g->nz - dx) > 1e-9 * dx || (g->ny > 1 && std::fabs(g->ly / g->ny - dx) > 1e-9 * dx))
       throw pf::ApiError(PF_ERR_ARG, "cells must be cubes: lx/nx = ly/ny = lz/nz");
-    if (g->precision != PF_FP64 && g->precision != PF_MIXED && g->precision != PF_MIXED_Z64)
-      throw pf::ApiError(PF_ERR_ARG, "precision must be PF_FP64, PF_MIXED or PF_MIXED_Z64");
+    if (g->precision != PF_FP64 && g->precision != PF_MIXED && g->precision != PF_MIXED_Z64 &&
+        g->precision != PF_MIXED_Z2F)
+      throw pf::ApiError(PF_ERR_ARG, "precision must be PF_FP64, PF_MIXED, PF_MIXED_Z64 or PF_MIXED_Z2F");
     if (g->nx % 2 || (g->ny > 1 && g->ny % 2)) throw pf::ApiError(PF_ERR_UNSUPPORTED, "nx and ny (3D) must be even");
     for (int n : {g->nx, g->ny, g->nz})
       if (!pf::smooth(n)) throw pf::ApiError(PF_ERR_UNSUPPORTED, "sizes must be 2^a 3^b 5^c 7^d");
@@ -2070,6 +2071,7 @@ int pf_init_grid(pf_ctx** out, const pf_grid_desc* g, void* stream) {
     }
     if (g->precision == PF_FP64) ctx->impl.reset(new pf::Impl<double, double>(*g, ctx->stream));
     else if (g->precision == PF_MIXED_Z64) ctx->impl.reset(new pf::Impl<float, double>(*g, ctx->stream));
+    else if (g->precision == PF_MIXED_Z2F) ctx->impl.reset(new pf::Impl<float, pf::DF>(*g, ctx->stream));
     else ctx->impl.reset(new pf::Impl<float, float>(*g, ctx->stream));
   });
   if (rc != PF_OK) {

@@ -48,8 +48,9 @@ extern "C" int pf_diagnostics_noalloc(const pf_grid_desc* g, const pf_params* pr
   auto fail = [](int code, const char*) { return code; };
   if (!g || !prm || !phi_device || !out) return fail(PF_ERR_ARG, "null argument");
   if (g->nx < 2 || g->ny < 1 || g->nz < 2 || !(g->lx > 0)) return fail(PF_ERR_ARG, "bad grid");
-  // PF_MIXED_Z64 stores phi as float, like PF_MIXED
-  if (g->precision != PF_FP64 && g->precision != PF_MIXED && g->precision != PF_MIXED_Z64)
+  // PF_MIXED_Z64 and PF_MIXED_Z2F store phi as float, like PF_MIXED
+  if (g->precision != PF_FP64 && g->precision != PF_MIXED && g->precision != PF_MIXED_Z64 &&
+      g->precision != PF_MIXED_Z2F)
     return fail(PF_ERR_ARG, "bad precision");
   if (!(prm->eta > 0) || !(prm->sigma > 0)) return fail(PF_ERR_ARG, "eta and sigma must be > 0");
   Dims d{};

@@ -27,6 +27,7 @@
 #include <cstddef>
 #include <type_traits>
 
+#include "df.cuh"
 #include "spectral.cuh"
 
 namespace pf {
@@ -37,6 +38,7 @@ constexpr int ZSEG = 16;
 template <class TC>
 __device__ __forceinline__ TC zs_val(TC x) { return x; }
 __device__ __forceinline__ double zs_val(Dual x) { return x.v; }
+__device__ __forceinline__ double zs_val(DF x) { return (double)x; }
 
 template <class TC>
 __device__ __forceinline__ TC zs_exp2(TC x) { return exp2(x); }
@@ -98,6 +100,7 @@ __global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 2 : 1) k_zsolve_seg(cpx
   TC* f1 = reinterpret_cast<TC*>(smraw);
   TC* f2 = dual ? f1 + (size_t)R * tx : f1;
   TC* car = f1 + (size_t)R * tx * (dual ? 2 : 1);  // [4][2][S][L]
+  TC* ccol = car + (size_t)8 * S * L;               // (8-byte factors) [2][tx][6], see below
   const int k0 = s * ZSEG;
   const int nk = max(0, min(ZSEG, R - k0));
   // ---- loads first: the rows of this lane, in flight during the factor phase ----
@@ -139,35 +142,83 @@ __global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 2 : 1) k_zsolve_seg(cpx
     return k >= (S)R ? R : (int)k;
   };
   // stores the factors of this lane's rows; returns the convergence row kc and 1/l1.
-  // (Only FP64 factors skip the division and take the constant passes: there an
-  // FP64 division costs far more than the registers the extra paths take; the
-  // FP32 form would spill.)
-  constexpr bool kConst = sizeof(TC) == 8;
-  auto factors = [&](TC sg, TC* f, TC& il) {
-    const LuClosed<TC> lu(R, zs.bc, sg);
-    const int kc = kConst ? conv_row(lu) : R;
-    il = lu.il1;
-    const TC rho = zs_exp2<TC>(lu.lr), rho2 = rho * rho;
-    TC pk = zs_exp2<TC>((TC)(k0 + part) * lu.lr);  // rho^k
+  // (Only 8-byte factors -- FP64, double-float -- skip the division and take the
+  // constant passes: there a division costs far more than the registers the extra
+  // paths take; the FP32 form would spill.  They also form a column's constants
+  // once, in one thread, and every segment its rho^k by powers of rho: the
+  // closed form's square root, logarithm and exponentials run at the FP64 rate
+  // and would otherwise be repeated by all segments of the column.)
+  constexpr bool kConst = sizeof(TC) == 8;  // FP64 and double-float
+  if constexpr (kConst) {
+    if (s == 0 && part == 0)
+      for (int w = 0; w < (dual ? 2 : 1); ++w) {
+        const LuClosed<TC> lu(R, zs.bc, w == 0 ? sg1 : sg2);
+        TC* cst = ccol + ((size_t)w * tx + c) * 6;
+        cst[0] = lu.il1;
+        cst[1] = lu.beta;
+        cst[2] = zs_exp2<TC>(lu.lr);  // rho
+        cst[3] = lu.d0;
+        cst[4] = R == 1 ? (TC)1 / lu.d0 : (TC)1 / (lu.d0 - lu.interior(R - 2));  // the last row
+        cst[5] = (TC)conv_row(lu);
+      }
+    __syncthreads();
+  }
+  auto ipow = [](TC x, int n) {
+    TC r = (TC)1;
+    while (n) {
+      if (n & 1) r *= x;
+      x *= x;
+      n >>= 1;
+    }
+    return r;
+  };
+  auto factors = [&](TC sg, TC* f, TC& il, int w) {
+    TC beta, rho, d0, mlast;
+    int kc;
+    if constexpr (kConst) {
+      const TC* cst = ccol + ((size_t)w * tx + c) * 6;
+      il = cst[0];
+      beta = cst[1];
+      rho = cst[2];
+      d0 = cst[3];
+      mlast = cst[4];
+      kc = (int)zs_val(cst[5]);
+    } else {
+      const LuClosed<TC> lu(R, zs.bc, sg);
+      il = lu.il1;
+      beta = lu.beta;
+      rho = zs_exp2<TC>(lu.lr);
+      d0 = lu.d0;
+      mlast = R == 1 ? (TC)1 / lu.d0 : (TC)1 / (lu.d0 - lu.interior(R - 2));
+      kc = R;
+    }
+    (void)d0;
+    const TC rho2 = rho * rho;
+    TC pk;  // rho^k
+    if constexpr (kConst) pk = ipow(rho, k0 + part);
+    else {
+      const LuClosed<TC> lu(R, zs.bc, sg);
+      pk = zs_exp2<TC>((TC)(k0 + part) * lu.lr);
+    }
     for (int j = part; j < nk; j += 2) {
       const int k = k0 + j;
       TC m;
-      if (R == 1) m = (TC)1 / lu.d0;
-      else if (k < R - 1) {
-        if (k >= kc) m = lu.il1;
-        else m = lu.il1 * ((TC)1 + lu.beta * pk) / ((TC)1 + lu.beta * pk * rho);
+      if (k < R - 1) {
+        if (k >= kc) m = il;
+        else m = il * ((TC)1 + beta * pk) / ((TC)1 + beta * pk * rho);
+      } else {
+        m = mlast;
       }
-      else m = (TC)1 / (lu.d0 - lu.interior(R - 2));
       f[(size_t)k * tx + c] = m;
       pk *= rho2;
     }
     return kc;
   };
   TC il1, il2;
-  const int kc1 = factors(sg1, f1, il1);
+  const int kc1 = factors(sg1, f1, il1, 0);
   int kc2 = kc1;
   il2 = il1;
-  if (dual) kc2 = factors(sg2, f2, il2);
+  if (dual) kc2 = factors(sg2, f2, il2, 1);
   // segments whose rows all take the constant factor, per solve (solve 2 reads
   // its factors mirrored, g_k = m2_{R-1-k}), decided for the whole warp so that
   // the passes below do not diverge
@@ -349,7 +400,7 @@ __global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 2 : 1) k_zsolve_seg(cpx
 template <class TC>
 inline size_t zsolve_seg_smem(int rows, int tx, bool dual) {
   const int S = (rows + ZSEG - 1) / ZSEG;
-  return sizeof(TC) * ((size_t)rows * tx * (dual ? 2 : 1) + (size_t)8 * S * 2 * tx);
+  return sizeof(TC) * ((size_t)rows * tx * (dual ? 2 : 1) + (size_t)8 * S * 2 * tx + (sizeof(TC) == 8 ? 12 * tx : 0));
 }
 
 }  // namespace pf

@@ -142,7 +142,7 @@ def test_config1_fp64_full_run():
     assert np.allclose(dg["centroid"], ob.centroid(ref.phi, g), rtol=1e-10, atol=1e-12)
 
 
-@pytest.mark.parametrize("prec", [binding.PF_MIXED, binding.PF_MIXED_Z64])
+@pytest.mark.parametrize("prec", [binding.PF_MIXED, binding.PF_MIXED_Z64, binding.PF_MIXED_Z2F])
 def test_config1_mixed_full_run(prec):
     """Mixed paths on config 1: 2e-4 max-abs on phi, 1e-3 relative on u, w."""
     w = wl.config("c1")
@@ -185,7 +185,8 @@ def test_mass_conservation_gpu_fp64_and_mixed():
     w = wl.scaled(wl.config("c2"), 32, 16)
     g = w.grid
     phi0 = wl.initial_phi(w)
-    for prec, tol in ((binding.PF_FP64, 1e-13), (binding.PF_MIXED, 1e-9), (binding.PF_MIXED_Z64, 1e-9)):
+    for prec, tol in ((binding.PF_FP64, 1e-13), (binding.PF_MIXED, 1e-9), (binding.PF_MIXED_Z64, 1e-9),
+                      (binding.PF_MIXED_Z2F, 1e-9)):
         s = binding.Solver(g, w.params, prec)
         s.load_state(phi0)
         m0 = s.diagnostics()["mass"]
@@ -194,7 +195,7 @@ def test_mass_conservation_gpu_fp64_and_mixed():
         assert abs(m1 - m0) < tol * np.sum(np.abs(phi0)) * g.h ** 2, prec
 
 
-@pytest.mark.parametrize("prec", [binding.PF_MIXED, binding.PF_MIXED_Z64, binding.PF_FP64])
+@pytest.mark.parametrize("prec", [binding.PF_MIXED, binding.PF_MIXED_Z64, binding.PF_MIXED_Z2F, binding.PF_FP64])
 def test_mixed_mass_is_the_stored_fields_own_sum(prec):
     """The FP64 mass reduction of every path is the exact sum of the stored
     field: the compensated FP32 phi's values plus remainders (PF_PHI_REM),
@@ -356,7 +357,7 @@ def test_long_z_lines_vs_oracle(dim, nx, nz):
         ref.step()
     names = ["u", "w", "p"] + (["v"] if dim == 3 else [])
     refs = {"u": ref.vel[0], "v": ref.vel[1] if dim == 3 else None, "w": ref.vel[2], "p": ref.p}
-    for prec in (binding.PF_FP64, binding.PF_MIXED, binding.PF_MIXED_Z64):
+    for prec in (binding.PF_FP64, binding.PF_MIXED, binding.PF_MIXED_Z64, binding.PF_MIXED_Z2F):
         s = binding.Solver(g, w.params, prec)
         s.load_state(phi0, vel)
         s.step(3)
@@ -530,7 +531,7 @@ def test_dynamic_contact_angle_fp64_and_mixed_vs_oracle(cfg, nx, nz):
     ref = ostep.State(g, w.params.as_dict(), phi0, vel0=vel)
     for _ in range(n):
         ref.step()
-    for prec in (binding.PF_FP64, binding.PF_MIXED, binding.PF_MIXED_Z64):
+    for prec in (binding.PF_FP64, binding.PF_MIXED, binding.PF_MIXED_Z64, binding.PF_MIXED_Z2F):
         s = binding.Solver(g, w.params, prec)
         s.load_state(phi0, vel)
         s.step(n)
@@ -579,3 +580,34 @@ def test_dynamic_contact_angle_ch_only_and_errors():
     with pytest.raises(binding.PFError) as e:
         binding.Solver(g, wl.Params(**{**w.params.as_dict(), "dw": -1.0}), binding.PF_FP64)
     assert e.value.code == -1
+
+
+
+def test_double_float_eliminations_track_the_fp64_ones():
+    """PF_MIXED_Z2F runs the wall-normal eliminations in double-float (two FP32
+    words, 48-bit significand).  After one full step from a seeded state, the
+    only arithmetic that differs between PF_MIXED, PF_MIXED_Z64 and
+    PF_MIXED_Z2F is those eliminations, whose results are stored in FP32: the
+    double-float results round to the same FP32 values as the FP64 ones except
+    at ties, while FP32 eliminations lose digits in the ill-conditioned low
+    modes of the pressure solve.  So the Z2F fields sit at least ten times
+    closer to the Z64 ones than the PF_MIXED fields do."""
+    w = wl.scaled(wl.config("c2"), 64, 64)
+    g = w.grid
+    phi0 = wl.initial_phi(w)
+    vel = wl.random_velocity(g, 17, 0.2)
+    out = {}
+    for prec in (binding.PF_MIXED_Z64, binding.PF_MIXED_Z2F, binding.PF_MIXED):
+        s = binding.Solver(g, w.params, prec)
+        s.load_state(phi0, vel)
+        s.step(1)
+        out[prec] = {n: s.coarse(n) for n in ("u", "w", "p")}
+        out[prec]["phi"] = s.fine("phi") + s.fine("phi_rem")
+        s.close()
+    z64 = out[binding.PF_MIXED_Z64]
+    dist = {prec: max(np.max(np.abs(out[prec][n] - z64[n])) / max(np.max(np.abs(z64[n])), 1e-300)
+                      for n in ("u", "w", "p"))
+            for prec in (binding.PF_MIXED_Z2F, binding.PF_MIXED)}
+    print("distance to the FP64-elimination fields:", dist)
+    assert dist[binding.PF_MIXED] > 0
+    assert dist[binding.PF_MIXED_Z2F] <= 0.1 * dist[binding.PF_MIXED], dist

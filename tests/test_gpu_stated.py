@@ -139,11 +139,13 @@ def test_c2_stated_steps_vs_oracle(oracle):
     """The 2D viscoelastic droplet as stated: full size, from rest, 2000 steps;
     FP64 at 1e-10, both mixed paths at the mixed tolerances."""
     w = wl.config("c2")
-    res = {p: gpu_fields(w, p, w.steps) for p in (binding.PF_FP64, binding.PF_MIXED, binding.PF_MIXED_Z64)}
+    res = {p: gpu_fields(w, p, w.steps) for p in (binding.PF_FP64, binding.PF_MIXED, binding.PF_MIXED_Z64,
+                                                   binding.PF_MIXED_Z2F)}
     ref = oracle["c2_stated"].result()
     check_fp64(res[binding.PF_FP64], ref, 2)
     check_mixed(res[binding.PF_MIXED], ref, 2)
     check_mixed(res[binding.PF_MIXED_Z64], ref, 2)
+    check_mixed(res[binding.PF_MIXED_Z2F], ref, 2)
 
 
 @pytest.mark.slow
@@ -154,7 +156,7 @@ def test_3d_stated_steps_mixed_vs_fp64(cfg):
     bench's launch configuration against the FP64 GPU path."""
     w = wl.config(cfg)
     d = gpu_fields(w, binding.PF_FP64, w.steps)
-    for prec in (binding.PF_MIXED, binding.PF_MIXED_Z64):
+    for prec in (binding.PF_MIXED, binding.PF_MIXED_Z64, binding.PF_MIXED_Z2F):
         m = gpu_fields(w, prec, w.steps, tune=prec == binding.PF_MIXED)
         check_mixed(m, d, 3)
         if prec == binding.PF_MIXED:

@@ -29,7 +29,7 @@ def _close(a, b, scale):
     return abs(a - b) <= TOL * (abs(b) + scale)
 
 
-@pytest.mark.parametrize("prec", [binding.PF_FP64, binding.PF_MIXED, binding.PF_MIXED_Z64])
+@pytest.mark.parametrize("prec", [binding.PF_FP64, binding.PF_MIXED, binding.PF_MIXED_Z64, binding.PF_MIXED_Z2F])
 @pytest.mark.parametrize("case", ["2d", "3d"])
 def test_noalloc_diagnostics_match_context_twice(prec, case):
     import torch
