@@ -161,14 +161,14 @@ __global__ void __launch_bounds__(MarchTile::NT, MINB) k_ch_rhs_march(const Fine
       lap = (lap + czp + czm - 2 * c0) * q.ih2;
       T B = 0;
       if (gz == 0) {
-        const Wide<T> g = wall_g(q.cbot, (Wide<T>)c0, (Wide<T>)czp, p.eta);
+        const Wide<T> g = wall_g(q.gbot, (Wide<T>)c0, (Wide<T>)czp);
         if (mcol[k] >= 0) gwall[mcol[k]] = g;
-        B += (T)(g / d.h);
+        B += (T)(g * q.ihw);
       }
       if (gz == fnz - 1) {
-        const Wide<T> g = wall_g(q.ctop, (Wide<T>)c0, (Wide<T>)czm, p.eta);
+        const Wide<T> g = wall_g(q.gtop, (Wide<T>)c0, (Wide<T>)czm);
         if (mcol[k] >= 0) gwall[plane + mcol[k]] = g;
-        B += (T)(g / d.h);
+        B += (T)(g * q.ihw);
       }
       mm[e] = c0 * (c0 * c0 - 1) * q.ie2 - (lap + B);
     }
@@ -613,14 +613,17 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
     const float* pm = ps + sm1 * TL::SPF + 4;
     const float* pc = ps + s0 * TL::SPF + 4;
     const float* pq = ps + sp1 * TL::SPF + 4;
+    static_assert(TL::KM == 2, "one full pass of the threads and one partial pass");
 #pragma unroll
     for (int k = 0; k < TL::KM; ++k) {
-      // whole warps take part (the x neighbours come by shuffle); lanes past
-      // the end repeat the last chunk and store nothing
-      const int e0 = t + k * TL::NT;
-      if (e0 - (t & 31) >= TL::NMC) continue;  // warp-uniform
-      const bool valid = e0 < TL::NMC;
-      const int e = valid ? e0 : TL::NMC - 1;
+      // whole warps take part (the x neighbours come by shuffle).  The partial
+      // second pass runs on the highest warps (the chunks NMC - NT + t), so that
+      // it does not fall on the warps that hold a second velocity-box element;
+      // its lanes below chunk NT repeat chunks of the first pass and store nothing
+      const int e0 = k == 0 ? t : t + (TL::NMC - TL::NT);
+      if (k > 0 && (t | 31) + (TL::NMC - TL::NT) < TL::NT) continue;  // warp-uniform
+      const bool valid = k == 0 || e0 >= TL::NT;
+      const int e = e0;
       float4* mo = reinterpret_cast<float4*>(mm) + e;
       if (gz < 0 || gz >= fnz) {
         if (valid) *mo = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -659,14 +662,14 @@ __global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineVi
           const bool own = valid && rown && gx >= x0 && gx < x0 + TL::TX && gx < fnx;
           const size_t col = (size_t)gy * fnx + gx;
           if (gz == 0) {
-            const double g = wall_g(q.cbot, (double)cv[i + 1], (double)zpv[i], p.eta);
+            const double g = wall_g(q.gbot, (double)cv[i + 1], (double)zpv[i]);
             if (own) gwall[col] = g;
-            outv[i] -= (float)(g / d.h);
+            outv[i] -= (float)(g * q.ihw);
           }
           if (gz == fnz - 1) {
-            const double g = wall_g(q.ctop, (double)cv[i + 1], (double)zmv[i], p.eta);
+            const double g = wall_g(q.gtop, (double)cv[i + 1], (double)zmv[i]);
             if (own) gwall[plane + col] = g;
-            outv[i] -= (float)(g / d.h);
+            outv[i] -= (float)(g * q.ihw);
           }
         }
       }

@@ -133,14 +133,14 @@ __device__ __forceinline__ void k_ch_rhs_b(const FineView<T> f, const CoarseVel<
       const bool own = mx >= 1 && mx <= TL::TX && (DIM == 2 || (my >= 1 && my <= TL::TY));
       const int gx = x0 - 1 + mx, gy = DIM == 3 ? y0 - 1 + my : 0;
       if (gz == 0) {
-        const Wide<T> g = wall_g(q.cbot, (Wide<T>)c0, (Wide<T>)czp, p.eta);
+        const Wide<T> g = wall_g(q.gbot, (Wide<T>)c0, (Wide<T>)czp);
         if (own && gx < fnx && gy < fny) gwall[(size_t)gy * fnx + gx] = g;
-        B += (T)(g / d.h);
+        B += (T)(g * q.ihw);
       }
       if (gz == fnz - 1) {
-        const Wide<T> g = wall_g(q.ctop, (Wide<T>)c0, (Wide<T>)czm, p.eta);
+        const Wide<T> g = wall_g(q.gtop, (Wide<T>)c0, (Wide<T>)czm);
         if (own && gx < fnx && gy < fny) gwall[plane + (size_t)gy * fnx + gx] = g;
-        B += (T)(g / d.h);
+        B += (T)(g * q.ihw);
       }
       ms[e] = c0 * (c0 * c0 - 1) * q.ie2 - (lap + B);
     }

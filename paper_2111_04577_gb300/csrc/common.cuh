@@ -82,7 +82,8 @@ struct PhysT {
   T ie2, lam;                         // 1/eta^2, lambda
   T dt, ilh, wtau;                    // dt, 1/lambda_H, mu_p/lambda_H
   T ag;                               // Giesekus mobility alpha (0: Oldroyd-B)
-  Wide<T> cbot, ctop;                 // cos(theta_s) of the two walls (FP64, or carrying a derivative)
+  Wide<T> gbot, gtop;                 // cos(theta_s)/(sqrt(2) eta) of the two walls (FP64, or carrying a derivative)
+  Wide<T> ihw;                        // 1/h in FP64: the wall flux enters R and mu* as g/h
   // approach 1 (Eq. NS11): lambda_H, mu_p and alpha of the two phases, mixed
   // per coarse centre by the restricted phi; ilh, wtau and ag above unused
   T lh1, lh2, mp1, mp2, ag2;

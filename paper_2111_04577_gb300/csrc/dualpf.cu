@@ -896,8 +896,9 @@ struct Impl : ImplBase {
     r.mp1 = (TT)p.mu_p1;
     r.mp2 = (TT)p.mu_p2;
     r.ag2 = (TT)p.alpha_g2;
-    r.cbot = p.cos_bot;
-    r.ctop = p.cos_top;
+    r.gbot = p.cos_bot / (1.4142135623730951 * p.eta);
+    r.gtop = p.cos_top / (1.4142135623730951 * p.eta);
+    r.ihw = 1.0 / d.h;
     return r;
   }
   void set_params(const pf_params& prm) override {

@@ -42,7 +42,7 @@ __global__ void k_robin_wall(FineView<T> f, Wide<T>* __restrict__ gE, Wide<T>* _
   const size_t cols = plane;
   for (int wall = 0; wall < 2; ++wall) {
     const int k0 = wall == 0 ? 0 : d.fnz - 1, k1 = wall == 0 ? 1 : d.fnz - 2;
-    const W cth = wall == 0 ? q.cbot : q.ctop;
+    const W cg = wall == 0 ? q.gbot : q.gtop;
     const double uw = wall == 0 ? p.uw_bot : p.uw_top;
     auto full = [&](const T* a, const T* lo, size_t o) { return lo ? (W)a[o] + (W)lo[o] : (W)a[o]; };
     // wall values of phi* (full precision) at column ii
@@ -53,7 +53,7 @@ __global__ void k_robin_wall(FineView<T> f, Wide<T>* __restrict__ gE, Wide<T>* _
       return 1.5 * s0 - 0.5 * s1;
     };
     const size_t o0 = (size_t)k0 * plane + (size_t)j * d.fnx + i, o1 = (size_t)k1 * plane + (size_t)j * d.fnx + i;
-    const W g0 = wall_g(cth, (W)((T)2 * f.pn[o0] - f.po[o0]), (W)((T)2 * f.pn[o1] - f.po[o1]), p.eta);
+    const W g0 = wall_g(cg, (W)((T)2 * f.pn[o0] - f.po[o0]), (W)((T)2 * f.pn[o1] - f.po[o1]));
     const W h0 = 2.0 * full(f.pn, f.ln, o0) - 0.5 * full(f.po, f.lo, o0);
     const W h1 = 2.0 * full(f.pn, f.ln, o1) - 0.5 * full(f.po, f.lo, o1);
     const W what = 1.5 * h0 - 0.5 * h1;

@@ -95,7 +95,8 @@ struct TangentRun {
       I.q.cj_dx.d = I.q.cj_dx.v / M;
     } else if (param == PF_PARAM_THETA_BOT) {
       const double th = I.raw_prm.theta_bot_deg * M_PI / 180.0;
-      I.q.cbot = Dual(std::cos(th), -std::sin(th));
+      const double s2eta = 1.4142135623730951 * I.p.eta;
+      I.q.gbot = Dual(std::cos(th) / s2eta, -std::sin(th) / s2eta);
     } else {
       throw ApiError(PF_ERR_ARG, "param must be PF_PARAM_WI, PF_PARAM_THETA_BOT, PF_PARAM_PHI0 or PF_PARAM_MOBILITY");
     }

@@ -40,6 +40,14 @@ __device__ __forceinline__ TC zs_val(TC x) { return x; }
 __device__ __forceinline__ double zs_val(Dual x) { return x.v; }
 __device__ __forceinline__ double zs_val(DF x) { return (double)x; }
 
+// the per-row division of the FP32 factors: a fast divide (within 2 ulp; the
+// operands are ratios of order one), where a correctly rounded one costs several
+// times the instructions on every row of every solve; wider types divide exactly
+template <class TC>
+__device__ __forceinline__ TC zs_div(TC a, TC b) { return a / b; }
+template <>
+__device__ __forceinline__ float zs_div<float>(float a, float b) { return __fdividef(a, b); }
+
 template <class TC>
 __device__ __forceinline__ TC zs_exp2(TC x) { return exp2(x); }
 template <>
@@ -205,7 +213,7 @@ __global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 2 : 1) k_zsolve_seg(cpx
       TC m;
       if (k < R - 1) {
         if (k >= kc) m = il;
-        else m = il * ((TC)1 + beta * pk) / ((TC)1 + beta * pk * rho);
+        else m = zs_div<TC>(il * ((TC)1 + beta * pk), (TC)1 + beta * pk * rho);
       } else {
         m = mlast;
       }
