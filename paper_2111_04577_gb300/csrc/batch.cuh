@@ -116,7 +116,7 @@ __device__ __forceinline__ void batch_run_item(const BatchProb<T>& B, int pass, 
       k_irfft_x_b<T, IncEpi<T>>(B.spW, IncEpi<T>{B.wt, B.w[fc], B.w[fo], d.nx, (size_t)d.nx * d.ny}, d.nx, d.nz - 1,
                                 B.pC, B.plCx, B.twCx, B.npairC, (T)1, bid, sm);
       break;
-    case BP_DIV: k_div_b<T>(B.u[fo], B.v[fo], B.wt, B.dv, d, B.div_coef, bid, sm); break;
+    case BP_DIV: k_div_b<T>(B.u[fo], B.v[fo], B.wt, B.dv, d, B.div_coef, (T)(1.0 / d.dx), bid, sm); break;
     case BP_P_RFFT:
       k_rfft_x_b<T, FinePro<T>>(FinePro<T>{B.dv, d.nx}, B.spP, d.nx, d.nz, B.pC, B.plCx, B.twCx, B.npairC, bid, sm);
       break;
@@ -127,7 +127,7 @@ __device__ __forceinline__ void batch_run_item(const BatchProb<T>& B, int pass, 
                                   bid, sm);
       break;
     case BP_CORR:
-      k_correct_b<T>(B.u[fo], B.v[fo], B.wt, B.w[fo], B.pp, B.pr[fc], B.pr[fo], d, B.corr_coef, bid, sm);
+      k_correct_b<T>(B.u[fo], B.v[fo], B.wt, B.w[fo], B.pp, B.pr[fc], B.pr[fo], d, B.corr_coef, (T)(1.0 / d.dx), bid, sm);
       break;
     case BP_POLY1: k_polymer_b<T, 2>(B.poly[fc][0], d, B.q, 1, bid, sm); break;
     case BP_POLY2: k_polymer_b<T, 2>(B.poly[fc][1], d, B.q, 2, bid, sm); break;

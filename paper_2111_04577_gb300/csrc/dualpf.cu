@@ -259,6 +259,7 @@ struct Impl : ImplBase {
   FftPlan plFx, plFy, plCx, plCy;
   cpx<T> *twFx, *twFy, *twCx, *twCy;
   double *eFx, *eFy, *eCx, *eCy;
+  float *k2F = nullptr, *k2C = nullptr;  // FP32 eliminations: -(lambda_x + lambda_y) per mode
   Wide<T>* zwork;
   double* partial;
   Wide<T>* wpartial;  // diagnostics partial sums
@@ -354,10 +355,20 @@ struct Impl : ImplBase {
     twFy = twiddles(d.fny);
     twCx = twiddles(d.nx);
     twCy = twiddles(d.ny);
-    eFx = eigs(d.fnx, d.h, d.fnx / 2 + 1);
-    eFy = d.dim == 3 ? eigs(d.fny, d.h, d.fny) : eigs(1, d.h, 1);
-    eCx = eigs(d.nx, d.dx, d.nx / 2 + 1);
-    eCy = d.dim == 3 ? eigs(d.ny, d.dx, d.ny) : eigs(1, d.dx, 1);
+    {
+      const auto hFx = eig_host(d.fnx, d.h, d.fnx / 2 + 1);
+      const auto hFy = d.dim == 3 ? eig_host(d.fny, d.h, d.fny) : eig_host(1, d.h, 1);
+      const auto hCx = eig_host(d.nx, d.dx, d.nx / 2 + 1);
+      const auto hCy = d.dim == 3 ? eig_host(d.ny, d.dx, d.ny) : eig_host(1, d.dx, 1);
+      eFx = upload(hFx);
+      eFy = upload(hFy);
+      eCx = upload(hCx);
+      eCy = upload(hCy);
+      if (std::is_same<TC, float>::value) {
+        k2F = k2_table(hFx, hFy);
+        k2C = k2_table(hCx, hCy);
+      }
+    }
     zwork = ar.get<Wide<T>>(4 * (size_t)(d.nz + 2));
     nred_blocks = 2 * 152;
     partial = ar.get<double>((size_t)nred_blocks * RED_N);
@@ -447,14 +458,27 @@ struct Impl : ImplBase {
     PF_CUDA_TRY(cudaMemcpy(dptr, h.data(), n * sizeof(cpx<T>), cudaMemcpyHostToDevice));
     return dptr;
   }
-  double* eigs(int n, double hh, int count) {
+  std::vector<double> eig_host(int n, double hh, int count) {
     std::vector<double> h(count);
     for (int k = 0; k < count; ++k) {
       const double s = std::sin(M_PI * (double)k / (double)n);
       h[k] = -4.0 / (hh * hh) * s * s;
     }
-    double* dptr = ar.get<double>(count);
-    PF_CUDA_TRY(cudaMemcpy(dptr, h.data(), count * sizeof(double), cudaMemcpyHostToDevice));
+    return h;
+  }
+  double* upload(const std::vector<double>& h) {
+    double* dptr = ar.get<double>(h.size());
+    PF_CUDA_TRY(cudaMemcpy(dptr, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+    return dptr;
+  }
+  // [ny][ncol] floats -(lambda_x + lambda_y), the rounding the FP32 elimination applied to
+  // the same FP64 sum on the device
+  float* k2_table(const std::vector<double>& hx, const std::vector<double>& hy) {
+    std::vector<float> t(hx.size() * hy.size());
+    for (size_t j = 0; j < hy.size(); ++j)
+      for (size_t c = 0; c < hx.size(); ++c) t[j * hx.size() + c] = (float)(-(hx[c] + hy[j]));
+    float* dptr = ar.get<float>(t.size());
+    PF_CUDA_TRY(cudaMemcpy(dptr, t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice));
     return dptr;
   }
 
@@ -614,6 +638,11 @@ struct Impl : ImplBase {
     zs.dshift1 = ds1;
     zs.dshift2 = ds2;
     zs.scale = scale;
+    zs.k2f = ex == eFx ? k2F : (ex == eCx ? k2C : nullptr);  // null unless the elimination is FP32
+    zs.h2f = (float)h2;
+    zs.s1f = (float)s1;
+    zs.s2f = (float)s2;
+    zs.rsf = (float)(h2 * scale);
     // the mean mode (kx = ky = 0) of the pressure has its own solve, which the
     // column solve skips; outside pf_profile it runs on st3 at the same time
     auto zero_mode = [&]() {
@@ -851,8 +880,9 @@ struct Impl : ImplBase {
     {
       constexpr int kzc = 8;
       const dim3 gc(d.ny * ((d.nz + 1 + kzc - 1) / kzc), lw.grid.y);
+      // 1/dx formed here: an FP64 division in every thread would sit on GB300's slow FP64 pipe
       k_correct_z<T><<<gc, lw.block, 0, st>>>(u[fo], v[fo], wt, w[fo], pp, pr[fc], pr[fo], d,
-                                               (T)(p.dt / (p.gamma0 * p.rho0)), kzc);
+                                               (T)(p.dt / (p.gamma0 * p.rho0)), (T)(1.0 / d.dx), kzc);
     }
     // ---- polymer ----
     if (p.visco && !defer) launch_polymer(fo, st);

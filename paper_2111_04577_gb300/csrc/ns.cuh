@@ -54,9 +54,8 @@ struct NsIn {
 
 // (gamma0 rho0/dt) div(u~) at centres; wt holds faces 1..nz-1 as rows 0..nz-2
 template <class T>
-__device__ __forceinline__ void k_div_b(const T* __restrict__ ut, const T* __restrict__ vt, const T* __restrict__ wt, T* __restrict__ out, Dims d, T coef, const int3 bid, unsigned char* smraw) {
+__device__ __forceinline__ void k_div_b(const T* __restrict__ ut, const T* __restrict__ vt, const T* __restrict__ wt, T* __restrict__ out, Dims d, T coef, T iD, const int3 bid, unsigned char* smraw) {
   const size_t plane = (size_t)d.nx * d.ny;
-  const T iD = (T)(1.0 / d.dx);
   RowIdx x;
   if (!row_index_b(bid, d.nx, d.ny, x)) return;
   {
@@ -73,17 +72,16 @@ __device__ __forceinline__ void k_div_b(const T* __restrict__ ut, const T* __res
 }
 
 template <class T>
-__global__ void k_div(const T* __restrict__ ut, const T* __restrict__ vt, const T* __restrict__ wt, T* __restrict__ out, Dims d, T coef) {
+__global__ void k_div(const T* __restrict__ ut, const T* __restrict__ vt, const T* __restrict__ wt, T* __restrict__ out, Dims d, T coef, T iD) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  k_div_b(ut, vt, wt, out, d, coef, make_int3(blockIdx.x, blockIdx.y, blockIdx.z), smraw);
+  k_div_b(ut, vt, wt, out, d, coef, iD, make_int3(blockIdx.x, blockIdx.y, blockIdx.z), smraw);
 }
 
 // u = u~ - cf grad p', p^{n+1} = p^n + p'.  u, v corrected in place (they hold
 // u~ on entry); w written with both walls zero from the face rows wt.
 template <class T>
-__device__ __forceinline__ void k_correct_b(T* __restrict__ u, T* __restrict__ v, const T* __restrict__ wt, T* __restrict__ w, const T* __restrict__ pp, const T* __restrict__ pn, T* __restrict__ pnew, Dims d, T cf, const int3 bid, unsigned char* smraw) {
+__device__ __forceinline__ void k_correct_b(T* __restrict__ u, T* __restrict__ v, const T* __restrict__ wt, T* __restrict__ w, const T* __restrict__ pp, const T* __restrict__ pn, T* __restrict__ pnew, Dims d, T cf, T iD, const int3 bid, unsigned char* smraw) {
   const size_t plane = (size_t)d.nx * d.ny;
-  const T iD = (T)(1.0 / d.dx);
   RowIdx x;
   if (!row_index_b(bid, d.nx, d.ny, x)) return;
   {
@@ -103,9 +101,9 @@ __device__ __forceinline__ void k_correct_b(T* __restrict__ u, T* __restrict__ v
 }
 
 template <class T>
-__global__ void k_correct(T* __restrict__ u, T* __restrict__ v, const T* __restrict__ wt, T* __restrict__ w, const T* __restrict__ pp, const T* __restrict__ pn, T* __restrict__ pnew, Dims d, T cf) {
+__global__ void k_correct(T* __restrict__ u, T* __restrict__ v, const T* __restrict__ wt, T* __restrict__ w, const T* __restrict__ pp, const T* __restrict__ pn, T* __restrict__ pnew, Dims d, T cf, T iD) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  k_correct_b(u, v, wt, w, pp, pn, pnew, d, cf, make_int3(blockIdx.x, blockIdx.y, blockIdx.z), smraw);
+  k_correct_b(u, v, wt, w, pp, pn, pnew, d, cf, iD, make_int3(blockIdx.x, blockIdx.y, blockIdx.z), smraw);
 }
 
 // The same update, each thread walking kz layers of its (i, j) column: p' of
@@ -114,12 +112,11 @@ __global__ void k_correct(T* __restrict__ u, T* __restrict__ v, const T* __restr
 template <class T>
 __global__ void k_correct_z(T* __restrict__ u, T* __restrict__ v, const T* __restrict__ wt, T* __restrict__ w,
                             const T* __restrict__ pp, const T* __restrict__ pn, T* __restrict__ pnew, Dims d, T cf,
-                            int kz) {
+                            T iD, int kz) {
   const int i = blockIdx.y * blockDim.x + threadIdx.x;
   if (i >= d.nx) return;
   const int j = blockIdx.x % d.ny, k0 = (blockIdx.x / d.ny) * kz;
   const size_t plane = (size_t)d.nx * d.ny;
-  const T iD = (T)(1.0 / d.dx);
   const int im = wrap(i - 1, d.nx);
   const size_t col = (size_t)j * d.nx, colm = (size_t)wrap(j - 1, d.ny) * d.nx;
   T pbelow = k0 > 0 ? pp[(size_t)(k0 - 1) * plane + col + i] : (T)0;

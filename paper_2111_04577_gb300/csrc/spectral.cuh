@@ -234,6 +234,10 @@ struct ZSolve {
   int skip_zero;   // the (0,0) column is handled by k_zero_mode
   double h2, shift1, shift2, scale;
   double dshift1, dshift2;  // derivatives of the shifts (used when TC carries derivatives)
+  // FP32 eliminations: -(lambda_x + lambda_y) per (ky, kx) mode ([ny][ncol]) and h^2,
+  // the shifts and h^2 scale, rounded to float on the host from the same FP64 values
+  const float* k2f;
+  float h2f, s1f, s2f, rsf;
 };
 
 // a shift in the elimination type: with Dual, its derivative as well

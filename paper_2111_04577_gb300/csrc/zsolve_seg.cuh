@@ -126,10 +126,28 @@ __global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 2 : 1) k_zsolve_seg(cpx
       gp += zstride;
     }
   }
-  const TC k2 = (TC)(-(eigx[in ? col : col0] + eigy[ky]));
-  const TC h2 = (TC)zs.h2;
-  const TC sg1 = (k2 + zshift<TC>(zs.shift1, zs.dshift1)) * h2;
-  const TC sg2 = (k2 + zshift<TC>(zs.shift2, zs.dshift2)) * h2;
+  // FP32 eliminations take -(lambda_x + lambda_y), h^2, the shifts and h^2 scale as
+  // floats formed on the host by the same roundings: no FP64 instruction (a burst
+  // of conversions at every CTA's start on GB300's slow FP64 pipe) in the kernel
+  TC k2, h2, s1, s2, rs;
+  if constexpr (std::is_same<TC, float>::value) {
+    if (zs.k2f) {
+      k2 = zs.k2f[(size_t)ky * zs.ncol + (in ? col : col0)];
+      h2 = zs.h2f;
+      s1 = zs.s1f;
+      s2 = zs.s2f;
+      rs = zs.rsf;
+    }
+  }
+  if (!std::is_same<TC, float>::value || !zs.k2f) {
+    k2 = (TC)(-(eigx[in ? col : col0] + eigy[ky]));
+    h2 = (TC)zs.h2;
+    s1 = zshift<TC>(zs.shift1, zs.dshift1);
+    s2 = zshift<TC>(zs.shift2, zs.dshift2);
+    rs = (TC)(zs.h2 * zs.scale);
+  }
+  const TC sg1 = (k2 + s1) * h2;
+  const TC sg2 = (k2 + s2) * h2;
   // ---- factors in closed form: the two lanes of a column share the rows ----
   // Each lane forms rows k0 + part, k0 + part + 2, ...; rho^k is advanced by
   // rho^2 from row to row instead of being raised afresh.  In FP64, from row kc
@@ -238,7 +256,6 @@ __global__ void __launch_bounds__(512, sizeof(TC) == 4 ? 2 : 1) k_zsolve_seg(cpx
     c2 = __all_sync(wmask, full_seg && k0 >= 1 && k0 + nk - 1 <= R - 1 - kc2);
   }
   __syncthreads();
-  const TC rs = (TC)(zs.h2 * zs.scale);
   // carried-in value of a linear recurrence, from the (product, last) pairs of the earlier segments
   auto carry_fwd = [&](const TC* cp) -> TC {
     const TC* cz = cp + (size_t)S * L;
