@@ -67,21 +67,21 @@ def replica_value(cells, steps, world, elapsed):
 # sha256 of the source files that define the kernel when the counters were
 # taken: once a kernel changes its traffic reads null until it is measured again.
 TRAFFIC = {
-    "ch_rhs": (23.122, ["paper_2111_04577_gb300/csrc/ch_march.cuh", "paper_2111_04577_gb300/csrc/ch.cuh"], "aa5fafef46154dc0"),
-    "ns_rhs": (16.916, ["paper_2111_04577_gb300/csrc/ns_march.cuh", "paper_2111_04577_gb300/csrc/ns_rhs.cuh", "paper_2111_04577_gb300/csrc/ns.cuh"], "ba80d12b3d6b2d81"),
-    "polymer_stage2": (13.907, ["paper_2111_04577_gb300/csrc/polymer.cuh"], "9cad53f3b20ccdc3"),
-    "polymer_stage1": (7.289, ["paper_2111_04577_gb300/csrc/polymer.cuh"], "9cad53f3b20ccdc3"),
-    "fft_y_fine": (10.575, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "5054e326fcfd8551"),
-    "fft_y_coarse": (4.041, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "5054e326fcfd8551"),
-    "ch_G_restrict": (6.760, ["paper_2111_04577_gb300/csrc/ch_march.cuh", "paper_2111_04577_gb300/csrc/ch.cuh"], "aa5fafef46154dc0"),
-    "ch_ifftx_finish": (25.718, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "5054e326fcfd8551"),
-    "zsolve_pair": (4.659, ["paper_2111_04577_gb300/csrc/zsolve_seg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh"], "5afeb807cb1122c1"),
-    "zsolve": (2.032, ["paper_2111_04577_gb300/csrc/zsolve_seg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh"], "5afeb807cb1122c1"),
-    "irfft_x_coarse": (4.988, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "5054e326fcfd8551"),
-    "rfft_x_fine": (4.995, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "5054e326fcfd8551"),
-    "rfft_x_coarse": (1.486, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "5054e326fcfd8551"),
-    "correct": (2.485, ["paper_2111_04577_gb300/csrc/ns.cuh"], "68dabd490b962e39"),
-    "div_rfft_x_coarse": (1.486, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "5054e326fcfd8551"),
+    "ch_rhs": (23.119, ["paper_2111_04577_gb300/csrc/ch_march.cuh", "paper_2111_04577_gb300/csrc/ch.cuh"], "aa5fafef46154dc0"),
+    "ns_rhs": (16.925, ["paper_2111_04577_gb300/csrc/ns_march.cuh", "paper_2111_04577_gb300/csrc/ns_rhs.cuh", "paper_2111_04577_gb300/csrc/ns.cuh"], "e0327193f48bff5a"),
+    "polymer_stage2": (13.893, ["paper_2111_04577_gb300/csrc/polymer.cuh"], "9cad53f3b20ccdc3"),
+    "polymer_stage1": (7.258, ["paper_2111_04577_gb300/csrc/polymer.cuh"], "9cad53f3b20ccdc3"),
+    "fft_y_fine": (10.581, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "d0c7ac2200da19dd"),
+    "fft_y_coarse": (4.041, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "d0c7ac2200da19dd"),
+    "ch_G_restrict": (6.733, ["paper_2111_04577_gb300/csrc/ch_march.cuh", "paper_2111_04577_gb300/csrc/ch.cuh"], "aa5fafef46154dc0"),
+    "ch_ifftx_finish": (25.731, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "d0c7ac2200da19dd"),
+    "zsolve_pair": (4.693, ["paper_2111_04577_gb300/csrc/zsolve_seg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh"], "e81cbcc2b80e6a28"),
+    "zsolve": (2.062, ["paper_2111_04577_gb300/csrc/zsolve_seg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh"], "e81cbcc2b80e6a28"),
+    "irfft_x_coarse": (4.987, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "d0c7ac2200da19dd"),
+    "rfft_x_fine": (4.997, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "d0c7ac2200da19dd"),
+    "rfft_x_coarse": (1.487, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "d0c7ac2200da19dd"),
+    "correct": (2.485, ["paper_2111_04577_gb300/csrc/ns.cuh"], "733228b8845497aa"),
+    "div_rfft_x_coarse": (1.486, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "d0c7ac2200da19dd"),
 }
 
 
