@@ -349,7 +349,8 @@ int pf_batch_tangent(pf_batch* b, int problem, int nsteps, int param, int object
  *                        16-row segment, at most 512)
  *   PF_TUNE_ROW_BLOCK    threads per CTA of the row kernels (multiple of 32)
  *   PF_TUNE_CH_ZCHUNK    fine z planes one CTA of the 3D CH right side walks (>= 2)
- *   PF_TUNE_CH_MINB      CTAs per SM the 3D CH right side's registers are sized for (2, 3, 4)
+ *   PF_TUNE_CH_MINB      CTAs per SM the 3D CH right side's registers are sized for (2, 3, 4;
+ *                        4 takes 14-row tiles of 224 threads, whose shared memory lets four fit)
  *   PF_TUNE_NS_MINB      CTAs per SM the NS right side's registers are sized for (3, 4)
  *   PF_TUNE_G_ZCHUNK     coarse layers one CTA of the 3D restriction walks (>= 1)
  *   PF_TUNE_NS_KZ        z rows one CTA of the NS right side walks (1..64)

@@ -520,11 +520,14 @@ namespace pf {
 // Planes carry 4 floats of padding on both ends: the halo chunks read one
 // float beyond their row, and only lanes that are never used depend on it.
 // ---------------------------------------------------------------------------
-struct March4 {
-  static constexpr int TX = 64, TY = 16, NT = 256, CH = TX / 4;  // 16 chunks per row
+// TY_ rows per CTA: 16 (256 threads, three CTAs per SM), or 14 (224 threads, 55.3 KB
+// of shared memory in 3D dual resolution: four CTAs per SM at up to 72 registers)
+template <int TY_>
+struct March4T {
+  static constexpr int TX = 64, TY = TY_, CH = TX / 4, NT = CH * TY;  // 16 chunks per row
   static constexpr int SXC = CH + 2, SXF = 4 * SXC;               // phi* chunks (x0-4 .. x0+68)
-  static constexpr int SY = TY + 4, SPF = SY * SXF + 8;            // phi* rows y0-2 .. y0+18, padded plane
-  static constexpr int MY = TY + 2, MPF = MY * SXF + 8;            // mu* rows y0-1 .. y0+17
+  static constexpr int SY = TY + 4, SPF = SY * SXF + 8;            // phi* rows y0-2 .. y0+TY+1, padded plane
+  static constexpr int MY = TY + 2, MPF = MY * SXF + 8;            // mu* rows y0-1 .. y0+TY
   static constexpr int NPS = 5, NMS = 3;
   static constexpr int NSC = SY * SXC, NMC = MY * SXC;             // staged / mu chunks per plane
   static constexpr int KS = (NSC + NT - 1) / NT, KM = (NMC + NT - 1) / NT;
@@ -534,16 +537,18 @@ struct March4 {
     return NPS * SPF + NMS * MPF + 4 * VX(rs) * VY(rs) + 8 * NSC;
   }
 };
+using March4 = March4T<16>;
 
 // AW: take div(u* phi*) from f.aw (WENO5-Z) instead of the central flux; a
 // template flag, so that the default form carries no trace of it
-template <int RS, int MINB, bool AW = false>
-__global__ void __launch_bounds__(March4::NT, MINB) k_ch_rhs_march4(const FineView<float> f, const CoarseVel<float> vel,
+template <int RS, int MINB, bool AW = false, int TYV = 16>
+__global__ void __launch_bounds__(March4T<TYV>::NT, MINB) k_ch_rhs_march4(const FineView<float> f, const CoarseVel<float> vel,
                                                                      float* __restrict__ R, double* __restrict__ gwall,
                                                                      const Dims d, const Phys p, const PhysT<float> q,
                                                                      const float inv_mldt, const float inv_ml,
                                                                      const int nzc) {
-  using TL = March4;
+  using TL = March4T<TYV>;
+  static_assert(TL::TY % 2 == 0, "tile rows start on even fine rows (the velocity box rows)");
   extern __shared__ __align__(16) unsigned char smraw[];
   float* ps = reinterpret_cast<float*>(smraw);  // [NPS][4 + SY*SXF + 4]
   float* ms = ps + TL::NPS * TL::SPF;           // [NMS][4 + MY*SXF + 4]

@@ -496,7 +496,10 @@ struct Impl : ImplBase {
     if constexpr (std::is_same<T, float>::value) {
       PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march4<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
       PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march4<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
-      PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march4<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+      PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march4<1, 4, false, 14>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+      // four 55.3 KB CTAs per SM need the whole shared-memory carveout
+      PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march4<1, 4, false, 14>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       (int)cudaSharedmemCarveoutMaxShared));
       PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march4<0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
       PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march4<1, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
       PF_CUDA_TRY(cudaFuncSetAttribute(k_ch_rhs_march4<0, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
@@ -730,7 +733,12 @@ struct Impl : ImplBase {
             else k_ch_rhs_march4<0, 2, true><<<g4, T4::NT, s4, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml, nzc);
           } else if (d.rs == 1) {
             if (mb == 2) k_ch_rhs_march4<1, 2><<<g4, T4::NT, s4, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml, nzc);
-            else if (mb == 4) k_ch_rhs_march4<1, 4><<<g4, T4::NT, s4, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml, nzc);
+            else if (mb == 4) {  // 14-row tiles of 224 threads: four CTAs per SM by shared memory and registers
+              using T14 = March4T<14>;
+              const dim3 g14((d.fnx + T14::TX - 1) / T14::TX, (d.fny + T14::TY - 1) / T14::TY, (d.fnz + nzc - 1) / nzc);
+              const size_t s14 = (size_t)T14::smem_floats(d.rs) * sizeof(float);
+              k_ch_rhs_march4<1, 4, false, 14><<<g14, T14::NT, s14, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml, nzc);
+            }
             else k_ch_rhs_march4<1, 3><<<g4, T4::NT, s4, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml, nzc);
           } else {
             k_ch_rhs_march4<0, 2><<<g4, T4::NT, s4, st>>>(fv, vel, mu, gwall, d, p, q, inv_mldt, inv_ml, nzc);
