@@ -67,19 +67,19 @@ def replica_value(cells, steps, world, elapsed):
 # sha256 of the source files that define the kernel when the counters were
 # taken: once a kernel changes its traffic reads null until it is measured again.
 TRAFFIC = {
-    "ch_rhs": (23.119, ["paper_2111_04577_gb300/csrc/ch_march.cuh", "paper_2111_04577_gb300/csrc/ch.cuh"], "aa5fafef46154dc0"),
-    "ns_rhs": (16.925, ["paper_2111_04577_gb300/csrc/ns_march.cuh", "paper_2111_04577_gb300/csrc/ns_rhs.cuh", "paper_2111_04577_gb300/csrc/ns.cuh"], "e0327193f48bff5a"),
-    "polymer_stage2": (13.893, ["paper_2111_04577_gb300/csrc/polymer.cuh"], "9cad53f3b20ccdc3"),
-    "polymer_stage1": (7.258, ["paper_2111_04577_gb300/csrc/polymer.cuh"], "9cad53f3b20ccdc3"),
-    "fft_y_fine": (10.581, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "d0c7ac2200da19dd"),
+    "ch_rhs": (23.110, ["paper_2111_04577_gb300/csrc/ch_march.cuh", "paper_2111_04577_gb300/csrc/ch.cuh"], "53d3dddcf51ae53d"),
+    "ns_rhs": (17.577, ["paper_2111_04577_gb300/csrc/ns_march.cuh", "paper_2111_04577_gb300/csrc/ns_rhs.cuh", "paper_2111_04577_gb300/csrc/ns.cuh"], "e0327193f48bff5a"),
+    "polymer_stage2": (13.902, ["paper_2111_04577_gb300/csrc/polymer.cuh"], "9cad53f3b20ccdc3"),
+    "polymer_stage1": (7.259, ["paper_2111_04577_gb300/csrc/polymer.cuh"], "9cad53f3b20ccdc3"),
+    "fft_y_fine": (10.578, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "d0c7ac2200da19dd"),
     "fft_y_coarse": (4.041, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "d0c7ac2200da19dd"),
-    "ch_G_restrict": (6.733, ["paper_2111_04577_gb300/csrc/ch_march.cuh", "paper_2111_04577_gb300/csrc/ch.cuh"], "aa5fafef46154dc0"),
-    "ch_ifftx_finish": (25.731, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "d0c7ac2200da19dd"),
-    "zsolve_pair": (4.693, ["paper_2111_04577_gb300/csrc/zsolve_seg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh"], "e81cbcc2b80e6a28"),
+    "ch_G_restrict": (6.739, ["paper_2111_04577_gb300/csrc/ch_march.cuh", "paper_2111_04577_gb300/csrc/ch.cuh"], "53d3dddcf51ae53d"),
+    "ch_ifftx_finish": (25.825, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "d0c7ac2200da19dd"),
+    "zsolve_pair": (4.675, ["paper_2111_04577_gb300/csrc/zsolve_seg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh"], "e81cbcc2b80e6a28"),
     "zsolve": (2.062, ["paper_2111_04577_gb300/csrc/zsolve_seg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh"], "e81cbcc2b80e6a28"),
     "irfft_x_coarse": (4.987, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "d0c7ac2200da19dd"),
-    "rfft_x_fine": (4.997, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "d0c7ac2200da19dd"),
-    "rfft_x_coarse": (1.487, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "d0c7ac2200da19dd"),
+    "rfft_x_fine": (5.013, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "d0c7ac2200da19dd"),
+    "rfft_x_coarse": (1.486, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "d0c7ac2200da19dd"),
     "correct": (2.485, ["paper_2111_04577_gb300/csrc/ns.cuh"], "733228b8845497aa"),
     "div_rfft_x_coarse": (1.486, ["paper_2111_04577_gb300/csrc/fft_reg.cuh", "paper_2111_04577_gb300/csrc/spectral.cuh", "paper_2111_04577_gb300/csrc/fft.cuh"], "d0c7ac2200da19dd"),
 }
